@@ -1,0 +1,235 @@
+"""Seeded synthetic inputs for the FST evaluation and refit path.
+
+This module only *draws* inputs: point clouds, field values, random functional
+sparse Tucker models and explicit row-index sets.  It contains none of the
+method's arithmetic (no basis evaluation, no contraction, no least squares), so
+the CUDA path and the CPU oracle can both be fed from it without sharing any
+computation.
+
+The combustion datasets of Sec. 6 (S3D "statistically planar" flame, SP3D/SP4D)
+are not available; these fields stand in for them: a thin reaction front
+(a tanh layer of width 0.1 across a curved surface) plus Gaussian blobs and a
+small noise floor, sampled at unstructured points of which a fixed share is
+clustered in a band around the front (the way an adaptive DNS mesh would
+concentrate its points).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field as dc_field
+
+import numpy as np
+
+
+def _rng(seed: int, stream: int) -> np.random.Generator:
+    return np.random.default_rng([int(seed) & 0xFFFFFFFFFFFFFFFF, int(stream)])
+
+
+# ----------------------------------------------------------------------------- points
+def points(Q: int, seed: int, clustered: float = 0.3, dtype=np.float64) -> np.ndarray:
+    """Q points in [-1,1]^3 as a (3, Q) structure-of-arrays array.
+
+    A share ``1 - clustered`` is uniform in the cube; the rest lie in a band of
+    width 0.05 (measured along x1) around the front surface
+    x1 = -0.3 sin(3 x2) + 0.2 x3, redrawn until inside the cube.  The two
+    groups are interleaved by a random permutation, so consecutive points are
+    unstructured.
+    """
+    Q = int(Q)
+    rng = _rng(seed, 1)
+    n_c = int(round(clustered * Q))
+    n_u = Q - n_c
+    uni = rng.uniform(-1.0, 1.0, size=(3, n_u))
+    cl = np.empty((3, n_c))
+    todo = np.arange(n_c)
+    while todo.size:
+        x2 = rng.uniform(-1.0, 1.0, size=todo.size)
+        x3 = rng.uniform(-1.0, 1.0, size=todo.size)
+        x1 = -0.3 * np.sin(3.0 * x2) + 0.2 * x3 + rng.uniform(-0.025, 0.025, size=todo.size)
+        ok = np.abs(x1) <= 1.0
+        cl[0, todo[ok]] = x1[ok]
+        cl[1, todo[ok]] = x2[ok]
+        cl[2, todo[ok]] = x3[ok]
+        todo = todo[~ok]
+    xyz = np.concatenate([uni, cl], axis=1)
+    perm = rng.permutation(Q)
+    return np.ascontiguousarray(xyz[:, perm], dtype=dtype)
+
+
+# ----------------------------------------------------------------------------- fields
+@dataclass
+class FieldSpec:
+    """A combustion-like scalar field: tanh fronts plus Gaussian blobs."""
+    fronts: list = dc_field(default_factory=list)   # (normal(3), offset, width, curvature amp)
+    gauss: list = dc_field(default_factory=list)    # (amp, width, centre(3))
+    noise: float = 1e-4
+
+
+def field_spec(seed: int, n_gauss: int, n_fronts: int = 1, randomize_fronts: bool = False,
+               noise: float = 1e-4) -> FieldSpec:
+    """Draw a field.  With ``randomize_fronts`` False the single front is the
+    fixed surface x1 + 0.3 sin(3 x2) - 0.2 x3 = 0 with width 0.1."""
+    rng = _rng(seed, 2)
+    spec = FieldSpec(noise=noise)
+    if not randomize_fronts:
+        spec.fronts.append((np.array([1.0, 0.0, -0.2]), 0.0, 0.1, 0.3))
+    else:
+        for _ in range(n_fronts):
+            nrm = rng.normal(size=3)
+            nrm /= np.linalg.norm(nrm)
+            spec.fronts.append((nrm, rng.uniform(-0.5, 0.5), rng.uniform(0.05, 0.2),
+                                rng.uniform(0.0, 0.3)))
+    for _ in range(n_gauss):
+        spec.gauss.append((rng.uniform(0.5, 1.0), rng.uniform(0.1, 0.4),
+                           rng.uniform(-1.0, 1.0, size=3)))
+    return spec
+
+
+def field_values(xyz: np.ndarray, spec: FieldSpec, seed: int, chunk: int = 1 << 22):
+    """Return (u, u_clean): noisy samples and the noise-free field at ``xyz``."""
+    xyz = np.asarray(xyz, dtype=np.float64)
+    Q = xyz.shape[1]
+    clean = np.empty(Q)
+    for s in range(0, Q, chunk):
+        x1, x2, x3 = xyz[0, s:s + chunk], xyz[1, s:s + chunk], xyz[2, s:s + chunk]
+        f = np.zeros_like(x1)
+        for nrm, off, width, amp in spec.fronts:
+            # fixed front: nrm=(1,0,-0.2), the curved term 0.3 sin(3 x2)
+            f += np.tanh((nrm[0] * x1 + nrm[1] * x2 + nrm[2] * x3 + amp * np.sin(3.0 * x2) - off)
+                         / width)
+        for a, sig, c in spec.gauss:
+            d2 = (x1 - c[0]) ** 2 + (x2 - c[1]) ** 2 + (x3 - c[2]) ** 2
+            f += a * np.exp(-d2 / (2.0 * sig * sig))
+        clean[s:s + chunk] = f
+    noise = _rng(seed, 3).normal(size=Q) * spec.noise
+    return clean + noise, clean
+
+
+# ----------------------------------------------------------------------------- models
+@dataclass
+class Model:
+    """A functional sparse Tucker model in host memory (eq. func_tuck, eq. sparse).
+
+    ``colptr[k]``, ``rowidx[k]``, ``val[k]`` hold the CSC coefficient matrix of
+    mode k: column j lists the degrees n and coefficients W^k_{n,j} of the
+    orthonormal Legendre functions sqrt(2n+1) L_n.  ``alpha`` is the core in
+    C order [j1][j2][j3].  ``lo``/``hi`` give the domain box mapped to [-1,1].
+    """
+    r: tuple
+    p: tuple
+    colptr: list
+    rowidx: list
+    val: list
+    alpha: np.ndarray
+    lo: np.ndarray = dc_field(default_factory=lambda: -np.ones(3))
+    hi: np.ndarray = dc_field(default_factory=lambda: np.ones(3))
+
+    @property
+    def R(self) -> int:
+        return int(self.r[0] * self.r[1] * self.r[2])
+
+    def dense(self, k: int) -> np.ndarray:
+        """Coefficient matrix of mode k as a dense (p_k+1) x r_k array."""
+        W = np.zeros((self.p[k] + 1, self.r[k]))
+        for j in range(self.r[k]):
+            s, e = self.colptr[k][j], self.colptr[k][j + 1]
+            W[self.rowidx[k][s:e], j] = self.val[k][s:e]
+        return W
+
+    def nnz(self) -> int:
+        return int(sum(len(v) for v in self.val))
+
+    def with_alpha(self, alpha: np.ndarray) -> "Model":
+        return Model(self.r, self.p, self.colptr, self.rowidx, self.val,
+                     np.asarray(alpha, dtype=np.float64).reshape(self.r), self.lo, self.hi)
+
+
+def random_model(r, p, seed: int, density: float = 0.6, decay: float = 1.0,
+                 lo=None, hi=None) -> Model:
+    """A random model with ranks ``r`` and maximum degrees ``p``.
+
+    Column j of mode k keeps max(1, round(density*(p_k+1))) randomly chosen
+    degrees (always including one of degree <= j, the way low singular vectors
+    are smooth); its coefficients are normal, scaled to unit 2-norm.  Core
+    entries are normal with magnitude decaying like 1/(1+j1+j2+j3)^decay, the
+    way a Tucker core sorted by singular value decays (Fig. 1).
+    """
+    r = tuple(int(v) for v in r)
+    p = tuple(int(v) for v in (p if np.ndim(p) else (p, p, p)))
+    rng = _rng(seed, 4)
+    colptr, rowidx, val = [], [], []
+    for k in range(3):
+        n = p[k] + 1
+        keep = max(1, min(n, int(round(density * n))))
+        cp, ri, vv = [0], [], []
+        for j in range(r[k]):
+            low = int(rng.integers(0, min(j, n - 1) + 1))
+            others = rng.permutation(np.setdiff1d(np.arange(n), [low]))[:keep - 1]
+            rows = np.sort(np.concatenate([[low], others])).astype(np.int32)
+            c = rng.normal(size=rows.size)
+            c /= np.linalg.norm(c)
+            ri.append(rows)
+            vv.append(c)
+            cp.append(cp[-1] + rows.size)
+        colptr.append(np.asarray(cp, dtype=np.int32))
+        rowidx.append(np.concatenate(ri).astype(np.int32))
+        val.append(np.concatenate(vv).astype(np.float64))
+    j1, j2, j3 = np.meshgrid(np.arange(r[0]), np.arange(r[1]), np.arange(r[2]), indexing="ij")
+    alpha = rng.normal(size=r) / (1.0 + j1 + j2 + j3) ** decay
+    lo = -np.ones(3) if lo is None else np.asarray(lo, dtype=np.float64)
+    hi = np.ones(3) if hi is None else np.asarray(hi, dtype=np.float64)
+    return Model(r, p, colptr, rowidx, val, alpha, lo, hi)
+
+
+def row_indices(Q: int, m: int, seed: int) -> np.ndarray:
+    """m distinct row indices of [0, Q), ascending (explicit sample sets for parity tests)."""
+    rng = _rng(seed, 5)
+    m = min(int(m), int(Q))
+    return np.sort(rng.choice(int(Q), size=m, replace=False)).astype(np.int64)
+
+
+# ----------------------------------------------------------------------------- workloads
+@dataclass
+class Workload:
+    """One named workload (point count, field, ranks, degree, refit oversampling)."""
+    name: str
+    Q: int
+    n_gauss: int
+    grid: int
+    sample_frac: float
+    max_rank: int
+    degree: int
+    oversample: float
+    eps: float
+    clustered: float
+    seed: int
+
+
+WORKLOADS = {
+    # 20,000 uniform points, 5 Gaussians, 5% onto 32^3, eps 1e-3, ranks <= 8, degree <= 15, m = 4R
+    "fp64_small": Workload("fp64_small", 20_000, 5, 32, 0.05, 8, 15, 4.0, 1e-3, 0.0, 101),
+    # 2^24 points (70% uniform, 30% in the front band), 20 Gaussians, 2% onto 128^3,
+    # ranks <= 24, degree <= 31, m = 8R
+    "fp32_16M": Workload("fp32_16M", 1 << 24, 20, 128, 0.02, 24, 31, 8.0, 1e-4, 0.3, 202),
+    # 2^26 points, 256^3 grid, ranks fixed at 24, degree <= 63, m = 8R
+    "precision_64M": Workload("precision_64M", 1 << 26, 20, 256, 0.02, 24, 63, 8.0, 0.0, 0.3, 303),
+}
+
+
+def log_uniform_int(rng: np.random.Generator, lo: float, hi: float, size=None):
+    return np.exp(rng.uniform(math.log(lo), math.log(hi), size=size)).astype(np.int64)
+
+
+def batch_instances(n_fields: int = 64, n_steps: int = 8, seed: int = 404,
+                    q_lo: float = 1e5, q_hi: float = 2e6, r_lo: int = 4, r_hi: int = 24):
+    """Instance table of the batching workload: fields x timesteps with uneven
+    ranks (independently U{r_lo..r_hi} per mode) and log-uniform point counts."""
+    rng = _rng(seed, 6)
+    out = []
+    for f in range(n_fields):
+        for t in range(n_steps):
+            r = tuple(int(v) for v in rng.integers(r_lo, r_hi + 1, size=3))
+            Q = int(log_uniform_int(rng, q_lo, q_hi))
+            out.append({"field": f, "step": t, "r": r, "Q": Q,
+                        "seed": int(rng.integers(0, 2**62))})
+    return out
