@@ -1,0 +1,378 @@
+#!/usr/bin/env python
+"""Benchmark of the FST hot path on GB300.
+
+One step = the randomized least-squares refit of the core on m = 8R rows sampled
+from the Q data points (Sec. 5, eq. rand_core, Algorithm 2 with uniform sampling),
+followed by the evaluation of the refitted model at all Q points (Sec. 6,
+reconstruction by evaluating the basis functions).  Workload: Q = 2^24
+unstructured points (70% uniform, 30% in a band around a curved tanh front),
+ranks 24^3, Legendre degree <= 31, m = 8R = 110,592.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle instead,
+on a bounded sample of the same workload, extrapolated to the same unit.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+from pathlib import Path
+
+import numpy as np
+
+ROOT = Path(__file__).resolve().parent
+sys.path.insert(0, str(ROOT))
+
+METRIC = "Mpoints/s fst_eval + LS refit ms on 1 GB300 at stated rel-L2 vs FP64 oracle"
+UNIT = "Mpoints/s"
+WORKLOAD = "fp32_16M"
+RANKS = (24, 24, 24)
+DEGREE = 31
+OVERSAMPLE = 8
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="fst", choices=["fst", "reference"])
+    ap.add_argument("--prec", default="fp32", help="refit Gram precision: fp32, tf32, bf16, bf16x3")
+    ap.add_argument("--eval-prec", default="fp32", help="evaluation precision: fp32, tf32, bf16, bf16x3")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--Q", type=int, default=1 << 24)
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------- workload
+def make_workload(Q: int, seed: int):
+    from paper_1907_05884_gb300 import synth
+    xyz = synth.points(Q, seed=seed + 1, clustered=0.3, dtype=np.float32)
+    u, _ = synth.field_values(xyz, synth.field_spec(seed + 2, 20), seed=seed + 3)
+    model = synth.random_model(RANKS, (DEGREE,) * 3, seed=seed + 4, orthonormal=True)
+    return xyz, u.astype(np.float32), model
+
+
+def workload_config(Q, R, m, prec, eval_prec):
+    return {"workload": f"{WORKLOAD}: Q={Q} unstructured points in [-1,1]^3 (70% uniform, 30% in a 0.05 band "
+                        f"around a tanh front), 20 Gaussians + 1e-4 noise, ranks {RANKS}, degree <= {DEGREE}, "
+                        f"refit on m = {OVERSAMPLE}R = {m} sampled rows, then evaluation at all Q points",
+            "Q": Q, "ranks": list(RANKS), "R": R, "degree": DEGREE, "m": m, "refit_prec": prec,
+            "eval_prec": eval_prec, "model": "seeded synthetic model with orthonormal factor functions",
+            "l2": "inputs larger than L2: xyz + u = 16 B/point = %.0f MB per step" % (16 * Q / 1e6)}
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: str | None):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        cmd = ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits", "-lms", "200"]
+        if gpu_index is not None:
+            cmd += ["-i", gpu_index]
+        try:
+            self.p = subprocess.Popen(cmd, stdout=self.f, stderr=subprocess.DEVNULL)
+        except (FileNotFoundError, PermissionError):
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        rows = [l.split(",") for l in Path(self.f.name).read_text().splitlines() if l.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def gpu_index_for_smi():
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    lr = int(os.environ.get("LOCAL_RANK", "0"))
+    if vis:
+        parts = [x for x in vis.split(",") if x.strip()]
+        if lr < len(parts):
+            return parts[lr].strip()
+    return str(lr)
+
+
+# ----------------------------------------------------------------------------- peaks
+def measured_peaks():
+    p = ROOT / "MEASURED_PEAKS.json"
+    if p.exists():
+        d = json.loads(p.read_text())
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+            "sm_max_mhz": 2070.0}, "fallback"
+
+
+def fp32_alu_peak_tflops(sm_mhz: float, sms: int) -> float:
+    """FP32 FMA pipe: 128 lanes per SM, 2 flops per FMA."""
+    return sms * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+# ----------------------------------------------------------------------------- oracle timing
+def oracle_sample_timing(model, xyz, u, Q, m, nthreads, budget_scale=1.0):
+    """Time the oracle on a bounded sample of the step and extrapolate to the full step.
+    Returns (seconds per full step, description)."""
+    import oracle
+    R = model.R
+    n_eval = int(8192 * budget_scale)
+    sel = np.arange(n_eval)
+    xs = np.ascontiguousarray(xyz[:, sel].astype(np.float64))
+    t0 = time.perf_counter()
+    oracle.eval_points(model, xs, nthreads=nthreads)
+    t_eval = (time.perf_counter() - t0) / n_eval * Q
+    m_s = max(4, int(16 * budget_scale))
+    idx = np.arange(m_s, dtype=np.int64)
+    x64 = np.ascontiguousarray(xyz[:, :m_s].astype(np.float64))
+    u64 = np.ascontiguousarray(u[:m_s].astype(np.float64))
+    t0 = time.perf_counter()
+    oracle.normal_equations(model, x64, u64, idx, nthreads=nthreads)
+    t_gram = (time.perf_counter() - t0) / m_s * m
+    R_s = int(768 * budget_scale ** (1 / 3))
+    rng = np.random.default_rng(0)
+    B = rng.normal(size=(R_s + 8, R_s))
+    G = B.T @ B
+    t0 = time.perf_counter()
+    oracle.cholesky(G, nthreads=nthreads)
+    t_chol = (time.perf_counter() - t0) * (R / R_s) ** 3
+    total = t_eval + t_gram + t_chol
+    desc = (f"oracle eval on {n_eval} points scaled to Q={Q}; oracle normal equations on {m_s} rows at R={R} "
+            f"scaled to m={m}; oracle Cholesky at R={R_s} scaled by (R/{R_s})^3; {nthreads} threads")
+    return total, {"eval_s": t_eval, "gram_s": t_gram, "cholesky_s": t_chol}, desc
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    Q = args.Q
+    xyz, u, model = make_workload(min(Q, 1 << 16), seed=2024)
+    R = model.R
+    m = OVERSAMPLE * R
+    nthreads = oracle.default_threads()
+    times = []
+    for it in range(args.warmup + args.steps):
+        t, parts, desc = oracle_sample_timing(model, xyz, u, Q, m, nthreads, budget_scale=0.5)
+        if it >= args.warmup:
+            times.append(t)
+    t = statistics.median(times)
+    value = Q / t / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(Q, R, m, "fp64", "fp64"),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": nthreads, "kind": "oracle", "sample": desc,
+                             "parts_s": parts},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------- GPU arm
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_1907_05884_gb300 import build as fbuild
+    fbuild.build()
+    from paper_1907_05884_gb300 import fst
+
+    Q = args.Q
+    xyz, u, model = make_workload(Q, seed=2024 + 17 * rank)
+    R = model.R
+    m = OVERSAMPLE * R
+    M = fst.Model(model)
+    stream = torch.cuda.current_stream()
+    xyz_d = torch.from_numpy(xyz).cuda()
+    u_d = torch.from_numpy(u).cuda()
+    out_d = torch.empty(Q, dtype=torch.float32, device="cuda")
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    reports = []
+    eval_ms = []
+
+    def step(i, timed_eval=False):
+        rep = M.refit(xyz_d, u_d, m, seed=1000 + i, prec=args.prec)
+        if timed_eval:
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+        M.eval(xyz_d, prec=args.eval_prec, out=out_d)
+        if timed_eval:
+            e1.record(stream)
+            return rep, (e0, e1)
+        return rep, None
+
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+
+    # device-resident timing
+    launches0 = fst.kernel_launches()
+    clocks = ClockSampler(gpu_index_for_smi()) if rank == 0 else None
+    barrier()
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    evs = []
+    for i in range(args.steps):
+        rep, ev = step(args.warmup + i, timed_eval=True)
+        reports.append(rep)
+        evs.append(ev)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop() if clocks else None
+    launches = fst.kernel_launches() - launches0
+    ms = t0.elapsed_time(t1)
+    eval_ms = [a.elapsed_time(b) for a, b in evs]
+    ms_t = torch.tensor([ms], device="cuda")
+    if world > 1:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms = float(ms_t.item())
+    ms_step = ms / args.steps
+    value = world * Q * args.steps / (ms / 1e3) / 1e6
+
+    # end to end through the public API with host buffers (pinned), copies inside the region
+    xyz_h = torch.from_numpy(xyz).pin_memory()
+    u_h = torch.from_numpy(u).pin_memory()
+    out_h = torch.empty(Q, dtype=torch.float32).pin_memory()
+    barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(args.steps):
+        xyz_d.copy_(xyz_h, non_blocking=True)
+        u_d.copy_(u_h, non_blocking=True)
+        M.refit(xyz_d, u_d, m, seed=5000 + i, prec=args.prec)
+        M.eval(xyz_d, prec=args.eval_prec, out=out_d)
+        out_h.copy_(out_d, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1)
+    e2e_t = torch.tensor([e2e_ms], device="cuda")
+    if world > 1:
+        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
+    e2e_value = world * Q * args.steps / (float(e2e_t.item()) / 1e3) / 1e6
+
+    if rank != 0:
+        if world > 1:
+            dist.barrier()
+            dist.destroy_process_group()
+        return 0
+
+    peaks, peak_kind = measured_peaks()
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    sm_max = (clk or {}).get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    gram_ms = statistics.mean(r["ms_gram"] for r in reports)
+    chol_ms = statistics.mean(r["ms_cholesky"] for r in reports)
+    refit_ms = statistics.mean(r["ms_sample"] + r["ms_factors"] + r["ms_gram"] + r["ms_cholesky"] + r["ms_refine"]
+                               for r in reports)
+    ev_ms = statistics.mean(eval_ms)
+    nnz = sum(len(v) for v in model.val)
+    gram_flops = m * R * (R + 1)                      # lower triangle of A^T A, 2 flops per product
+    eval_flops_pt = 2 * (R + RANKS[0] * RANKS[1] + RANKS[0]) + 2 * nnz + 5 * 3 * DEGREE
+    eval_flops = eval_flops_pt * Q
+    alu_peak = fp32_alu_peak_tflops(sm_max, sms)
+    roof_gram = {"kernel": "gram (A^T A over sampled Khatri-Rao rows)", "bound": "alu",
+                 "achieved": gram_flops / (gram_ms / 1e3) / 1e12, "peak": alu_peak, "unit": "TFLOP/s",
+                 "traffic": None}
+    roof_gram["frac"] = roof_gram["achieved"] / roof_gram["peak"]
+    roof_eval = {"kernel": "eval (basis + factor values + core contraction)", "bound": "alu",
+                 "achieved": eval_flops / (ev_ms / 1e3) / 1e12, "peak": alu_peak, "unit": "TFLOP/s",
+                 "traffic": None, "hbm_GBps": 16 * Q / (ev_ms / 1e3) / 1e9, "hbm_peak_GBps": peaks["hbm_gbs"]}
+    roof_eval["frac"] = roof_eval["achieved"] / roof_eval["peak"]
+    dominant = roof_gram if gram_ms >= ev_ms else roof_eval
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32" if args.prec == "fp32" and args.eval_prec == "fp32" else
+            f"{args.prec}/{args.eval_prec}",
+            "data": "synthetic", "config": workload_config(Q, R, m, args.prec, args.eval_prec),
+            "refit_ms": refit_ms, "refit_gram_ms": gram_ms, "refit_cholesky_ms": chol_ms,
+            "refit_refine_steps": statistics.mean(r["refine_steps"] for r in reports),
+            "refit_fallback_fp64": max(r["fallback_fp64"] for r in reports),
+            "eval_ms": ev_ms, "eval_Mpoints_s": Q / ev_ms / 1e3,
+            "roofline": {k: v for k, v in dominant.items() if k != "kernel"} | {"kernel": dominant["kernel"],
+                                                                                 "peak_source": f"FP32 ALU: {sms} SMs x 128 FMA/clk x 2 x {sm_max:.0f} MHz"},
+            "rooflines": {"gram": roof_gram, "eval": roof_eval},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 16 * Q - 4 * Q,
+                    "d2h_bytes_per_step": 4 * Q},
+            "gpu_launches": launches, "clocks": clk, "peaks": peak_kind}
+    line["e2e"]["h2d_bytes_per_step"] = xyz.nbytes + u.nbytes
+
+    if world == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        nthreads = oracle.default_threads()
+        t_cpu, parts, desc = oracle_sample_timing(model, xyz, u, Q, m, nthreads)
+        line["cpu_baseline"] = {"value": Q / t_cpu / 1e6, "unit": UNIT, "cores": nthreads, "kind": "oracle",
+                                "sample": desc, "parts_s": parts}
+        # accuracy stated against the FP64 oracle: evaluation at 2048 sampled points with the
+        # refitted core, and the normal-equation residual of the last refit
+        from paper_1907_05884_gb300 import synth
+        cur = M.read()
+        om = synth.Model(model.r, model.p, model.colptr, model.rowidx, model.val, cur["alpha"])
+        sel = np.random.default_rng(1).choice(Q, 2048, replace=False)
+        ref = oracle.eval_points(om, xyz[:, sel].astype(np.float64), nthreads=nthreads)
+        got = out_d.cpu().numpy()[sel]
+        line["rel_l2_eval_vs_oracle"] = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+        idx = oracle.sample(5000 + args.steps - 1, Q, m)
+        g = oracle.normal_residual(om, xyz.astype(np.float64), u.astype(np.float64), idx, cur["alpha"],
+                                   nthreads=nthreads)
+        h = oracle.normal_residual(om, xyz.astype(np.float64), u.astype(np.float64), idx, np.zeros(R),
+                                   nthreads=nthreads)
+        line["refit_normal_residual_rel"] = float(np.linalg.norm(g) / np.linalg.norm(h))
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,175 @@
+/*
+ * fst.h -- C ABI of libfst: GB300-native (sm_103a) evaluation and randomized
+ * least-squares core refit of functional sparse Tucker (FST) models.
+ *
+ * Paper: P. Rai, H. Kolla, L. Cannada, A. Gorodetsky, "Randomized Functional
+ * Sparse Tucker Tensor for Compression and Fast Visualization of Scientific
+ * Data", arXiv 1907.05884.
+ *
+ * Conventions (all entry points):
+ *   - Plain C types only.  Pointers documented "device" must be CUDA device (or
+ *     managed) memory of the current device; "host" pointers are ordinary CPU memory.
+ *   - The caller owns every point, value, index and output buffer.  The library
+ *     owns fst_model objects and the scratch memory it keeps inside them.
+ *   - Work is enqueued on the given stream (0 = legacy default stream).  Calls
+ *     documented "asynchronous" return before the GPU finishes; the others end
+ *     with a synchronisation of that stream because they return host results.
+ *   - Errors are returned as fst_status, never thrown; fst_last_error() gives a
+ *     thread-local message for the last failing call of the calling thread.
+ *   - Points are structure-of-arrays: xyz[0..n) = y1, xyz[n..2n) = y2,
+ *     xyz[2n..3n) = y3.  Points outside the model box are evaluated by polynomial
+ *     extrapolation (no clamping).
+ *   - Limits: 1 <= r_k <= FST_MAX_RANK, 0 <= p_k <= FST_MAX_DEGREE.
+ */
+#ifndef FST_H
+#define FST_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FST_MAX_RANK 32
+#define FST_MAX_DEGREE 127
+
+typedef struct fst_model fst_model;            /* opaque, device-resident, owned by the library */
+typedef struct CUstream_st* fst_stream;        /* a cudaStream_t */
+
+typedef enum {
+    FST_OK = 0,
+    FST_EINVAL = -1,        /* bad argument (null pointer, size, rank, degree) */
+    FST_ENOMEM = -2,        /* device or host allocation failed */
+    FST_ECUDA = -3,         /* a CUDA runtime call failed; see fst_last_error() */
+    FST_ENOTSPD = -4,       /* normal matrix not positive definite (rank-deficient sample) */
+    FST_ERANK = -5,         /* fewer sampled rows than unknowns (m < R) */
+    FST_ETIMEOUT = -6,      /* a bounded device wait gave up */
+    FST_EFORMAT = -7,       /* model file malformed */
+    FST_ENOTCONV = -8,      /* iterative refinement did not converge */
+    FST_EUNSUPPORTED = -9   /* precision or shape not supported by this build */
+} fst_status;
+
+/* Arithmetic of the contraction / Gram assembly.  FP64 and FP32 run on the CUDA
+ * cores; TF32, BF16 and BF16X3 (A = A_hi + A_lo split, three products) run the
+ * contraction on the tcgen05 tensor cores with FP32 accumulation. */
+typedef enum { FST_FP64 = 0, FST_FP32 = 1, FST_TF32 = 2, FST_BF16 = 3, FST_BF16X3 = 4 } fst_prec;
+
+/* Host description of a model with d = 3 (Sec. 2, eq. func_tuck and eq. sparse).
+ *   r[k]      Tucker rank of mode k.
+ *   p[k]      maximum Legendre degree of mode k (p[k]+1 basis functions).
+ *   lo, hi    the box mapped affinely onto [-1,1]^3.
+ *   colptr[k] (r[k]+1 entries), rowidx[k], val[k]: column j of mode k holds the
+ *             degrees n (0 <= n <= p[k], strictly increasing within a column) and
+ *             coefficients W^k_{n,j} of the orthonormal Legendre functions
+ *             phi_n(t) = sqrt(2n+1) L_n(t), i.e. w^(k)_j(t) = sum_n W^k_{n,j} phi_n(t).
+ *   alpha     core, r1*r2*r3 values in C order [j1][j2][j3].
+ * All host pointers; fst_model_create copies them. */
+typedef struct {
+    int32_t r[3];
+    int32_t p[3];
+    double lo[3];
+    double hi[3];
+    const int32_t* colptr[3];
+    const int32_t* rowidx[3];
+    const double* val[3];
+    const double* alpha;
+} fst_model_desc;
+
+/* ---------------------------------------------------------------- models */
+
+/* Copy a host description to the current device (synchronous).  Fails with
+ * FST_EINVAL on out-of-range ranks/degrees or unsorted/out-of-range degrees. */
+fst_status fst_model_create(const fst_model_desc* desc, fst_model** out);
+
+/* Free a model and its scratch (synchronises the device first).  NULL is a no-op. */
+void fst_model_free(fst_model* model);
+
+/* Shape: ranks, degrees and stored coefficients per mode.  Any output may be NULL. */
+fst_status fst_model_shape(const fst_model* model, int32_t r[3], int32_t p[3], int32_t nnz[3]);
+
+/* Copy the model back to caller-owned host buffers sized from fst_model_shape:
+ * colptr[k] (r[k]+1), rowidx[k] and val[k] (nnz[k]), alpha (r1 r2 r3), lo/hi (3).
+ * Any pointer may be NULL to skip that part.  Synchronous. */
+fst_status fst_model_read(const fst_model* model, int32_t* colptr[3], int32_t* rowidx[3],
+                          double* val[3], double* alpha, double lo[3], double hi[3]);
+
+/* Replace the core with r1 r2 r3 host values (C order).  Synchronous. */
+fst_status fst_model_set_core(fst_model* model, const double* alpha);
+
+/* Binary model file (".fstm", little-endian): magic "FSTM", version, ranks,
+ * degrees, box, CSC coefficients and the core, all values FP64. */
+fst_status fst_model_save(const fst_model* model, const char* path);
+fst_status fst_model_load(const char* path, fst_model** out);
+
+/* ---------------------------------------------------------------- evaluation */
+
+/* u~(y) at n points (Sec. 6: reconstruction is the evaluation of the basis
+ * functions at the points of interest; eq. func_tuck).  xyz: device, 3n floats
+ * SoA; out: device, n floats.  prec selects the contraction arithmetic (FST_FP32
+ * on CUDA cores, or a tensor-core precision).  Asynchronous; allocates nothing. */
+fst_status fst_eval(const fst_model* model, const float* xyz, int64_t n, float* out,
+                    fst_prec prec, fst_stream stream);
+
+/* The same in FP64 throughout (device xyz: 3n doubles, out: n doubles).  Asynchronous. */
+fst_status fst_eval_f64(const fst_model* model, const double* xyz, int64_t n, double* out,
+                        fst_stream stream);
+
+/* ---------------------------------------------------------------- sampling */
+
+/* Uniform sample of m distinct rows of [0,Q) without replacement (Algorithm 2,
+ * sampling step): row q gets the key splitmix64(seed, q) -- the (q+1)-th output
+ * of a splitmix64 stream seeded with `seed` -- and the m rows with the smallest
+ * keys are written to idx (device, m int64) in ascending order.  m >= Q gives
+ * every row.  Asynchronous; uses model-free scratch owned by the library. */
+fst_status fst_sample_rows(uint64_t seed, int64_t Q, int64_t m, int64_t* idx, fst_stream stream);
+
+/* ---------------------------------------------------------------- refit */
+
+typedef struct {
+    int32_t max_refine;       /* refinement steps after the first solve (default 8) */
+    double refine_tol;        /* stop when ||delta|| <= tol ||alpha|| (default 1e-12 FP64, 1e-9 else) */
+    int32_t fp64_cholesky;    /* 1: factor the normal matrix in FP64 (default: FP64 only for FST_FP64) */
+} fst_refit_opts;
+
+typedef struct {
+    int64_t m;                /* rows used */
+    int32_t refine_steps;     /* refinement steps taken */
+    int32_t fallback_fp64;    /* 1 if the FP32 factorisation failed and FP64 was used */
+    double first_rel_change;  /* ||alpha_refined - alpha_first|| / ||alpha_refined|| */
+    double last_rel_update;   /* ||delta|| / ||alpha|| of the last step */
+    double ms_sample, ms_factors, ms_gram, ms_cholesky, ms_refine;   /* GPU time per phase */
+} fst_refit_report;
+
+/* Re-estimate the core by least squares over sampled rows of the original data
+ * (Sec. 5, eq. rand_core; Algorithm 2 with uniform sampling of S = m > R rows,
+ * without the sign-flip/mixing steps): draws idx with fst_sample_rows(seed),
+ * forms the normal equations G = A^T A, h = A^T b over the Khatri-Rao rows
+ * a_q = w1(y1_q) (x) w2(y2_q) (x) w3(y3_q) in `prec`, factors G by Cholesky and
+ * refines alpha += G^-1 A^T (b - A alpha) with the residual accumulated in FP64.
+ * xyz (3Q floats SoA), u (Q floats): device.  idx: device int64 rows to use, or
+ * NULL to draw m rows with `seed`.  opts, report: host, may be NULL.  On success
+ * the model's core is replaced.  Synchronous (returns host status).
+ * FST_ERANK if m < R, FST_ENOTSPD if G is not positive definite in FP64. */
+fst_status fst_refit(fst_model* model, const float* xyz, const float* u, int64_t Q,
+                     const int64_t* idx, int64_t m, uint64_t seed, fst_prec prec,
+                     const fst_refit_opts* opts, fst_refit_report* report, fst_stream stream);
+
+/* FP64 refit (xyz 3Q doubles, u Q doubles; FP64 Gram, FP64 Cholesky). */
+fst_status fst_refit_f64(fst_model* model, const double* xyz, const double* u, int64_t Q,
+                         const int64_t* idx, int64_t m, uint64_t seed,
+                         const fst_refit_opts* opts, fst_refit_report* report, fst_stream stream);
+
+/* ---------------------------------------------------------------- errors */
+
+const char* fst_status_str(fst_status s);
+const char* fst_last_error(void);
+/* Library build description (arch, version) -- a static string. */
+const char* fst_build_info(void);
+/* Number of CUDA kernels libfst has launched in this process (all devices). */
+uint64_t fst_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

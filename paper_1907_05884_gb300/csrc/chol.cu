@@ -1,0 +1,272 @@
+// chol.cu -- blocked right-looking Cholesky G = L L^T of the normal matrix of the
+// sampled least-squares problem (Algorithm 2, last step: solve the sampled LS), and
+// the two triangular solves x <- L^-T L^-1 x.
+//
+// G is R x R row-major; only its lower triangle is read and L overwrites it.  Panel
+// width NB = 64.  Per panel: (1) one block factors the diagonal block in shared
+// memory; (2) a block per 64 rows solves the panel below, L21 = A21 L11^-T;
+// (3) the trailing lower triangle is updated, A22 -= L21 L21^T, in 64 x 64 tiles.
+// A non-positive (or NaN) pivot sets *d_flag; the caller reads it after the stream
+// synchronises, so no step waits on the device.
+#include <math.h>
+
+#include "fst_internal.cuh"
+
+namespace fst {
+
+constexpr int NB = 64;
+
+// Pivot floor: 16 * unit roundoff * the largest diagonal entry of G.  A pivot at or
+// below it means G is numerically singular in T.
+template <typename T>
+__global__ void pivot_floor_kernel(const T* G, int R, T* floor_out) {
+    __shared__ T red[256];
+    T mx = T(0);
+    for (int i = threadIdx.x; i < R; i += blockDim.x) {
+        const T d = G[(size_t)i * R + i];
+        mx = d > mx ? d : mx;
+    }
+    red[threadIdx.x] = mx;
+    __syncthreads();
+    for (int o = 128; o; o >>= 1) {
+        if (threadIdx.x < o && red[threadIdx.x + o] > red[threadIdx.x]) red[threadIdx.x] = red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const T eps = sizeof(T) == 4 ? T(1.1920929e-7) : T(2.220446049250313e-16);
+        *floor_out = T(16) * eps * red[0];
+    }
+}
+
+template <typename T>
+__global__ void potrf_diag_kernel(T* G, int R, int k0, int kb, int* flag, const T* floor_p) {
+    __shared__ T A[NB][NB + 1];
+    const int tid = threadIdx.x, B = blockDim.x;
+    for (int e = tid; e < kb * kb; e += B) {
+        const int i = e / kb, j = e - i * kb;
+        A[i][j] = j <= i ? G[(size_t)(k0 + i) * R + k0 + j] : T(0);
+    }
+    __syncthreads();
+    for (int j = 0; j < kb; ++j) {
+        if (tid == 0) {
+            const T d = A[j][j];
+            if (!(d > *floor_p)) atomicOr(flag, 1);
+            A[j][j] = sqrt(d);
+        }
+        __syncthreads();
+        const T piv = A[j][j];
+        for (int i = j + 1 + tid; i < kb; i += B) A[i][j] /= piv;
+        __syncthreads();
+        const int w = kb - j - 1;
+        for (int e = tid; e < w * w; e += B) {
+            const int i = j + 1 + e / w, c = j + 1 + e % w;
+            if (c <= i) A[i][c] -= A[i][j] * A[c][j];
+        }
+        __syncthreads();
+    }
+    for (int e = tid; e < kb * kb; e += B) {
+        const int i = e / kb, j = e - i * kb;
+        if (j <= i) G[(size_t)(k0 + i) * R + k0 + j] = A[i][j];
+    }
+}
+
+// L21 = A21 L11^-T for rows row0 .. row0+63 (row0 = k0 + kb + 64*blockIdx.x).
+template <typename T>
+__global__ void trsm_panel_kernel(T* G, int R, int k0, int kb) {
+    extern __shared__ __align__(16) unsigned char trsm_smem[];
+    T (*L)[NB + 1] = reinterpret_cast<T (*)[NB + 1]>(trsm_smem);
+    T (*X)[NB + 1] = L + NB;
+    const int tid = threadIdx.x, B = blockDim.x;
+    const int row0 = k0 + kb + NB * blockIdx.x;
+    const int rows = R - row0 < NB ? R - row0 : NB;
+    for (int e = tid; e < kb * kb; e += B) {
+        const int i = e / kb, j = e - i * kb;
+        L[i][j] = j <= i ? G[(size_t)(k0 + i) * R + k0 + j] : T(0);
+    }
+    for (int e = tid; e < rows * kb; e += B) {
+        const int i = e / kb, j = e - i * kb;
+        X[i][j] = G[(size_t)(row0 + i) * R + k0 + j];
+    }
+    __syncthreads();
+    if (tid < rows) {
+        for (int c = 0; c < kb; ++c) {
+            T s = X[tid][c];
+            for (int cc = 0; cc < c; ++cc) s -= X[tid][cc] * L[c][cc];
+            X[tid][c] = s / L[c][c];
+        }
+    }
+    __syncthreads();
+    for (int e = tid; e < rows * kb; e += B) {
+        const int i = e / kb, j = e - i * kb;
+        G[(size_t)(row0 + i) * R + k0 + j] = X[i][j];
+    }
+}
+
+// A22 -= L21 L21^T on lower 64x64 tiles of the trailing matrix starting at t0 = k0 + kb.
+template <typename T>
+__global__ void __launch_bounds__(256) syrk_update_kernel(T* G, int R, int k0, int kb, int t0) {
+    constexpr int KC = 32;                    // panel columns staged per step
+    __shared__ __align__(16) T As[KC][NB];   // [t][row within tile]
+    __shared__ __align__(16) T Bs[KC][NB];
+    // lower tile index (ti >= tc) from the linear block id
+    const long long b = blockIdx.x;
+    int ti = (int)((sqrt(8.0 * (double)b + 1.0) - 1.0) * 0.5);
+    while ((long long)(ti + 1) * (ti + 2) / 2 <= b) ++ti;
+    while ((long long)ti * (ti + 1) / 2 > b) --ti;
+    const int tc = (int)(b - (long long)ti * (ti + 1) / 2);
+    const int r0 = t0 + ti * NB, c0 = t0 + tc * NB;
+    const int tid = threadIdx.x;
+    const int ty = tid >> 4, tx = tid & 15;
+    T acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[a][c] = T(0);
+    for (int tb = 0; tb < kb; tb += KC) {
+        __syncthreads();
+        for (int e = tid; e < NB * KC; e += 256) {
+            const int i = e / KC, t = e - i * KC;
+            const bool inb = tb + t < kb;
+            As[t][i] = (r0 + i < R && inb) ? G[(size_t)(r0 + i) * R + k0 + tb + t] : T(0);
+            Bs[t][i] = (c0 + i < R && inb) ? G[(size_t)(c0 + i) * R + k0 + tb + t] : T(0);
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int t = 0; t < KC; ++t) {
+            T av[4], bv[4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) av[a] = As[t][ty * 4 + a];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) bv[c] = Bs[t][tx * 4 + c];
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) acc[a][c] = fma(av[a], bv[c], acc[a][c]);
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        const int i = r0 + ty * 4 + a;
+        if (i >= R) continue;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int j = c0 + tx * 4 + c;
+            if (j < R && j <= i) G[(size_t)i * R + j] -= acc[a][c];
+        }
+    }
+}
+
+template <typename T>
+fst_status cholesky_lower(T* G, int R, int* d_flag, cudaStream_t s) {
+    // d_flag points at two ints of scratch: the flag, then room for the pivot floor
+    T* floor_p = reinterpret_cast<T*>(d_flag + 2);
+    pivot_floor_kernel<T><<<1, 256, 0, s>>>(G, R, floor_p);
+    FST_CHECK_LAUNCH();
+    const size_t trsm_smem = 2 * NB * (NB + 1) * sizeof(T);
+    FST_CUDA(cudaFuncSetAttribute(trsm_panel_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)trsm_smem));
+    for (int k0 = 0; k0 < R; k0 += NB) {
+        const int kb = R - k0 < NB ? R - k0 : NB;
+        potrf_diag_kernel<T><<<1, 256, 0, s>>>(G, R, k0, kb, d_flag, floor_p);
+        FST_CHECK_LAUNCH();
+        const int t0 = k0 + kb;
+        const int rest = R - t0;
+        if (rest <= 0) break;
+        trsm_panel_kernel<T><<<(rest + NB - 1) / NB, NB, trsm_smem, s>>>(G, R, k0, kb);
+        FST_CHECK_LAUNCH();
+        const long long nt = (rest + NB - 1) / NB;
+        syrk_update_kernel<T><<<(unsigned)(nt * (nt + 1) / 2), 256, 0, s>>>(G, R, k0, kb, t0);
+        FST_CHECK_LAUNCH();
+    }
+    return FST_OK;
+}
+
+// ------------------------------------------------------------------ triangular solves
+// Forward: x_b <- L_bb^-1 x_b (one warp), then x_i -= L_ib x_b for rows i below (warp per row).
+template <typename T>
+__global__ void fwd_diag_kernel(const T* L, int R, int k0, int kb, double* x) {
+    __shared__ double xs[NB];
+    const int lane = threadIdx.x;
+    for (int i = lane; i < kb; i += 32) xs[i] = x[k0 + i];
+    __syncwarp();
+    for (int r = 0; r < kb; ++r) {
+        double s = 0.0;
+        for (int c = lane; c < r; c += 32) s += (double)L[(size_t)(k0 + r) * R + k0 + c] * xs[c];
+        for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) xs[r] = (xs[r] - s) / (double)L[(size_t)(k0 + r) * R + k0 + r];
+        __syncwarp();
+    }
+    for (int i = lane; i < kb; i += 32) x[k0 + i] = xs[i];
+}
+
+template <typename T>
+__global__ void fwd_update_kernel(const T* L, int R, int k0, int kb, double* x) {
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    const int i = k0 + kb + warp;
+    if (i >= R) return;
+    double s = 0.0;
+    for (int c = lane; c < kb; c += 32) s += (double)L[(size_t)i * R + k0 + c] * x[k0 + c];
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) x[i] -= s;
+}
+
+// Backward: x_b <- L_bb^-T x_b, then x_i -= sum_{c in b} L_ci x_c for rows i above (thread per i).
+template <typename T>
+__global__ void bwd_diag_kernel(const T* L, int R, int k0, int kb, double* x) {
+    __shared__ double xs[NB];
+    const int lane = threadIdx.x;
+    for (int i = lane; i < kb; i += 32) xs[i] = x[k0 + i];
+    __syncwarp();
+    for (int r = kb - 1; r >= 0; --r) {
+        double s = 0.0;
+        for (int c = r + 1 + lane; c < kb; c += 32) s += (double)L[(size_t)(k0 + c) * R + k0 + r] * xs[c];
+        for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) xs[r] = (xs[r] - s) / (double)L[(size_t)(k0 + r) * R + k0 + r];
+        __syncwarp();
+    }
+    for (int i = lane; i < kb; i += 32) x[k0 + i] = xs[i];
+}
+
+template <typename T>
+__global__ void bwd_update_kernel(const T* L, int R, int k0, int kb, double* x) {
+    __shared__ double xs[NB];
+    for (int i = threadIdx.x; i < kb; i += blockDim.x) xs[i] = x[k0 + i];
+    __syncthreads();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= k0) return;
+    double s = 0.0;
+    for (int c = 0; c < kb; ++c) s += (double)L[(size_t)(k0 + c) * R + i] * xs[c];
+    x[i] -= s;
+}
+
+template <typename T>
+fst_status chol_solve(const T* L, int R, double* x, cudaStream_t s) {
+    for (int k0 = 0; k0 < R; k0 += NB) {
+        const int kb = R - k0 < NB ? R - k0 : NB;
+        fwd_diag_kernel<T><<<1, 32, 0, s>>>(L, R, k0, kb, x);
+        FST_CHECK_LAUNCH();
+        const int rest = R - k0 - kb;
+        if (rest > 0) {
+            fwd_update_kernel<T><<<(rest + 7) / 8, 256, 0, s>>>(L, R, k0, kb, x);
+            FST_CHECK_LAUNCH();
+        }
+    }
+    const int last = ((R - 1) / NB) * NB;
+    for (int k0 = last; k0 >= 0; k0 -= NB) {
+        const int kb = R - k0 < NB ? R - k0 : NB;
+        bwd_diag_kernel<T><<<1, 32, 0, s>>>(L, R, k0, kb, x);
+        FST_CHECK_LAUNCH();
+        if (k0 > 0) {
+            bwd_update_kernel<T><<<(k0 + 255) / 256, 256, 0, s>>>(L, R, k0, kb, x);
+            FST_CHECK_LAUNCH();
+        }
+    }
+    return FST_OK;
+}
+
+template fst_status cholesky_lower<float>(float*, int, int*, cudaStream_t);
+template fst_status cholesky_lower<double>(double*, int, int*, cudaStream_t);
+template fst_status chol_solve<float>(const float*, int, double*, cudaStream_t);
+template fst_status chol_solve<double>(const double*, int, double*, cudaStream_t);
+
+}  // namespace fst

@@ -1,0 +1,125 @@
+// fst_internal.cuh -- shared declarations of libfst's translation units.
+//
+// Device data layout of a model (all on the device the model was created on):
+//   W64[k], W32[k]  dense coefficient matrix of mode k, (p_k+1) x r_k row-major,
+//                   entry [n][j] = W^k_{n,j} * sqrt(2n+1), i.e. the coefficient of the
+//                   plain Legendre polynomial L_n in w^(k)_j (eq. sparse, Sec. 2).
+//   rowmask[k]      one byte per degree n: 1 if row n of W^k has a nonzero.
+//   alpha64/32      core, C order [j1][j2][j3] (eq. func_tuck).
+//   tc_*            tensor-core operand images of the core (see eval_tc.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "fst.h"
+
+namespace fst {
+
+void set_error(const char* fmt, ...);
+fst_status cuda_fail(cudaError_t e, const char* what, const char* file, int line);
+
+#define FST_CUDA(expr)                                                                  \
+    do {                                                                                \
+        cudaError_t _e = (expr);                                                        \
+        if (_e != cudaSuccess) return ::fst::cuda_fail(_e, #expr, __FILE__, __LINE__);  \
+    } while (0)
+// Every kernel launch in libfst is followed by FST_CHECK_LAUNCH(), which also counts it.
+void count_launch();
+#define FST_CHECK_LAUNCH()          \
+    do {                            \
+        ::fst::count_launch();      \
+        FST_CUDA(cudaGetLastError()); \
+    } while (0)
+#define FST_TRY(expr)                        \
+    do {                                     \
+        fst_status _s = (expr);              \
+        if (_s != FST_OK) return _s;         \
+    } while (0)
+#define FST_REQUIRE(cond, ...)                       \
+    do {                                             \
+        if (!(cond)) {                               \
+            ::fst::set_error(__VA_ARGS__);           \
+            return FST_EINVAL;                       \
+        }                                            \
+    } while (0)
+
+// A device buffer that only grows.
+struct DevBuf {
+    void* ptr = nullptr;
+    size_t bytes = 0;
+    fst_status ensure(size_t need);
+    void release();
+    template <typename T> T* as() const { return static_cast<T*>(ptr); }
+};
+
+// Scratch of the refit, kept inside the model between calls.
+struct RefitScratch {
+    DevBuf idx, U[3], b, G, G64, res, g, z, delta, alpha, norms, flag;
+};
+
+}  // namespace fst
+
+struct fst_model {
+    int device = 0;
+    int r[3] = {0, 0, 0};
+    int p[3] = {0, 0, 0};
+    int p_eff[3] = {0, 0, 0};    // 1 + highest degree with a nonzero coefficient
+    double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+    std::vector<int32_t> colptr[3], rowidx[3];
+    std::vector<double> val[3];
+    std::vector<double> alpha;   // host copy of the core
+
+    double* W64[3] = {nullptr, nullptr, nullptr};
+    float* W32[3] = {nullptr, nullptr, nullptr};
+    uint8_t* rowmask[3] = {nullptr, nullptr, nullptr};
+    double* alpha64 = nullptr;
+    float* alpha32 = nullptr;
+
+    // tensor-core images of the core, built on demand (eval_tc.cu)
+    void* tc_core = nullptr;
+    size_t tc_core_bytes = 0;
+    int tc_core_kind = -1;
+
+    fst::RefitScratch rs;
+    std::mutex mu;
+
+    int R() const { return r[0] * r[1] * r[2]; }
+};
+
+namespace fst {
+
+// Device upload of the derived layouts after the host copy changed.
+fst_status model_upload_core(fst_model* m);
+fst_status model_invalidate_tc(fst_model* m);
+
+// Number of SMs of the current device (cached).
+int sm_count();
+// Device of a pointer, or -1 for host memory.
+int pointer_device(const void* p);
+
+// Evaluation entry points used by the refit (residual path).
+template <typename T>
+fst_status eval_simt_launch(const fst_model* m, const T* xyz, int64_t n, T* out, cudaStream_t s);
+
+// Row sampler (sample.cu).
+fst_status sample_rows(uint64_t seed, int64_t Q, int64_t m, int64_t* idx, cudaStream_t s);
+
+// Tensor-core eval (eval_tc.cu).
+fst_status eval_tc_launch(fst_model* m, const float* xyz, int64_t n, float* out, fst_prec prec,
+                          cudaStream_t s);
+// Tensor-core Gram (gram_tc.cu): lower triangle of G = A^T A, FP32 accumulation.
+fst_status gram_tc_launch(const fst_model* m, const float* U1, const float* U2, const float* U3,
+                          int64_t mrows, float* G, fst_prec prec, cudaStream_t s);
+
+// Cholesky and triangular solves (chol.cu).
+template <typename T>
+fst_status cholesky_lower(T* G, int R, int* d_flag, cudaStream_t s);
+template <typename T>
+fst_status chol_solve(const T* L, int R, double* x, cudaStream_t s);  // x <- (L L^T)^-1 x
+
+}  // namespace fst

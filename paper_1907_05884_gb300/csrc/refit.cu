@@ -1,0 +1,567 @@
+// refit.cu -- randomized least-squares re-estimation of the core (Sec. 5,
+// eq. rand_core; Algorithm 2 with uniform row sampling) and its entry points.
+//
+//   alpha^ = argmin_alpha || b - A alpha ||,  A_{s,(i,j,k)} = w1_i(y1_s) w2_j(y2_s) w3_k(y3_s)
+//
+// over m sampled rows s.  Steps:
+//   1. rows: given, or drawn by the splitmix64 key sampler (sample.cu);
+//   2. factor values U_k[s][j] = w^(k)_j(y_k of row s), b_s = u of row s;
+//   3. normal matrix G = A^T A, lower triangle, in the working precision, the Khatri-Rao
+//      rows generated on the fly from U_1..U_3 (never stored), h = A^T b in FP64;
+//   4. Cholesky G = L L^T (chol.cu) and alpha_0 = L^-T L^-1 h;
+//   5. refinement alpha += L^-T L^-1 A^T (b - A alpha), residual and A^T r accumulated
+//      in FP64 through the factored (Khatri-Rao) form of A, so the fixed point is the
+//      least-squares solution even when G carries only working-precision accuracy.
+// If the working-precision factorisation fails or refinement diverges, the FP64 path
+// (FP64 G, FP64 Cholesky) is used.
+#include <math.h>
+
+#include <vector>
+
+#include "basis.cuh"
+
+namespace fst {
+
+// ------------------------------------------------------------------ step 2
+template <typename T, int RM>
+__global__ void __launch_bounds__(128) sampled_factors_kernel(const EvalArgs<T> a, const T* __restrict__ xyz,
+                                                              int64_t Q, const int64_t* __restrict__ idx,
+                                                              int64_t m, const T* __restrict__ u, T* U1, T* U2,
+                                                              T* U3, T* bvec) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int B = blockDim.x, tid = threadIdx.x;
+    T* ra = reinterpret_cast<T*>(smem);
+    T* rb = ra + a.pm;
+    T* Ws[3];
+    Ws[0] = rb + a.pm;
+    Ws[1] = Ws[0] + a.pe[0] * RM;
+    Ws[2] = Ws[1] + a.pe[1] * RM;
+    uint8_t* mk = reinterpret_cast<uint8_t*>(Ws[2] + a.pe[2] * RM);
+    for (int i = tid; i < a.pm; i += B) {
+        ra[i] = T(2 * i + 1) / T(i + 1);
+        rb[i] = T(i) / T(i + 1);
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const int rk = a.r[k];
+        for (int e = tid; e < a.pe[k] * RM; e += B) {
+            const int nn = e / RM, j = e - nn * RM;
+            Ws[k][e] = j < rk ? a.W[k][nn * rk + j] : T(0);
+        }
+        for (int e = tid; e < a.pm; e += B) mk[k * a.pm + e] = e < a.pe[k] ? a.mask[k][e] : 0;
+    }
+    __syncthreads();
+    T* outs[3] = {U1, U2, U3};
+    for (int64_t s = (int64_t)blockIdx.x * B + tid; s < m; s += (int64_t)gridDim.x * B) {
+        const int64_t q = idx[s];
+        bvec[s] = u[q];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            T t[1] = {fma(xyz[k * Q + q], a.sc[k], a.of[k])};
+            T acc[1][RM];
+            factor_values<T, RM, 1>(t, Ws[k], mk + k * a.pm, a.pe[k], ra, rb, acc);
+            const int rk = a.r[k];
+            for (int j = 0; j < rk; ++j) outs[k][s * rk + j] = acc[0][j];
+        }
+    }
+}
+
+// ------------------------------------------------------------------ step 3 (CUDA cores)
+// Lower 64x64 tiles of G = A^T A; K loop over sampled rows in chunks of 32.
+template <typename T>
+__global__ void __launch_bounds__(256) gram_simt_kernel(const T* __restrict__ U1, const T* __restrict__ U2,
+                                                        const T* __restrict__ U3, int64_t m, int r1, int r2,
+                                                        int r3, T* G) {
+    constexpr int TS = 64, KC = 32;
+    __shared__ __align__(16) T As[KC][TS];
+    __shared__ __align__(16) T Bs[KC][TS];
+    const int R = r1 * r2 * r3;
+    const long long b = blockIdx.x;
+    int ti = (int)((sqrt(8.0 * (double)b + 1.0) - 1.0) * 0.5);
+    while ((long long)(ti + 1) * (ti + 2) / 2 <= b) ++ti;
+    while ((long long)ti * (ti + 1) / 2 > b) --ti;
+    const int tc = (int)(b - (long long)ti * (ti + 1) / 2);
+    const int tid = threadIdx.x;
+    // the column of A this thread generates for the row tile and the column tile
+    const int col = tid & 63, soff = tid >> 6;
+    const int ar = ti * TS + col, ac = tc * TS + col;
+    const bool vr = ar < R, vc = ac < R;
+    const int ir = vr ? ar / (r2 * r3) : 0, jr = vr ? (ar / r3) % r2 : 0, kr = vr ? ar % r3 : 0;
+    const int ic = vc ? ac / (r2 * r3) : 0, jc = vc ? (ac / r3) % r2 : 0, kc = vc ? ac % r3 : 0;
+    const int ty = tid >> 4, tx = tid & 15;
+    T acc[4][4];
+#pragma unroll
+    for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) acc[x][y] = T(0);
+    for (int64_t s0 = 0; s0 < m; s0 += KC) {
+        __syncthreads();
+#pragma unroll
+        for (int l = 0; l < KC / 4; ++l) {
+            const int ss = soff + 4 * l;
+            const int64_t s = s0 + ss;
+            T vr_v = T(0), vc_v = T(0);
+            if (s < m) {
+                if (vr) vr_v = U1[s * r1 + ir] * U2[s * r2 + jr] * U3[s * r3 + kr];
+                if (vc) vc_v = U1[s * r1 + ic] * U2[s * r2 + jc] * U3[s * r3 + kc];
+            }
+            As[ss][col] = vr_v;
+            Bs[ss][col] = vc_v;
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int t = 0; t < KC; ++t) {
+            T av[4], bv[4];
+#pragma unroll
+            for (int x = 0; x < 4; ++x) av[x] = As[t][ty * 4 + x];
+#pragma unroll
+            for (int y = 0; y < 4; ++y) bv[y] = Bs[t][tx * 4 + y];
+#pragma unroll
+            for (int x = 0; x < 4; ++x)
+#pragma unroll
+                for (int y = 0; y < 4; ++y) acc[x][y] = fma(av[x], bv[y], acc[x][y]);
+        }
+    }
+#pragma unroll
+    for (int x = 0; x < 4; ++x) {
+        const int i = ti * TS + ty * 4 + x;
+        if (i >= R) continue;
+#pragma unroll
+        for (int y = 0; y < 4; ++y) {
+            const int j = tc * TS + tx * 4 + y;
+            if (j < R && j <= i) G[(size_t)i * R + j] = acc[x][y];
+        }
+    }
+}
+
+// ------------------------------------------------------------------ A^T r and b - A alpha
+// g += A^T r over a chunk of rows per block: thread per (i,j) pair, r3 accumulators,
+// rows staged through shared memory; partial sums added to g with FP64 atomics.
+template <typename T, int R3M>
+__global__ void __launch_bounds__(256) atr_kernel(const T* __restrict__ U1, const T* __restrict__ U2,
+                                                  const T* __restrict__ U3, const double* __restrict__ rv,
+                                                  int64_t m, int r1, int r2, int r3, int64_t rows_per_block,
+                                                  double* g) {
+    constexpr int S = 32;
+    __shared__ T u1s[S][FST_MAX_RANK + 1], u2s[S][FST_MAX_RANK + 1];
+    __shared__ __align__(16) T u3s[S][R3M];
+    __shared__ T rs[S];
+    const int64_t lo = (int64_t)blockIdx.x * rows_per_block;
+    const int64_t hi = lo + rows_per_block < m ? lo + rows_per_block : m;
+    const int npairs = r1 * r2;
+    for (int p0 = 0; p0 < npairs; p0 += blockDim.x) {
+        const int p = p0 + threadIdx.x;
+        const int i = p < npairs ? p / r2 : 0, j = p < npairs ? p % r2 : 0;
+        T acc[R3M];
+#pragma unroll
+        for (int k = 0; k < R3M; ++k) acc[k] = T(0);
+        for (int64_t s0 = lo; s0 < hi; s0 += S) {
+            __syncthreads();
+            for (int e = threadIdx.x; e < S * FST_MAX_RANK; e += blockDim.x) {
+                const int ss = e / FST_MAX_RANK, c = e - ss * FST_MAX_RANK;
+                const int64_t s = s0 + ss;
+                const bool ok = s < hi;
+                if (c < r1) u1s[ss][c] = ok ? U1[s * r1 + c] : T(0);
+                if (c < r2) u2s[ss][c] = ok ? U2[s * r2 + c] : T(0);
+                if (c < R3M) u3s[ss][c] = (ok && c < r3) ? U3[s * r3 + c] : T(0);
+                if (c == 0) rs[ss] = ok ? (T)rv[s] : T(0);
+            }
+            __syncthreads();
+            if (p < npairs) {
+#pragma unroll 4
+                for (int ss = 0; ss < S; ++ss) {
+                    const T c = rs[ss] * u1s[ss][i] * u2s[ss][j];
+#pragma unroll
+                    for (int k = 0; k < R3M; ++k) acc[k] = fma(c, u3s[ss][k], acc[k]);
+                }
+            }
+        }
+        if (p < npairs)
+            for (int k = 0; k < r3; ++k) atomicAdd(&g[(size_t)p * r3 + k], (double)acc[k]);
+    }
+}
+
+// r_s = b_s - sum_i w1_i sum_j w2_j sum_k alpha_ijk w3_k (inner sum in T, outer sums in FP64).
+template <typename T, int R3M>
+__global__ void __launch_bounds__(128) residual_kernel(const T* __restrict__ U1, const T* __restrict__ U2,
+                                                       const T* __restrict__ U3, const T* __restrict__ bvec,
+                                                       const double* __restrict__ alpha, int64_t m, int r1,
+                                                       int r2, int r3, double* rv) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    T* As = reinterpret_cast<T*>(smem);   // [r1*r2][R3M]
+    for (int e = threadIdx.x; e < r1 * r2 * R3M; e += blockDim.x) {
+        const int ij = e / R3M, k = e - ij * R3M;
+        As[e] = k < r3 ? (T)alpha[ij * r3 + k] : T(0);
+    }
+    __syncthreads();
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < m; s += (int64_t)gridDim.x * blockDim.x) {
+        T w3[R3M];
+#pragma unroll
+        for (int k = 0; k < R3M; ++k) w3[k] = k < r3 ? U3[s * r3 + k] : T(0);
+        double f = 0.0;
+        for (int i = 0; i < r1; ++i) {
+            double si = 0.0;
+            for (int j = 0; j < r2; ++j) {
+                const T* arow = As + (i * r2 + j) * R3M;
+                T t0 = T(0), t1 = T(0);
+#pragma unroll
+                for (int k = 0; k < R3M; k += 4) {
+                    T a0, a1, a2, a3;
+                    load4(arow + k, a0, a1, a2, a3);
+                    t0 = fma(a0, w3[k], t0);
+                    t1 = fma(a1, w3[k + 1], t1);
+                    t0 = fma(a2, w3[k + 2], t0);
+                    t1 = fma(a3, w3[k + 3], t1);
+                }
+                si = fma((double)(t0 + t1), (double)U2[s * r2 + j], si);
+            }
+            f = fma(si, (double)U1[s * r1 + i], f);
+        }
+        rv[s] = (double)bvec[s] - f;
+    }
+}
+
+template <typename T>
+__global__ void to_double_kernel(const T* src, double* dst, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = (double)src[i];
+}
+
+// alpha += delta; norms[0] += ||delta||^2, norms[1] += ||alpha||^2 (norms zeroed by the caller)
+__global__ void axpy_norms_kernel(double* alpha, const double* delta, int n, double* norms) {
+    double d2 = 0.0, a2 = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double a = alpha[i] + delta[i];
+        alpha[i] = a;
+        d2 += delta[i] * delta[i];
+        a2 += a * a;
+    }
+    for (int o = 16; o; o >>= 1) {
+        d2 += __shfl_xor_sync(0xffffffffu, d2, o);
+        a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&norms[0], d2);
+        atomicAdd(&norms[1], a2);
+    }
+}
+
+// ------------------------------------------------------------------ driver
+struct EventTimer {
+    cudaEvent_t a = nullptr, b = nullptr;
+    cudaStream_t s;
+    explicit EventTimer(cudaStream_t st) : s(st) {
+        cudaEventCreate(&a);
+        cudaEventCreate(&b);
+        cudaEventRecord(a, s);
+    }
+    double stop() {
+        cudaEventRecord(b, s);
+        cudaEventSynchronize(b);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, a, b);
+        cudaEventRecord(a, s);
+        return ms;
+    }
+    ~EventTimer() {
+        cudaEventDestroy(a);
+        cudaEventDestroy(b);
+    }
+};
+
+static int grid_for(int64_t n, int block, int cap_per_sm = 8) {
+    int64_t g = (n + block - 1) / block;
+    const int64_t cap = (int64_t)sm_count() * cap_per_sm;
+    if (g > cap) g = cap;
+    return g < 1 ? 1 : (int)g;
+}
+
+template <typename T>
+static fst_status launch_factors(const fst_model* M, const T* xyz, int64_t Q, const int64_t* idx, int64_t m,
+                                 const T* u, T* U[3], T* bvec, cudaStream_t s) {
+    EvalArgs<T> a = make_args<T>(M);
+    bind(a, M);
+    int rmax = M->r[0] > M->r[1] ? M->r[0] : M->r[1];
+    rmax = M->r[2] > rmax ? M->r[2] : rmax;
+    const int RMb = rmax <= 8 ? 8 : rmax <= 16 ? 16 : rmax <= 24 ? 24 : 32;
+    const size_t smem = (2 * (size_t)a.pm + (size_t)(a.pe[0] + a.pe[1] + a.pe[2]) * RMb) * sizeof(T) + 3 * a.pm;
+#define FST_FACT(RMV)                                                                                      \
+    {                                                                                                      \
+        auto kern = sampled_factors_kernel<T, RMV>;                                                        \
+        FST_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));      \
+        kern<<<grid_for(m, 128), 128, smem, s>>>(a, xyz, Q, idx, m, u, U[0], U[1], U[2], bvec);           \
+    }
+    if (RMb == 8) FST_FACT(8) else if (RMb == 16) FST_FACT(16) else if (RMb == 24) FST_FACT(24) else FST_FACT(32)
+#undef FST_FACT
+    FST_CHECK_LAUNCH();
+    return FST_OK;
+}
+
+template <typename T>
+static fst_status launch_atr(const fst_model* M, const T* const U[3], const double* rv, int64_t m, double* g,
+                             cudaStream_t s) {
+    const int r1 = M->r[0], r2 = M->r[1], r3 = M->r[2];
+    FST_CUDA(cudaMemsetAsync(g, 0, sizeof(double) * (size_t)M->R(), s));
+    const int64_t rows_per_block = 1024;
+    const unsigned grid = (unsigned)((m + rows_per_block - 1) / rows_per_block);
+    if (grid == 0) return FST_OK;
+    if (r3 <= 8) atr_kernel<T, 8><<<grid, 256, 0, s>>>(U[0], U[1], U[2], rv, m, r1, r2, r3, rows_per_block, g);
+    else if (r3 <= 16) atr_kernel<T, 16><<<grid, 256, 0, s>>>(U[0], U[1], U[2], rv, m, r1, r2, r3, rows_per_block, g);
+    else if (r3 <= 24) atr_kernel<T, 24><<<grid, 256, 0, s>>>(U[0], U[1], U[2], rv, m, r1, r2, r3, rows_per_block, g);
+    else atr_kernel<T, 32><<<grid, 256, 0, s>>>(U[0], U[1], U[2], rv, m, r1, r2, r3, rows_per_block, g);
+    FST_CHECK_LAUNCH();
+    return FST_OK;
+}
+
+template <typename T>
+static fst_status launch_residual(const fst_model* M, const T* const U[3], const T* bvec, const double* alpha,
+                                  int64_t m, double* rv, cudaStream_t s) {
+    const int r1 = M->r[0], r2 = M->r[1], r3 = M->r[2];
+    const int R3M = r3 <= 8 ? 8 : r3 <= 16 ? 16 : r3 <= 24 ? 24 : 32;
+    const size_t smem = (size_t)r1 * r2 * R3M * sizeof(T);
+    const int grid = grid_for(m, 128, 4);
+#define FST_RES(V)                                                                                          \
+    {                                                                                                       \
+        auto kern = residual_kernel<T, V>;                                                                  \
+        FST_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));       \
+        kern<<<grid, 128, smem, s>>>(U[0], U[1], U[2], bvec, alpha, m, r1, r2, r3, rv);                     \
+    }
+    if (R3M == 8) FST_RES(8) else if (R3M == 16) FST_RES(16) else if (R3M == 24) FST_RES(24) else FST_RES(32)
+#undef FST_RES
+    FST_CHECK_LAUNCH();
+    return FST_OK;
+}
+
+template <typename T>
+static fst_status launch_gram_simt(const fst_model* M, const T* const U[3], int64_t m, T* G, cudaStream_t s) {
+    const int R = M->R();
+    const long long nt = (R + 63) / 64;
+    gram_simt_kernel<T><<<(unsigned)(nt * (nt + 1) / 2), 256, 0, s>>>(U[0], U[1], U[2], m, M->r[0], M->r[1],
+                                                                      M->r[2], G);
+    FST_CHECK_LAUNCH();
+    return FST_OK;
+}
+
+// Working precision T for factors, Gram and Cholesky; FP64 vectors and refinement.
+template <typename T>
+static fst_status refit_impl(fst_model* M, const T* xyz, const T* u, int64_t Q, const int64_t* idx_in, int64_t m,
+                             uint64_t seed, fst_prec prec, const fst_refit_opts* opts, fst_refit_report* rep,
+                             cudaStream_t s) {
+    const int R = M->R();
+    RefitScratch& W = M->rs;
+    const bool fp64 = sizeof(T) == 8;
+    const int max_refine = opts ? opts->max_refine : 8;
+    const double tol = (opts && opts->refine_tol > 0) ? opts->refine_tol : (fp64 ? 1e-13 : 1e-10);
+    const bool force64 = opts && opts->fp64_cholesky;
+    fst_refit_report r;
+    memset(&r, 0, sizeof r);
+    r.m = m;
+
+    EventTimer tm(s);
+    // 1. rows
+    const int64_t* idx = idx_in;
+    if (!idx) {
+        FST_TRY(W.idx.ensure(sizeof(int64_t) * (size_t)m));
+        FST_TRY(sample_rows(seed, Q, m, W.idx.as<int64_t>(), s));
+        idx = W.idx.as<int64_t>();
+    }
+    r.ms_sample = tm.stop();
+    // 2. factor values of the sampled rows
+    T* U[3];
+    for (int k = 0; k < 3; ++k) {
+        FST_TRY(W.U[k].ensure(sizeof(T) * (size_t)m * M->r[k]));
+        U[k] = W.U[k].as<T>();
+    }
+    FST_TRY(W.b.ensure(sizeof(T) * (size_t)m));
+    T* bvec = W.b.as<T>();
+    FST_TRY(launch_factors<T>(M, xyz, Q, idx, m, u, U, bvec, s));
+    r.ms_factors = tm.stop();
+
+    FST_TRY(W.res.ensure(sizeof(double) * (size_t)m));
+    FST_TRY(W.g.ensure(sizeof(double) * (size_t)R));
+    FST_TRY(W.alpha.ensure(sizeof(double) * (size_t)R));
+    FST_TRY(W.z.ensure(sizeof(double) * (size_t)R));
+    FST_TRY(W.norms.ensure(sizeof(double) * 2));
+    FST_TRY(W.flag.ensure(4 * sizeof(int)));   // flag + 8-byte aligned pivot floor
+    double* rv = W.res.as<double>();
+    double* g = W.g.as<double>();
+    double* alpha = W.alpha.as<double>();
+    double* alpha0 = W.z.as<double>();
+    double* norms = W.norms.as<double>();
+    int* flag = W.flag.as<int>();
+    const T* const Uc[3] = {U[0], U[1], U[2]};
+
+    // h = A^T b
+    {
+        const int grid = grid_for(m, 256);
+        to_double_kernel<T><<<grid, 256, 0, s>>>(bvec, rv, m);
+        FST_CHECK_LAUNCH();
+    }
+    FST_TRY(launch_atr<T>(M, Uc, rv, m, g, s));
+
+    // 3-4. Gram and Cholesky in the working precision (or FP64 when asked / on failure)
+    bool use64 = fp64 || force64;
+    void* Lp = nullptr;
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        FST_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), s));
+        if (!use64) {
+            FST_TRY(W.G.ensure(sizeof(float) * (size_t)R * R));
+            float* G = W.G.as<float>();
+            if (prec == FST_FP32) {
+                FST_TRY(launch_gram_simt<float>(M, reinterpret_cast<const float* const*>(Uc), m, G, s));
+            } else {
+                FST_TRY(gram_tc_launch(M, reinterpret_cast<const float*>(Uc[0]),
+                                       reinterpret_cast<const float*>(Uc[1]),
+                                       reinterpret_cast<const float*>(Uc[2]), m, G, prec, s));
+            }
+            r.ms_gram += tm.stop();
+            FST_TRY(cholesky_lower<float>(G, R, flag, s));
+            Lp = G;
+        } else {
+            FST_TRY(W.G64.ensure(sizeof(double) * (size_t)R * R));
+            double* G = W.G64.as<double>();
+            const double* U64[3];
+            if (fp64) {
+                for (int k = 0; k < 3; ++k) U64[k] = reinterpret_cast<const double*>(Uc[k]);
+            } else {
+                // promote the working-precision factor values
+                FST_TRY(W.delta.ensure(sizeof(double) * (size_t)m * (M->r[0] + M->r[1] + M->r[2])));
+                double* base = W.delta.as<double>();
+                for (int k = 0; k < 3; ++k) {
+                    const int64_t n = m * M->r[k];
+                    to_double_kernel<T><<<grid_for(n, 256), 256, 0, s>>>(Uc[k], base, n);
+                    FST_CHECK_LAUNCH();
+                    U64[k] = base;
+                    base += n;
+                }
+            }
+            FST_TRY(launch_gram_simt<double>(M, U64, m, G, s));
+            r.ms_gram += tm.stop();
+            FST_TRY(cholesky_lower<double>(G, R, flag, s));
+            Lp = G;
+        }
+        int hflag = 0;
+        FST_CUDA(cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+        FST_CUDA(cudaStreamSynchronize(s));
+        r.ms_cholesky += tm.stop();
+        if (!hflag) break;
+        if (use64) {
+            set_error("normal matrix is not positive definite in FP64 (rank-deficient sample)");
+            if (rep) *rep = r;
+            return FST_ENOTSPD;
+        }
+        use64 = true;
+        r.fallback_fp64 = 1;
+    }
+
+    auto solve = [&](double* x) -> fst_status {
+        if (use64) return chol_solve<double>(static_cast<const double*>(Lp), R, x, s);
+        return chol_solve<float>(static_cast<const float*>(Lp), R, x, s);
+    };
+    // alpha_0 = G^-1 h
+    FST_CUDA(cudaMemcpyAsync(alpha, g, sizeof(double) * R, cudaMemcpyDeviceToDevice, s));
+    FST_TRY(solve(alpha));
+    FST_CUDA(cudaMemcpyAsync(alpha0, alpha, sizeof(double) * R, cudaMemcpyDeviceToDevice, s));
+
+    // 5. refinement
+    double last = 0.0, hn[2] = {0, 0};
+    int steps = 0;
+    bool converged = max_refine <= 0;
+    for (int it = 0; it < max_refine; ++it) {
+        FST_TRY(launch_residual<T>(M, Uc, bvec, alpha, m, rv, s));
+        FST_TRY(launch_atr<T>(M, Uc, rv, m, g, s));
+        FST_TRY(solve(g));
+        FST_CUDA(cudaMemsetAsync(norms, 0, 2 * sizeof(double), s));
+        axpy_norms_kernel<<<grid_for(R, 256, 2), 256, 0, s>>>(alpha, g, R, norms);
+        FST_CHECK_LAUNCH();
+        FST_CUDA(cudaMemcpyAsync(hn, norms, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+        FST_CUDA(cudaStreamSynchronize(s));
+        ++steps;
+        last = hn[1] > 0 ? sqrt(hn[0] / hn[1]) : 0.0;
+        if (!isfinite(last)) break;
+        if (last <= tol) {
+            converged = true;
+            break;
+        }
+    }
+    r.ms_refine = tm.stop();
+    r.refine_steps = steps;
+    r.last_rel_update = last;
+    if (!converged && max_refine > 0 && !(last < 1e-6)) {
+        if (!use64 && !fp64) {
+            // the working-precision factor is too weak a preconditioner: redo in FP64
+            fst_refit_opts o = opts ? *opts : fst_refit_opts{8, 0.0, 0};
+            o.fp64_cholesky = 1;
+            fst_refit_report r2;
+            fst_status st = refit_impl<T>(M, xyz, u, Q, idx, m, seed, prec, &o, &r2, s);
+            r2.fallback_fp64 = 1;
+            r2.ms_sample += r.ms_sample;
+            if (rep) *rep = r2;
+            return st;
+        }
+        set_error("refinement did not converge (last relative update %.3e)", last);
+        if (rep) *rep = r;
+        return FST_ENOTCONV;
+    }
+    // first_rel_change and the new core
+    std::vector<double> ha(R), h0(R);
+    FST_CUDA(cudaMemcpyAsync(ha.data(), alpha, sizeof(double) * R, cudaMemcpyDeviceToHost, s));
+    FST_CUDA(cudaMemcpyAsync(h0.data(), alpha0, sizeof(double) * R, cudaMemcpyDeviceToHost, s));
+    FST_CUDA(cudaStreamSynchronize(s));
+    double dn = 0, an = 0;
+    for (int i = 0; i < R; ++i) {
+        dn += (ha[i] - h0[i]) * (ha[i] - h0[i]);
+        an += ha[i] * ha[i];
+    }
+    r.first_rel_change = an > 0 ? sqrt(dn / an) : 0.0;
+    for (int i = 0; i < R; ++i)
+        if (!isfinite(ha[i])) {
+            set_error("refit produced a non-finite core");
+            if (rep) *rep = r;
+            return FST_ENOTSPD;
+        }
+    M->alpha = ha;
+    FST_TRY(model_upload_core(M));
+    if (rep) *rep = r;
+    return FST_OK;
+}
+
+template <typename T>
+static fst_status refit_entry(fst_model* M, const T* xyz, const T* u, int64_t Q, const int64_t* idx, int64_t m,
+                              uint64_t seed, fst_prec prec, const fst_refit_opts* opts, fst_refit_report* rep,
+                              cudaStream_t s) {
+    FST_REQUIRE(M != nullptr, "model is NULL");
+    FST_REQUIRE(Q > 0 && m > 0, "Q and m must be positive");
+    FST_REQUIRE(xyz && u, "xyz or u is NULL");
+    if (m > Q) m = Q;
+    FST_REQUIRE(m <= (int64_t)1 << 31, "m too large");
+    if (m < (int64_t)M->R()) {
+        set_error("m = %lld sampled rows < R = %d unknowns", (long long)m, M->R());
+        return FST_ERANK;
+    }
+    int dev = 0;
+    FST_CUDA(cudaGetDevice(&dev));
+    FST_REQUIRE(dev == M->device, "model lives on device %d, current device is %d", M->device, dev);
+    FST_REQUIRE(pointer_device(xyz) == dev && pointer_device(u) == dev, "xyz and u must be device memory");
+    FST_REQUIRE(!idx || pointer_device(idx) == dev, "idx must be device memory");
+    std::lock_guard<std::mutex> lk(M->mu);
+    return refit_impl<T>(M, xyz, u, Q, idx, m, seed, prec, opts, rep, s);
+}
+
+}  // namespace fst
+
+using namespace fst;
+
+extern "C" fst_status fst_refit(fst_model* model, const float* xyz, const float* u, int64_t Q, const int64_t* idx,
+                                int64_t m, uint64_t seed, fst_prec prec, const fst_refit_opts* opts,
+                                fst_refit_report* report, fst_stream stream) {
+    FST_REQUIRE(prec == FST_FP32 || prec == FST_TF32 || prec == FST_BF16 || prec == FST_BF16X3,
+                "fst_refit takes FP32/TF32/BF16/BF16X3; use fst_refit_f64 for FP64");
+    return refit_entry<float>(model, xyz, u, Q, idx, m, seed, prec, opts, report, (cudaStream_t)stream);
+}
+
+extern "C" fst_status fst_refit_f64(fst_model* model, const double* xyz, const double* u, int64_t Q,
+                                    const int64_t* idx, int64_t m, uint64_t seed, const fst_refit_opts* opts,
+                                    fst_refit_report* report, fst_stream stream) {
+    return refit_entry<double>(model, xyz, u, Q, idx, m, seed, FST_FP64, opts, report, (cudaStream_t)stream);
+}

@@ -1,0 +1,238 @@
+"""ctypes binding of libfst (include/fst.h): argument marshalling only.
+
+Every step of evaluation, sampling and refit runs in libfst's CUDA kernels; this
+module converts Python objects to the C ABI's plain pointers and sizes.  PyTorch
+provides device memory and streams.  Importing this module loads the in-tree
+``libfst.so`` and raises if it has not been built (there is no CPU fallback).
+"""
+from __future__ import annotations
+
+import ctypes as C
+from pathlib import Path
+
+import numpy as np
+
+_PKG = Path(__file__).resolve().parent
+LIB_PATH = _PKG / "libfst.so"
+
+FST_FP64, FST_FP32, FST_TF32, FST_BF16, FST_BF16X3 = 0, 1, 2, 3, 4
+PREC = {"fp64": FST_FP64, "fp32": FST_FP32, "tf32": FST_TF32, "bf16": FST_BF16, "bf16x3": FST_BF16X3}
+STATUS = {0: "FST_OK", -1: "FST_EINVAL", -2: "FST_ENOMEM", -3: "FST_ECUDA", -4: "FST_ENOTSPD",
+          -5: "FST_ERANK", -6: "FST_ETIMEOUT", -7: "FST_EFORMAT", -8: "FST_ENOTCONV",
+          -9: "FST_EUNSUPPORTED"}
+
+
+class FstError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class ModelDesc(C.Structure):
+    _fields_ = [
+        ("r", C.c_int32 * 3), ("p", C.c_int32 * 3),
+        ("lo", C.c_double * 3), ("hi", C.c_double * 3),
+        ("colptr", C.c_void_p * 3), ("rowidx", C.c_void_p * 3), ("val", C.c_void_p * 3),
+        ("alpha", C.c_void_p),
+    ]
+
+
+class RefitOpts(C.Structure):
+    _fields_ = [("max_refine", C.c_int32), ("refine_tol", C.c_double), ("fp64_cholesky", C.c_int32)]
+
+
+class RefitReport(C.Structure):
+    _fields_ = [("m", C.c_int64), ("refine_steps", C.c_int32), ("fallback_fp64", C.c_int32),
+                ("first_rel_change", C.c_double), ("last_rel_update", C.c_double),
+                ("ms_sample", C.c_double), ("ms_factors", C.c_double), ("ms_gram", C.c_double),
+                ("ms_cholesky", C.c_double), ("ms_refine", C.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+def _load():
+    if not LIB_PATH.exists():
+        raise ImportError(f"{LIB_PATH} is missing: build it with paper_1907_05884_gb300.build.build() "
+                          "(libfst has no CPU fallback)")
+    L = C.CDLL(str(LIB_PATH))
+    P, I32, I64, U64 = C.c_void_p, C.c_int32, C.c_int64, C.c_uint64
+    sig = {
+        "fst_model_create": (I32, [P, P]),
+        "fst_model_free": (None, [P]),
+        "fst_model_shape": (I32, [P, P, P, P]),
+        "fst_model_read": (I32, [P, P, P, P, P, P, P]),
+        "fst_model_set_core": (I32, [P, P]),
+        "fst_model_save": (I32, [P, C.c_char_p]),
+        "fst_model_load": (I32, [C.c_char_p, P]),
+        "fst_eval": (I32, [P, P, I64, P, I32, P]),
+        "fst_eval_f64": (I32, [P, P, I64, P, P]),
+        "fst_sample_rows": (I32, [U64, I64, I64, P, P]),
+        "fst_refit": (I32, [P, P, P, I64, P, I64, U64, I32, P, P, P]),
+        "fst_refit_f64": (I32, [P, P, P, I64, P, I64, U64, P, P, P]),
+        "fst_status_str": (C.c_char_p, [I32]),
+        "fst_last_error": (C.c_char_p, []),
+        "fst_build_info": (C.c_char_p, []),
+        "fst_kernel_launches": (U64, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    return L
+
+
+lib = _load()
+
+
+def _check(st: int):
+    if st != 0:
+        raise FstError(st, lib.fst_last_error().decode(errors="replace"))
+
+
+def _stream(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _dptr(t) -> C.c_void_p:
+    return C.c_void_p(t.data_ptr())
+
+
+class Model:
+    """A device-resident FST model owned by libfst."""
+
+    def __init__(self, host_model=None, _handle=None):
+        self._h = C.c_void_p()
+        if _handle is not None:
+            self._h = _handle
+            return
+        m = host_model
+        d = ModelDesc()
+        keep = []
+        for k in range(3):
+            d.r[k] = int(m.r[k])
+            d.p[k] = int(m.p[k])
+            d.lo[k] = float(m.lo[k])
+            d.hi[k] = float(m.hi[k])
+            cp = np.ascontiguousarray(m.colptr[k], dtype=np.int32)
+            ri = np.ascontiguousarray(m.rowidx[k], dtype=np.int32)
+            vv = np.ascontiguousarray(m.val[k], dtype=np.float64)
+            if ri.size == 0:
+                ri, vv = np.zeros(1, np.int32), np.zeros(1)
+            keep += [cp, ri, vv]
+            d.colptr[k], d.rowidx[k], d.val[k] = cp.ctypes.data, ri.ctypes.data, vv.ctypes.data
+        al = np.ascontiguousarray(np.asarray(m.alpha, dtype=np.float64).reshape(-1))
+        keep.append(al)
+        d.alpha = al.ctypes.data
+        _check(lib.fst_model_create(C.byref(d), C.byref(self._h)))
+
+    @classmethod
+    def load(cls, path: str) -> "Model":
+        h = C.c_void_p()
+        _check(lib.fst_model_load(str(path).encode(), C.byref(h)))
+        return cls(_handle=h)
+
+    def save(self, path: str):
+        _check(lib.fst_model_save(self._h, str(path).encode()))
+
+    def free(self):
+        if self._h:
+            lib.fst_model_free(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    def shape(self):
+        r, p, nnz = (C.c_int32 * 3)(), (C.c_int32 * 3)(), (C.c_int32 * 3)()
+        _check(lib.fst_model_shape(self._h, r, p, nnz))
+        return tuple(r), tuple(p), tuple(nnz)
+
+    def read(self):
+        """Host copy: dict with colptr, rowidx, val (lists per mode), alpha (r1,r2,r3), lo, hi."""
+        r, p, nnz = self.shape()
+        cps = [np.empty(r[k] + 1, np.int32) for k in range(3)]
+        ris = [np.empty(max(nnz[k], 1), np.int32) for k in range(3)]
+        vvs = [np.empty(max(nnz[k], 1), np.float64) for k in range(3)]
+        al = np.empty(r[0] * r[1] * r[2])
+        lo, hi = np.empty(3), np.empty(3)
+        arr = lambda xs: (C.c_void_p * 3)(*[x.ctypes.data for x in xs])
+        _check(lib.fst_model_read(self._h, arr(cps), arr(ris), arr(vvs), al.ctypes.data,
+                                  lo.ctypes.data, hi.ctypes.data))
+        return {"r": r, "p": p, "colptr": cps, "rowidx": [ris[k][:nnz[k]] for k in range(3)],
+                "val": [vvs[k][:nnz[k]] for k in range(3)], "alpha": al.reshape(r), "lo": lo, "hi": hi}
+
+    def set_core(self, alpha):
+        al = np.ascontiguousarray(np.asarray(alpha, dtype=np.float64).reshape(-1))
+        _check(lib.fst_model_set_core(self._h, al.ctypes.data))
+
+    # ---------------------------------------------------------------- evaluation
+    def eval(self, xyz, prec: str = "fp32", out=None, stream=None):
+        """xyz: CUDA tensor (3, n) float32 (SoA); returns a CUDA float32 tensor (n,)."""
+        import torch
+        assert xyz.is_cuda and xyz.dtype == torch.float32 and xyz.is_contiguous() and xyz.shape[0] == 3
+        n = xyz.shape[1]
+        if out is None:
+            out = torch.empty(n, dtype=torch.float32, device=xyz.device)
+        _check(lib.fst_eval(self._h, _dptr(xyz), n, _dptr(out), PREC[prec], _stream(stream)))
+        return out
+
+    def eval_f64(self, xyz, out=None, stream=None):
+        import torch
+        assert xyz.is_cuda and xyz.dtype == torch.float64 and xyz.is_contiguous() and xyz.shape[0] == 3
+        n = xyz.shape[1]
+        if out is None:
+            out = torch.empty(n, dtype=torch.float64, device=xyz.device)
+        _check(lib.fst_eval_f64(self._h, _dptr(xyz), n, _dptr(out), _stream(stream)))
+        return out
+
+    # ---------------------------------------------------------------- refit
+    def refit(self, xyz, u, m: int, seed: int = 0, prec: str = "fp32", idx=None,
+              max_refine: int = 8, refine_tol: float = 0.0, fp64_cholesky: bool = False, stream=None):
+        """Least-squares core refit over m sampled rows (or the rows in ``idx``).  xyz (3,Q) and u (Q,)
+        are CUDA tensors, float32 (or float64 with prec='fp64').  Returns the report as a dict."""
+        import torch
+        Q = xyz.shape[1]
+        opts = RefitOpts(int(max_refine), float(refine_tol), int(bool(fp64_cholesky)))
+        rep = RefitReport()
+        ip = C.c_void_p(0) if idx is None else _dptr(idx)
+        if idx is not None:
+            assert idx.is_cuda and idx.dtype == torch.int64
+            m = idx.numel()
+        if prec == "fp64":
+            assert xyz.dtype == torch.float64 and u.dtype == torch.float64
+            _check(lib.fst_refit_f64(self._h, _dptr(xyz), _dptr(u), Q, ip, int(m),
+                                     C.c_uint64(seed & 0xFFFFFFFFFFFFFFFF), C.byref(opts), C.byref(rep),
+                                     _stream(stream)))
+        else:
+            assert xyz.dtype == torch.float32 and u.dtype == torch.float32
+            _check(lib.fst_refit(self._h, _dptr(xyz), _dptr(u), Q, ip, int(m),
+                                 C.c_uint64(seed & 0xFFFFFFFFFFFFFFFF), PREC[prec], C.byref(opts),
+                                 C.byref(rep), _stream(stream)))
+        return rep.as_dict()
+
+
+def sample_rows(seed: int, Q: int, m: int, device="cuda", stream=None):
+    import torch
+    m = min(int(m), int(Q))
+    idx = torch.empty(m, dtype=torch.int64, device=device)
+    _check(lib.fst_sample_rows(C.c_uint64(seed & 0xFFFFFFFFFFFFFFFF), int(Q), m, _dptr(idx),
+                               _stream(stream)))
+    return idx
+
+
+def kernel_launches() -> int:
+    return int(lib.fst_kernel_launches())
+
+
+def build_info() -> str:
+    return lib.fst_build_info().decode()

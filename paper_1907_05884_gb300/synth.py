@@ -145,7 +145,7 @@ class Model:
 
 
 def random_model(r, p, seed: int, density: float = 0.6, decay: float = 1.0,
-                 lo=None, hi=None) -> Model:
+                 lo=None, hi=None, orthonormal: bool = False) -> Model:
     """A random model with ranks ``r`` and maximum degrees ``p``.
 
     Column j of mode k keeps max(1, round(density*(p_k+1))) randomly chosen
@@ -153,6 +153,10 @@ def random_model(r, p, seed: int, density: float = 0.6, decay: float = 1.0,
     are smooth); its coefficients are normal, scaled to unit 2-norm.  Core
     entries are normal with magnitude decaying like 1/(1+j1+j2+j3)^decay, the
     way a Tucker core sorted by singular value decays (Fig. 1).
+
+    With ``orthonormal`` the coefficient columns of each mode are instead the
+    first r_k columns of a random orthogonal matrix (all degrees stored), so the
+    factor functions are orthonormal on [-1,1] like fitted singular vectors.
     """
     r = tuple(int(v) for v in r)
     p = tuple(int(v) for v in (p if np.ndim(p) else (p, p, p)))
@@ -160,6 +164,14 @@ def random_model(r, p, seed: int, density: float = 0.6, decay: float = 1.0,
     colptr, rowidx, val = [], [], []
     for k in range(3):
         n = p[k] + 1
+        if orthonormal:
+            if r[k] > n:
+                raise ValueError("orthonormal factors need r_k <= p_k + 1")
+            Qm = np.linalg.qr(rng.normal(size=(n, n)))[0][:, :r[k]]
+            colptr.append(np.arange(0, n * r[k] + 1, n, dtype=np.int32))
+            rowidx.append(np.tile(np.arange(n, dtype=np.int32), r[k]))
+            val.append(np.ascontiguousarray(Qm.T).reshape(-1))
+            continue
         keep = max(1, min(n, int(round(density * n))))
         cp, ri, vv = [0], [], []
         for j in range(r[k]):
