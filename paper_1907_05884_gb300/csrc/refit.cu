@@ -181,17 +181,24 @@ __global__ void __launch_bounds__(256) atr_kernel(const T* __restrict__ U1, cons
     }
 }
 
-// r_s = b_s - sum_i w1_i sum_j w2_j sum_k alpha_ijk w3_k (inner sum in T, outer sums in FP64).
+// r_s = b_s - sum_i w1_i sum_j w2_j sum_k alpha_ijk w3_k.  The inner sum over k runs in T;
+// for T = float alpha is split into alpha_hi + alpha_lo (both FP32) so the core itself
+// carries FP64 accuracy into the residual; the sums over j and i run in FP64.
 template <typename T, int R3M>
 __global__ void __launch_bounds__(128) residual_kernel(const T* __restrict__ U1, const T* __restrict__ U2,
                                                        const T* __restrict__ U3, const T* __restrict__ bvec,
                                                        const double* __restrict__ alpha, int64_t m, int r1,
                                                        int r2, int r3, double* rv) {
+    constexpr bool kSplit = sizeof(T) == 4;
     extern __shared__ __align__(16) unsigned char smem[];
-    T* As = reinterpret_cast<T*>(smem);   // [r1*r2][R3M]
+    T* As = reinterpret_cast<T*>(smem);        // [r1*r2][R3M]
+    T* Al = As + r1 * r2 * R3M;                // low parts (FP32 only)
     for (int e = threadIdx.x; e < r1 * r2 * R3M; e += blockDim.x) {
         const int ij = e / R3M, k = e - ij * R3M;
-        As[e] = k < r3 ? (T)alpha[ij * r3 + k] : T(0);
+        const double a = k < r3 ? alpha[ij * r3 + k] : 0.0;
+        const T hi = (T)a;
+        As[e] = hi;
+        if (kSplit) Al[e] = (T)(a - (double)hi);
     }
     __syncthreads();
     for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < m; s += (int64_t)gridDim.x * blockDim.x) {
@@ -213,7 +220,22 @@ __global__ void __launch_bounds__(128) residual_kernel(const T* __restrict__ U1,
                     t0 = fma(a2, w3[k + 2], t0);
                     t1 = fma(a3, w3[k + 3], t1);
                 }
-                si = fma((double)(t0 + t1), (double)U2[s * r2 + j], si);
+                double t = (double)t0 + (double)t1;
+                if (kSplit) {
+                    const T* lrow = Al + (i * r2 + j) * R3M;
+                    T l0 = T(0), l1 = T(0);
+#pragma unroll
+                    for (int k = 0; k < R3M; k += 4) {
+                        T a0, a1, a2, a3;
+                        load4(lrow + k, a0, a1, a2, a3);
+                        l0 = fma(a0, w3[k], l0);
+                        l1 = fma(a1, w3[k + 1], l1);
+                        l0 = fma(a2, w3[k + 2], l0);
+                        l1 = fma(a3, w3[k + 3], l1);
+                    }
+                    t += (double)l0 + (double)l1;
+                }
+                si = fma(t, (double)U2[s * r2 + j], si);
             }
             f = fma(si, (double)U1[s * r1 + i], f);
         }
@@ -318,7 +340,7 @@ static fst_status launch_residual(const fst_model* M, const T* const U[3], const
                                   int64_t m, double* rv, cudaStream_t s) {
     const int r1 = M->r[0], r2 = M->r[1], r3 = M->r[2];
     const int R3M = r3 <= 8 ? 8 : r3 <= 16 ? 16 : r3 <= 24 ? 24 : 32;
-    const size_t smem = (size_t)r1 * r2 * R3M * sizeof(T);
+    const size_t smem = (size_t)r1 * r2 * R3M * sizeof(T) * (sizeof(T) == 4 ? 2 : 1);
     const int grid = grid_for(m, 128, 4);
 #define FST_RES(V)                                                                                          \
     {                                                                                                       \
@@ -464,7 +486,10 @@ static fst_status refit_impl(fst_model* M, const T* xyz, const T* u, int64_t Q, 
     FST_CUDA(cudaMemcpyAsync(alpha0, alpha, sizeof(double) * R, cudaMemcpyDeviceToDevice, s));
 
     // 5. refinement
-    double last = 0.0, hn[2] = {0, 0};
+    // Stop at tol, or when the update stops shrinking (the rounding floor of the working
+    // precision); a floor above `floor_ok` means the preconditioner is too weak.
+    const double floor_ok = fp64 ? 1e-10 : 1e-5;
+    double last = 0.0, prev = 0.0, hn[2] = {0, 0};
     int steps = 0;
     bool converged = max_refine <= 0;
     for (int it = 0; it < max_refine; ++it) {
@@ -477,17 +502,19 @@ static fst_status refit_impl(fst_model* M, const T* xyz, const T* u, int64_t Q, 
         FST_CUDA(cudaMemcpyAsync(hn, norms, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
         FST_CUDA(cudaStreamSynchronize(s));
         ++steps;
+        prev = last;
         last = hn[1] > 0 ? sqrt(hn[0] / hn[1]) : 0.0;
         if (!isfinite(last)) break;
-        if (last <= tol) {
+        if (last <= tol || (it >= 2 && last > 0.5 * prev && last <= floor_ok)) {
             converged = true;
             break;
         }
     }
+    if (!converged && isfinite(last) && last <= floor_ok) converged = true;
     r.ms_refine = tm.stop();
     r.refine_steps = steps;
     r.last_rel_update = last;
-    if (!converged && max_refine > 0 && !(last < 1e-6)) {
+    if (!converged && max_refine > 0) {
         if (!use64 && !fp64) {
             // the working-precision factor is too weak a preconditioner: redo in FP64
             fst_refit_opts o = opts ? *opts : fst_refit_opts{8, 0.0, 0};
