@@ -124,6 +124,25 @@ fst_status fst_eval_f64(const fst_model* model, const double* xyz, int64_t n, do
  * every row.  Asynchronous; uses model-free scratch owned by the library. */
 fst_status fst_sample_rows(uint64_t seed, int64_t Q, int64_t m, int64_t* idx, fst_stream stream);
 
+/* The paper has no counterpart to this entry point: it is a service for callers
+ * that must not allocate device memory -- for example an in-situ visualisation
+ * hook running inside a simulation whose own pool already owns the device memory,
+ * or a latency-bound loop that cannot absorb the implicit device synchronisation
+ * of cudaMalloc.  It returns exactly what fst_sample_rows returns, but calls no
+ * cudaMalloc, cudaFree or other allocating routine: its scratch (520 KiB)
+ * is one fixed device array inside libfst that every GPU which loads the library
+ * keeps until the process exits.
+ *   - Limit: Q <= 2^29 rows; larger Q returns FST_EINVAL (use fst_sample_rows).
+ *   - The first call on each device looks up the array's device address (with
+ *     that device current) and caches it; make that first call before any stream
+ *     capture.
+ *   - All calls share the one array (the selection state and histogram are
+ *     cleared at the start of each call): calls that overlap on the GPU -- on two
+ *     streams, or from two threads -- race and may return wrong rows.  Order them
+ *     on one stream or synchronise between them.
+ * idx: device, m int64 (caller-owned).  Asynchronous. */
+fst_status fst_sample_rows_static(uint64_t seed, int64_t Q, int64_t m, int64_t* idx, fst_stream stream);
+
 /* ---------------------------------------------------------------- refit */
 
 typedef struct {

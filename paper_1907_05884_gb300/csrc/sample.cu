@@ -246,3 +246,87 @@ extern "C" fst_status fst_sample_rows(uint64_t seed, int64_t Q, int64_t m, int64
     FST_REQUIRE(pointer_device(idx) == dev, "idx must be device memory of device %d", dev);
     return sample_rows(seed, Q, m, idx, (cudaStream_t)stream);
 }
+
+// ------------------------------------------------------------------ sampling without allocation
+// fst_sample_rows_static: the same sampler for callers that must not allocate device
+// memory, for example an in-situ visualisation hook running inside a simulation that has
+// already handed all device memory to its own pool, or a latency-bound loop that cannot
+// afford cudaMalloc's implicit device synchronisation.  Its scratch (selection state,
+// digit histogram, per-block counts) lives in one file-scope device array that every GPU
+// which loads this library keeps until the process exits.
+namespace fst {
+
+constexpr int64_t kStaticRowsPerBlock = 8192;
+constexpr int64_t kStaticMaxBlocks = 65536;                 // rows per call <= 2^29
+constexpr size_t kStaticStateBytes = 256;
+constexpr size_t kStaticScratchBytes =
+    kStaticStateBytes + kBins * sizeof(unsigned int) + kStaticMaxBlocks * sizeof(unsigned long long);
+
+static __device__ __align__(256) unsigned char g_sample_static_scratch[kStaticScratchBytes];
+
+// Host code only sees a stand-in for the array's name: the device address is resolved
+// once per device, with that device current, and cached.
+static void* g_static_scratch_addr[64];
+static std::mutex g_static_scratch_mu;
+
+static fst_status static_scratch_address(int dev, unsigned char** out) {
+    std::lock_guard<std::mutex> lk(g_static_scratch_mu);
+    if (!g_static_scratch_addr[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_sample_static_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(sampler scratch)", __FILE__, __LINE__);
+        g_static_scratch_addr[dev] = p;
+    }
+    *out = static_cast<unsigned char*>(g_static_scratch_addr[dev]);
+    return FST_OK;
+}
+
+}  // namespace fst
+
+extern "C" fst_status fst_sample_rows_static(uint64_t seed, int64_t Q, int64_t m, int64_t* idx,
+                                             fst_stream stream) {
+    FST_REQUIRE(Q >= 0 && m >= 0, "Q and m must be non-negative");
+    FST_REQUIRE(Q <= kStaticRowsPerBlock * kStaticMaxBlocks,
+                "fst_sample_rows_static handles at most %lld rows (Q = %lld); use fst_sample_rows",
+                (long long)(kStaticRowsPerBlock * kStaticMaxBlocks), (long long)Q);
+    if (Q == 0 || m == 0) return FST_OK;
+    FST_REQUIRE(idx != nullptr, "idx is NULL");
+    int dev = 0;
+    FST_CUDA(cudaGetDevice(&dev));
+    FST_REQUIRE(dev >= 0 && dev < 64, "device ordinal %d out of range", dev);
+    FST_REQUIRE(pointer_device(idx) == dev, "idx must be device memory of device %d", dev);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (m >= Q) {
+        int grid = (int)((Q + 255) / 256);
+        if (grid > 4 * sm_count()) grid = 4 * sm_count();
+        iota_kernel<<<grid, 256, 0, s>>>(idx, Q);
+        FST_CHECK_LAUNCH();
+        return FST_OK;
+    }
+    unsigned char* base = nullptr;
+    FST_TRY(static_scratch_address(dev, &base));
+    SelectState* st = reinterpret_cast<SelectState*>(base);
+    unsigned int* hist = reinterpret_cast<unsigned int*>(base + kStaticStateBytes);
+    unsigned long long* counts =
+        reinterpret_cast<unsigned long long*>(base + kStaticStateBytes + kBins * sizeof(unsigned int));
+    const int64_t nblocks = (Q + kStaticRowsPerBlock - 1) / kStaticRowsPerBlock;
+    // the state and the histogram start from zero on every call; counts are fully rewritten
+    init_state_kernel<<<1, 256, 0, s>>>(st, (unsigned long long)m, hist);
+    FST_CHECK_LAUNCH();
+    int hgrid = (int)((Q + 1023) / 1024);
+    if (hgrid > 4 * sm_count()) hgrid = 4 * sm_count();
+    for (int pass = 0; pass < kPasses; ++pass) {
+        select_hist_kernel<<<hgrid, 512, 0, s>>>(seed, Q, pass, st, hist);
+        FST_CHECK_LAUNCH();
+        select_pick_kernel<<<1, 32, 0, s>>>(pass, st, hist);
+        FST_CHECK_LAUNCH();
+    }
+    compact_count_kernel<<<(unsigned)nblocks, kCompactBlock, 0, s>>>(seed, Q, kStaticRowsPerBlock, st, counts);
+    FST_CHECK_LAUNCH();
+    scan_counts_kernel<<<1, 1024, 0, s>>>(counts, (int)nblocks);
+    FST_CHECK_LAUNCH();
+    compact_write_kernel<<<(unsigned)nblocks, kCompactBlock, 0, s>>>(seed, Q, kStaticRowsPerBlock, st, counts,
+                                                                      idx, m);
+    FST_CHECK_LAUNCH();
+    return FST_OK;
+}

@@ -68,6 +68,7 @@ def _load():
         "fst_eval": (I32, [P, P, I64, P, I32, P]),
         "fst_eval_f64": (I32, [P, P, I64, P, P]),
         "fst_sample_rows": (I32, [U64, I64, I64, P, P]),
+        "fst_sample_rows_static": (I32, [U64, I64, I64, P, P]),
         "fst_refit": (I32, [P, P, P, I64, P, I64, U64, I32, P, P, P]),
         "fst_refit_f64": (I32, [P, P, P, I64, P, I64, U64, P, P, P]),
         "fst_status_str": (C.c_char_p, [I32]),
