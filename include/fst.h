@@ -146,7 +146,7 @@ fst_status fst_sample_rows_static(uint64_t seed, int64_t Q, int64_t m, int64_t* 
 /* ---------------------------------------------------------------- refit */
 
 typedef struct {
-    int32_t max_refine;       /* refinement steps after the first solve (default 8) */
+    int32_t max_refine;       /* refinement (preconditioned CG) steps after the first solve (default 32) */
     double refine_tol;        /* stop when ||delta|| <= tol ||alpha|| (default 1e-12 FP64, 1e-9 else) */
     int32_t fp64_cholesky;    /* 1: factor the normal matrix in FP64 (default: FP64 only for FST_FP64) */
 } fst_refit_opts;
@@ -165,7 +165,8 @@ typedef struct {
  * without the sign-flip/mixing steps): draws idx with fst_sample_rows(seed),
  * forms the normal equations G = A^T A, h = A^T b over the Khatri-Rao rows
  * a_q = w1(y1_q) (x) w2(y2_q) (x) w3(y3_q) in `prec`, factors G by Cholesky and
- * refines alpha += G^-1 A^T (b - A alpha) with the residual accumulated in FP64.
+ * refines alpha by conjugate gradients on the normal equations preconditioned by
+ * that factor, with A p and A^T q accumulated in FP64.
  * xyz (3Q floats SoA), u (Q floats): device.  idx: device int64 rows to use, or
  * NULL to draw m rows with `seed`.  opts, report: host, may be NULL.  On success
  * the model's core is replaced.  Synchronous (returns host status).
@@ -173,6 +174,16 @@ typedef struct {
 fst_status fst_refit(fst_model* model, const float* xyz, const float* u, int64_t Q,
                      const int64_t* idx, int64_t m, uint64_t seed, fst_prec prec,
                      const fst_refit_opts* opts, fst_refit_report* report, fst_stream stream);
+
+/* The normal equations of the sampled problem alone (eq. rand_core restricted to the
+ * rows idx): G = A^T A (device, R x R FP32 row-major; the lower triangle is written,
+ * the upper triangle is unspecified) with A_{s,(i,j,k)} = w1_i w2_j w3_k at the points
+ * of rows idx (device, m int64), assembled in `prec` (FP32 on CUDA cores; TF32, BF16,
+ * BF16X3 on tensor cores with FP32 accumulation), and, if h is not NULL, h = A^T b
+ * (device, R doubles) with b = u[idx].  Synchronous for tensor-core precisions. */
+fst_status fst_normal_matrix(const fst_model* model, const float* xyz, const float* u, int64_t Q,
+                             const int64_t* idx, int64_t m, fst_prec prec, float* G, double* h,
+                             fst_stream stream);
 
 /* FP64 refit (xyz 3Q doubles, u Q doubles; FP64 Gram, FP64 Cholesky). */
 fst_status fst_refit_f64(fst_model* model, const double* xyz, const double* u, int64_t Q,

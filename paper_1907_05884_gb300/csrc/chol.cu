@@ -182,91 +182,120 @@ fst_status cholesky_lower(T* G, int R, int* d_flag, cudaStream_t s) {
 }
 
 // ------------------------------------------------------------------ triangular solves
-// Forward: x_b <- L_bb^-1 x_b (one warp), then x_i -= L_ib x_b for rows i below (warp per row).
+// Linv[b] = L_bb^-1 for every 64 x 64 diagonal block (computed once per factorisation):
+// thread c solves L_bb X = e_c by forward substitution for column c of the inverse.
 template <typename T>
-__global__ void fwd_diag_kernel(const T* L, int R, int k0, int kb, double* x) {
-    __shared__ double xs[NB];
-    const int lane = threadIdx.x;
-    for (int i = lane; i < kb; i += 32) xs[i] = x[k0 + i];
-    __syncwarp();
-    for (int r = 0; r < kb; ++r) {
-        double s = 0.0;
-        for (int c = lane; c < r; c += 32) s += (double)L[(size_t)(k0 + r) * R + k0 + c] * xs[c];
-        for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) xs[r] = (xs[r] - s) / (double)L[(size_t)(k0 + r) * R + k0 + r];
-        __syncwarp();
+__global__ void invert_diag_kernel(const T* L, int R, T* Linv) {
+    __shared__ T Ls[NB][NB + 1];
+    const int b = blockIdx.x, k0 = b * NB;
+    const int kb = R - k0 < NB ? R - k0 : NB;
+    for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+        const int i = e / NB, j = e - i * NB;
+        Ls[i][j] = (i < kb && j <= i) ? L[(size_t)(k0 + i) * R + k0 + j] : T(i == j ? 1 : 0);
     }
-    for (int i = lane; i < kb; i += 32) x[k0 + i] = xs[i];
-}
-
-template <typename T>
-__global__ void fwd_update_kernel(const T* L, int R, int k0, int kb, double* x) {
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-    const int i = k0 + kb + warp;
-    if (i >= R) return;
-    double s = 0.0;
-    for (int c = lane; c < kb; c += 32) s += (double)L[(size_t)i * R + k0 + c] * x[k0 + c];
-    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) x[i] -= s;
-}
-
-// Backward: x_b <- L_bb^-T x_b, then x_i -= sum_{c in b} L_ci x_c for rows i above (thread per i).
-template <typename T>
-__global__ void bwd_diag_kernel(const T* L, int R, int k0, int kb, double* x) {
-    __shared__ double xs[NB];
-    const int lane = threadIdx.x;
-    for (int i = lane; i < kb; i += 32) xs[i] = x[k0 + i];
-    __syncwarp();
-    for (int r = kb - 1; r >= 0; --r) {
-        double s = 0.0;
-        for (int c = r + 1 + lane; c < kb; c += 32) s += (double)L[(size_t)(k0 + c) * R + k0 + r] * xs[c];
-        for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) xs[r] = (xs[r] - s) / (double)L[(size_t)(k0 + r) * R + k0 + r];
-        __syncwarp();
-    }
-    for (int i = lane; i < kb; i += 32) x[k0 + i] = xs[i];
-}
-
-template <typename T>
-__global__ void bwd_update_kernel(const T* L, int R, int k0, int kb, double* x) {
-    __shared__ double xs[NB];
-    for (int i = threadIdx.x; i < kb; i += blockDim.x) xs[i] = x[k0 + i];
     __syncthreads();
+    T* out = Linv + (size_t)b * NB * NB;    // row-major [i][c]
+    const int c = threadIdx.x;
+    if (c < NB) {
+        T col[NB];
+#pragma unroll
+        for (int i = 0; i < NB; ++i) {
+            T s = i == c ? T(1) : T(0);
+#pragma unroll
+            for (int k = 0; k < i; ++k) s -= Ls[i][k] * col[k];
+            col[i] = i < c ? T(0) : s / Ls[i][i];
+        }
+#pragma unroll
+        for (int i = 0; i < NB; ++i) out[i * NB + c] = col[i];
+    }
+}
+
+// Forward step for diagonal block b: every block forms x_b = Linv_bb xin_b, block 0 stores it
+// in y; rows below block b (64 per block, a warp per row) subtract L_{i,b} x_b from xin.
+template <typename T>
+__global__ void __launch_bounds__(256) fwd_step_kernel(const T* L, const T* Linv, int R, int b, T* xin, T* y) {
+    __shared__ T xs[NB], xb[NB];
+    const int k0 = b * NB, kb = R - k0 < NB ? R - k0 : NB;
+    for (int i = threadIdx.x; i < NB; i += blockDim.x) xs[i] = i < kb ? xin[k0 + i] : T(0);
+    __syncthreads();
+    const T* Li = Linv + (size_t)b * NB * NB;
+    for (int i = threadIdx.x; i < NB; i += blockDim.x) {
+        T s = T(0);
+        for (int c = 0; c < NB; ++c) s += Li[i * NB + c] * xs[c];
+        xb[i] = s;
+    }
+    __syncthreads();
+    if (blockIdx.x == 0)
+        for (int i = threadIdx.x; i < kb; i += blockDim.x) y[k0 + i] = xb[i];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int r0 = k0 + kb + blockIdx.x * NB;
+    for (int rr = warp; rr < NB; rr += blockDim.x >> 5) {
+        const int i = r0 + rr;
+        if (i >= R) break;
+        T s = T(0);
+        for (int c = lane; c < kb; c += 32) s += L[(size_t)i * R + k0 + c] * xb[c];
+        for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) xin[i] -= s;
+    }
+}
+
+// Backward step for block b: x_b = Linv_bb^T yin_b stored in out; rows above subtract
+// L_{b,i}^T x_b from yin (thread per row, coalesced along i).
+template <typename T>
+__global__ void __launch_bounds__(256) bwd_step_kernel(const T* L, const T* Linv, int R, int b, T* yin, T* out) {
+    __shared__ T ys[NB], xb[NB];
+    const int k0 = b * NB, kb = R - k0 < NB ? R - k0 : NB;
+    for (int i = threadIdx.x; i < NB; i += blockDim.x) ys[i] = i < kb ? yin[k0 + i] : T(0);
+    __syncthreads();
+    const T* Li = Linv + (size_t)b * NB * NB;
+    for (int i = threadIdx.x; i < NB; i += blockDim.x) {
+        T s = T(0);
+        for (int c = 0; c < NB; ++c) s += Li[c * NB + i] * ys[c];
+        xb[i] = s;
+    }
+    __syncthreads();
+    if (blockIdx.x == 0)
+        for (int i = threadIdx.x; i < kb; i += blockDim.x) out[k0 + i] = xb[i];
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= k0) return;
-    double s = 0.0;
-    for (int c = 0; c < kb; ++c) s += (double)L[(size_t)(k0 + c) * R + i] * xs[c];
-    x[i] -= s;
+    if (i < k0) {
+        T s = T(0);
+        for (int c = 0; c < kb; ++c) s += L[(size_t)(k0 + c) * R + i] * xb[c];
+        yin[i] -= s;
+    }
 }
 
 template <typename T>
-fst_status chol_solve(const T* L, int R, double* x, cudaStream_t s) {
-    for (int k0 = 0; k0 < R; k0 += NB) {
-        const int kb = R - k0 < NB ? R - k0 : NB;
-        fwd_diag_kernel<T><<<1, 32, 0, s>>>(L, R, k0, kb, x);
+fst_status chol_invert_diag(const T* L, int R, T* Linv, cudaStream_t s) {
+    const int nblk = (R + NB - 1) / NB;
+    invert_diag_kernel<T><<<nblk, NB, 0, s>>>(L, R, Linv);
+    FST_CHECK_LAUNCH();
+    return FST_OK;
+}
+
+// x <- L^-T L^-1 x (x and y: R values of T; y is scratch).
+template <typename T>
+fst_status chol_solve(const T* L, const T* Linv, int R, T* x, T* y, cudaStream_t s) {
+    const int nblk = (R + NB - 1) / NB;
+    for (int b = 0; b < nblk; ++b) {
+        const int rest = R - (b + 1) * NB;
+        const int grid = rest > 0 ? (rest + NB - 1) / NB : 1;
+        fwd_step_kernel<T><<<grid, 256, 0, s>>>(L, Linv, R, b, x, y);
         FST_CHECK_LAUNCH();
-        const int rest = R - k0 - kb;
-        if (rest > 0) {
-            fwd_update_kernel<T><<<(rest + 7) / 8, 256, 0, s>>>(L, R, k0, kb, x);
-            FST_CHECK_LAUNCH();
-        }
     }
-    const int last = ((R - 1) / NB) * NB;
-    for (int k0 = last; k0 >= 0; k0 -= NB) {
-        const int kb = R - k0 < NB ? R - k0 : NB;
-        bwd_diag_kernel<T><<<1, 32, 0, s>>>(L, R, k0, kb, x);
+    for (int b = nblk - 1; b >= 0; --b) {
+        const int k0 = b * NB;
+        const int grid = k0 > 0 ? (k0 + 255) / 256 : 1;
+        bwd_step_kernel<T><<<grid, 256, 0, s>>>(L, Linv, R, b, y, x);
         FST_CHECK_LAUNCH();
-        if (k0 > 0) {
-            bwd_update_kernel<T><<<(k0 + 255) / 256, 256, 0, s>>>(L, R, k0, kb, x);
-            FST_CHECK_LAUNCH();
-        }
     }
     return FST_OK;
 }
 
 template fst_status cholesky_lower<float>(float*, int, int*, cudaStream_t);
 template fst_status cholesky_lower<double>(double*, int, int*, cudaStream_t);
-template fst_status chol_solve<float>(const float*, int, double*, cudaStream_t);
-template fst_status chol_solve<double>(const double*, int, double*, cudaStream_t);
+template fst_status chol_invert_diag<float>(const float*, int, float*, cudaStream_t);
+template fst_status chol_invert_diag<double>(const double*, int, double*, cudaStream_t);
+template fst_status chol_solve<float>(const float*, const float*, int, float*, float*, cudaStream_t);
+template fst_status chol_solve<double>(const double*, const double*, int, double*, double*, cudaStream_t);
 
 }  // namespace fst

@@ -59,7 +59,7 @@ struct DevBuf {
 
 // Scratch of the refit, kept inside the model between calls.
 struct RefitScratch {
-    DevBuf idx, U[3], b, G, G64, res, g, z, delta, alpha, norms, flag;
+    DevBuf idx, U[3], b, G, G64, res, g, z, delta, alpha, norms, flag, Linv, xw, yw, pcg;
 };
 
 }  // namespace fst
@@ -120,6 +120,8 @@ fst_status gram_tc_launch(const fst_model* m, const float* U1, const float* U2, 
 template <typename T>
 fst_status cholesky_lower(T* G, int R, int* d_flag, cudaStream_t s);
 template <typename T>
-fst_status chol_solve(const T* L, int R, double* x, cudaStream_t s);  // x <- (L L^T)^-1 x
+fst_status chol_invert_diag(const T* L, int R, T* Linv, cudaStream_t s);   // 64x64 diagonal blocks
+template <typename T>
+fst_status chol_solve(const T* L, const T* Linv, int R, T* x, T* y, cudaStream_t s);  // x <- (L L^T)^-1 x
 
 }  // namespace fst

@@ -108,6 +108,10 @@ static void free_device(fst_model* m) {
     s.alpha.release();
     s.norms.release();
     s.flag.release();
+    s.Linv.release();
+    s.xw.release();
+    s.yw.release();
+    s.pcg.release();
 }
 
 fst_status model_invalidate_tc(fst_model* m) {

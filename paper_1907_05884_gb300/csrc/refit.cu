@@ -23,30 +23,32 @@
 namespace fst {
 
 // ------------------------------------------------------------------ step 2
+// Factor values of the sampled rows, computed in FP64 from the stored points and rounded
+// once to the working precision T (so the Khatri-Rao rows carry no recurrence error).
 template <typename T, int RM>
-__global__ void __launch_bounds__(128) sampled_factors_kernel(const EvalArgs<T> a, const T* __restrict__ xyz,
+__global__ void __launch_bounds__(128) sampled_factors_kernel(const EvalArgs<double> a, const T* __restrict__ xyz,
                                                               int64_t Q, const int64_t* __restrict__ idx,
                                                               int64_t m, const T* __restrict__ u, T* U1, T* U2,
                                                               T* U3, T* bvec) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int B = blockDim.x, tid = threadIdx.x;
-    T* ra = reinterpret_cast<T*>(smem);
-    T* rb = ra + a.pm;
-    T* Ws[3];
+    double* ra = reinterpret_cast<double*>(smem);
+    double* rb = ra + a.pm;
+    double* Ws[3];
     Ws[0] = rb + a.pm;
     Ws[1] = Ws[0] + a.pe[0] * RM;
     Ws[2] = Ws[1] + a.pe[1] * RM;
     uint8_t* mk = reinterpret_cast<uint8_t*>(Ws[2] + a.pe[2] * RM);
     for (int i = tid; i < a.pm; i += B) {
-        ra[i] = T(2 * i + 1) / T(i + 1);
-        rb[i] = T(i) / T(i + 1);
+        ra[i] = double(2 * i + 1) / double(i + 1);
+        rb[i] = double(i) / double(i + 1);
     }
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         const int rk = a.r[k];
         for (int e = tid; e < a.pe[k] * RM; e += B) {
             const int nn = e / RM, j = e - nn * RM;
-            Ws[k][e] = j < rk ? a.W[k][nn * rk + j] : T(0);
+            Ws[k][e] = j < rk ? a.W[k][nn * rk + j] : 0.0;
         }
         for (int e = tid; e < a.pm; e += B) mk[k * a.pm + e] = e < a.pe[k] ? a.mask[k][e] : 0;
     }
@@ -57,11 +59,11 @@ __global__ void __launch_bounds__(128) sampled_factors_kernel(const EvalArgs<T> 
         bvec[s] = u[q];
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            T t[1] = {fma(xyz[k * Q + q], a.sc[k], a.of[k])};
-            T acc[1][RM];
-            factor_values<T, RM, 1>(t, Ws[k], mk + k * a.pm, a.pe[k], ra, rb, acc);
+            double t[1] = {fma((double)xyz[k * Q + q], a.sc[k], a.of[k])};
+            double acc[1][RM];
+            factor_values<double, RM, 1>(t, Ws[k], mk + k * a.pm, a.pe[k], ra, rb, acc);
             const int rk = a.r[k];
-            for (int j = 0; j < rk; ++j) outs[k][s * rk + j] = acc[0][j];
+            for (int j = 0; j < rk; ++j) outs[k][s * rk + j] = (T)acc[0][j];
         }
     }
 }
@@ -188,7 +190,7 @@ template <typename T, int R3M>
 __global__ void __launch_bounds__(128) residual_kernel(const T* __restrict__ U1, const T* __restrict__ U2,
                                                        const T* __restrict__ U3, const T* __restrict__ bvec,
                                                        const double* __restrict__ alpha, int64_t m, int r1,
-                                                       int r2, int r3, double* rv) {
+                                                       int r2, int r3, double scale, double* rv) {
     constexpr bool kSplit = sizeof(T) == 4;
     extern __shared__ __align__(16) unsigned char smem[];
     T* As = reinterpret_cast<T*>(smem);        // [r1*r2][R3M]
@@ -239,14 +241,44 @@ __global__ void __launch_bounds__(128) residual_kernel(const T* __restrict__ U1,
             }
             f = fma(si, (double)U1[s * r1 + i], f);
         }
-        rv[s] = (double)bvec[s] - f;
+        rv[s] = (bvec ? (double)bvec[s] : 0.0) + scale * f;
     }
+}
+
+// out[k] = sum_i x_k[i] * y_k[i] for k < nd (out zeroed by the caller)
+__global__ void dots_kernel(const double* x0, const double* y0, const double* x1, const double* y1, int n, int nd,
+                            double* out) {
+    double a0 = 0.0, a1 = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        a0 += x0[i] * y0[i];
+        if (nd > 1) a1 += x1[i] * y1[i];
+    }
+    for (int o = 16; o; o >>= 1) {
+        a0 += __shfl_xor_sync(0xffffffffu, a0, o);
+        a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&out[0], a0);
+        if (nd > 1) atomicAdd(&out[1], a1);
+    }
+}
+
+// y += a x, or (with xpby) y = x + b y
+__global__ void axpy_kernel(double* y, const double* x, double a, int n, int xpby) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        y[i] = xpby ? x[i] + a * y[i] : y[i] + a * x[i];
 }
 
 template <typename T>
 __global__ void to_double_kernel(const T* src, double* dst, int64_t n) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         dst[i] = (double)src[i];
+}
+
+template <typename T>
+__global__ void from_double_kernel(const double* src, T* dst, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = (T)src[i];
 }
 
 // alpha += delta; norms[0] += ||delta||^2, norms[1] += ||alpha||^2 (norms zeroed by the caller)
@@ -301,12 +333,12 @@ static int grid_for(int64_t n, int block, int cap_per_sm = 8) {
 template <typename T>
 static fst_status launch_factors(const fst_model* M, const T* xyz, int64_t Q, const int64_t* idx, int64_t m,
                                  const T* u, T* U[3], T* bvec, cudaStream_t s) {
-    EvalArgs<T> a = make_args<T>(M);
+    EvalArgs<double> a = make_args<double>(M);
     bind(a, M);
     int rmax = M->r[0] > M->r[1] ? M->r[0] : M->r[1];
     rmax = M->r[2] > rmax ? M->r[2] : rmax;
     const int RMb = rmax <= 8 ? 8 : rmax <= 16 ? 16 : rmax <= 24 ? 24 : 32;
-    const size_t smem = (2 * (size_t)a.pm + (size_t)(a.pe[0] + a.pe[1] + a.pe[2]) * RMb) * sizeof(T) + 3 * a.pm;
+    const size_t smem = (2 * (size_t)a.pm + (size_t)(a.pe[0] + a.pe[1] + a.pe[2]) * RMb) * sizeof(double) + 3 * a.pm;
 #define FST_FACT(RMV)                                                                                      \
     {                                                                                                      \
         auto kern = sampled_factors_kernel<T, RMV>;                                                        \
@@ -337,7 +369,7 @@ static fst_status launch_atr(const fst_model* M, const T* const U[3], const doub
 
 template <typename T>
 static fst_status launch_residual(const fst_model* M, const T* const U[3], const T* bvec, const double* alpha,
-                                  int64_t m, double* rv, cudaStream_t s) {
+                                  int64_t m, double* rv, cudaStream_t s, double scale = -1.0) {
     const int r1 = M->r[0], r2 = M->r[1], r3 = M->r[2];
     const int R3M = r3 <= 8 ? 8 : r3 <= 16 ? 16 : r3 <= 24 ? 24 : 32;
     const size_t smem = (size_t)r1 * r2 * R3M * sizeof(T) * (sizeof(T) == 4 ? 2 : 1);
@@ -346,7 +378,7 @@ static fst_status launch_residual(const fst_model* M, const T* const U[3], const
     {                                                                                                       \
         auto kern = residual_kernel<T, V>;                                                                  \
         FST_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));       \
-        kern<<<grid, 128, smem, s>>>(U[0], U[1], U[2], bvec, alpha, m, r1, r2, r3, rv);                     \
+        kern<<<grid, 128, smem, s>>>(U[0], U[1], U[2], bvec, alpha, m, r1, r2, r3, scale, rv);              \
     }
     if (R3M == 8) FST_RES(8) else if (R3M == 16) FST_RES(16) else if (R3M == 24) FST_RES(24) else FST_RES(32)
 #undef FST_RES
@@ -372,7 +404,7 @@ static fst_status refit_impl(fst_model* M, const T* xyz, const T* u, int64_t Q, 
     const int R = M->R();
     RefitScratch& W = M->rs;
     const bool fp64 = sizeof(T) == 8;
-    const int max_refine = opts ? opts->max_refine : 8;
+    const int max_refine = opts ? opts->max_refine : 32;
     const double tol = (opts && opts->refine_tol > 0) ? opts->refine_tol : (fp64 ? 1e-13 : 1e-10);
     const bool force64 = opts && opts->fp64_cholesky;
     fst_refit_report r;
@@ -462,6 +494,13 @@ static fst_status refit_impl(fst_model* M, const T* xyz, const T* u, int64_t Q, 
             FST_TRY(cholesky_lower<double>(G, R, flag, s));
             Lp = G;
         }
+        if (use64) {
+            FST_TRY(W.Linv.ensure(sizeof(double) * (size_t)((R + 63) / 64) * 64 * 64));
+            FST_TRY(chol_invert_diag<double>(static_cast<const double*>(Lp), R, W.Linv.as<double>(), s));
+        } else {
+            FST_TRY(W.Linv.ensure(sizeof(float) * (size_t)((R + 63) / 64) * 64 * 64));
+            FST_TRY(chol_invert_diag<float>(static_cast<const float*>(Lp), R, W.Linv.as<float>(), s));
+        }
         int hflag = 0;
         FST_CUDA(cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, s));
         FST_CUDA(cudaStreamSynchronize(s));
@@ -476,48 +515,98 @@ static fst_status refit_impl(fst_model* M, const T* xyz, const T* u, int64_t Q, 
         r.fallback_fp64 = 1;
     }
 
+    // the preconditioner solve runs in the factor's precision on a working copy
+    FST_TRY(W.xw.ensure(sizeof(double) * (size_t)R));
+    FST_TRY(W.yw.ensure(sizeof(double) * (size_t)R));
     auto solve = [&](double* x) -> fst_status {
-        if (use64) return chol_solve<double>(static_cast<const double*>(Lp), R, x, s);
-        return chol_solve<float>(static_cast<const float*>(Lp), R, x, s);
+        const int grid = grid_for(R, 256, 2);
+        if (use64) {
+            return chol_solve<double>(static_cast<const double*>(Lp), W.Linv.as<double>(), R, x,
+                                      W.yw.as<double>(), s);
+        }
+        float* xw = W.xw.as<float>();
+        from_double_kernel<float><<<grid, 256, 0, s>>>(x, xw, R);
+        FST_CHECK_LAUNCH();
+        FST_TRY(chol_solve<float>(static_cast<const float*>(Lp), W.Linv.as<float>(), R, xw, W.yw.as<float>(), s));
+        to_double_kernel<float><<<grid, 256, 0, s>>>(xw, x, R);
+        FST_CHECK_LAUNCH();
+        return FST_OK;
     };
     // alpha_0 = G^-1 h
     FST_CUDA(cudaMemcpyAsync(alpha, g, sizeof(double) * R, cudaMemcpyDeviceToDevice, s));
     FST_TRY(solve(alpha));
     FST_CUDA(cudaMemcpyAsync(alpha0, alpha, sizeof(double) * R, cudaMemcpyDeviceToDevice, s));
 
-    // 5. refinement
-    // Stop at tol, or when the update stops shrinking (the rounding floor of the working
-    // precision); a floor above `floor_ok` means the preconditioner is too weak.
+    // 5. refinement: conjugate gradients on the normal equations A^T A alpha = A^T b,
+    // preconditioned by the factor L L^T of the working-precision G.  A p and A^T q are
+    // applied through the factored Khatri-Rao form with FP64 accumulation, so the limit is
+    // the least-squares solution whatever the accuracy of G (which only sets the speed).
+    // Stop at tol, or when the step stops shrinking at a level below `floor_ok`.
     const double floor_ok = fp64 ? 1e-10 : 1e-5;
-    double last = 0.0, prev = 0.0, hn[2] = {0, 0};
+    FST_TRY(W.pcg.ensure(sizeof(double) * (size_t)R * 4));
+    double* rr = W.pcg.as<double>();     // residual of the normal equations
+    double* zz = rr + R;                 // preconditioned residual
+    double* pp = zz + R;                 // search direction
+    double* ww = pp + R;                 // A^T A p
+    const int vgrid = grid_for(R, 256, 2);
+    auto dots = [&](const double* x0, const double* y0, const double* x1, const double* y1, int nd,
+                    double* hout) -> fst_status {
+        FST_CUDA(cudaMemsetAsync(norms, 0, 2 * sizeof(double), s));
+        dots_kernel<<<vgrid, 256, 0, s>>>(x0, y0, x1, y1, R, nd, norms);
+        FST_CHECK_LAUNCH();
+        FST_CUDA(cudaMemcpyAsync(hout, norms, nd * sizeof(double), cudaMemcpyDeviceToHost, s));
+        FST_CUDA(cudaStreamSynchronize(s));
+        return FST_OK;
+    };
+    double last = 0.0, prev = 0.0;
     int steps = 0;
     bool converged = max_refine <= 0;
-    for (int it = 0; it < max_refine; ++it) {
-        FST_TRY(launch_residual<T>(M, Uc, bvec, alpha, m, rv, s));
-        FST_TRY(launch_atr<T>(M, Uc, rv, m, g, s));
-        FST_TRY(solve(g));
-        FST_CUDA(cudaMemsetAsync(norms, 0, 2 * sizeof(double), s));
-        axpy_norms_kernel<<<grid_for(R, 256, 2), 256, 0, s>>>(alpha, g, R, norms);
-        FST_CHECK_LAUNCH();
-        FST_CUDA(cudaMemcpyAsync(hn, norms, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
-        FST_CUDA(cudaStreamSynchronize(s));
-        ++steps;
-        prev = last;
-        last = hn[1] > 0 ? sqrt(hn[0] / hn[1]) : 0.0;
-        if (!isfinite(last)) break;
-        if (last <= tol || (it >= 2 && last > 0.5 * prev && last <= floor_ok)) {
-            converged = true;
-            break;
+    if (max_refine > 0) {
+        FST_TRY(launch_residual<T>(M, Uc, bvec, alpha, m, rv, s));         // b - A alpha
+        FST_TRY(launch_atr<T>(M, Uc, rv, m, rr, s));                       // r = A^T (b - A alpha)
+        FST_CUDA(cudaMemcpyAsync(zz, rr, sizeof(double) * R, cudaMemcpyDeviceToDevice, s));
+        FST_TRY(solve(zz));
+        FST_CUDA(cudaMemcpyAsync(pp, zz, sizeof(double) * R, cudaMemcpyDeviceToDevice, s));
+        double rz[2];
+        FST_TRY(dots(rr, zz, alpha, alpha, 2, rz));
+        double rzv = rz[0];
+        for (int it = 0; it < max_refine; ++it) {
+            FST_TRY(launch_residual<T>(M, Uc, nullptr, pp, m, rv, s, 1.0));   // q = A p
+            FST_TRY(launch_atr<T>(M, Uc, rv, m, ww, s));                      // w = A^T q
+            double pw[2];
+            FST_TRY(dots(pp, ww, pp, pp, 2, pw));
+            if (!(pw[0] > 0.0) || !isfinite(rzv)) break;
+            const double ak = rzv / pw[0];
+            axpy_kernel<<<vgrid, 256, 0, s>>>(alpha, pp, ak, R, 0);
+            FST_CHECK_LAUNCH();
+            axpy_kernel<<<vgrid, 256, 0, s>>>(rr, ww, -ak, R, 0);
+            FST_CHECK_LAUNCH();
+            FST_CUDA(cudaMemcpyAsync(zz, rr, sizeof(double) * R, cudaMemcpyDeviceToDevice, s));
+            FST_TRY(solve(zz));
+            double nx[2];
+            FST_TRY(dots(rr, zz, alpha, alpha, 2, nx));
+            ++steps;
+            prev = last;
+            last = nx[1] > 0 ? fabs(ak) * sqrt(pw[1] / nx[1]) : 0.0;
+            if (!isfinite(last)) break;
+            if (last <= tol || (it >= 2 && last > 0.5 * prev && last <= floor_ok)) {
+                converged = true;
+                break;
+            }
+            const double beta = nx[0] / rzv;
+            rzv = nx[0];
+            axpy_kernel<<<vgrid, 256, 0, s>>>(pp, zz, beta, R, 1);          // p = z + beta p
+            FST_CHECK_LAUNCH();
         }
+        if (!converged && isfinite(last) && last <= floor_ok) converged = true;
     }
-    if (!converged && isfinite(last) && last <= floor_ok) converged = true;
     r.ms_refine = tm.stop();
     r.refine_steps = steps;
     r.last_rel_update = last;
     if (!converged && max_refine > 0) {
-        if (!use64 && !fp64) {
+        if (!use64 && !fp64 && !force64) {
             // the working-precision factor is too weak a preconditioner: redo in FP64
-            fst_refit_opts o = opts ? *opts : fst_refit_opts{8, 0.0, 0};
+            fst_refit_opts o = opts ? *opts : fst_refit_opts{32, 0.0, 0};
             o.fp64_cholesky = 1;
             fst_refit_report r2;
             fst_status st = refit_impl<T>(M, xyz, u, Q, idx, m, seed, prec, &o, &r2, s);
@@ -591,4 +680,44 @@ extern "C" fst_status fst_refit_f64(fst_model* model, const double* xyz, const d
                                     const int64_t* idx, int64_t m, uint64_t seed, const fst_refit_opts* opts,
                                     fst_refit_report* report, fst_stream stream) {
     return refit_entry<double>(model, xyz, u, Q, idx, m, seed, FST_FP64, opts, report, (cudaStream_t)stream);
+}
+
+// ------------------------------------------------------------------ normal matrix only
+extern "C" fst_status fst_normal_matrix(const fst_model* M, const float* xyz, const float* u, int64_t Q,
+                                        const int64_t* idx, int64_t m, fst_prec prec, float* G, double* h,
+                                        fst_stream stream) {
+    FST_REQUIRE(M != nullptr && xyz && u && idx && G, "model, xyz, u, idx or G is NULL");
+    FST_REQUIRE(Q > 0 && m > 0 && m <= Q, "need 0 < m <= Q");
+    FST_REQUIRE(prec == FST_FP32 || prec == FST_TF32 || prec == FST_BF16 || prec == FST_BF16X3,
+                "fst_normal_matrix takes FP32, TF32, BF16 or BF16X3");
+    int dev = 0;
+    FST_CUDA(cudaGetDevice(&dev));
+    FST_REQUIRE(dev == M->device, "model lives on device %d, current device is %d", M->device, dev);
+    FST_REQUIRE(pointer_device(xyz) == dev && pointer_device(u) == dev && pointer_device(idx) == dev &&
+                    pointer_device(G) == dev && (!h || pointer_device(h) == dev),
+                "xyz, u, idx, G and h must be device memory");
+    fst_model* MM = const_cast<fst_model*>(M);
+    std::lock_guard<std::mutex> lk(MM->mu);
+    cudaStream_t s = (cudaStream_t)stream;
+    RefitScratch& W = MM->rs;
+    float* U[3];
+    for (int k = 0; k < 3; ++k) {
+        FST_TRY(W.U[k].ensure(sizeof(float) * (size_t)m * M->r[k]));
+        U[k] = W.U[k].as<float>();
+    }
+    FST_TRY(W.b.ensure(sizeof(float) * (size_t)m));
+    FST_TRY(launch_factors<float>(M, xyz, Q, idx, m, u, U, W.b.as<float>(), s));
+    const float* const Uc[3] = {U[0], U[1], U[2]};
+    if (prec == FST_FP32) {
+        FST_TRY(launch_gram_simt<float>(M, Uc, m, G, s));
+    } else {
+        FST_TRY(gram_tc_launch(M, Uc[0], Uc[1], Uc[2], m, G, prec, s));
+    }
+    if (h) {
+        FST_TRY(W.res.ensure(sizeof(double) * (size_t)m));
+        to_double_kernel<float><<<grid_for(m, 256), 256, 0, s>>>(W.b.as<float>(), W.res.as<double>(), m);
+        FST_CHECK_LAUNCH();
+        FST_TRY(launch_atr<float>(M, Uc, W.res.as<double>(), m, h, s));
+    }
+    return FST_OK;
 }

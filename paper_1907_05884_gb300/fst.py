@@ -71,6 +71,7 @@ def _load():
         "fst_sample_rows_static": (I32, [U64, I64, I64, P, P]),
         "fst_refit": (I32, [P, P, P, I64, P, I64, U64, I32, P, P, P]),
         "fst_refit_f64": (I32, [P, P, P, I64, P, I64, U64, P, P, P]),
+        "fst_normal_matrix": (I32, [P, P, P, I64, P, I64, I32, P, P, P]),
         "fst_status_str": (C.c_char_p, [I32]),
         "fst_last_error": (C.c_char_p, []),
         "fst_build_info": (C.c_char_p, []),
@@ -198,7 +199,7 @@ class Model:
 
     # ---------------------------------------------------------------- refit
     def refit(self, xyz, u, m: int, seed: int = 0, prec: str = "fp32", idx=None,
-              max_refine: int = 8, refine_tol: float = 0.0, fp64_cholesky: bool = False, stream=None):
+              max_refine: int = 32, refine_tol: float = 0.0, fp64_cholesky: bool = False, stream=None):
         """Least-squares core refit over m sampled rows (or the rows in ``idx``).  xyz (3,Q) and u (Q,)
         are CUDA tensors, float32 (or float64 with prec='fp64').  Returns the report as a dict."""
         import torch
@@ -220,6 +221,19 @@ class Model:
                                  C.c_uint64(seed & 0xFFFFFFFFFFFFFFFF), PREC[prec], C.byref(opts),
                                  C.byref(rep), _stream(stream)))
         return rep.as_dict()
+
+
+def normal_matrix(model: "Model", xyz, u, idx, prec: str = "tf32", with_h: bool = True, stream=None):
+    """G = A^T A (lower triangle valid) and h = A^T b over the rows idx, as CUDA tensors."""
+    import torch
+    r, _, _ = model.shape()
+    R = r[0] * r[1] * r[2]
+    G = torch.zeros((R, R), dtype=torch.float32, device=xyz.device)
+    h = torch.zeros(R, dtype=torch.float64, device=xyz.device) if with_h else None
+    _check(lib.fst_normal_matrix(model.handle, _dptr(xyz), _dptr(u), xyz.shape[1], _dptr(idx), idx.numel(),
+                                 PREC[prec], _dptr(G), _dptr(h) if h is not None else C.c_void_p(0),
+                                 _stream(stream)))
+    return G, h
 
 
 def sample_rows(seed: int, Q: int, m: int, device="cuda", stream=None):
