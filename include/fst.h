@@ -106,10 +106,22 @@ fst_status fst_model_load(const char* path, fst_model** out);
 
 /* u~(y) at n points (Sec. 6: reconstruction is the evaluation of the basis
  * functions at the points of interest; eq. func_tuck).  xyz: device, 3n floats
- * SoA; out: device, n floats.  prec selects the contraction arithmetic (FST_FP32
- * on CUDA cores, or a tensor-core precision).  Asynchronous; allocates nothing. */
+ * SoA; out: device, n floats.  prec selects the contraction arithmetic: FST_FP32 on
+ * CUDA cores, or FST_TF32 / FST_BF16 / FST_BF16X3 with the core contraction on the
+ * tcgen05 tensor cores (factor values in FP32, FP32 accumulation).  Asynchronous and
+ * allocation-free once the model is prepared (see fst_eval_prepare). */
 fst_status fst_eval(const fst_model* model, const float* xyz, int64_t n, float* out,
                     fst_prec prec, fst_stream stream);
+
+/* Build, ahead of time, what fst_eval needs for a tensor-core precision (the core as
+ * tensor-core operand tiles; rebuilt after the core changes).  fst_eval does this itself
+ * on first use with a synchronous upload; call this first to keep fst_eval free of
+ * allocation and synchronisation.  Synchronous. */
+fst_status fst_eval_prepare(fst_model* model, fst_prec prec);
+
+/* Report (and clear) a bounded device wait that expired inside a tensor-core evaluation
+ * on this device since the last check: FST_ETIMEOUT, else FST_OK.  Synchronises stream. */
+fst_status fst_eval_check(fst_stream stream);
 
 /* The same in FP64 throughout (device xyz: 3n doubles, out: n doubles).  Asynchronous. */
 fst_status fst_eval_f64(const fst_model* model, const double* xyz, int64_t n, double* out,

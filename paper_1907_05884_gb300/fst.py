@@ -67,6 +67,8 @@ def _load():
         "fst_model_load": (I32, [C.c_char_p, P]),
         "fst_eval": (I32, [P, P, I64, P, I32, P]),
         "fst_eval_f64": (I32, [P, P, I64, P, P]),
+        "fst_eval_prepare": (I32, [P, I32]),
+        "fst_eval_check": (I32, [P]),
         "fst_sample_rows": (I32, [U64, I64, I64, P, P]),
         "fst_sample_rows_static": (I32, [U64, I64, I64, P, P]),
         "fst_refit": (I32, [P, P, P, I64, P, I64, U64, I32, P, P, P]),
@@ -188,6 +190,9 @@ class Model:
         _check(lib.fst_eval(self._h, _dptr(xyz), n, _dptr(out), PREC[prec], _stream(stream)))
         return out
 
+    def prepare(self, prec: str):
+        _check(lib.fst_eval_prepare(self._h, PREC[prec]))
+
     def eval_f64(self, xyz, out=None, stream=None):
         import torch
         assert xyz.is_cuda and xyz.dtype == torch.float64 and xyz.is_contiguous() and xyz.shape[0] == 3
@@ -243,6 +248,10 @@ def sample_rows(seed: int, Q: int, m: int, device="cuda", stream=None):
     _check(lib.fst_sample_rows(C.c_uint64(seed & 0xFFFFFFFFFFFFFFFF), int(Q), m, _dptr(idx),
                                _stream(stream)))
     return idx
+
+
+def eval_check(stream=None):
+    _check(lib.fst_eval_check(_stream(stream)))
 
 
 def kernel_launches() -> int:
