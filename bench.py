@@ -43,8 +43,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="fst", choices=["fst", "reference"])
-    ap.add_argument("--prec", default="fp32", help="refit Gram precision: fp32, tf32, bf16, bf16x3")
-    ap.add_argument("--eval-prec", default="fp32", help="evaluation precision: fp32, tf32, bf16, bf16x3")
+    ap.add_argument("--prec", default="bf16",
+                    help="normal-matrix (Gram) precision of the refit: fp32, tf32, bf16, bf16x3; the PCG "
+                         "refinement with FP64-accumulated residuals makes the core independent of it")
+    ap.add_argument("--eval-prec", default="bf16x3", help="evaluation precision: fp32, tf32, bf16, bf16x3")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--Q", type=int, default=1 << 24)
     return ap.parse_args()
@@ -236,6 +238,8 @@ def main():
 
     def step(i, timed_eval=False):
         rep = M.refit(xyz_d, u_d, m, seed=1000 + i, prec=args.prec)
+        if args.eval_prec != "fp32":
+            M.prepare(args.eval_prec)        # the refitted core as tensor-core operand tiles
         if timed_eval:
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
@@ -290,6 +294,8 @@ def main():
         xyz_d.copy_(xyz_h, non_blocking=True)
         u_d.copy_(u_h, non_blocking=True)
         M.refit(xyz_d, u_d, m, seed=5000 + i, prec=args.prec)
+        if args.eval_prec != "fp32":
+            M.prepare(args.eval_prec)
         M.eval(xyz_d, prec=args.eval_prec, out=out_d)
         out_h.copy_(out_d, non_blocking=True)
     e1.record(stream)
@@ -311,39 +317,52 @@ def main():
     sm_max = (clk or {}).get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0)
     gram_ms = statistics.mean(r["ms_gram"] for r in reports)
     chol_ms = statistics.mean(r["ms_cholesky"] for r in reports)
+    refine_ms = statistics.mean(r["ms_refine"] for r in reports)
     refit_ms = statistics.mean(r["ms_sample"] + r["ms_factors"] + r["ms_gram"] + r["ms_cholesky"] + r["ms_refine"]
                                for r in reports)
     ev_ms = statistics.mean(eval_ms)
     nnz = sum(len(v) for v in model.val)
     gram_flops = m * R * (R + 1)                      # lower triangle of A^T A, 2 flops per product
-    eval_flops_pt = 2 * (R + RANKS[0] * RANKS[1] + RANKS[0]) + 2 * nnz + 5 * 3 * DEGREE
-    eval_flops = eval_flops_pt * Q
+    eval_tc_flops = 2 * R * Q                         # T = U1 C_(1): 2 r1 r2 r3 flops per point
+    eval_alu_flops_pt = 2 * (RANKS[0] * RANKS[1] + RANKS[0]) + 2 * nnz + 5 * 3 * DEGREE
     alu_peak = fp32_alu_peak_tflops(sm_max, sms)
-    roof_gram = {"kernel": "gram (A^T A over sampled Khatri-Rao rows)", "bound": "alu",
-                 "achieved": gram_flops / (gram_ms / 1e3) / 1e12, "peak": alu_peak, "unit": "TFLOP/s",
-                 "traffic": None}
+    # tensor peaks: measured cuBLAS BF16 (sustained: the kernel runs inside a long step);
+    # TF32 = BF16 x 0.5 (nominal dense ratio); BF16x3 runs three BF16 products per term
+    bf16_peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
+    tc_peak = {"tf32": bf16_peak * 0.5, "bf16": bf16_peak, "bf16x3": bf16_peak / 3.0}
+    if args.prec == "fp32":
+        roof_gram = {"kernel": "gram_simt (A^T A over sampled Khatri-Rao rows, CUDA cores)", "bound": "alu",
+                     "achieved": gram_flops / (gram_ms / 1e3) / 1e12, "peak": alu_peak, "unit": "TFLOP/s",
+                     "peak_source": f"FP32 ALU: {sms} SMs x 128 FMA/clk x 2 x {sm_max:.0f} MHz"}
+    else:
+        roof_gram = {"kernel": f"gram_tc_kernel<{args.prec}> (A^T A over sampled Khatri-Rao rows, tcgen05)",
+                     "bound": "tensor", "achieved": gram_flops / (gram_ms / 1e3) / 1e12,
+                     "peak": tc_peak[args.prec], "unit": "TFLOP/s",
+                     "peak_source": f"{peak_kind} bf16_tflops_sustained {bf16_peak} x "
+                                    f"{ {'tf32': 0.5, 'bf16': 1.0, 'bf16x3': 1 / 3}[args.prec]:.3f}"}
+    roof_gram["traffic"] = None
     roof_gram["frac"] = roof_gram["achieved"] / roof_gram["peak"]
-    roof_eval = {"kernel": "eval (basis + factor values + core contraction)", "bound": "alu",
-                 "achieved": eval_flops / (ev_ms / 1e3) / 1e12, "peak": alu_peak, "unit": "TFLOP/s",
-                 "traffic": None, "hbm_GBps": 16 * Q / (ev_ms / 1e3) / 1e9, "hbm_peak_GBps": peaks["hbm_gbs"]}
-    roof_eval["frac"] = roof_eval["achieved"] / roof_eval["peak"]
-    dominant = roof_gram if gram_ms >= ev_ms else roof_eval
+    roof_eval = {"kernel": f"eval ({args.eval_prec})", "ms": ev_ms,
+                 "tensor_TFLOPs": eval_tc_flops / (ev_ms / 1e3) / 1e12,
+                 "alu_TFLOPs": eval_alu_flops_pt * Q / (ev_ms / 1e3) / 1e12, "alu_peak": alu_peak,
+                 "hbm_GBps": 16 * Q / (ev_ms / 1e3) / 1e9, "hbm_peak_GBps": peaks["hbm_gbs"]}
+    if args.eval_prec != "fp32":
+        roof_eval["tensor_frac"] = roof_eval["tensor_TFLOPs"] / tc_peak[args.eval_prec]
+    dominant = roof_gram
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32" if args.prec == "fp32" and args.eval_prec == "fp32" else
-            f"{args.prec}/{args.eval_prec}",
+            "vs_baseline": None, "dtype": args.prec if args.prec == args.eval_prec else f"{args.prec}+{args.eval_prec}",
             "data": "synthetic", "config": workload_config(Q, R, m, args.prec, args.eval_prec),
             "refit_ms": refit_ms, "refit_gram_ms": gram_ms, "refit_cholesky_ms": chol_ms,
-            "refit_refine_steps": statistics.mean(r["refine_steps"] for r in reports),
+            "refit_pcg_ms": refine_ms,
+            "refit_pcg_steps": statistics.mean(r["refine_steps"] for r in reports),
             "refit_fallback_fp64": max(r["fallback_fp64"] for r in reports),
             "eval_ms": ev_ms, "eval_Mpoints_s": Q / ev_ms / 1e3,
-            "roofline": {k: v for k, v in dominant.items() if k != "kernel"} | {"kernel": dominant["kernel"],
-                                                                                 "peak_source": f"FP32 ALU: {sms} SMs x 128 FMA/clk x 2 x {sm_max:.0f} MHz"},
+            "roofline": {k: v for k, v in dominant.items()},
             "rooflines": {"gram": roof_gram, "eval": roof_eval},
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 16 * Q - 4 * Q,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": xyz.nbytes + u.nbytes,
                     "d2h_bytes_per_step": 4 * Q},
             "gpu_launches": launches, "clocks": clk, "peaks": peak_kind}
-    line["e2e"]["h2d_bytes_per_step"] = xyz.nbytes + u.nbytes
 
     if world == 1 and not args.no_cpu_baseline:
         import oracle
@@ -361,7 +380,7 @@ def main():
         ref = oracle.eval_points(om, xyz[:, sel].astype(np.float64), nthreads=nthreads)
         got = out_d.cpu().numpy()[sel]
         line["rel_l2_eval_vs_oracle"] = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
-        idx = oracle.sample(5000 + args.steps - 1, Q, m)
+        idx = oracle.sample(5000 + args.steps - 1, Q, m)   # rows of the last refit (e2e loop)
         g = oracle.normal_residual(om, xyz.astype(np.float64), u.astype(np.float64), idx, cur["alpha"],
                                    nthreads=nthreads)
         h = oracle.normal_residual(om, xyz.astype(np.float64), u.astype(np.float64), idx, np.zeros(R),
