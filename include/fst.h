@@ -113,6 +113,39 @@ fst_status fst_model_load(const char* path, fst_model** out);
 fst_status fst_eval(const fst_model* model, const float* xyz, int64_t n, float* out,
                     fst_prec prec, fst_stream stream);
 
+/* One evaluation instance of a batch: a model, its points (device, 3n floats SoA) and
+ * its output (device, n floats). */
+typedef struct {
+    const fst_model* model;
+    const float* xyz;
+    int64_t n;
+    float* out;
+} fst_eval_item;
+
+/* Evaluate many instances -- different models, uneven ranks and point counts -- with one
+ * persistent launch per size class of ranks (tensor-core precisions): the items are cut
+ * into runs of 128-point tiles, about four runs per SM, the runs are split over the blocks
+ * by estimated cost, and a block reloads a model's core tiles only when the instance
+ * changes.  Every result equals the single-instance fst_eval of that item bit for bit.
+ * FST_FP32 runs one CUDA-core launch per item.  items: host array; a model must not be
+ * refitted while it is being evaluated.  Asynchronous: the work lists go through a
+ * per-device ring of 8 pinned/device staging slots that only grow (the ninth call in
+ * flight waits for the first); models not yet prepared for prec are prepared first
+ * (synchronously). */
+fst_status fst_eval_batched(const fst_eval_item* items, int32_t count, fst_prec prec, fst_stream stream);
+
+/* A prepared batch (the persistent batched launch): the items' work lists and size classes
+ * are built and uploaded once; fst_eval_plan_run then only launches (one persistent kernel
+ * per size class of ranks), allocates nothing and does not synchronise, so it can be
+ * captured into a CUDA graph and replayed.  The models' cores and the items' buffers must
+ * stay as they were when the plan was made (a refit changes the core: make a new plan).
+ * Tensor-core precisions only. */
+typedef struct fst_eval_plan fst_eval_plan;
+fst_status fst_eval_plan_create(const fst_eval_item* items, int32_t count, fst_prec prec,
+                                fst_eval_plan** out);
+fst_status fst_eval_plan_run(const fst_eval_plan* plan, fst_stream stream);
+void fst_eval_plan_free(fst_eval_plan* plan);   /* waits for the device (cudaFree) */
+
 /* Build, ahead of time, what fst_eval needs for a tensor-core precision (the core as
  * tensor-core operand tiles; rebuilt after the core changes).  fst_eval does this itself
  * on first use with a synchronous upload; call this first to keep fst_eval free of
@@ -126,6 +159,13 @@ fst_status fst_eval_check(fst_stream stream);
 /* The same in FP64 throughout (device xyz: 3n doubles, out: n doubles).  Asynchronous. */
 fst_status fst_eval_f64(const fst_model* model, const double* xyz, int64_t n, double* out,
                         fst_stream stream);
+
+/* Points of an axis-aligned slice -- the 2D visualisation query of Sec. 6 (Fig. 6) --
+ * written into a device buffer: the plane y_axis = value, the two other axes sampled on a
+ * res0 x res1 node grid spanning [lo, hi] (both ends included; the lower-numbered free
+ * axis varies slowest).  xyz: device, 3 * res0 * res1 floats, SoA.  Asynchronous. */
+fst_status fst_slice_points(int32_t axis, double value, const double lo[3], const double hi[3],
+                            int32_t res0, int32_t res1, float* xyz, fst_stream stream);
 
 /* ---------------------------------------------------------------- sampling */
 

@@ -17,6 +17,10 @@
 // r1 to the MMA K granule with zeros, which contribute nothing.  Waits are bounded.
 #include <cuda_bf16.h>
 
+#include <string.h>
+
+#include <algorithm>
+#include <memory>
 #include <vector>
 
 #include "basis.cuh"
@@ -103,13 +107,19 @@ std::vector<unsigned char> build_core_image(const fst_model* m, const CoreImage&
     return img;
 }
 
-struct EvalTcArgs {
+// One evaluation instance as the kernel sees it.
+struct TcItem {
     EvalArgs<float> a;
-    const unsigned char* core_img;
-    int img_bytes;
-    int nchunks;
-    int kp;
-    int err_code;
+    const unsigned char* core_img;   // operand image of C_(1) (device)
+    int img_bytes, nchunks, kp, tab_bytes;
+    const float* xyz;
+    float* out;
+    long long n;
+};
+// A run of consecutive 128-point tiles of one instance.
+struct TcUnit {
+    int item, pad;
+    long long tile0, ntiles;
 };
 
 __device__ __forceinline__ uint32_t tf32_dev(float x) {
@@ -122,9 +132,16 @@ __device__ __forceinline__ uint32_t pack2_bf16(float a, float b) {
     return *reinterpret_cast<uint32_t*>(&h);
 }
 
+constexpr int kBarBytes = 1024;
+
+// Persistent kernel over a work list of units (instance, tile range).  Block b takes the
+// contiguous unit range [cta_start[b], cta_start[b+1]) (cut by estimated cost on the host);
+// it reloads the core image and the factor tables into shared memory only when the
+// instance changes.
 template <int MODE, int R3P, int RM>
 __global__ void __launch_bounds__(kThreadsE, 1)
-eval_tc_kernel(const EvalTcArgs P, const float* __restrict__ xyz, int64_t n, float* __restrict__ out,
+eval_tc_kernel(const TcItem* __restrict__ items, const TcUnit* __restrict__ units, const int* __restrict__ cta_start,
+               int core_max, int kb_max, const float* __restrict__ xyz_ov, float* __restrict__ out_ov,
                int* __restrict__ err) {
     constexpr int ES = MODE == eTF32 ? 4 : 2;
     constexpr int JC = jc_for(R3P);
@@ -132,52 +149,22 @@ eval_tc_kernel(const EvalTcArgs P, const float* __restrict__ xyz, int64_t n, flo
     constexpr int NCP = (NC + 15) / 16 * 16;
     constexpr int MAXCH = (FST_MAX_RANK + JC - 1) / JC;
     constexpr int PARTS = MODE == eBF16X3 ? 2 : 1;
-    const EvalArgs<float>& a = P.a;
-    const int KP = P.kp, KB = KP * ES;
-    const int SBO_A = (KB / 16) * 128;
-    const int r1 = a.r[0];
 
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    unsigned char* core = smem;                                           // P.img_bytes
-    unsigned char* abuf = core + ((P.img_bytes + 1023) & ~1023);          // kGroups x PARTS x 128 x KB
-    const int abytes = 128 * KB;
-    float* fsm = reinterpret_cast<float*>(abuf + kGroups * PARTS * abytes);   // recurrence + W tables
-    float* ra = fsm;
-    float* rb = ra + a.pm;
-    float* Ws[3];
-    Ws[0] = rb + a.pm;
-    Ws[1] = Ws[0] + a.pe[0] * RM;
-    Ws[2] = Ws[1] + a.pe[1] * RM;
-    uint8_t* mk = reinterpret_cast<uint8_t*>(Ws[2] + a.pe[2] * RM);
-    uint64_t* bars = reinterpret_cast<uint64_t*>(((uintptr_t)(mk + 3 * a.pm) + 15) & ~(uintptr_t)15);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
     uint64_t* a_full = bars;                 // [kGroups] workers -> MMA: A tile written
     uint64_t* a_empty = bars + kGroups;      // [kGroups] MMA -> workers: A tile consumed
     uint64_t* d_full = bars + 2 * kGroups;   // [kGroups] MMA -> workers: chunk in TMEM
     uint64_t* d_empty = bars + 3 * kGroups;  // [kGroups] workers -> MMA: chunk read
     uint64_t* drain = bars + 4 * kGroups;
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+    unsigned char* core = smem + kBarBytes;
+    unsigned char* abuf = core + core_max;                       // kGroups x PARTS x 128 x kb_max
+    float* fsm = reinterpret_cast<float*>(abuf + kGroups * PARTS * 128 * kb_max);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (warp == 0) tc::tmem_alloc(tmem_slot, 512);
-    // shared tables: core image, recurrence, dense coefficient rows
-    {
-        const uint4* src = reinterpret_cast<const uint4*>(P.core_img);
-        uint4* dst = reinterpret_cast<uint4*>(core);
-        for (int e = tid; e < P.img_bytes / 16; e += blockDim.x) dst[e] = src[e];
-        for (int i = tid; i < a.pm; i += blockDim.x) {
-            ra[i] = float(2 * i + 1) / float(i + 1);
-            rb[i] = float(i) / float(i + 1);
-        }
-        for (int k = 0; k < 3; ++k) {
-            const int rk = a.r[k];
-            for (int e = tid; e < a.pe[k] * RM; e += blockDim.x) {
-                const int nn = e / RM, j = e - nn * RM;
-                Ws[k][e] = j < rk ? a.W[k][nn * rk + j] : 0.f;
-            }
-            for (int e = tid; e < a.pm; e += blockDim.x) mk[k * a.pm + e] = e < a.pe[k] ? a.mask[k][e] : 0;
-        }
-    }
     if (tid == 0) {
         for (int g = 0; g < kGroups; ++g) {
             tc::mbar_init(&a_full[g], 4);
@@ -188,169 +175,212 @@ eval_tc_kernel(const EvalTcArgs P, const float* __restrict__ xyz, int64_t n, flo
         tc::mbar_init(drain, 1);
         tc::fence_mbar_init();
     }
-    tc::fence_async_smem();
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = *tmem_slot;
-    const long long ntiles = (n + 127) / 128;
-    const int nch = P.nchunks;
 
-    if (warp < kWorkers) {
-        // ------------------------------------------------------------------ workers
-        const int g = warp >> 2, sub = warp & 3, row = sub * 32 + lane;   // TMEM lane = row
-        unsigned char* A = abuf + g * PARTS * abytes;
-        int lt = 0;            // tiles of this group
-        int cc = 0;            // chunks of this group
-        bool dead = false;
-        for (long long t = blockIdx.x + (long long)g * gridDim.x; t < ntiles;
-             t += (long long)kGroups * gridDim.x, ++lt) {
-            const int64_t q = t * 128 + row;
-            const bool ok = q < n;
-            float tt[3][1];
-#pragma unroll
-            for (int k = 0; k < 3; ++k) tt[k][0] = fmaf(ok ? xyz[k * n + q] : 0.f, a.sc[k], a.of[k]);
-            float w[1][RM], u2[RM], u3[RM];
-            factor_values<float, RM, 1>(tt[1], Ws[1], mk + a.pm, a.pe[1], ra, rb, w);
-#pragma unroll
-            for (int j = 0; j < RM; ++j) u2[j] = w[0][j];
-            factor_values<float, RM, 1>(tt[2], Ws[2], mk + 2 * a.pm, a.pe[2], ra, rb, w);
-#pragma unroll
-            for (int j = 0; j < RM; ++j) u3[j] = j < a.r[2] ? w[0][j] : 0.f;
-            factor_values<float, RM, 1>(tt[0], Ws[0], mk, a.pe[0], ra, rb, w);   // w1 -> A operand
-            if (!tc::mbar_wait(&a_empty[g], (uint32_t)(lt & 1) ^ 1u, kWaitLimitE)) {
-                atomicOr(err, 1);
-                dead = true;
+    const int u0 = cta_start[blockIdx.x], u1 = cta_start[blockIdx.x + 1];
+    int cur = -1;
+    // per-role phase counters run across units
+    int lt = 0, cc = 0;                          // worker group
+    int mlt[kGroups] = {0, 0}, mcc[kGroups] = {0, 0};
+    bool issued = false, dead = false;
+    float *ra = nullptr, *rb = nullptr, *Ws0 = nullptr, *Ws1 = nullptr, *Ws2 = nullptr;
+    uint8_t* mk = nullptr;
+    for (int u = u0; u < u1; ++u) {
+        const TcUnit U = units[u];
+        const TcItem& I = items[U.item];
+        const EvalArgs<float>& a = I.a;
+        if (U.item != cur) {
+            // every role has finished the previous instance: its MMAs completed before the
+            // workers' last chunk wait, so shared memory can be refilled
+            tc::fence_before_sync();
+            __syncthreads();
+            const uint4* src = reinterpret_cast<const uint4*>(I.core_img);
+            uint4* dst = reinterpret_cast<uint4*>(core);
+            for (int e = tid; e < I.img_bytes / 16; e += blockDim.x) dst[e] = src[e];
+            ra = fsm;
+            rb = ra + a.pm;
+            Ws0 = rb + a.pm;
+            Ws1 = Ws0 + a.pe[0] * RM;
+            Ws2 = Ws1 + a.pe[1] * RM;
+            mk = reinterpret_cast<uint8_t*>(Ws2 + a.pe[2] * RM);
+            for (int i = tid; i < a.pm; i += blockDim.x) {
+                ra[i] = float(2 * i + 1) / float(i + 1);
+                rb[i] = float(i) / float(i + 1);
             }
-            if (!dead) {
-                // row `row` of the A tile: KP values of w1 (zero beyond r1), 16 bytes at a time
-#pragma unroll
-                for (int c16 = 0; c16 < (RM * ES + 15) / 16 + 1; ++c16) {
-                    if (c16 * 16 >= KB) break;
-                    const uint32_t off = tc::kmajor_offset(row, c16 * 16, KB);
-                    if (MODE == eTF32) {
-                        uint32_t v4[4];
-#pragma unroll
-                        for (int e = 0; e < 4; ++e) {
-                            const int i = c16 * 4 + e;
-                            v4[e] = tf32_dev(i < RM && i < r1 ? w[0][i < RM ? i : 0] : 0.f);
-                        }
-                        *reinterpret_cast<uint4*>(A + off) = make_uint4(v4[0], v4[1], v4[2], v4[3]);
-                    } else {
-                        float h[8], l[8];
-#pragma unroll
-                        for (int e = 0; e < 8; ++e) {
-                            const int i = c16 * 8 + e;
-                            const float x = (i < RM && i < r1) ? w[0][i < RM ? i : 0] : 0.f;
-                            h[e] = x;
-                            l[e] = x - __bfloat162float(__float2bfloat16_rn(x));
-                        }
-                        *reinterpret_cast<uint4*>(A + off) =
-                            make_uint4(pack2_bf16(h[0], h[1]), pack2_bf16(h[2], h[3]), pack2_bf16(h[4], h[5]),
-                                       pack2_bf16(h[6], h[7]));
-                        if (MODE == eBF16X3)
-                            *reinterpret_cast<uint4*>(A + abytes + off) =
-                                make_uint4(pack2_bf16(l[0], l[1]), pack2_bf16(l[2], l[3]), pack2_bf16(l[4], l[5]),
-                                           pack2_bf16(l[6], l[7]));
-                    }
+            float* Wk[3] = {Ws0, Ws1, Ws2};
+            for (int k = 0; k < 3; ++k) {
+                const int rk = a.r[k];
+                for (int e = tid; e < a.pe[k] * RM; e += blockDim.x) {
+                    const int nn = e / RM, j = e - nn * RM;
+                    Wk[k][e] = j < rk ? a.W[k][nn * rk + j] : 0.f;
                 }
-                tc::fence_async_smem();
+                for (int e = tid; e < a.pm; e += blockDim.x) mk[k * a.pm + e] = e < a.pe[k] ? a.mask[k][e] : 0;
             }
-            __syncwarp();
-            if (lane == 0) tc::mbar_arrive(&a_full[g]);
-            // Khatri-Rao epilogue, chunk by chunk
-            float f = 0.f;
-            const uint32_t tbase = tmem + ((uint32_t)(sub * 32) << 16) + (uint32_t)(g * 256);
+            tc::fence_async_smem();
+            tc::fence_before_sync();
+            __syncthreads();
+            tc::fence_after_sync();
+            cur = U.item;
+        }
+        const int KB = I.kp * ES;
+        const int SBO = (KB / 16) * 128;
+        const int abytes = 128 * KB;
+        const int r1 = a.r[0];
+        const int nch = I.nchunks;
+        const long long n = I.n;
+        if (warp < kWorkers) {
+            // -------------------------------------------------------------- workers
+            const int g = warp >> 2, sub = warp & 3, row = sub * 32 + lane;   // TMEM lane = row
+            unsigned char* A = abuf + g * PARTS * 128 * kb_max;
+            for (long long t = U.tile0 + g; t < U.tile0 + U.ntiles; t += kGroups, ++lt) {
+                const long long q = t * 128 + row;
+                const bool ok = q < n;
+                float tt[3][1];
 #pragma unroll
-            for (int ch = 0; ch < MAXCH; ++ch) {
-                if (ch < nch) {
-                    if (!tc::mbar_wait(&d_full[g], (uint32_t)(cc & 1), kWaitLimitE)) {
-                        atomicOr(err, 2);
-                        dead = true;
+                const float* X = xyz_ov ? xyz_ov : I.xyz;
+                for (int k = 0; k < 3; ++k) tt[k][0] = fmaf(ok ? X[k * n + q] : 0.f, a.sc[k], a.of[k]);
+                float w[1][RM], u2[RM], u3[RM];
+                factor_values<float, RM, 1>(tt[1], Ws1, mk + a.pm, a.pe[1], ra, rb, w);
+#pragma unroll
+                for (int j = 0; j < RM; ++j) u2[j] = w[0][j];
+                factor_values<float, RM, 1>(tt[2], Ws2, mk + 2 * a.pm, a.pe[2], ra, rb, w);
+#pragma unroll
+                for (int j = 0; j < RM; ++j) u3[j] = j < a.r[2] ? w[0][j] : 0.f;
+                factor_values<float, RM, 1>(tt[0], Ws0, mk, a.pe[0], ra, rb, w);   // w1 -> A operand
+                if (!tc::mbar_wait(&a_empty[g], (uint32_t)(lt & 1) ^ 1u, kWaitLimitE)) {
+                    atomicOr(err, 1);
+                    dead = true;
+                }
+                if (!dead) {
+#pragma unroll
+                    for (int c16 = 0; c16 < (RM * ES + 15) / 16 + 1; ++c16) {
+                        if (c16 * 16 >= KB) break;
+                        const uint32_t off = tc::kmajor_offset(row, c16 * 16, KB);
+                        if (MODE == eTF32) {
+                            uint32_t v4[4];
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) {
+                                const int i = c16 * 4 + e;
+                                v4[e] = tf32_dev(i < RM && i < r1 ? w[0][i < RM ? i : 0] : 0.f);
+                            }
+                            *reinterpret_cast<uint4*>(A + off) = make_uint4(v4[0], v4[1], v4[2], v4[3]);
+                        } else {
+                            float h[8], l[8];
+#pragma unroll
+                            for (int e = 0; e < 8; ++e) {
+                                const int i = c16 * 8 + e;
+                                const float x = (i < RM && i < r1) ? w[0][i < RM ? i : 0] : 0.f;
+                                h[e] = x;
+                                l[e] = x - __bfloat162float(__float2bfloat16_rn(x));
+                            }
+                            *reinterpret_cast<uint4*>(A + off) =
+                                make_uint4(pack2_bf16(h[0], h[1]), pack2_bf16(h[2], h[3]),
+                                           pack2_bf16(h[4], h[5]), pack2_bf16(h[6], h[7]));
+                            if (MODE == eBF16X3)
+                                *reinterpret_cast<uint4*>(A + abytes + off) =
+                                    make_uint4(pack2_bf16(l[0], l[1]), pack2_bf16(l[2], l[3]),
+                                               pack2_bf16(l[4], l[5]), pack2_bf16(l[6], l[7]));
+                        }
                     }
-                    tc::fence_after_sync();
-                    float s = 0.f;
+                    tc::fence_async_smem();
+                }
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(&a_full[g]);
+                // Khatri-Rao epilogue, chunk by chunk
+                float f = 0.f;
+                const uint32_t tbase = tmem + ((uint32_t)(sub * 32) << 16) + (uint32_t)(g * 256);
 #pragma unroll
-                    for (int c0 = 0; c0 < NC; c0 += 16) {
-                        float v[16];
-                        tc::tmem_ld16(tbase + c0, v);
-                        tc::tmem_wait_ld();
+                for (int ch = 0; ch < MAXCH; ++ch) {
+                    if (ch < nch) {
+                        if (!tc::mbar_wait(&d_full[g], (uint32_t)(cc & 1), kWaitLimitE)) {
+                            atomicOr(err, 2);
+                            dead = true;
+                        }
+                        tc::fence_after_sync();
+                        float s = 0.f;
 #pragma unroll
-                        for (int e = 0; e < 16; ++e) {
-                            const int col = c0 + e;
-                            if (col < NC) {
-                                const int jl = col / R3P, k = col % R3P;
-                                s = fmaf(v[e], u3[k], s);
-                                if (k == R3P - 1) {
-                                    const int j = ch * JC + jl;
-                                    if (j < RM) f = fmaf(s, u2[j < RM ? j : 0], f);
-                                    s = 0.f;
+                        for (int c0 = 0; c0 < NC; c0 += 16) {
+                            float v[16];
+                            tc::tmem_ld16(tbase + c0, v);
+                            tc::tmem_wait_ld();
+#pragma unroll
+                            for (int e = 0; e < 16; ++e) {
+                                const int col = c0 + e;
+                                if (col < NC) {
+                                    const int jl = col / R3P, k = col % R3P;
+                                    s = fmaf(v[e], u3[k], s);
+                                    if (k == R3P - 1) {
+                                        const int j = ch * JC + jl;
+                                        if (j < RM) f = fmaf(s, u2[j < RM ? j : 0], f);
+                                        s = 0.f;
+                                    }
                                 }
                             }
                         }
+                        tc::fence_before_sync();
+                        __syncwarp();
+                        if (lane == 0) tc::mbar_arrive(&d_empty[g]);
+                        ++cc;
                     }
-                    tc::fence_before_sync();
-                    __syncwarp();
-                    if (lane == 0) tc::mbar_arrive(&d_empty[g]);
-                    ++cc;
                 }
+                if (ok) (out_ov ? out_ov : I.out)[q] = f;
             }
-            if (ok) out[q] = f;
-        }
-    } else if (lane == 0) {
-        // ------------------------------------------------------------------ MMA issuer
-        constexpr uint32_t idesc = MODE == eTF32 ? tc::idesc_tf32(128, NCP) : tc::idesc_bf16(128, NCP);
-        const int kst = KB / 32;                   // MMAs (32 bytes of K each) per product
-        const uint32_t SBO_B = SBO_A;              // same K extent
-        const uint32_t core_u32 = tc::smem_u32(core);
-        const uint32_t chunk_bytes = (uint32_t)(NCP * KB);
-        int lt[kGroups] = {0, 0}, cc[kGroups] = {0, 0};
-        bool issued = false, dead = false;
-        for (long long t = blockIdx.x; t < ntiles && !dead; t += gridDim.x) {
-            const int g = (int)(((t - blockIdx.x) / gridDim.x) % kGroups);
-            const uint32_t abase = tc::smem_u32(abuf + g * PARTS * abytes);
-            if (!tc::mbar_wait(&a_full[g], (uint32_t)(lt[g] & 1), kWaitLimitE)) {
-                atomicOr(err, 4);
-                break;
-            }
-            tc::fence_after_sync();
-            for (int ch = 0; ch < nch; ++ch) {
-                if (!tc::mbar_wait(&d_empty[g], (uint32_t)(cc[g] & 1) ^ 1u, kWaitLimitE)) {
-                    atomicOr(err, 8);
+        } else if (lane == 0 && !dead) {
+            // -------------------------------------------------------------- MMA issuer
+            constexpr uint32_t idesc = MODE == eTF32 ? tc::idesc_tf32(128, NCP) : tc::idesc_bf16(128, NCP);
+            const int kst = KB / 32;
+            const uint32_t core_u32 = tc::smem_u32(core);
+            const uint32_t chunk_bytes = (uint32_t)(NCP * KB);
+            for (long long t = U.tile0; t < U.tile0 + U.ntiles && !dead; ++t) {
+                const int g = (int)((t - U.tile0) & 1);
+                const uint32_t abase = tc::smem_u32(abuf + g * PARTS * 128 * kb_max);
+                if (!tc::mbar_wait(&a_full[g], (uint32_t)(mlt[g] & 1), kWaitLimitE)) {
+                    atomicOr(err, 4);
                     dead = true;
                     break;
                 }
                 tc::fence_after_sync();
-                const uint32_t d = tmem + (uint32_t)(g * 256);
-                const uint32_t bb = core_u32 + ch * chunk_bytes;
-                for (int ks = 0; ks < kst; ++ks) {
-                    const uint32_t ko = ks * 256;
-                    const uint64_t ad = tc::make_desc(abase + ko, 128, SBO_A);
-                    const uint64_t bd = tc::make_desc(bb + ko, 128, SBO_B);
-                    if (MODE == eTF32) {
-                        tc::mma_tf32(d, ad, bd, idesc, ks > 0);
-                    } else {
-                        tc::mma_bf16(d, ad, bd, idesc, ks > 0);
-                        if (MODE == eBF16X3) {
-                            const uint64_t al = tc::make_desc(abase + abytes + ko, 128, SBO_A);
-                            const uint64_t bl = tc::make_desc(bb + nch * chunk_bytes + ko, 128, SBO_B);
-                            tc::mma_bf16(d, ad, bl, idesc, 1u);
-                            tc::mma_bf16(d, al, bd, idesc, 1u);
+                for (int ch = 0; ch < nch; ++ch) {
+                    if (!tc::mbar_wait(&d_empty[g], (uint32_t)(mcc[g] & 1) ^ 1u, kWaitLimitE)) {
+                        atomicOr(err, 8);
+                        dead = true;
+                        break;
+                    }
+                    tc::fence_after_sync();
+                    const uint32_t d = tmem + (uint32_t)(g * 256);
+                    const uint32_t bb = core_u32 + ch * chunk_bytes;
+                    for (int ks = 0; ks < kst; ++ks) {
+                        const uint32_t ko = ks * 256;
+                        const uint64_t ad = tc::make_desc(abase + ko, 128, SBO);
+                        const uint64_t bd = tc::make_desc(bb + ko, 128, SBO);
+                        if (MODE == eTF32) {
+                            tc::mma_tf32(d, ad, bd, idesc, ks > 0);
+                        } else {
+                            tc::mma_bf16(d, ad, bd, idesc, ks > 0);
+                            if (MODE == eBF16X3) {
+                                const uint64_t al = tc::make_desc(abase + abytes + ko, 128, SBO);
+                                const uint64_t bl = tc::make_desc(bb + nch * chunk_bytes + ko, 128, SBO);
+                                tc::mma_bf16(d, ad, bl, idesc, 1u);
+                                tc::mma_bf16(d, al, bd, idesc, 1u);
+                            }
                         }
                     }
+                    tc::mma_commit(&d_full[g]);
+                    issued = true;
+                    ++mcc[g];
                 }
-                tc::mma_commit(&d_full[g]);
-                issued = true;
-                ++cc[g];
+                if (dead) break;
+                tc::mma_commit(&a_empty[g]);
+                ++mlt[g];
             }
-            if (dead) break;
-            tc::mma_commit(&a_empty[g]);
-            ++lt[g];
         }
-        if (issued) {
-            tc::mma_commit(drain);
-            if (!tc::mbar_wait(drain, 0u, kWaitLimitE)) atomicOr(err, 16);
-        }
+    }
+    if (warp == kWorkers && lane == 0 && issued) {
+        tc::mma_commit(drain);
+        if (!tc::mbar_wait(drain, 0u, kWaitLimitE)) atomicOr(err, 16);
     }
     tc::fence_before_sync();
     __syncthreads();
@@ -363,6 +393,181 @@ struct EvalErr {
     DevBuf flag;
 };
 EvalErr g_eval_err[64];
+
+struct HostItem {
+    fst_model* m;
+    const float* xyz;
+    long long n;
+    float* out;
+};
+
+int bucket8(int r) { return r <= 8 ? 8 : r <= 16 ? 16 : r <= 24 ? 24 : 32; }
+
+// One size class of a batch: instances sharing the (rank, r3) padding, one launch.
+struct Bucket {
+    int mode = 0, r3p = 8, rm = 8;
+    std::vector<TcItem> items;
+    std::vector<TcUnit> units;
+    std::vector<int> cta_start;
+    int core_max = 0, kb_max = 32, grid = 1;
+    size_t smem = 0;
+    size_t items_off = 0, units_off = 0, cta_off = 0, bytes = 0;   // device image layout
+};
+
+fst_status build_buckets(const std::vector<HostItem>& hitems, int mode, std::vector<Bucket>& out) {
+    out.clear();
+    const int ES = mode == eTF32 ? 4 : 2;
+    const int PARTS = mode == eBF16X3 ? 2 : 1;
+    const int sms = sm_count();
+    std::vector<std::vector<size_t>> members;
+    std::vector<std::pair<int, int>> keys;
+    for (size_t i = 0; i < hitems.size(); ++i) {
+        const fst_model* m = hitems[i].m;
+        const int rm = bucket8(std::max(m->r[0], std::max(m->r[1], m->r[2])));
+        const int r3p = std::min(bucket8(m->r[2]), rm);
+        size_t b = 0;
+        while (b < keys.size() && keys[b] != std::make_pair(rm, r3p)) ++b;
+        if (b == keys.size()) {
+            keys.push_back({rm, r3p});
+            members.emplace_back();
+        }
+        members[b].push_back(i);
+    }
+    for (size_t b = 0; b < keys.size(); ++b) {
+        Bucket B;
+        B.mode = mode;
+        B.rm = keys[b].first;
+        B.r3p = keys[b].second;
+        std::vector<double> tile_cost;
+        int tab_max = 0;
+        for (size_t idx : members[b]) {
+            fst_model* m = hitems[idx].m;
+            FST_TRY(prepare_core_image(m, mode, B.r3p));
+            const CoreImage ci = core_image_shape(m, mode, B.r3p);
+            TcItem it;
+            it.a = make_args<float>(m);
+            bind(it.a, m);
+            it.core_img = static_cast<const unsigned char*>(m->tc_core);
+            it.img_bytes = (int)ci.bytes;
+            it.nchunks = ci.nchunks;
+            it.kp = ci.kp;
+            it.tab_bytes = (int)((2 * (size_t)it.a.pm + (size_t)(it.a.pe[0] + it.a.pe[1] + it.a.pe[2]) * B.rm) * 4 +
+                                 3 * it.a.pm);
+            it.xyz = hitems[idx].xyz;
+            it.out = hitems[idx].out;
+            it.n = hitems[idx].n;
+            B.core_max = std::max(B.core_max, (int)((ci.bytes + 1023) & ~(size_t)1023));
+            B.kb_max = std::max(B.kb_max, ci.kb);
+            tab_max = std::max(tab_max, it.tab_bytes);
+            // per-tile cost: factor values (CUDA cores) + contraction and epilogue per chunk
+            tile_cost.push_back(1.0 + (double)B.rm * (it.a.pe[0] + it.a.pe[1] + it.a.pe[2]) / 64.0 +
+                                (double)ci.nchunks * ci.ncp * (PARTS == 2 ? 1.5 : 1.0) / 64.0);
+            B.items.push_back(it);
+        }
+        B.smem = 1024 + kBarBytes + B.core_max + (size_t)kGroups * PARTS * 128 * B.kb_max + tab_max + 16;
+        if (B.smem > 227 * 1024) {
+            set_error("model too large for the tensor-core evaluator (%zu bytes of shared memory)", B.smem);
+            return FST_EUNSUPPORTED;
+        }
+        long long total_tiles = 0;
+        double total_cost = 0;
+        for (size_t i = 0; i < B.items.size(); ++i) {
+            const long long nt = (B.items[i].n + 127) / 128;
+            total_tiles += nt;
+            total_cost += nt * tile_cost[i];
+        }
+        if (total_tiles == 0) continue;
+        long long run = (total_tiles + 4LL * sms - 1) / (4LL * sms);
+        if (run < 2) run = 2;
+        std::vector<double> unit_cost;
+        for (size_t i = 0; i < B.items.size(); ++i) {
+            const long long nt = (B.items[i].n + 127) / 128;
+            for (long long t0 = 0; t0 < nt; t0 += run) {
+                TcUnit u;
+                u.item = (int)i;
+                u.pad = 0;
+                u.tile0 = t0;
+                u.ntiles = std::min(run, nt - t0);
+                B.units.push_back(u);
+                unit_cost.push_back(u.ntiles * tile_cost[i]);
+            }
+        }
+        B.grid = (int)std::min<long long>(sms, (long long)B.units.size());
+        B.cta_start.assign(B.grid + 1, (int)B.units.size());
+        B.cta_start[0] = 0;
+        double acc = 0;
+        int c = 1;
+        for (size_t u = 0; u < B.units.size() && c < B.grid; ++u) {
+            acc += unit_cost[u];
+            while (c < B.grid && acc >= total_cost * c / B.grid) B.cta_start[c++] = (int)u + 1;
+        }
+        for (; c < B.grid; ++c) B.cta_start[c] = (int)B.units.size();
+        B.items_off = 0;
+        B.units_off = (B.items.size() * sizeof(TcItem) + 15) & ~(size_t)15;
+        B.cta_off = (B.units_off + B.units.size() * sizeof(TcUnit) + 15) & ~(size_t)15;
+        B.bytes = B.cta_off + B.cta_start.size() * sizeof(int);
+        out.push_back(std::move(B));
+    }
+    return FST_OK;
+}
+
+void bucket_image(const Bucket& B, std::vector<unsigned char>& img) {
+    img.assign(B.bytes, 0);
+    memcpy(img.data() + B.items_off, B.items.data(), B.items.size() * sizeof(TcItem));
+    memcpy(img.data() + B.units_off, B.units.data(), B.units.size() * sizeof(TcUnit));
+    memcpy(img.data() + B.cta_off, B.cta_start.data(), B.cta_start.size() * sizeof(int));
+}
+
+struct Overrides {
+    const float* xyz = nullptr;
+    float* out = nullptr;
+};
+
+template <int MODE, int R3P, int RM>
+fst_status launch_bucket_t(const Bucket& B, const unsigned char* dimg, int* err, cudaStream_t s, Overrides ov) {
+    auto kern = eval_tc_kernel<MODE, R3P, RM>;
+    FST_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)B.smem));
+    kern<<<B.grid, kThreadsE, B.smem, s>>>(reinterpret_cast<const TcItem*>(dimg + B.items_off),
+                                           reinterpret_cast<const TcUnit*>(dimg + B.units_off),
+                                           reinterpret_cast<const int*>(dimg + B.cta_off), B.core_max, B.kb_max,
+                                           ov.xyz, ov.out, err);
+    FST_CHECK_LAUNCH();
+    return FST_OK;
+}
+
+template <int MODE>
+fst_status launch_bucket_m(const Bucket& B, const unsigned char* dimg, int* err, cudaStream_t s, Overrides ov) {
+#define FST_EB(R3, RMV) \
+    if (B.r3p == R3 && B.rm == RMV) return launch_bucket_t<MODE, R3, RMV>(B, dimg, err, s, ov);
+    FST_EB(8, 8) FST_EB(8, 16) FST_EB(16, 16) FST_EB(8, 24) FST_EB(16, 24) FST_EB(24, 24)
+    FST_EB(8, 32) FST_EB(16, 32) FST_EB(24, 32) FST_EB(32, 32)
+#undef FST_EB
+    set_error("no evaluator instance for r3 padding %d, rank bound %d", B.r3p, B.rm);
+    return FST_EUNSUPPORTED;
+}
+
+fst_status launch_bucket(const Bucket& B, const unsigned char* dimg, int* err, cudaStream_t s, Overrides ov) {
+    switch (B.mode) {
+        case eTF32: return launch_bucket_m<eTF32>(B, dimg, err, s, ov);
+        case eBF16: return launch_bucket_m<eBF16>(B, dimg, err, s, ov);
+        default: return launch_bucket_m<eBF16X3>(B, dimg, err, s, ov);
+    }
+}
+
+int mode_of(fst_prec p) { return p == FST_TF32 ? eTF32 : p == FST_BF16 ? eBF16 : eBF16X3; }
+
+fst_status error_word(int** out) {
+    int dev = 0;
+    FST_CUDA(cudaGetDevice(&dev));
+    EvalErr& ee = g_eval_err[dev & 63];
+    std::lock_guard<std::mutex> lk(ee.mu);
+    if (!ee.flag.ptr) {
+        FST_TRY(ee.flag.ensure(sizeof(int)));
+        FST_CUDA(cudaMemset(ee.flag.ptr, 0, sizeof(int)));
+    }
+    *out = ee.flag.as<int>();
+    return FST_OK;
+}
 
 }  // namespace
 
@@ -381,84 +586,137 @@ fst_status prepare_core_image(fst_model* m, int mode, int r3p) {
     }
     FST_CUDA(cudaMemcpy(m->tc_core, img.data(), img.size(), cudaMemcpyHostToDevice));
     m->tc_core_kind = kind;
+    ++m->tc_core_kind_version;
     return FST_OK;
 }
 
-namespace {
+}  // namespace fst
 
-template <int MODE, int R3P, int RM>
-fst_status launch_eval_tc(fst_model* m, const float* xyz, int64_t n, float* out, cudaStream_t s, int* err) {
-    const CoreImage ci = core_image_shape(m, MODE, R3P);
-    FST_TRY(prepare_core_image(m, MODE, R3P));
-    EvalTcArgs P;
-    P.a = make_args<float>(m);
-    bind(P.a, m);
-    P.core_img = static_cast<const unsigned char*>(m->tc_core);
-    P.img_bytes = (int)ci.bytes;
-    P.nchunks = ci.nchunks;
-    P.kp = ci.kp;
-    P.err_code = 0;
-    const int ES = MODE == eTF32 ? 4 : 2;
-    const int PARTS = MODE == eBF16X3 ? 2 : 1;
-    const size_t smem = 1024 + (((size_t)ci.bytes + 1023) & ~(size_t)1023) + (size_t)kGroups * PARTS * 128 * ci.kp * ES +
-                        (2 * (size_t)P.a.pm + (size_t)(P.a.pe[0] + P.a.pe[1] + P.a.pe[2]) * RM) * 4 + 3 * P.a.pm +
-                        16 + 8 * (4 * kGroups + 2);
-    if (smem > 227 * 1024) {
-        set_error("model too large for the tensor-core evaluator (%zu bytes of shared memory)", smem);
-        return FST_EUNSUPPORTED;
+// A prepared batch: work lists of every size class uploaded once.
+struct fst_eval_plan {
+    int device = 0;
+    std::vector<fst::Bucket> buckets;
+    unsigned char* dimg = nullptr;
+    std::vector<size_t> offs;
+};
+
+namespace fst {
+
+fst_status plan_build(const std::vector<HostItem>& items, fst_prec prec, fst_eval_plan** out) {
+    std::unique_ptr<fst_eval_plan> P(new fst_eval_plan());
+    FST_CUDA(cudaGetDevice(&P->device));
+    FST_TRY(build_buckets(items, mode_of(prec), P->buckets));
+    size_t total = 0;
+    for (const Bucket& B : P->buckets) {
+        P->offs.push_back(total);
+        total += (B.bytes + 255) & ~(size_t)255;
     }
-    auto kern = eval_tc_kernel<MODE, R3P, RM>;
-    FST_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    const long long ntiles = (n + 127) / 128;
-    long long grid = sm_count();
-    if (ntiles < grid) grid = ntiles;
-    kern<<<(unsigned)grid, kThreadsE, smem, s>>>(P, xyz, n, out, err);
-    FST_CHECK_LAUNCH();
+    if (total) {
+        FST_CUDA(cudaMalloc(&P->dimg, total));
+        std::vector<unsigned char> img;
+        for (size_t b = 0; b < P->buckets.size(); ++b) {
+            bucket_image(P->buckets[b], img);
+            FST_CUDA(cudaMemcpy(P->dimg + P->offs[b], img.data(), img.size(), cudaMemcpyHostToDevice));
+        }
+    }
+    *out = P.release();
     return FST_OK;
 }
 
-template <int MODE>
-fst_status dispatch_r3(fst_model* m, const float* xyz, int64_t n, float* out, cudaStream_t s, int* err) {
-    int rmax = m->r[0] > m->r[1] ? m->r[0] : m->r[1];
-    rmax = m->r[2] > rmax ? m->r[2] : rmax;
-    const int r3 = m->r[2];
-    // RM bounds all three ranks (register arrays); R3P pads r3 for the chunk layout
-    if (rmax <= 8) return launch_eval_tc<MODE, 8, 8>(m, xyz, n, out, s, err);
-    if (rmax <= 16) return r3 <= 8 ? launch_eval_tc<MODE, 8, 16>(m, xyz, n, out, s, err)
-                                   : launch_eval_tc<MODE, 16, 16>(m, xyz, n, out, s, err);
-    if (rmax <= 24) return r3 <= 8    ? launch_eval_tc<MODE, 8, 24>(m, xyz, n, out, s, err)
-                           : r3 <= 16 ? launch_eval_tc<MODE, 16, 24>(m, xyz, n, out, s, err)
-                                      : launch_eval_tc<MODE, 24, 24>(m, xyz, n, out, s, err);
-    return r3 <= 8    ? launch_eval_tc<MODE, 8, 32>(m, xyz, n, out, s, err)
-           : r3 <= 16 ? launch_eval_tc<MODE, 16, 32>(m, xyz, n, out, s, err)
-           : r3 <= 24 ? launch_eval_tc<MODE, 24, 32>(m, xyz, n, out, s, err)
-                      : launch_eval_tc<MODE, 32, 32>(m, xyz, n, out, s, err);
+fst_status plan_run(const fst_eval_plan* P, cudaStream_t s, Overrides ov = Overrides()) {
+    int* err = nullptr;
+    FST_TRY(error_word(&err));
+    for (size_t b = 0; b < P->buckets.size(); ++b)
+        FST_TRY(launch_bucket(P->buckets[b], P->dimg + P->offs[b], err, s, ov));
+    return FST_OK;
 }
 
-}  // namespace
+void plan_free(fst_eval_plan* P) {
+    if (!P) return;
+    if (P->dimg) cudaFree(P->dimg);   // cudaFree waits for work in flight on the device
+    delete P;
+}
+
+// Asynchronous batch: the size classes are built on the host, their work lists staged in a
+// pinned buffer and copied to a device slot of a per-device ring; a slot is reused only
+// after the launches that read it have finished (its event).  Buffers only grow, so a
+// steady stream of batches allocates nothing.
+struct BatchRing {
+    std::mutex mu;
+    DevBuf dev[8];
+    unsigned char* host[8] = {};
+    size_t host_bytes[8] = {};
+    cudaEvent_t done[8] = {};
+    int next = 0;
+};
+BatchRing g_batch_ring[64];
+
+fst_status eval_tc_batch(const std::vector<HostItem>& items, fst_prec prec, cudaStream_t s) {
+    std::vector<Bucket> buckets;
+    FST_TRY(build_buckets(items, mode_of(prec), buckets));
+    if (buckets.empty()) return FST_OK;
+    std::vector<size_t> offs;
+    size_t total = 0;
+    for (const Bucket& B : buckets) {
+        offs.push_back(total);
+        total += (B.bytes + 255) & ~(size_t)255;
+    }
+    int dev = 0;
+    FST_CUDA(cudaGetDevice(&dev));
+    BatchRing& ring = g_batch_ring[dev & 63];
+    std::lock_guard<std::mutex> lk(ring.mu);
+    const int slot = ring.next;
+    ring.next = (ring.next + 1) % 8;
+    if (ring.done[slot]) FST_CUDA(cudaEventSynchronize(ring.done[slot]));
+    else FST_CUDA(cudaEventCreateWithFlags(&ring.done[slot], cudaEventDisableTiming));
+    FST_TRY(ring.dev[slot].ensure(total));
+    if (ring.host_bytes[slot] < total) {
+        if (ring.host[slot]) cudaFreeHost(ring.host[slot]);
+        ring.host[slot] = nullptr;
+        ring.host_bytes[slot] = 0;
+        FST_CUDA(cudaMallocHost(&ring.host[slot], total));
+        ring.host_bytes[slot] = total;
+    }
+    std::vector<unsigned char> img;
+    for (size_t b = 0; b < buckets.size(); ++b) {
+        bucket_image(buckets[b], img);
+        memcpy(ring.host[slot] + offs[b], img.data(), img.size());
+    }
+    unsigned char* d = ring.dev[slot].as<unsigned char>();
+    FST_CUDA(cudaMemcpyAsync(d, ring.host[slot], total, cudaMemcpyHostToDevice, s));
+    int* err = nullptr;
+    FST_TRY(error_word(&err));
+    for (size_t b = 0; b < buckets.size(); ++b) FST_TRY(launch_bucket(buckets[b], d + offs[b], err, s, Overrides()));
+    FST_CUDA(cudaEventRecord(ring.done[slot], s));
+    return FST_OK;
+}
 
 fst_status eval_tc_launch(fst_model* m, const float* xyz, int64_t n, float* out, fst_prec prec, cudaStream_t s) {
     if (n == 0) return FST_OK;
-    int dev = 0;
-    FST_CUDA(cudaGetDevice(&dev));
-    EvalErr& ee = g_eval_err[dev & 63];
     std::lock_guard<std::mutex> lk(m->mu);
-    {
-        std::lock_guard<std::mutex> lk2(ee.mu);
-        if (!ee.flag.ptr) {
-            FST_TRY(ee.flag.ensure(sizeof(int)));
-            FST_CUDA(cudaMemset(ee.flag.ptr, 0, sizeof(int)));
+    // single instance: the work list depends on n, the precision and the core image only; it
+    // is kept in the model, and the point and output buffers are passed at launch
+    const int mode = mode_of(prec);
+    const int rm = bucket8(std::max(m->r[0], std::max(m->r[1], m->r[2])));
+    FST_TRY(prepare_core_image(m, mode, std::min(bucket8(m->r[2]), rm)));
+    fst_eval_plan*& P = m->eval_plan;
+    if (!P || m->eval_plan_n != (long long)n || m->eval_plan_prec != (int)prec ||
+        m->eval_plan_core != m->tc_core_kind_version) {
+        if (P) {
+            FST_CUDA(cudaStreamSynchronize(s));
+            plan_free(P);
+            P = nullptr;
         }
+        std::vector<HostItem> one{HostItem{m, xyz, (long long)n, out}};
+        FST_TRY(plan_build(one, prec, &P));
+        m->eval_plan_n = (long long)n;
+        m->eval_plan_prec = (int)prec;
+        m->eval_plan_core = m->tc_core_kind_version;
     }
-    int* err = ee.flag.as<int>();
-    switch (prec) {
-        case FST_TF32: return dispatch_r3<eTF32>(m, xyz, n, out, s, err);
-        case FST_BF16: return dispatch_r3<eBF16>(m, xyz, n, out, s, err);
-        case FST_BF16X3: return dispatch_r3<eBF16X3>(m, xyz, n, out, s, err);
-        default:
-            set_error("tensor-core evaluation takes TF32, BF16 or BF16X3");
-            return FST_EINVAL;
-    }
+    Overrides ov;
+    ov.xyz = xyz;
+    ov.out = out;
+    return plan_run(P, s, ov);
 }
 
 // Device error word of the tensor-core evaluator (bounded waits that expired), read and
@@ -503,3 +761,66 @@ extern "C" fst_status fst_eval_prepare(fst_model* m, fst_prec prec) {
     (void)s;
     return fst::prepare_core_image(m, mode, r3p);
 }
+
+extern "C" fst_status fst_eval_batched(const fst_eval_item* items, int32_t count, fst_prec prec,
+                                       fst_stream stream) {
+    using namespace fst;
+    FST_REQUIRE(count >= 0 && (count == 0 || items != nullptr), "items is NULL");
+    int dev = 0;
+    FST_CUDA(cudaGetDevice(&dev));
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<HostItem> work;
+    for (int i = 0; i < count; ++i) {
+        const fst_eval_item& it = items[i];
+        FST_REQUIRE(it.model != nullptr && it.n >= 0, "item %d: model NULL or n < 0", i);
+        if (it.n == 0) continue;
+        FST_REQUIRE(it.xyz && it.out, "item %d: xyz or out is NULL", i);
+        FST_REQUIRE(it.model->device == dev, "item %d: model lives on another device", i);
+        FST_REQUIRE(pointer_device(it.xyz) == dev && pointer_device(it.out) == dev,
+                    "item %d: xyz and out must be device memory of device %d", i, dev);
+        work.push_back(HostItem{const_cast<fst_model*>(it.model), it.xyz, (long long)it.n, it.out});
+    }
+    if (work.empty()) return FST_OK;
+    if (prec == FST_FP32) {
+        for (const HostItem& h : work) FST_TRY(eval_simt_launch<float>(h.m, h.xyz, h.n, h.out, s));
+        return FST_OK;
+    }
+    FST_REQUIRE(prec == FST_TF32 || prec == FST_BF16 || prec == FST_BF16X3,
+                "fst_eval_batched takes FP32, TF32, BF16 or BF16X3");
+    return eval_tc_batch(work, prec, s);
+}
+
+extern "C" fst_status fst_eval_plan_create(const fst_eval_item* items, int32_t count, fst_prec prec,
+                                           fst_eval_plan** out) {
+    using namespace fst;
+    FST_REQUIRE(out != nullptr, "out is NULL");
+    *out = nullptr;
+    FST_REQUIRE(count >= 0 && (count == 0 || items != nullptr), "items is NULL");
+    FST_REQUIRE(prec == FST_TF32 || prec == FST_BF16 || prec == FST_BF16X3,
+                "evaluation plans take TF32, BF16 or BF16X3");
+    int dev = 0;
+    FST_CUDA(cudaGetDevice(&dev));
+    std::vector<HostItem> work;
+    for (int i = 0; i < count; ++i) {
+        const fst_eval_item& it = items[i];
+        FST_REQUIRE(it.model != nullptr && it.n >= 0, "item %d: model NULL or n < 0", i);
+        if (it.n == 0) continue;
+        FST_REQUIRE(it.xyz && it.out, "item %d: xyz or out is NULL", i);
+        FST_REQUIRE(it.model->device == dev, "item %d: model lives on another device", i);
+        FST_REQUIRE(pointer_device(it.xyz) == dev && pointer_device(it.out) == dev,
+                    "item %d: xyz and out must be device memory of device %d", i, dev);
+        work.push_back(HostItem{const_cast<fst_model*>(it.model), it.xyz, (long long)it.n, it.out});
+    }
+    return plan_build(work, prec, out);
+}
+
+extern "C" fst_status fst_eval_plan_run(const fst_eval_plan* plan, fst_stream stream) {
+    using namespace fst;
+    FST_REQUIRE(plan != nullptr, "plan is NULL");
+    int dev = 0;
+    FST_CUDA(cudaGetDevice(&dev));
+    FST_REQUIRE(dev == plan->device, "plan was made on device %d, current device is %d", plan->device, dev);
+    return plan_run(plan, (cudaStream_t)stream);
+}
+
+extern "C" void fst_eval_plan_free(fst_eval_plan* plan) { fst::plan_free(plan); }

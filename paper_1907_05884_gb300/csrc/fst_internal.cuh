@@ -64,6 +64,8 @@ struct RefitScratch {
 
 }  // namespace fst
 
+struct fst_eval_plan;
+
 struct fst_model {
     int device = 0;
     int r[3] = {0, 0, 0};
@@ -84,6 +86,11 @@ struct fst_model {
     void* tc_core = nullptr;
     size_t tc_core_bytes = 0;
     int tc_core_kind = -1;
+    long long tc_core_kind_version = 0;
+    // cached single-instance tensor-core work list (eval_tc.cu)
+    fst_eval_plan* eval_plan = nullptr;
+    long long eval_plan_n = -1, eval_plan_core = -1;
+    int eval_plan_prec = -1;
 
     fst::RefitScratch rs;
     std::mutex mu;
@@ -92,6 +99,8 @@ struct fst_model {
 };
 
 namespace fst {
+
+void plan_free(fst_eval_plan* p);
 
 // Device upload of the derived layouts after the host copy changed.
 fst_status model_upload_core(fst_model* m);

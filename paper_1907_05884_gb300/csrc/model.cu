@@ -90,6 +90,8 @@ static void free_device(fst_model* m) {
     if (m->alpha64) cudaFree(m->alpha64);
     if (m->alpha32) cudaFree(m->alpha32);
     if (m->tc_core) cudaFree(m->tc_core);
+    if (m->eval_plan) plan_free(m->eval_plan);
+    m->eval_plan = nullptr;
     m->alpha64 = nullptr;
     m->alpha32 = nullptr;
     m->tc_core = nullptr;

@@ -17,7 +17,11 @@ import numpy as np
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("what", choices=["gram", "eval", "refit", "sample"])
+    ap.add_argument("what", choices=["gram", "eval", "refit", "sample", "batch", "serve"])
+    ap.add_argument("--queries", type=int, default=2000)
+    ap.add_argument("--q-lo", type=float, default=1e5)
+    ap.add_argument("--q-hi", type=float, default=2e6)
+    ap.add_argument("--instances", type=int, default=512)
     ap.add_argument("--prec", default="bf16")
     ap.add_argument("--m", type=int, default=16384)
     ap.add_argument("--n", type=int, default=1 << 22)
@@ -31,6 +35,10 @@ def main():
     build.build()
     from paper_1907_05884_gb300 import fst, synth
 
+    if args.what == "batch":
+        return batch(args)
+    if args.what == "serve":
+        return serve_loads(args)
     model = synth.random_model(tuple(args.ranks), (args.degree,) * 3, seed=4, orthonormal=True)
     M = fst.Model(model)
     Q = max(args.n, 2 * args.m)
@@ -57,6 +65,78 @@ def main():
         e1.record()
         torch.cuda.synchronize()
         print(f"{args.what} prec={args.prec} m={args.m} n={args.n} ms={e0.elapsed_time(e1):.3f}{extra}", flush=True)
+
+
+def batch(args):
+    """Batched-evaluation workload: instances (fields x timesteps) with ranks U{4..24} per mode
+    and point counts log-uniform in [1e5, 2e6]; one fst_eval_batched launch against one
+    fst_eval launch per instance."""
+    import torch
+    from paper_1907_05884_gb300 import fst, synth
+    table = synth.batch_instances(n_fields=max(1, args.instances // 8), n_steps=8, q_lo=args.q_lo,
+                                  q_hi=args.q_hi)[:args.instances]
+    models, xs, outs = [], [], []
+    for k, inst in enumerate(table):
+        m = synth.random_model(inst["r"], (args.degree,) * 3, seed=inst["seed"] % (1 << 31), density=0.6)
+        models.append(fst.Model(m))
+        x = torch.rand((3, inst["Q"]), device="cuda", generator=None) * 2 - 1
+        xs.append(x.contiguous())
+        outs.append(torch.empty(inst["Q"], device="cuda"))
+        models[-1].prepare(args.prec)
+    total = sum(x.shape[1] for x in xs)
+    plan = fst.EvalPlan(models, xs, outs, prec=args.prec)
+    graph = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        plan.run()
+    torch.cuda.current_stream().wait_stream(side)
+    with torch.cuda.graph(graph):
+        plan.run()
+    for Mi, x, o in zip(models, xs, outs):       # single-instance work lists built before timing
+        Mi.eval(x, prec=args.prec, out=o)
+    torch.cuda.synchronize()
+    for r in range(args.reps):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        ev[0].record()
+        plan.run()
+        ev[1].record()
+        graph.replay()
+        ev[2].record()
+        for Mi, x, o in zip(models, xs, outs):
+            Mi.eval(x, prec=args.prec, out=o)
+        ev[3].record()
+        torch.cuda.synchronize()
+        tp, tg, ts = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2]), ev[2].elapsed_time(ev[3])
+        print(f"batch instances={len(models)} points={total} prec={args.prec} "
+              f"plan_ms={tp:.3f} ({total / tp / 1e3:.1f} Mpoints/s) graph_ms={tg:.3f} "
+              f"({total / tg / 1e3:.1f} Mpoints/s) per_instance_ms={ts:.3f} ({total / ts / 1e3:.1f} Mpoints/s)",
+              flush=True)
+
+
+def serve_loads(args):
+    """Serving workload: 64 resident fields (ranks <= 24, degree 31); Poisson queries, half
+    slices (side 512..2048), half point sets (1e3..1e7 points); precision 50/50 FP32/BF16.
+    Saturation throughput from a closed run, then offered loads of 25/50/75/90% of it."""
+    import json
+    import torch
+    from paper_1907_05884_gb300 import fst, serve, synth
+    rng = np.random.default_rng(11)
+    models = [fst.Model(synth.random_model(tuple(int(v) for v in rng.integers(4, 25, size=3)),
+                                           (args.degree,) * 3, seed=200 + i, density=0.6)) for i in range(64)]
+    pool = torch.from_numpy(synth.points(10_000_000, seed=12, clustered=0.3).astype(np.float32)).pin_memory()
+    srv = serve.FieldServer(models, pool, mem_budget=8 << 30, streams=2)
+    srv.prepare(("bf16",))
+    closed = serve.make_queries(min(args.queries, 400), 64, rate_qps=0.0, seed=13)
+    srv.run(closed[:50])
+    sat = serve.latency_stats(srv.run(closed))
+    print(json.dumps({"load": "closed", **sat}), flush=True)
+    mean_pts = np.mean([q.npoints() for q in closed])
+    for frac in (0.25, 0.5, 0.75, 0.9):
+        rate = frac * sat["Mpoints_s"] * 1e6 / mean_pts
+        qs = serve.make_queries(args.queries, 64, rate_qps=rate, seed=14 + int(frac * 100))
+        st = serve.latency_stats(srv.run(qs))
+        print(json.dumps({"load": frac, "rate_qps": rate, **st}), flush=True)
 
 
 if __name__ == "__main__":

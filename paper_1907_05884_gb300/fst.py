@@ -37,6 +37,10 @@ class ModelDesc(C.Structure):
     ]
 
 
+class EvalItem(C.Structure):
+    _fields_ = [("model", C.c_void_p), ("xyz", C.c_void_p), ("n", C.c_int64), ("out", C.c_void_p)]
+
+
 class RefitOpts(C.Structure):
     _fields_ = [("max_refine", C.c_int32), ("refine_tol", C.c_double), ("fp64_cholesky", C.c_int32)]
 
@@ -68,6 +72,11 @@ def _load():
         "fst_eval": (I32, [P, P, I64, P, I32, P]),
         "fst_eval_f64": (I32, [P, P, I64, P, P]),
         "fst_eval_prepare": (I32, [P, I32]),
+        "fst_eval_batched": (I32, [P, I32, I32, P]),
+        "fst_slice_points": (I32, [I32, C.c_double, P, P, I32, I32, P, P]),
+        "fst_eval_plan_create": (I32, [P, I32, I32, P]),
+        "fst_eval_plan_run": (I32, [P, P]),
+        "fst_eval_plan_free": (None, [P]),
         "fst_eval_check": (I32, [P]),
         "fst_sample_rows": (I32, [U64, I64, I64, P, P]),
         "fst_sample_rows_static": (I32, [U64, I64, I64, P, P]),
@@ -248,6 +257,57 @@ def sample_rows(seed: int, Q: int, m: int, device="cuda", stream=None):
     _check(lib.fst_sample_rows(C.c_uint64(seed & 0xFFFFFFFFFFFFFFFF), int(Q), m, _dptr(idx),
                                _stream(stream)))
     return idx
+
+
+def eval_batched(models, xyzs, outs=None, prec: str = "bf16x3", stream=None):
+    """Evaluate model i at points xyzs[i] (CUDA (3, n_i) float32) for all i in one launch."""
+    import torch
+    if outs is None:
+        outs = [torch.empty(x.shape[1], dtype=torch.float32, device=x.device) for x in xyzs]
+    arr = (EvalItem * len(models))()
+    for i, (m, x, o) in enumerate(zip(models, xyzs, outs)):
+        assert x.is_cuda and x.dtype == torch.float32 and x.is_contiguous() and x.shape[0] == 3
+        arr[i] = EvalItem(m.handle.value, x.data_ptr(), x.shape[1], o.data_ptr())
+    _check(lib.fst_eval_batched(arr, len(models), PREC[prec], _stream(stream)))
+    return outs
+
+
+class EvalPlan:
+    """A prepared batch: plan.run(stream) launches only (capturable in a CUDA graph)."""
+
+    def __init__(self, models, xyzs, outs, prec: str = "bf16x3"):
+        self._keep = (list(models), list(xyzs), list(outs))
+        arr = (EvalItem * len(models))()
+        for i, (m, x, o) in enumerate(zip(models, xyzs, outs)):
+            arr[i] = EvalItem(m.handle.value, x.data_ptr(), x.shape[1], o.data_ptr())
+        self._h = C.c_void_p()
+        _check(lib.fst_eval_plan_create(arr, len(models), PREC[prec], C.byref(self._h)))
+
+    def run(self, stream=None):
+        _check(lib.fst_eval_plan_run(self._h, _stream(stream)))
+
+    def free(self):
+        if self._h:
+            lib.fst_eval_plan_free(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def slice_points(axis: int, value: float, lo, hi, res0: int, res1: int, out=None, device="cuda", stream=None):
+    """Points of the slice y_axis = value as a CUDA (3, res0*res1) float32 tensor."""
+    import torch
+    if out is None:
+        out = torch.empty((3, res0 * res1), dtype=torch.float32, device=device)
+    lo_a = (C.c_double * 3)(*[float(v) for v in lo])
+    hi_a = (C.c_double * 3)(*[float(v) for v in hi])
+    _check(lib.fst_slice_points(int(axis), float(value), lo_a, hi_a, int(res0), int(res1), _dptr(out),
+                                _stream(stream)))
+    return out
 
 
 def eval_check(stream=None):
