@@ -235,13 +235,27 @@ eval_tc_kernel(const TcItem* __restrict__ items, const TcUnit* __restrict__ unit
             // -------------------------------------------------------------- workers
             const int g = warp >> 2, sub = warp & 3, row = sub * 32 + lane;   // TMEM lane = row
             unsigned char* A = abuf + g * PARTS * 128 * kb_max;
+            const float* X = xyz_ov ? xyz_ov : I.xyz;
+            // coordinates of this group's next tile are loaded one tile ahead
+            float nxt[3];
+            {
+                const long long q = (U.tile0 + g) * 128 + row;
+                const bool ok = U.tile0 + g < U.tile0 + U.ntiles && q < n;
+#pragma unroll
+                for (int k = 0; k < 3; ++k) nxt[k] = ok ? X[k * n + q] : 0.f;
+            }
             for (long long t = U.tile0 + g; t < U.tile0 + U.ntiles; t += kGroups, ++lt) {
                 const long long q = t * 128 + row;
                 const bool ok = q < n;
                 float tt[3][1];
 #pragma unroll
-                const float* X = xyz_ov ? xyz_ov : I.xyz;
-                for (int k = 0; k < 3; ++k) tt[k][0] = fmaf(ok ? X[k * n + q] : 0.f, a.sc[k], a.of[k]);
+                for (int k = 0; k < 3; ++k) tt[k][0] = fmaf(nxt[k], a.sc[k], a.of[k]);
+                {
+                    const long long q2 = q + kGroups * 128;
+                    const bool ok2 = t + kGroups < U.tile0 + U.ntiles && q2 < n;
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) nxt[k] = ok2 ? X[k * n + q2] : 0.f;
+                }
                 float w[1][RM], u2[RM], u3[RM];
                 factor_values<float, RM, 1>(tt[1], Ws1, mk + a.pm, a.pe[1], ra, rb, w);
 #pragma unroll

@@ -27,7 +27,8 @@ namespace fst {
 
 namespace {
 
-constexpr int kProducerWarps = 8;
+constexpr int kProducerWarps = 16;
+constexpr int kEpilogueWarps = 8;       // producer warps 0-7 also drain the accumulators
 constexpr int kThreads = (kProducerWarps + 1) * 32;
 constexpr int kStages = 2;
 constexpr int kTile = 256;              // super-tile edge
@@ -40,17 +41,31 @@ struct Cfg {
     static constexpr int ES = MODE == kTF32 ? 4 : 2;                 // operand element bytes
     static constexpr int KB = MODE == kBF16X3 ? 64 : 128;            // operand row bytes per stage
     static constexpr int KC = KB / ES;                                // sampled rows per stage
-    static constexpr int QPC = 16 / ES;                               // rows per 16-byte chunk
+    static constexpr int QPC = 16 / ES;                               // sampled rows per 16-byte chunk
     static constexpr int NG = KC / QPC;                               // chunks per operand row
     static constexpr int PARTS = MODE == kBF16X3 ? 2 : 1;             // hi (+ lo)
     static constexpr int TILE_BYTES = kTile * KB;                     // one 256-row operand tile
-    static constexpr int USTRIDE = KC + 4;                            // padded row of the U stage
-    static constexpr int U_FLOATS = 3 * FST_MAX_RANK * USTRIDE;
-    static constexpr int STAGE_BYTES = 2 * PARTS * TILE_BYTES + U_FLOATS * 4;
-    static constexpr int ROWTAB = 2 * 2 * kTile * 8;                  // per-tile row table, 2 buffers
-    static constexpr int SMEM = kStages * STAGE_BYTES + ROWTAB + 2048; // + barriers, alignment slack
+    static constexpr int STAGE_BYTES = 2 * PARTS * TILE_BYTES;        // A and B operand tiles
+    // staging of one stage: pair products of the A and B tiles' pairs, then w3 rows; the
+    // number of rows and of staging buffers (the cp.async prefetch depth) is set at launch
+    static constexpr int PSTRIDE = KC + 4;                            // floats per staged row
+    static constexpr int FIXED = kStages * STAGE_BYTES + 2048;
     static constexpr int KSTEPS = KB / 32;                            // MMAs per stage per product
 };
+
+struct TaskInfo {
+    int op, k, g, plo, pb, pe, base;
+};
+// tasks per producer warp: 2 operands x 4 groups of 8 k (r3 <= 32) x 2 chunk groups x 4
+// quarters of the pair range, over the producer warps
+constexpr int kSplit = 4;
+constexpr int kMaxTasks = (2 * 4 * 2 * kSplit) / 16;
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(tc::smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 __device__ __forceinline__ uint32_t to_tf32(float x) {
     uint32_t r;
@@ -80,27 +95,27 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
 
 template <int MODE>
 __global__ void __launch_bounds__(kThreads, 1)
-gram_tc_kernel(const float* __restrict__ U1, const float* __restrict__ U2, const float* __restrict__ U3,
-               int64_t m, int r1, int r2, int r3, float* __restrict__ G, int* __restrict__ err) {
+gram_tc_kernel(const float* __restrict__ PT, const float* __restrict__ U3T, int64_t m, int64_t mpad, int r1, int r2,
+               int r3, int halfp, int nstg, float* __restrict__ G, int* __restrict__ err) {
     using C = Cfg<MODE>;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStages * C::STAGE_BYTES);
+    float* stg0 = reinterpret_cast<float*>(smem + kStages * C::STAGE_BYTES);
+    const int stg_floats = (2 * halfp + r3) * C::PSTRIDE;
+    uint64_t* full = reinterpret_cast<uint64_t*>(stg0 + nstg * stg_floats);
     uint64_t* empty = full + kStages;
     uint64_t* tmem_full = empty + kStages;
     uint64_t* tmem_empty = tmem_full + 1;
     uint64_t* drain = tmem_empty + 1;
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
-    // rowtab[buf][row] = {off(w1_i) | off(w2_j) << 16, off(w3_k) | valid << 31}: shared-memory
-    // offsets of the factor rows of operand row `row` (0..255 super-tile rows, 256..511 columns)
-    int2* rowtab = reinterpret_cast<int2*>(smem + kStages * C::STAGE_BYTES + 1024);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int R = r1 * r2 * r3;
+    const int npairs = r1 * r2;
     const int nT = (R + kTile - 1) / kTile;
     const long long ntiles = (long long)nT * (nT + 1) / 2;
-    const long long nK = (m + C::KC - 1) / C::KC;
+    const int nK = (int)((m + C::KC - 1) / C::KC);
 
     if (warp == 0) tc::tmem_alloc(tmem_slot, 512);
     if (tid == 0) {
@@ -109,7 +124,7 @@ gram_tc_kernel(const float* __restrict__ U1, const float* __restrict__ U2, const
             tc::mbar_init(&empty[s], 1);
         }
         tc::mbar_init(tmem_full, 1);
-        tc::mbar_init(tmem_empty, kProducerWarps);
+        tc::mbar_init(tmem_empty, kEpilogueWarps);
         tc::mbar_init(drain, 1);
         *abort_flag = 0;
         tc::fence_mbar_init();
@@ -123,133 +138,201 @@ gram_tc_kernel(const float* __restrict__ U1, const float* __restrict__ U2, const
         *abort_flag = 1;
         atomicOr(err, code);
     };
+    auto decode = [&](long long t, int& ti, int& tj) {
+        ti = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+        while ((long long)(ti + 1) * (ti + 2) / 2 <= t) ++ti;
+        while ((long long)ti * (ti + 1) / 2 > t) --ti;
+        tj = (int)(t - (long long)ti * (ti + 1) / 2);
+    };
+    // pairs (i, j) whose rows (p r3 .. p r3 + r3 - 1) meet operand tile `tile`
+    auto pair_range = [&](int tile, int& plo, int& phi) {
+        const int row0 = tile * kTile;
+        const int row1 = min(row0 + kTile, R) - 1;
+        plo = row0 / r3;
+        phi = row1 / r3;
+    };
 
     if (warp < kProducerWarps) {
         // ------------------------------------------------------------ producers + epilogue
-        long long gs = 0;   // global stage counter
-        int tcount = 0;
-        bool stop = false;
-        // Factor values of the next stage are loaded into registers one stage ahead
-        // (every tile walks the same sampled rows, so the prefetch ignores tile bounds).
-        constexpr int kPer = C::KC * 3 * FST_MAX_RANK / (kProducerWarps * 32);
-        float pre[kPer];
-        auto load_stage = [&](long long kc) {
-            const long long q0 = kc * C::KC;
-#pragma unroll
-            for (int it = 0; it < kPer; ++it) {
-                const int e = tid + it * kProducerWarps * 32;
-                const int q = e / (3 * FST_MAX_RANK), c = e - q * (3 * FST_MAX_RANK);
-                const int mode = c / FST_MAX_RANK, col = c - mode * FST_MAX_RANK;
-                const long long srow = q0 + q;
-                const int rk = mode == 0 ? r1 : mode == 1 ? r2 : r3;
-                const float* Uk = mode == 0 ? U1 : mode == 1 ? U2 : U3;
-                pre[it] = (col < rk && srow < m) ? __ldg(Uk + srow * rk + col) : 0.f;
+        // Stage loads (pair products and w3 rows of KC sampled rows) go through cp.async
+        // nstg-1 stages ahead, into a ring of nstg staging buffers (one commit group per stage).
+        // prefetch position: tile (decoded once per tile) and stage within it
+        long long pf_t = blockIdx.x;
+        int pf_kc = 0;
+        int pf_alo = 0, pf_ahi = -1, pf_blo = 0, pf_bhi = -1;
+        auto pf_decode = [&]() {
+            if (pf_t < ntiles) {
+                int ti, tj;
+                decode(pf_t, ti, tj);
+                pair_range(ti, pf_alo, pf_ahi);
+                pair_range(tj, pf_blo, pf_bhi);
             }
         };
-        load_stage(0);
-        for (long long t = blockIdx.x; t < ntiles && !stop; t += gridDim.x, ++tcount) {
-            int ti = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
-            while ((long long)(ti + 1) * (ti + 2) / 2 <= t) ++ti;
-            while ((long long)ti * (ti + 1) / 2 > t) --ti;
-            const int tj = (int)(t - (long long)ti * (ti + 1) / 2);
-            int2* tab = rowtab + (tcount & 1) * 2 * kTile;
-            for (int row = tid; row < 2 * kTile; row += kProducerWarps * 32) {
-                const int a = (row >= kTile ? tj : ti) * kTile + (row & (kTile - 1));
-                int2 e = make_int2(0, 0);
-                if (a < R) {
-                    const int i = a / (r2 * r3), j = (a / r3) % r2, k = a % r3;
-                    e = make_int2((i * C::USTRIDE) | ((FST_MAX_RANK + j) * C::USTRIDE) << 16,
-                                  ((2 * FST_MAX_RANK + k) * C::USTRIDE) | (int)0x80000000);
+        pf_decode();
+        auto issue_loads = [&](int kc, int buf) {
+            const int alo = pf_alo, ahi = pf_ahi, blo = pf_blo, bhi = pf_bhi;
+            const int nA = ahi - alo + 1, nB = bhi - blo + 1;
+            float* P = stg0 + buf * stg_floats;
+            const long long q0 = (long long)kc * C::KC;
+            constexpr int CPR = C::KC / 4;                       // 16-byte chunks per row
+            const int rows = nA + nB + r3;
+            for (int c = tid; c < rows * CPR; c += kProducerWarps * 32) {
+                const int r = c / CPR, cc = c - r * CPR;
+                const float* src;
+                float* dst;
+                if (r < nA) {
+                    src = PT + (size_t)(alo + r) * mpad;
+                    dst = P + r * C::PSTRIDE;
+                } else if (r < nA + nB) {
+                    src = PT + (size_t)(blo + r - nA) * mpad;
+                    dst = P + (halfp + r - nA) * C::PSTRIDE;
+                } else {
+                    src = U3T + (size_t)(r - nA - nB) * mpad;
+                    dst = P + (2 * halfp + r - nA - nB) * C::PSTRIDE;
                 }
-                tab[row] = e;
+                cp_async16(dst + cc * 4, src + q0 + cc * 4);
             }
-            // (the first stage's producer barrier orders these writes before their use; the
-            //  other buffer may still be read by a slower warp finishing the previous tile)
-            for (long long kc = 0; kc < nK; ++kc, ++gs) {
-                const int st = (int)(gs % kStages);
+            cp_async_commit();
+        };
+        int gs = 0;         // global stage counter
+        int tcount = 0;
+        bool stop = false;
+        // stages are prefetched in order; issue_next() loads the next one (or commits an
+        // empty group past the last stage, keeping one group per stage)
+        auto issue_next = [&](int buf) {
+            if (pf_t < ntiles) {
+                issue_loads(pf_kc, buf);
+                if (++pf_kc == nK) {
+                    pf_kc = 0;
+                    pf_t += gridDim.x;
+                    pf_decode();
+                }
+            } else {
+                cp_async_commit();
+            }
+        };
+        for (int g0 = 0; g0 < nstg - 1; ++g0) issue_next(g0);
+        const int KG = (r3 + 7) / 8;
+        const int ntasks = 2 * KG * (C::NG / 4) * kSplit;
+        for (long long t = blockIdx.x; t < ntiles && !stop; t += gridDim.x, ++tcount) {
+            int ti, tj;
+            decode(t, ti, tj);
+            // this warp's generation tasks for the tile: (operand, 8 values of k, 4 chunks, half
+            // of the pairs), fixed for all of the tile's stages
+            TaskInfo tinfo[kMaxTasks];
+#pragma unroll
+            for (int ti_ = 0; ti_ < kMaxTasks; ++ti_) {
+                const int task = warp + ti_ * kProducerWarps;
+                int x = task;
+                const int part = x % kSplit;
+                x /= kSplit;
+                const int cgrp = x % (C::NG / 4);
+                x /= (C::NG / 4);
+                const int kg = x % KG;
+                const int op = x / KG;
+                TaskInfo& T = tinfo[ti_];
+                T.op = op;
+                T.k = kg * 8 + (lane & 7);
+                T.g = cgrp * 4 + (lane >> 3);
+                int plo, phi;
+                pair_range(op ? tj : ti, plo, phi);
+                const int np = phi - plo + 1;
+                T.plo = plo;
+                T.pb = plo + (np * part) / kSplit;
+                T.pe = plo + (np * (part + 1)) / kSplit;
+                T.base = (op ? tj : ti) * kTile;
+            }
+            for (int kc = 0; kc < nK; ++kc, ++gs) {
+                const int st = gs & (kStages - 1);
+                const int buf = gs % nstg;
                 const uint32_t ph = (uint32_t)((gs / kStages) & 1);
                 const bool ok = tc::mbar_wait(&empty[st], ph ^ 1u, kWaitLimit);
                 if (!ok) fail(1);
-                const bool skip = !ok || *abort_flag;
+                // this stage's group is the oldest of the nstg-1 in flight
+                if (nstg >= 4) asm volatile("cp.async.wait_group 2;" ::: "memory");
+                else if (nstg == 3) asm volatile("cp.async.wait_group 1;" ::: "memory");
+                else cp_async_wait_all();
+                if (producers_any(!ok || *abort_flag)) { stop = true; break; }
+                // the buffer of stage gs+nstg-1 was last read by stage gs-1's generation,
+                // which every producer finished before the barrier above
+                issue_next((gs + nstg - 1) % nstg);
+                const float* P = stg0 + buf * stg_floats;
+                const float* U3s = P + 2 * halfp * C::PSTRIDE;
                 unsigned char* sbase = smem + st * C::STAGE_BYTES;
-                float* us = reinterpret_cast<float*>(sbase + 2 * C::PARTS * C::TILE_BYTES);
-                float* u1T = us;
-                float* u2T = us + FST_MAX_RANK * C::USTRIDE;
-                float* u3T = us + 2 * FST_MAX_RANK * C::USTRIDE;
-                // store this stage's factor values (transposed), then start loading the next
-                if (!skip) {
+                const int kl = lane & 7, cl = lane >> 3;
+                for (int ti_ = 0; ti_ < kMaxTasks; ++ti_) {
+                    const int task = warp + ti_ * kProducerWarps;
+                    if (task >= ntasks) break;
+                    const TaskInfo& T = tinfo[ti_];
+                    const int op = T.op, k = T.k, g = T.g, plo = T.plo, pb = T.pb, pe = T.pe, base = T.base;
+                    float u3v[C::QPC];
 #pragma unroll
-                    for (int it = 0; it < kPer; ++it) {
-                        const int e = tid + it * kProducerWarps * 32;
-                        const int q = e / (3 * FST_MAX_RANK), c = e - q * (3 * FST_MAX_RANK);
-                        const int mode = c / FST_MAX_RANK, col = c - mode * FST_MAX_RANK;
-                        us[mode * FST_MAX_RANK * C::USTRIDE + col * C::USTRIDE + q] = pre[it];
+                    for (int e = 0; e < C::QPC; e += 4) {
+                        const float4 x4 = k < r3 ? *reinterpret_cast<const float4*>(U3s + k * C::PSTRIDE + g * C::QPC + e)
+                                                 : make_float4(0.f, 0.f, 0.f, 0.f);
+                        u3v[e] = x4.x; u3v[e + 1] = x4.y; u3v[e + 2] = x4.z; u3v[e + 3] = x4.w;
                     }
-                }
-                load_stage(kc + 1 < nK ? kc + 1 : 0);
-                if (producers_any(skip)) { stop = true; break; }
-                // operand rows: 0..255 -> A (super-tile rows), 256..511 -> B (super-tile columns)
-                constexpr int kTasks = (2 * kTile / 8) * (C::NG / 4);   // warp tasks of 8 rows x 4 chunks
-                for (int task = warp; task < kTasks; task += kProducerWarps) {
-                    const int rowblk = task / (C::NG / 4);
-                    const int g = (task % (C::NG / 4)) * 4 + (lane >> 3);
-                    const int row = rowblk * 8 + (lane & 7);
-                    const bool isB = row >= kTile;
-                    const int lrow = isB ? row - kTile : row;
-                    const int2 te = tab[row];
-                    float v[C::QPC];
-                    if (te.y < 0) {
-                        const float* p1 = us + (te.x & 0xFFFF) + g * C::QPC;
-                        const float* p2 = us + ((unsigned)te.x >> 16) + g * C::QPC;
-                        const float* p3 = us + (te.y & 0x7FFFFFFF) + g * C::QPC;
+                    unsigned char* tile = sbase + op * C::PARTS * C::TILE_BYTES;
+                    const float* Pop = P + (op ? halfp : 0) * C::PSTRIDE;
+                    for (int p = pb; p < pe; ++p) {
+                        const int row = p * r3 + k - base;
+                        if (k >= r3 || row < 0 || row >= kTile) continue;
+                        const float* pr = Pop + (p - plo) * C::PSTRIDE + g * C::QPC;
+                        float v[C::QPC];
 #pragma unroll
                         for (int e = 0; e < C::QPC; e += 4) {
-                            const float4 x1 = *reinterpret_cast<const float4*>(p1 + e);
-                            const float4 x2 = *reinterpret_cast<const float4*>(p2 + e);
-                            const float4 x3 = *reinterpret_cast<const float4*>(p3 + e);
-                            v[e] = x1.x * x2.x * x3.x;
-                            v[e + 1] = x1.y * x2.y * x3.y;
-                            v[e + 2] = x1.z * x2.z * x3.z;
-                            v[e + 3] = x1.w * x2.w * x3.w;
+                            const float4 x4 = *reinterpret_cast<const float4*>(pr + e);
+                            v[e] = x4.x * u3v[e];
+                            v[e + 1] = x4.y * u3v[e + 1];
+                            v[e + 2] = x4.z * u3v[e + 2];
+                            v[e + 3] = x4.w * u3v[e + 3];
                         }
-                    } else {
+                        const uint32_t off = tc::kmajor_offset(row, g * 16, C::KB);
+                        if (MODE == kTF32) {
+                            *reinterpret_cast<uint4*>(tile + off) =
+                                make_uint4(to_tf32(v[0]), to_tf32(v[1]), to_tf32(v[2]), to_tf32(v[3]));
+                        } else {
+                            *reinterpret_cast<uint4*>(tile + off) =
+                                make_uint4(pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]), pack_bf16(v[4], v[5]),
+                                           pack_bf16(v[6], v[7]));
+                            if (MODE == kBF16X3) {
+                                float lo[8];
 #pragma unroll
-                        for (int e = 0; e < C::QPC; ++e) v[e] = 0.f;
+                                for (int e = 0; e < 8; ++e) lo[e] = v[e] - __bfloat162float(__float2bfloat16_rn(v[e]));
+                                *reinterpret_cast<uint4*>(tile + C::TILE_BYTES + off) =
+                                    make_uint4(pack_bf16(lo[0], lo[1]), pack_bf16(lo[2], lo[3]), pack_bf16(lo[4], lo[5]),
+                                               pack_bf16(lo[6], lo[7]));
+                            }
+                        }
                     }
-                    const uint32_t off = tc::kmajor_offset(lrow, g * 16, C::KB);
-                    unsigned char* tile = sbase + (isB ? C::PARTS * C::TILE_BYTES : 0);
-                    uint4 w;
-                    if (MODE == kTF32) {
-                        w = make_uint4(to_tf32(v[0]), to_tf32(v[1]), to_tf32(v[2]), to_tf32(v[3]));
-                        *reinterpret_cast<uint4*>(tile + off) = w;
-                    } else {
-                        w = make_uint4(pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]), pack_bf16(v[4], v[5]),
-                                       pack_bf16(v[6], v[7]));
-                        *reinterpret_cast<uint4*>(tile + off) = w;
-                        if (MODE == kBF16X3) {
-                            float lo[8];
-#pragma unroll
-                            for (int e = 0; e < 8; ++e)
-                                lo[e] = v[e] - __bfloat162float(__float2bfloat16_rn(v[e]));
-                            const uint4 wl = make_uint4(pack_bf16(lo[0], lo[1]), pack_bf16(lo[2], lo[3]),
-                                                        pack_bf16(lo[4], lo[5]), pack_bf16(lo[6], lo[7]));
-                            *reinterpret_cast<uint4*>(tile + C::TILE_BYTES + off) = wl;
-                        }
+                }
+                // operand rows beyond R (last tiles only) are zero in every stage
+                for (int op = 0; op < 2; ++op) {
+                    const int base = (op ? tj : ti) * kTile;
+                    const int first = R - base;
+                    if (first >= kTile) continue;
+                    unsigned char* tile = sbase + op * C::PARTS * C::TILE_BYTES;
+                    const int nz = (kTile - (first > 0 ? first : 0)) * C::NG;
+                    for (int e = tid; e < nz; e += kProducerWarps * 32) {
+                        const int row = (first > 0 ? first : 0) + e / C::NG, g = e % C::NG;
+                        const uint32_t off = tc::kmajor_offset(row, g * 16, C::KB);
+                        *reinterpret_cast<uint4*>(tile + off) = make_uint4(0, 0, 0, 0);
+                        if (MODE == kBF16X3) *reinterpret_cast<uint4*>(tile + C::TILE_BYTES + off) = make_uint4(0, 0, 0, 0);
                     }
                 }
                 tc::fence_async_smem();
                 __syncwarp();
                 if (lane == 0) tc::mbar_arrive(&full[st]);
-                // U stage reuse is ordered by the next `empty` wait of this stage
             }
             if (stop) break;
             // ---------------------------------------------------------- epilogue
+            if (warp >= kEpilogueWarps) continue;
             if (!tc::mbar_wait(tmem_full, (uint32_t)(tcount & 1), kWaitLimit)) fail(2);
             tc::fence_after_sync();
-            const int half = warp >> 2;                 // accumulator 0: rows 0..127, 1: rows 128..255
+            const int hh = warp >> 2;                   // accumulator 0: rows 0..127, 1: rows 128..255
             const int sub = warp & 3;                   // TMEM lanes 32*sub .. 32*sub+31
-            const int row = ti * kTile + half * 128 + sub * 32 + lane;
-            const uint32_t taddr = tmem + ((uint32_t)(sub * 32) << 16) + (uint32_t)(half * 256);
+            const int row = ti * kTile + hh * 128 + sub * 32 + lane;
+            const uint32_t taddr = tmem + ((uint32_t)(sub * 32) << 16) + (uint32_t)(hh * 256);
             for (int c0 = 0; c0 < kTile; c0 += 16) {
                 float v[16];
                 tc::tmem_ld16(taddr + c0, v);
@@ -270,18 +353,19 @@ gram_tc_kernel(const float* __restrict__ U1, const float* __restrict__ U2, const
             __syncwarp();
             if (lane == 0) tc::mbar_arrive(tmem_empty);
         }
+        cp_async_wait_all();
     } else if (lane == 0) {
         // ------------------------------------------------------------ MMA issuer
         constexpr uint32_t idesc = MODE == kTF32 ? tc::idesc_tf32(128, 256) : tc::idesc_bf16(128, 256);
         constexpr uint32_t SBO = (C::KB / 16) * 128;
-        long long gs = 0;
+        int gs = 0;
         int tcount = 0;
         bool issued = false;
         for (long long t = blockIdx.x; t < ntiles && !*abort_flag; t += gridDim.x, ++tcount) {
             if (!tc::mbar_wait(tmem_empty, (uint32_t)(tcount & 1) ^ 1u, kWaitLimit)) { fail(4); break; }
             tc::fence_after_sync();
-            for (long long kc = 0; kc < nK; ++kc, ++gs) {
-                const int st = (int)(gs % kStages);
+            for (int kc = 0; kc < nK; ++kc, ++gs) {
+                const int st = gs & (kStages - 1);
                 const uint32_t ph = (uint32_t)((gs / kStages) & 1);
                 if (!tc::mbar_wait(&full[st], ph, kWaitLimit)) { fail(8); break; }
                 tc::fence_after_sync();
@@ -328,25 +412,50 @@ gram_tc_kernel(const float* __restrict__ U1, const float* __restrict__ U2, const
     if (warp == 0) tc::tmem_dealloc(tmem, 512);
 }
 
+// PT[(i r2 + j) mpad + q] = w1_i(q) w2_j(q) and U3T[k mpad + q] = w3_k(q) (zero for q >= m):
+// the factor values of the sampled rows rearranged pair-major for 16-byte stage copies.
+__global__ void pair_products_kernel(const float* __restrict__ U1, const float* __restrict__ U2,
+                                     const float* __restrict__ U3, int64_t m, int64_t mpad, int r1, int r2, int r3,
+                                     float* __restrict__ PT, float* __restrict__ U3T) {
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < mpad; q += (int64_t)gridDim.x * blockDim.x) {
+        const bool ok = q < m;
+        for (int k = 0; k < r3; ++k) U3T[(size_t)k * mpad + q] = ok ? U3[q * r3 + k] : 0.f;
+        for (int i = 0; i < r1; ++i) {
+            const float a = ok ? U1[q * r1 + i] : 0.f;
+            for (int j = 0; j < r2; ++j) PT[(size_t)(i * r2 + j) * mpad + q] = ok ? a * U2[q * r2 + j] : 0.f;
+        }
+    }
+}
+
 template <int MODE>
-fst_status launch(const float* U1, const float* U2, const float* U3, int64_t m, int r1, int r2, int r3, float* G,
+fst_status launch(const float* PT, const float* U3T, int64_t m, int64_t mpad, int r1, int r2, int r3, float* G,
                   int* err, cudaStream_t s) {
     using C = Cfg<MODE>;
     auto kern = gram_tc_kernel<MODE>;
-    FST_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
+    const int halfp = (kTile - 1) / r3 + 2;                  // pairs one 256-row tile can span
+    const size_t stg_bytes = (size_t)(2 * halfp + r3) * C::PSTRIDE * 4;
+    const size_t limit = 227 * 1024;
+    int nstg = 4;
+    while (nstg > 2 && C::FIXED + nstg * stg_bytes > limit) --nstg;
+    const size_t smem = C::FIXED + nstg * stg_bytes;
+    if (smem > limit) {
+        set_error("tensor-core Gram: ranks need %zu bytes of shared memory", smem);
+        return FST_EUNSUPPORTED;
+    }
+    FST_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int R = r1 * r2 * r3;
     const long long nT = (R + kTile - 1) / kTile;
     const long long ntiles = nT * (nT + 1) / 2;
     int grid = sm_count();
     if (ntiles < grid) grid = (int)ntiles;
-    kern<<<grid, kThreads, C::SMEM, s>>>(U1, U2, U3, m, r1, r2, r3, G, err);
+    kern<<<grid, kThreads, smem, s>>>(PT, U3T, m, mpad, r1, r2, r3, halfp, nstg, G, err);
     FST_CHECK_LAUNCH();
     return FST_OK;
 }
 
 struct GramErr {
     std::mutex mu;
-    DevBuf flag;
+    DevBuf flag, pt, u3t;
 };
 GramErr g_gram_err[64];
 
@@ -362,11 +471,26 @@ fst_status gram_tc_launch(const fst_model* M, const float* U1, const float* U2, 
     int* err = ge.flag.as<int>();
     FST_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
     const int r1 = M->r[0], r2 = M->r[1], r3 = M->r[2];
+    if (r3 < 4) {
+        set_error("tensor-core Gram needs r3 >= 4");
+        return FST_EUNSUPPORTED;
+    }
+    const int64_t mpad = (m + 63) / 64 * 64;
+    FST_TRY(ge.pt.ensure(sizeof(float) * (size_t)r1 * r2 * mpad));
+    FST_TRY(ge.u3t.ensure(sizeof(float) * (size_t)r3 * mpad));
+    float* PT = ge.pt.as<float>();
+    float* U3T = ge.u3t.as<float>();
+    {
+        int grid = (int)((mpad + 255) / 256);
+        if (grid > 8 * sm_count()) grid = 8 * sm_count();
+        pair_products_kernel<<<grid, 256, 0, s>>>(U1, U2, U3, m, mpad, r1, r2, r3, PT, U3T);
+        FST_CHECK_LAUNCH();
+    }
     fst_status st;
     switch (prec) {
-        case FST_TF32: st = launch<kTF32>(U1, U2, U3, m, r1, r2, r3, G, err, s); break;
-        case FST_BF16: st = launch<kBF16>(U1, U2, U3, m, r1, r2, r3, G, err, s); break;
-        case FST_BF16X3: st = launch<kBF16X3>(U1, U2, U3, m, r1, r2, r3, G, err, s); break;
+        case FST_TF32: st = launch<kTF32>(PT, U3T, m, mpad, r1, r2, r3, G, err, s); break;
+        case FST_BF16: st = launch<kBF16>(PT, U3T, m, mpad, r1, r2, r3, G, err, s); break;
+        case FST_BF16X3: st = launch<kBF16X3>(PT, U3T, m, mpad, r1, r2, r3, G, err, s); break;
         default:
             set_error("tensor-core Gram takes TF32, BF16 or BF16X3");
             return FST_EINVAL;

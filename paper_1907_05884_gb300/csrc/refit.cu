@@ -464,9 +464,12 @@ static fst_status refit_impl(fst_model* M, const T* xyz, const T* u, int64_t Q, 
             if (prec == FST_FP32) {
                 FST_TRY(launch_gram_simt<float>(M, reinterpret_cast<const float* const*>(Uc), m, G, s));
             } else {
-                FST_TRY(gram_tc_launch(M, reinterpret_cast<const float*>(Uc[0]),
-                                       reinterpret_cast<const float*>(Uc[1]),
-                                       reinterpret_cast<const float*>(Uc[2]), m, G, prec, s));
+                fst_status gst = gram_tc_launch(M, reinterpret_cast<const float*>(Uc[0]),
+                                                reinterpret_cast<const float*>(Uc[1]),
+                                                reinterpret_cast<const float*>(Uc[2]), m, G, prec, s);
+                if (gst == FST_EUNSUPPORTED)   // r3 < 4: the CUDA-core Gram
+                    gst = launch_gram_simt<float>(M, reinterpret_cast<const float* const*>(Uc), m, G, s);
+                FST_TRY(gst);
             }
             r.ms_gram += tm.stop();
             FST_TRY(cholesky_lower<float>(G, R, flag, s));
@@ -711,7 +714,9 @@ extern "C" fst_status fst_normal_matrix(const fst_model* M, const float* xyz, co
     if (prec == FST_FP32) {
         FST_TRY(launch_gram_simt<float>(M, Uc, m, G, s));
     } else {
-        FST_TRY(gram_tc_launch(M, Uc[0], Uc[1], Uc[2], m, G, prec, s));
+        fst_status gst = gram_tc_launch(M, Uc[0], Uc[1], Uc[2], m, G, prec, s);
+        if (gst == FST_EUNSUPPORTED) gst = launch_gram_simt<float>(M, Uc, m, G, s);   // r3 < 4
+        FST_TRY(gst);
     }
     if (h) {
         FST_TRY(W.res.ensure(sizeof(double) * (size_t)m));
