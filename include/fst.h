@@ -199,7 +199,7 @@ fst_status fst_sample_rows_static(uint64_t seed, int64_t Q, int64_t m, int64_t* 
 
 typedef struct {
     int32_t max_refine;       /* refinement (preconditioned CG) steps after the first solve (default 32) */
-    double refine_tol;        /* stop when ||delta|| <= tol ||alpha|| (default 1e-12 FP64, 1e-9 else) */
+    double refine_tol;        /* stop when the CG step is <= tol ||alpha|| (default 1e-13 FP64, 1e-8 else) */
     int32_t fp64_cholesky;    /* 1: factor the normal matrix in FP64 (default: FP64 only for FST_FP64) */
 } fst_refit_opts;
 

@@ -156,12 +156,192 @@ __global__ void __launch_bounds__(256) syrk_update_kernel(T* G, int R, int k0, i
     }
 }
 
+// ---------------------------------------------------------------- FP32 path, 128-wide panels
+// Diagonal block of width kb <= PB in shared memory (dynamic).
+template <int PB>
+__global__ void potrf_diag_wide_kernel(float* G, int R, int k0, int kb, int* flag, const float* floor_p) {
+    extern __shared__ __align__(16) unsigned char dsm[];
+    float (*A)[PB + 1] = reinterpret_cast<float (*)[PB + 1]>(dsm);
+    const int tid = threadIdx.x, B = blockDim.x;
+    for (int e = tid; e < kb * kb; e += B) {
+        const int i = e / kb, j = e - i * kb;
+        A[i][j] = j <= i ? G[(size_t)(k0 + i) * R + k0 + j] : 0.f;
+    }
+    __syncthreads();
+    for (int j = 0; j < kb; ++j) {
+        if (tid == 0) {
+            const float d = A[j][j];
+            if (!(d > *floor_p)) atomicOr(flag, 1);
+            A[j][j] = sqrtf(d);
+        }
+        __syncthreads();
+        const float inv = 1.f / A[j][j];
+        for (int i = j + 1 + tid; i < kb; i += B) A[i][j] *= inv;
+        __syncthreads();
+        // trailing update of the block: a 16 x (B/16) thread grid over (row, column)
+        const int tc = tid & 15, tr = tid >> 4, nr = B >> 4;
+        for (int i = j + 1 + tr; i < kb; i += nr) {
+            const float lij = A[i][j];
+            for (int c = j + 1 + tc; c <= i; c += 16) A[i][c] -= lij * A[c][j];
+        }
+        __syncthreads();
+    }
+    for (int e = tid; e < kb * kb; e += B) {
+        const int i = e / kb, j = e - i * kb;
+        if (j <= i) G[(size_t)(k0 + i) * R + k0 + j] = A[i][j];
+    }
+}
+
+// L21 = A21 L11^-T, 32 rows per block, thread per row.
+template <int PB>
+__global__ void trsm_panel_wide_kernel(float* G, int R, int k0, int kb) {
+    extern __shared__ __align__(16) unsigned char dsm[];
+    float (*L)[PB + 1] = reinterpret_cast<float (*)[PB + 1]>(dsm);
+    float (*X)[PB + 1] = L + PB;
+    const int tid = threadIdx.x, B = blockDim.x;
+    const int row0 = k0 + kb + 32 * blockIdx.x;
+    const int rows = R - row0 < 32 ? R - row0 : 32;
+    for (int e = tid; e < kb * kb; e += B) {
+        const int i = e / kb, j = e - i * kb;
+        L[i][j] = j <= i ? G[(size_t)(k0 + i) * R + k0 + j] : 0.f;
+    }
+    for (int e = tid; e < rows * kb; e += B) {
+        const int i = e / kb, j = e - i * kb;
+        X[i][j] = G[(size_t)(row0 + i) * R + k0 + j];
+    }
+    __shared__ float Linvd[PB];
+    for (int c = tid; c < kb; c += B) Linvd[c] = 1.f / G[(size_t)(k0 + c) * R + k0 + c];
+    __syncthreads();
+    if (tid < rows) {
+        // forward substitution along the row, four independent partial sums per column
+        for (int c = 0; c < kb; ++c) {
+            float s0 = X[tid][c], s1 = 0.f, s2 = 0.f, s3 = 0.f;
+            int cc = 0;
+            for (; cc + 3 < c; cc += 4) {
+                s0 -= X[tid][cc] * L[c][cc];
+                s1 -= X[tid][cc + 1] * L[c][cc + 1];
+                s2 -= X[tid][cc + 2] * L[c][cc + 2];
+                s3 -= X[tid][cc + 3] * L[c][cc + 3];
+            }
+            for (; cc < c; ++cc) s0 -= X[tid][cc] * L[c][cc];
+            X[tid][c] = ((s0 + s1) + (s2 + s3)) * Linvd[c];
+        }
+    }
+    __syncthreads();
+    for (int e = tid; e < rows * kb; e += B) {
+        const int i = e / kb, j = e - i * kb;
+        G[(size_t)(row0 + i) * R + k0 + j] = X[i][j];
+    }
+}
+
+// A22 -= L21 L21^T on lower 128 x 128 tiles, 8 x 8 outputs per thread, K in chunks of 32.
+__global__ void __launch_bounds__(256) syrk128_kernel(float* G, int R, int k0, int kb, int t0) {
+    constexpr int TS = 128, KC = 32;
+    __shared__ __align__(16) float As[KC][TS + 4];
+    __shared__ __align__(16) float Bs[KC][TS + 4];
+    const long long b = blockIdx.x;
+    int ti = (int)((sqrtf(8.f * (float)b + 1.f) - 1.f) * 0.5f);
+    while ((long long)(ti + 1) * (ti + 2) / 2 <= b) ++ti;
+    while ((long long)ti * (ti + 1) / 2 > b) --ti;
+    const int tj = (int)(b - (long long)ti * (ti + 1) / 2);
+    const int r0 = t0 + ti * TS, c0 = t0 + tj * TS;
+    const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+    const bool vec = (R & 3) == 0 && (k0 & 3) == 0;
+    float acc[8][8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+    for (int tb = 0; tb < kb; tb += KC) {
+        __syncthreads();
+#pragma unroll
+        for (int l = 0; l < 4; ++l) {
+            const int e = tid + l * 256;
+            const int row = e >> 3, c4 = (e & 7) * 4;
+            float va[4] = {0.f, 0.f, 0.f, 0.f}, vb[4] = {0.f, 0.f, 0.f, 0.f};
+            const int ga = r0 + row, gb = c0 + row, kk = tb + c4;
+            if (vec && kk + 3 < kb) {
+                if (ga < R) {
+                    const float4 x = *reinterpret_cast<const float4*>(G + (size_t)ga * R + k0 + kk);
+                    va[0] = x.x; va[1] = x.y; va[2] = x.z; va[3] = x.w;
+                }
+                if (gb < R) {
+                    const float4 x = *reinterpret_cast<const float4*>(G + (size_t)gb * R + k0 + kk);
+                    vb[0] = x.x; vb[1] = x.y; vb[2] = x.z; vb[3] = x.w;
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    if (kk + q < kb) {
+                        if (ga < R) va[q] = G[(size_t)ga * R + k0 + kk + q];
+                        if (gb < R) vb[q] = G[(size_t)gb * R + k0 + kk + q];
+                    }
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                As[c4 + q][row] = va[q];
+                Bs[c4 + q][row] = vb[q];
+            }
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int k = 0; k < KC; ++k) {
+            const float4 a0 = *reinterpret_cast<const float4*>(&As[k][ty * 8]);
+            const float4 a1 = *reinterpret_cast<const float4*>(&As[k][ty * 8 + 4]);
+            const float4 b0 = *reinterpret_cast<const float4*>(&Bs[k][tx * 8]);
+            const float4 b1 = *reinterpret_cast<const float4*>(&Bs[k][tx * 8 + 4]);
+            const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int gi = r0 + ty * 8 + i;
+        if (gi >= R) continue;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int gj = c0 + tx * 8 + j;
+            if (gj < R && gj <= gi) G[(size_t)gi * R + gj] -= acc[i][j];
+        }
+    }
+}
+
 template <typename T>
 fst_status cholesky_lower(T* G, int R, int* d_flag, cudaStream_t s) {
     // d_flag points at two ints of scratch: the flag, then room for the pivot floor
     T* floor_p = reinterpret_cast<T*>(d_flag + 2);
     pivot_floor_kernel<T><<<1, 256, 0, s>>>(G, R, floor_p);
     FST_CHECK_LAUNCH();
+    if (sizeof(T) == 4) {
+        constexpr int PB = 128;
+        float* Gf = reinterpret_cast<float*>(G);
+        const float* fl = reinterpret_cast<const float*>(floor_p);
+        const size_t diag_smem = (size_t)PB * (PB + 1) * sizeof(float);
+        const size_t trsm_smem = (size_t)(PB + 32) * (PB + 1) * sizeof(float);
+        FST_CUDA(cudaFuncSetAttribute(potrf_diag_wide_kernel<PB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)diag_smem));
+        FST_CUDA(cudaFuncSetAttribute(trsm_panel_wide_kernel<PB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)trsm_smem));
+        for (int k0 = 0; k0 < R; k0 += PB) {
+            const int kb = R - k0 < PB ? R - k0 : PB;
+            potrf_diag_wide_kernel<PB><<<1, 512, diag_smem, s>>>(Gf, R, k0, kb, d_flag, fl);
+            FST_CHECK_LAUNCH();
+            const int t0 = k0 + kb;
+            const int rest = R - t0;
+            if (rest <= 0) break;
+            trsm_panel_wide_kernel<PB><<<(rest + 31) / 32, 128, trsm_smem, s>>>(Gf, R, k0, kb);
+            FST_CHECK_LAUNCH();
+            const long long nt = (rest + 127) / 128;
+            syrk128_kernel<<<(unsigned)(nt * (nt + 1) / 2), 256, 0, s>>>(Gf, R, k0, kb, t0);
+            FST_CHECK_LAUNCH();
+        }
+        return FST_OK;
+    }
     const size_t trsm_smem = 2 * NB * (NB + 1) * sizeof(T);
     FST_CUDA(cudaFuncSetAttribute(trsm_panel_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)trsm_smem));
@@ -219,10 +399,15 @@ __global__ void __launch_bounds__(256) fwd_step_kernel(const T* L, const T* Linv
     for (int i = threadIdx.x; i < NB; i += blockDim.x) xs[i] = i < kb ? xin[k0 + i] : T(0);
     __syncthreads();
     const T* Li = Linv + (size_t)b * NB * NB;
-    for (int i = threadIdx.x; i < NB; i += blockDim.x) {
+    {
+        // x_b = Linv_bb xs: four threads per row, 16 contiguous entries each (coalesced)
+        const int i = threadIdx.x >> 2, part = threadIdx.x & 3;
         T s = T(0);
-        for (int c = 0; c < NB; ++c) s += Li[i * NB + c] * xs[c];
-        xb[i] = s;
+#pragma unroll
+        for (int c = 0; c < NB / 4; ++c) s += Li[i * NB + part * (NB / 4) + c] * xs[part * (NB / 4) + c];
+        s += __shfl_xor_sync(0xffffffffu, s, 1);
+        s += __shfl_xor_sync(0xffffffffu, s, 2);
+        if (part == 0) xb[i] = s;
     }
     __syncthreads();
     if (blockIdx.x == 0)
@@ -293,6 +478,44 @@ fst_status chol_solve(const T* L, const T* Linv, int R, T* x, T* y, cudaStream_t
 
 template fst_status cholesky_lower<float>(float*, int, int*, cudaStream_t);
 template fst_status cholesky_lower<double>(double*, int, int*, cudaStream_t);
+template <typename T>
+fst_status chol_solve_graph(SolveGraph& g, const T* L, const T* Linv, int R, T* x, T* y, cudaStream_t s) {
+    if (!g.exec || g.L != L || g.Linv != Linv || g.x != x || g.R != R || g.elem != (int)sizeof(T)) {
+        if (g.exec) {
+            FST_CUDA(cudaStreamSynchronize(s));
+            cudaGraphExecDestroy(g.exec);
+            g.exec = nullptr;
+        }
+        if (!g.cap) FST_CUDA(cudaStreamCreateWithFlags(&g.cap, cudaStreamNonBlocking));
+        FST_CUDA(cudaStreamBeginCapture(g.cap, cudaStreamCaptureModeThreadLocal));
+        const uint64_t before = fst_kernel_launches();
+        fst_status st = chol_solve<T>(L, Linv, R, x, y, g.cap);
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamEndCapture(g.cap, &graph);
+        if (st != FST_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return st;
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture", __FILE__, __LINE__);
+        e = cudaGraphInstantiate(&g.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate", __FILE__, __LINE__);
+        g.nodes = fst_kernel_launches() - before;
+        g.L = L;
+        g.Linv = Linv;
+        g.x = x;
+        g.R = R;
+        g.elem = (int)sizeof(T);
+    }
+    FST_CUDA(cudaGraphLaunch(g.exec, s));
+    count_launches(g.nodes);
+    return FST_OK;
+}
+
+template fst_status chol_solve_graph<float>(SolveGraph&, const float*, const float*, int, float*, float*, cudaStream_t);
+template fst_status chol_solve_graph<double>(SolveGraph&, const double*, const double*, int, double*, double*,
+                                             cudaStream_t);
+
 template fst_status chol_invert_diag<float>(const float*, int, float*, cudaStream_t);
 template fst_status chol_invert_diag<double>(const double*, int, double*, cudaStream_t);
 template fst_status chol_solve<float>(const float*, const float*, int, float*, float*, cudaStream_t);

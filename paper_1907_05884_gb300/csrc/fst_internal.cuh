@@ -28,8 +28,10 @@ fst_status cuda_fail(cudaError_t e, const char* what, const char* file, int line
         cudaError_t _e = (expr);                                                        \
         if (_e != cudaSuccess) return ::fst::cuda_fail(_e, #expr, __FILE__, __LINE__);  \
     } while (0)
-// Every kernel launch in libfst is followed by FST_CHECK_LAUNCH(), which also counts it.
+// Every kernel launch in libfst is followed by FST_CHECK_LAUNCH(), which also counts it;
+// graph replays add their kernel nodes with count_launches.
 void count_launch();
+void count_launches(uint64_t n);
 #define FST_CHECK_LAUNCH()          \
     do {                            \
         ::fst::count_launch();      \
@@ -57,9 +59,22 @@ struct DevBuf {
     template <typename T> T* as() const { return static_cast<T*>(ptr); }
 };
 
+// A captured triangular-solve sequence (chol.cu), replayed with one graph launch.
+struct SolveGraph {
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t cap = nullptr;
+    const void* L = nullptr;
+    const void* Linv = nullptr;
+    void* x = nullptr;
+    int R = 0, elem = 0;
+    uint64_t nodes = 0;
+    void release();
+};
+
 // Scratch of the refit, kept inside the model between calls.
 struct RefitScratch {
     DevBuf idx, U[3], b, G, G64, res, g, z, delta, alpha, norms, flag, Linv, xw, yw, pcg;
+    SolveGraph solve;
 };
 
 }  // namespace fst
@@ -132,5 +147,8 @@ template <typename T>
 fst_status chol_invert_diag(const T* L, int R, T* Linv, cudaStream_t s);   // 64x64 diagonal blocks
 template <typename T>
 fst_status chol_solve(const T* L, const T* Linv, int R, T* x, T* y, cudaStream_t s);  // x <- (L L^T)^-1 x
+// The same through a CUDA graph captured on first use for (L, Linv, x, y, R) and replayed.
+template <typename T>
+fst_status chol_solve_graph(SolveGraph& g, const T* L, const T* Linv, int R, T* x, T* y, cudaStream_t s);
 
 }  // namespace fst

@@ -18,6 +18,18 @@ static thread_local std::string g_last_error;
 static std::atomic<uint64_t> g_launches{0};
 
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void count_launches(uint64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+void SolveGraph::release() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (cap) cudaStreamDestroy(cap);
+    exec = nullptr;
+    cap = nullptr;
+    L = Linv = nullptr;
+    x = nullptr;
+    R = elem = 0;
+    nodes = 0;
+}
 
 void set_error(const char* fmt, ...) {
     char buf[1024];
@@ -114,6 +126,7 @@ static void free_device(fst_model* m) {
     s.xw.release();
     s.yw.release();
     s.pcg.release();
+    s.solve.release();
 }
 
 fst_status model_invalidate_tc(fst_model* m) {

@@ -183,9 +183,10 @@ __global__ void __launch_bounds__(256) atr_kernel(const T* __restrict__ U1, cons
     }
 }
 
-// r_s = b_s - sum_i w1_i sum_j w2_j sum_k alpha_ijk w3_k.  The inner sum over k runs in T;
-// for T = float alpha is split into alpha_hi + alpha_lo (both FP32) so the core itself
-// carries FP64 accuracy into the residual; the sums over j and i run in FP64.
+// r_s = b_s - sum_i w1_i sum_j w2_j sum_k alpha_ijk w3_k (or, with scale +1 and no b, the
+// product A alpha).  The sums over k and j run in T; for T = float alpha is split into
+// alpha_hi + alpha_lo (both FP32) so the core keeps its FP64 digits; the sum over i and the
+// subtraction from b run in FP64.
 template <typename T, int R3M>
 __global__ void __launch_bounds__(128) residual_kernel(const T* __restrict__ U1, const T* __restrict__ U2,
                                                        const T* __restrict__ U3, const T* __restrict__ bvec,
@@ -209,7 +210,7 @@ __global__ void __launch_bounds__(128) residual_kernel(const T* __restrict__ U1,
         for (int k = 0; k < R3M; ++k) w3[k] = k < r3 ? U3[s * r3 + k] : T(0);
         double f = 0.0;
         for (int i = 0; i < r1; ++i) {
-            double si = 0.0;
+            T si = T(0);
             for (int j = 0; j < r2; ++j) {
                 const T* arow = As + (i * r2 + j) * R3M;
                 T t0 = T(0), t1 = T(0);
@@ -222,7 +223,7 @@ __global__ void __launch_bounds__(128) residual_kernel(const T* __restrict__ U1,
                     t0 = fma(a2, w3[k + 2], t0);
                     t1 = fma(a3, w3[k + 3], t1);
                 }
-                double t = (double)t0 + (double)t1;
+                T t = t0 + t1;
                 if (kSplit) {
                     const T* lrow = Al + (i * r2 + j) * R3M;
                     T l0 = T(0), l1 = T(0);
@@ -235,11 +236,11 @@ __global__ void __launch_bounds__(128) residual_kernel(const T* __restrict__ U1,
                         l0 = fma(a2, w3[k + 2], l0);
                         l1 = fma(a3, w3[k + 3], l1);
                     }
-                    t += (double)l0 + (double)l1;
+                    t += l0 + l1;
                 }
-                si = fma(t, (double)U2[s * r2 + j], si);
+                si = fma(t, U2[s * r2 + j], si);
             }
-            f = fma(si, (double)U1[s * r1 + i], f);
+            f = fma((double)si, (double)U1[s * r1 + i], f);
         }
         rv[s] = (bvec ? (double)bvec[s] : 0.0) + scale * f;
     }
@@ -405,7 +406,8 @@ static fst_status refit_impl(fst_model* M, const T* xyz, const T* u, int64_t Q, 
     RefitScratch& W = M->rs;
     const bool fp64 = sizeof(T) == 8;
     const int max_refine = opts ? opts->max_refine : 32;
-    const double tol = (opts && opts->refine_tol > 0) ? opts->refine_tol : (fp64 ? 1e-13 : 1e-10);
+    // FP32-valued factors bound the attainable accuracy near 1e-7: stop the CG at 1e-8
+    const double tol = (opts && opts->refine_tol > 0) ? opts->refine_tol : (fp64 ? 1e-13 : 1e-8);
     const bool force64 = opts && opts->fp64_cholesky;
     fst_refit_report r;
     memset(&r, 0, sizeof r);
@@ -524,13 +526,18 @@ static fst_status refit_impl(fst_model* M, const T* xyz, const T* u, int64_t Q, 
     auto solve = [&](double* x) -> fst_status {
         const int grid = grid_for(R, 256, 2);
         if (use64) {
-            return chol_solve<double>(static_cast<const double*>(Lp), W.Linv.as<double>(), R, x,
-                                      W.yw.as<double>(), s);
+            double* xw = W.xw.as<double>();
+            FST_CUDA(cudaMemcpyAsync(xw, x, sizeof(double) * R, cudaMemcpyDeviceToDevice, s));
+            FST_TRY(chol_solve_graph<double>(W.solve, static_cast<const double*>(Lp), W.Linv.as<double>(), R, xw,
+                                             W.yw.as<double>(), s));
+            FST_CUDA(cudaMemcpyAsync(x, xw, sizeof(double) * R, cudaMemcpyDeviceToDevice, s));
+            return FST_OK;
         }
         float* xw = W.xw.as<float>();
         from_double_kernel<float><<<grid, 256, 0, s>>>(x, xw, R);
         FST_CHECK_LAUNCH();
-        FST_TRY(chol_solve<float>(static_cast<const float*>(Lp), W.Linv.as<float>(), R, xw, W.yw.as<float>(), s));
+        FST_TRY(chol_solve_graph<float>(W.solve, static_cast<const float*>(Lp), W.Linv.as<float>(), R, xw,
+                                        W.yw.as<float>(), s));
         to_double_kernel<float><<<grid, 256, 0, s>>>(xw, x, R);
         FST_CHECK_LAUNCH();
         return FST_OK;
