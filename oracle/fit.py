@@ -22,7 +22,12 @@ Readings where the paper is silent (stated again in the design notes):
     rank r_k >= 1 whose discarded eigenvalues sum to at most eps^2 ||U||_F^2 / d,
     capped at max_rank; each eigenvector's largest-magnitude entry is made positive;
   * the stored coefficients are the least-squares fit on the chosen support
-    (hybrid LARS), the support being the path breakpoint with the least LOO error.
+    (hybrid LARS), the support being the path breakpoint with the least LOO error;
+  * a fitted factor function that lies in the span of the earlier ones of its mode
+    (relative residual norm <= 1e-6 after in-order Gram-Schmidt on the orthonormal
+    Legendre coefficients) is dropped: the refit's least squares (Sec. 5) needs
+    linearly independent Khatri-Rao columns, and noise columns of the ST-HOSVD often
+    collapse to the same low-degree fit.  The refit re-estimates the whole core.
 Parity of the whole fit against the GPU fit is unpinned pointwise (support, rank
 and sign choices are discrete); it is compared by reconstruction error.
 """
@@ -301,6 +306,27 @@ def sparse_fit(Phi: np.ndarray, y: np.ndarray):
     return np.asarray(S, dtype=np.int32), np.asarray(coef, dtype=np.float64), err
 
 
+def independent_columns(C: np.ndarray, tol: float = 1e-12) -> list:
+    """Columns of C kept, in order, by modified Gram-Schmidt (two passes): column j is
+    dropped when its squared residual against the kept ones is <= tol * ||c_j||^2, or it
+    is zero.  With orthonormal basis functions the coefficient inner product is the
+    function inner product, so this is linear dependence of the factor functions."""
+    kept, Qs = [], []
+    for j in range(C.shape[1]):
+        c = np.asarray(C[:, j], dtype=np.float64)
+        n2 = float(c @ c)
+        v = c.copy()
+        for _ in range(2):
+            for q in Qs:
+                v -= (q @ v) * q
+        r2 = float(v @ v)
+        if n2 == 0.0 or r2 <= tol * n2:
+            continue
+        kept.append(j)
+        Qs.append(v / math.sqrt(r2))
+    return kept
+
+
 # ----------------------------------------------------------------------------- driver
 @dataclass
 class FitModel:
@@ -340,8 +366,10 @@ class FitParams:
 
 @dataclass
 class FitReport:
-    ranks: tuple = ()
-    nnz: list = field(default_factory=list)
+    ranks: tuple = ()                 # after dropping dependent factor functions
+    hosvd_ranks: tuple = ()           # chosen by the ST-HOSVD
+    dropped: list = field(default_factory=list)   # per mode: dropped column indices
+    nnz: list = field(default_factory=list)       # per ST-HOSVD column
     loo: list = field(default_factory=list)
     fill_sweeps: int = 0
     m: int = 0
@@ -375,23 +403,25 @@ def fit(xyz: np.ndarray, u: np.ndarray, params: FitParams, lo=None, hi=None,
     else:
         U = np.asarray(grid_values, dtype=np.float64)
     core, Ws, _ = st_hosvd(U, params.eps, params.max_rank, params.fixed_rank)
-    r = tuple(W.shape[1] for W in Ws)
-    rep.ranks = r
+    rep.hosvd_ranks = tuple(W.shape[1] for W in Ws)
     colptr, rowidx, val = [], [], []
     for k in range(3):
         Phi = legendre_matrix(grid_nodes(U.shape[k]), params.max_degree)
-        cp, ri, vv, lo_k = [0], [], [], []
-        for j in range(r[k]):
-            rows, coef, err = sparse_fit(Phi, Ws[k][:, j])
-            ri.append(rows)
-            vv.append(coef)
-            cp.append(cp[-1] + rows.size)
-            lo_k.append(err)
-        colptr.append(np.asarray(cp, np.int32))
-        rowidx.append(np.concatenate(ri).astype(np.int32))
-        val.append(np.concatenate(vv))
-        rep.nnz.append([int(x) for x in np.diff(cp)])
-        rep.loo.append(lo_k)
+        fits = [sparse_fit(Phi, Ws[k][:, j]) for j in range(Ws[k].shape[1])]
+        rep.nnz.append([int(f[0].size) for f in fits])
+        rep.loo.append([f[2] for f in fits])
+        C = np.zeros((params.max_degree + 1, len(fits)))
+        for j, (rows, coef, _) in enumerate(fits):
+            C[rows, j] = coef
+        kept = independent_columns(C)
+        rep.dropped.append([j for j in range(len(fits)) if j not in kept])
+        core = np.take(core, kept, axis=k)
+        cp = np.concatenate([[0], np.cumsum([fits[j][0].size for j in kept])]).astype(np.int32)
+        colptr.append(cp)
+        rowidx.append(np.concatenate([fits[j][0] for j in kept]).astype(np.int32))
+        val.append(np.concatenate([fits[j][1] for j in kept]))
+    r = tuple(c.size - 1 for c in colptr)
+    rep.ranks = r
     p3 = (params.max_degree,) * 3
     model = FitModel(r, p3, colptr, rowidx, val, core, lo, hi)
     R = model.R

@@ -162,6 +162,18 @@ def test_sparse_fit_recovers_exact_sparse_polynomial():
     assert err < 1e-20
 
 
+def test_independent_columns_drops_dependent_factor_functions():
+    """In-order Gram-Schmidt keeps a column only if it adds a direction: duplicates, scalings,
+    sums of kept columns and zero columns go; a 1e-5 relative new direction stays."""
+    rng = np.random.default_rng(4)
+    a, b, c, d = (rng.normal(size=16) for _ in range(4))
+    C = np.stack([a, b, 2 * a, a + b, np.zeros(16), c, -3 * c + b, a + 1e-5 * d], axis=1)
+    assert F.independent_columns(C) == [0, 1, 5, 7]
+    assert F.independent_columns(rng.normal(size=(16, 9))) == list(range(9))
+    # more columns than the dimension: exactly the first 4 survive
+    assert F.independent_columns(rng.normal(size=(4, 7))) == [0, 1, 2, 3]
+
+
 # ----------------------------------------------------------------------------- end to end
 def test_fit_exact_low_rank_legendre_field(oracle_lib):
     """A field that is an exact separable low-rank polynomial of degree <= p is recovered
