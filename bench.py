@@ -357,6 +357,8 @@ def main():
             "refit_pcg_ms": refine_ms,
             "refit_pcg_steps": statistics.mean(r["refine_steps"] for r in reports),
             "refit_fallback_fp64": max(r["fallback_fp64"] for r in reports),
+            "refit_fallback_bf16x3": max(r["fallback_bf16x3"] for r in reports),
+            "refit_shifted_preconditioner": max(r["shifted_preconditioner"] for r in reports),
             "eval_ms": ev_ms, "eval_Mpoints_s": Q / ev_ms / 1e3,
             "roofline": {k: v for k, v in dominant.items()},
             "rooflines": {"gram": roof_gram, "eval": roof_eval},

@@ -207,6 +207,9 @@ typedef struct {
     int64_t m;                /* rows used */
     int32_t refine_steps;     /* refinement steps taken */
     int32_t fallback_fp64;    /* 1 if the FP32 factorisation failed and FP64 was used */
+    int32_t fallback_bf16x3;  /* 1 if a TF32 / BF16 Gram failed to factor and the BF16x3 Gram was used */
+    int32_t shifted_preconditioner; /* 1 if the factor is of G + 2^-12 diag(G) (G too ill-conditioned
+                                       for an FP32 factorisation; the CG still solves G) */
     double first_rel_change;  /* ||alpha_refined - alpha_first|| / ||alpha_refined|| */
     double last_rel_update;   /* ||delta|| / ||alpha|| of the last step */
     double ms_sample, ms_factors, ms_gram, ms_cholesky, ms_refine;   /* GPU time per phase */
@@ -218,7 +221,9 @@ typedef struct {
  * forms the normal equations G = A^T A, h = A^T b over the Khatri-Rao rows
  * a_q = w1(y1_q) (x) w2(y2_q) (x) w3(y3_q) in `prec`, factors G by Cholesky and
  * refines alpha by conjugate gradients on the normal equations preconditioned by
- * that factor, with A p and A^T q accumulated in FP64.
+ * that factor, with A p and A^T q accumulated in FP64.  If the FP32 factorisation of a
+ * TF32 / BF16 Gram fails, the BF16x3 Gram is factored; if that fails, G + 2^-12 diag(G);
+ * then everything is redone in FP64.
  * xyz (3Q floats SoA), u (Q floats): device.  idx: device int64 rows to use, or
  * NULL to draw m rows with `seed`.  opts, report: host, may be NULL.  On success
  * the model's core is replaced.  Synchronous (returns host status).
@@ -237,10 +242,96 @@ fst_status fst_normal_matrix(const fst_model* model, const float* xyz, const flo
                              const int64_t* idx, int64_t m, fst_prec prec, float* G, double* h,
                              fst_stream stream);
 
+/* The factorisation step of the refit on its own: G = L L^T in place for an R x R
+ * row-major FP32 symmetric positive definite matrix (device).  The lower triangle is read
+ * and overwritten by L; the strict upper triangle is left as it was.  128-wide panels:
+ * diagonal blocks and panel solves in FP32 on the CUDA cores; trailing updates on the
+ * tcgen05 tensor cores in BF16x3 (each L entry split into BF16 high and low parts, three
+ * products, FP32 accumulation), so L has relative errors near 1e-5: in the refit it is the
+ * preconditioner of the conjugate gradients, which set the final accuracy.  Synchronous;
+ * allocates and frees its scratch.  FST_ENOTSPD if a pivot is at or below
+ * 16 eps_32 max_i G_ii. */
+fst_status fst_cholesky_f32(float* G, int32_t R, fst_stream stream);
+
 /* FP64 refit (xyz 3Q doubles, u Q doubles; FP64 Gram, FP64 Cholesky). */
 fst_status fst_refit_f64(fst_model* model, const double* xyz, const double* u, int64_t Q,
                          const int64_t* idx, int64_t m, uint64_t seed,
                          const fst_refit_opts* opts, fst_refit_report* report, fst_stream stream);
+
+/* ---------------------------------------------------------------- construction */
+
+/* Parameters of the construction (Algorithm 1 and Sec. 4).  Limits: 2 <= grid[k] <= 256,
+ * 1 <= max_rank[k] <= FST_MAX_RANK, 0 <= max_degree <= 63. */
+typedef struct {
+    int32_t grid[3];          /* interpolation grid: grid[k] equispaced nodes on [-1,1], both ends included */
+    double sample_frac;       /* fraction of the Q points splatted onto the grid, in (0, 1] */
+    double eps;               /* ST-HOSVD precision: per mode, discarded eigenvalues sum to <= eps^2 ||U||^2 / 3 */
+    int32_t max_rank[3];      /* rank caps (the rank is also at most grid[k]) */
+    int32_t max_degree;       /* Legendre degree p of every mode (p + 1 candidate functions per column) */
+    int32_t fixed_rank;       /* 1: r_k = min(max_rank[k], grid[k]) instead of the eps rule */
+    double oversample;        /* refit rows m = min(ceil(oversample * R), Q) */
+    uint64_t seed;            /* interpolation subset: fst_sample_rows(seed); refit rows: seed + 0x632BE59BD9B4E019 */
+    const double* grid_values;/* host, optional: grid[0]*grid[1]*grid[2] values (C order) that replace the
+                                 interpolation step (sample_frac is then ignored) */
+} fst_fit_params;
+
+typedef struct {
+    int32_t r[3];             /* Tucker ranks of the model (after dependent functions are dropped) */
+    int32_t r_hosvd[3];       /* ranks chosen by the ST-HOSVD */
+    int32_t nnz[3];           /* stored Legendre coefficients per mode */
+    int32_t fill_sweeps;      /* Jacobi sweeps needed to fill the empty grid nodes */
+    int32_t eig_sweeps[3];    /* Jacobi eigensolver sweeps per mode */
+    int64_t n_interp;         /* points splatted onto the grid */
+    int64_t m;                /* rows of the core refit */
+    double compression_ratio; /* Q / (R + nnz): values only, positions not counted (Sec. 2, Table 2) */
+    double ms_interp, ms_hosvd, ms_sparse, ms_refit;   /* GPU time per step */
+    fst_refit_report refit;
+} fst_fit_report;
+
+/* Optional host outputs of the intermediate steps; any pointer may be NULL.
+ *   grid_values  grid[0]*grid[1]*grid[2]: the filled grid tensor U (C order)
+ *   eigvals[k]   grid[k]: eigenvalues of the mode-k Gram matrix of the partially reduced
+ *                tensor, descending
+ *   W[k]         grid[k] * max_rank[k] (capacity): the kept eigenvectors, grid[k] x r[k]
+ *                row-major, each with its largest-magnitude entry positive
+ *   core_hosvd   max_rank product (capacity): the ST-HOSVD core, r1 r2 r3 values
+ *   col_nnz      r1 + r2 + r3 (capacity, mode-major): coefficients kept per column
+ *   col_loo      r1 + r2 + r3 (capacity): leave-one-out error of the chosen support
+ *   col_kept     r1 + r2 + r3 (capacity): 1 if the fitted function was kept, 0 if dropped
+ * (r here: the ST-HOSVD ranks) */
+typedef struct {
+    double* grid_values;
+    double* eigvals[3];
+    double* W[3];
+    double* core_hosvd;
+    int32_t* col_nnz;
+    double* col_loo;
+    int32_t* col_kept;
+} fst_fit_trace;
+
+/* Build a model from Q scattered values (Algorithm 1, then the core refit of Algorithm 2):
+ *   1. fst_sample_rows(seed) draws ceil(sample_frac Q) points; each is splatted onto the
+ *      8 nodes of its grid cell with trilinear weights and a node takes the weighted mean;
+ *      empty nodes are filled by Jacobi sweeps (an empty node takes the mean of its filled
+ *      6-neighbours of the previous sweep) -- the paper's linear interpolation to a grid
+ *      (Sec. 4.1);
+ *   2. ST-HOSVD of the grid tensor at precision eps (Sec. 4.1): modes 1, 2, 3 in order, the
+ *      eigenvectors of the FP64 mode Gram matrix (parallel cyclic Jacobi);
+ *   3. each factor column gets a sparse orthonormal-Legendre expansion: the Lasso-LARS path
+ *      on the grid nodes, every visited support refitted by least squares and the one with
+ *      the least leave-one-out error kept (Sec. 3, Sec. 4.2); a fitted function in the span
+ *      of the earlier ones of its mode (relative residual <= 1e-6, in-order Gram-Schmidt on
+ *      the coefficients) is dropped, so the refit below has independent columns;
+ *   4. fst_refit of the core on m = min(ceil(oversample R), Q) rows drawn with
+ *      seed + 0x632BE59BD9B4E019, in `prec` (FST_FP64: the points are widened to FP64 and
+ *      fst_refit_f64 runs).
+ * Steps 1-3 are FP64.  xyz (3Q floats SoA), u (Q floats): device.  lo, hi: host box mapped
+ * onto [-1,1]^3 (NULL: [-1,1]).  opts, trace, report: host, may be NULL.  On success *out
+ * is a new model owned by the caller (fst_model_free).  Synchronous.
+ * FST_EINVAL if no grid node receives a sample; refit errors as fst_refit. */
+fst_status fst_fit(const float* xyz, const float* u, int64_t Q, const double lo[3], const double hi[3],
+                   const fst_fit_params* params, fst_prec prec, const fst_refit_opts* opts,
+                   fst_fit_trace* trace, fst_fit_report* report, fst_model** out, fst_stream stream);
 
 /* ---------------------------------------------------------------- errors */
 

@@ -2,44 +2,36 @@
 // sampled least-squares problem (Algorithm 2, last step: solve the sampled LS), and
 // the two triangular solves x <- L^-T L^-1 x.
 //
-// G is R x R row-major; only its lower triangle is read and L overwrites it.  Panel
-// width NB = 64.  Per panel: (1) one block factors the diagonal block in shared
-// memory; (2) a block per 64 rows solves the panel below, L21 = A21 L11^-T;
-// (3) the trailing lower triangle is updated, A22 -= L21 L21^T, in 64 x 64 tiles.
-// A non-positive (or NaN) pivot sets *d_flag; the caller reads it after the stream
-// synchronises, so no step waits on the device.
+// G is R x R row-major; only its lower triangle is read and L overwrites it.  FP64: panel
+// width NB = 64; per panel (1) one block factors the diagonal block in shared memory;
+// (2) a block per 64 rows solves the panel below, L21 = A21 L11^-T; (3) the trailing
+// lower triangle is updated, A22 -= L21 L21^T, in 64 x 64 tiles on the CUDA cores.
+// FP32: 128-wide panels with the trailing update on the tensor cores (see below).
+// A non-positive (or NaN) pivot sets d_flag[0]; the caller reads it after the stream
+// synchronises, so no step waits on the host.
 #include <math.h>
 
+#include <cuda_bf16.h>
+
 #include "fst_internal.cuh"
+#include "tc_ptx.cuh"
 
 namespace fst {
 
 constexpr int NB = 64;
 
-// Pivot floor: 16 * unit roundoff * the largest diagonal entry of G.  A pivot at or
-// below it means G is numerically singular in T.
+// Pivot floors, one per column: 16 * unit roundoff * G_jj.  A pivot (the Schur complement
+// of column j) at or below its floor means G is numerically singular in T at the scale of
+// that column; the test is invariant under diagonal scaling of G.
 template <typename T>
-__global__ void pivot_floor_kernel(const T* G, int R, T* floor_out) {
-    __shared__ T red[256];
-    T mx = T(0);
-    for (int i = threadIdx.x; i < R; i += blockDim.x) {
-        const T d = G[(size_t)i * R + i];
-        mx = d > mx ? d : mx;
-    }
-    red[threadIdx.x] = mx;
-    __syncthreads();
-    for (int o = 128; o; o >>= 1) {
-        if (threadIdx.x < o && red[threadIdx.x + o] > red[threadIdx.x]) red[threadIdx.x] = red[threadIdx.x + o];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-        const T eps = sizeof(T) == 4 ? T(1.1920929e-7) : T(2.220446049250313e-16);
-        *floor_out = T(16) * eps * red[0];
-    }
+__global__ void pivot_floor_kernel(const T* G, int R, T* floors) {
+    const T eps = sizeof(T) == 4 ? T(1.1920929e-7) : T(2.220446049250313e-16);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < R; i += gridDim.x * blockDim.x)
+        floors[i] = T(16) * eps * G[(size_t)i * R + i];
 }
 
 template <typename T>
-__global__ void potrf_diag_kernel(T* G, int R, int k0, int kb, int* flag, const T* floor_p) {
+__global__ void potrf_diag_kernel(T* G, int R, int k0, int kb, int* flag, const T* floors) {
     __shared__ T A[NB][NB + 1];
     const int tid = threadIdx.x, B = blockDim.x;
     for (int e = tid; e < kb * kb; e += B) {
@@ -50,7 +42,7 @@ __global__ void potrf_diag_kernel(T* G, int R, int k0, int kb, int* flag, const 
     for (int j = 0; j < kb; ++j) {
         if (tid == 0) {
             const T d = A[j][j];
-            if (!(d > *floor_p)) atomicOr(flag, 1);
+            if (!(d > floors[k0 + j])) atomicOr(flag, 1);
             A[j][j] = sqrt(d);
         }
         __syncthreads();
@@ -156,198 +148,435 @@ __global__ void __launch_bounds__(256) syrk_update_kernel(T* G, int R, int k0, i
     }
 }
 
-// ---------------------------------------------------------------- FP32 path, 128-wide panels
-// Diagonal block of width kb <= PB in shared memory (dynamic).
-template <int PB>
-__global__ void potrf_diag_wide_kernel(float* G, int R, int k0, int kb, int* flag, const float* floor_p) {
+// ---------------------------------------------------------------- FP32 path, tensor cores
+// 128-wide panels.  Per panel: (1) one block factors the diagonal block in shared memory in
+// 32-wide sub-panels (a warp factors each 32 x 32 block in registers, the rows below solve
+// against it, the rest of the block takes a register-tiled rank-32 update) and inverts the
+// four 32 x 32 diagonal blocks of L11; (2) the panel below, L21 = A21 L11^-T, is solved by
+// 32-column block substitution with those inverses and written to G in FP32 and, split into
+// BF16 high and low parts, as tensor-core operand tiles; (3) each lower 128 x 128 tile of
+// the trailing matrix takes A22 -= L21_i L21_j^T from tcgen05 MMAs (BF16x3: hi*hi + hi*lo +
+// lo*hi, FP32 accumulation in tensor memory), operands moved by bulk copies and the G tile
+// read ahead into registers.
+constexpr int PB = 128;
+constexpr int SUB = 32;
+constexpr int AS = PB + 4;                          // row stride (floats) of shared panels
+constexpr uint32_t kPartBytes = 16384;              // 128 rows x 64 K BF16, one of hi / lo
+constexpr uint32_t kHalfBytes = 2 * kPartBytes;     // K-half: hi then lo
+constexpr uint32_t kTileBytes = 2 * kHalfBytes;     // two K-halves of a 128-row operand tile
+constexpr long long kCholWaitLimit = 2000000000LL;  // ~1 s of clock cycles
+
+// byte offset of (row, k) of a packed operand tile (hi part; the lo part is kPartBytes on)
+__device__ __forceinline__ uint32_t packed_off(int row, int k) {
+    return (uint32_t)(k >> 6) * kHalfBytes + tc::kmajor_offset((uint32_t)row, (uint32_t)(k & 63) * 2u, 128u);
+}
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
+    const uint32_t lo = __bfloat16_as_ushort(__float2bfloat16_rn(a));
+    const uint32_t hi = __bfloat16_as_ushort(__float2bfloat16_rn(b));
+    return lo | (hi << 16);
+}
+
+// Diagonal block [k0, k0+kb) factored in place (L11 written to G).  With want_inv, the
+// inverses of its four 32 x 32 diagonal blocks go to Dinv (4 x 32 x 32, row-major).
+// 512 threads; dynamic shared memory: A (PB x AS) and the transposed sub-panel P (SUB x PB).
+__global__ void __launch_bounds__(512) potrf_inv_kernel(float* G, int R, int k0, int kb, int* flag,
+                                                        const float* floors, float* Dinv, int want_inv) {
     extern __shared__ __align__(16) unsigned char dsm[];
-    float (*A)[PB + 1] = reinterpret_cast<float (*)[PB + 1]>(dsm);
-    const int tid = threadIdx.x, B = blockDim.x;
-    for (int e = tid; e < kb * kb; e += B) {
-        const int i = e / kb, j = e - i * kb;
-        A[i][j] = j <= i ? G[(size_t)(k0 + i) * R + k0 + j] : 0.f;
+    float (*A)[AS] = reinterpret_cast<float (*)[AS]>(dsm);
+    float (*P)[PB] = reinterpret_cast<float (*)[PB]>(dsm + sizeof(float) * PB * AS);   // P[k][row]
+    __shared__ float invd[PB];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    for (int e = tid; e < PB * PB; e += 512) {
+        const int i = e >> 7, j = e & (PB - 1);
+        A[i][j] = (i < kb && j <= i) ? G[(size_t)(k0 + i) * R + k0 + j] : 0.f;
     }
     __syncthreads();
-    for (int j = 0; j < kb; ++j) {
-        if (tid == 0) {
-            const float d = A[j][j];
-            if (!(d > *floor_p)) atomicOr(flag, 1);
-            A[j][j] = sqrtf(d);
+    for (int sb = 0; sb < kb; sb += SUB) {
+        const int w = kb - sb < SUB ? kb - sb : SUB;
+        if (warp == 0) {
+            // (a) 32 x 32 diagonal block in registers: lane i holds row sb + i (padded rows
+            // beyond kb are identity rows)
+            float a[SUB];
+            float dinv = 1.f;
+#pragma unroll
+            for (int c = 0; c < SUB; ++c)
+                a[c] = lane < w ? (c <= lane ? A[sb + lane][sb + c] : 0.f) : (c == lane ? 1.f : 0.f);
+#pragma unroll 32
+            for (int j = 0; j < SUB; ++j) {
+                const float d = __shfl_sync(0xffffffffu, a[j], j);
+                if (lane == 0 && j < w && !(d > floors[k0 + sb + j])) atomicOr(flag, 1);
+                const float sq = sqrtf(d);
+                const float inv = 1.f / sq;
+                if (lane == j) dinv = inv;
+                a[j] = lane == j ? sq : (lane > j ? a[j] * inv : a[j]);
+#pragma unroll 31
+                for (int c = j + 1; c < SUB; ++c) {
+                    const float lcj = __shfl_sync(0xffffffffu, a[j], c);
+                    if (lane >= c) a[c] = fmaf(-a[j], lcj, a[c]);
+                }
+            }
+            if (lane < w) {
+#pragma unroll
+                for (int c = 0; c < SUB; ++c) {
+                    const float v = c <= lane ? a[c] : 0.f;
+                    A[sb + lane][sb + c] = v;
+                    P[c][sb + lane] = v;
+                }
+                invd[sb + lane] = dinv;
+            }
         }
         __syncthreads();
-        const float inv = 1.f / A[j][j];
-        for (int i = j + 1 + tid; i < kb; i += B) A[i][j] *= inv;
+        const int below = sb + w, nb = kb - below;
+        // (b) rows below the sub-block: x = a L_sub^-T, thread per row
+        if (tid < nb) {
+            const int i = below + tid;
+            float x[SUB];
+#pragma unroll
+            for (int c = 0; c < SUB; ++c) x[c] = A[i][sb + c];
+#pragma unroll
+            for (int c = 0; c < SUB; ++c) {
+                float s0 = x[c], s1 = 0.f;
+#pragma unroll
+                for (int k = 0; k < c; k += 2) {
+                    s0 = fmaf(-x[k], A[sb + c][sb + k], s0);
+                    if (k + 1 < c) s1 = fmaf(-x[k + 1], A[sb + c][sb + k + 1], s1);
+                }
+                x[c] = (s0 + s1) * invd[sb + c];
+            }
+#pragma unroll
+            for (int c = 0; c < SUB; ++c) {
+                A[i][sb + c] = x[c];
+                P[c][i] = x[c];
+            }
+        }
         __syncthreads();
-        // trailing update of the block: a 16 x (B/16) thread grid over (row, column)
-        const int tc = tid & 15, tr = tid >> 4, nr = B >> 4;
-        for (int i = j + 1 + tr; i < kb; i += nr) {
-            const float lij = A[i][j];
-            for (int c = j + 1 + tc; c <= i; c += 16) A[i][c] -= lij * A[c][j];
+        // (c) rank-32 update of the rest of the block, 4 x 4 lower tiles per thread
+        const int nt4 = (nb + 3) >> 2;
+        for (int t = tid; t < nt4 * (nt4 + 1) / 2; t += 512) {
+            int ti = (int)((sqrtf(8.f * (float)t + 1.f) - 1.f) * 0.5f);
+            while ((ti + 1) * (ti + 2) / 2 <= t) ++ti;
+            while (ti * (ti + 1) / 2 > t) --ti;
+            const int tcol = t - ti * (ti + 1) / 2;
+            const int i0 = below + 4 * ti, c0 = below + 4 * tcol;
+            float acc[4][4];
+#pragma unroll
+            for (int x = 0; x < 4; ++x)
+#pragma unroll
+                for (int y = 0; y < 4; ++y) acc[x][y] = 0.f;
+#pragma unroll 8
+            for (int k = 0; k < SUB; ++k) {
+                const float4 pi = *reinterpret_cast<const float4*>(&P[k][i0]);
+                const float4 pc = *reinterpret_cast<const float4*>(&P[k][c0]);
+                const float vi[4] = {pi.x, pi.y, pi.z, pi.w}, vc[4] = {pc.x, pc.y, pc.z, pc.w};
+#pragma unroll
+                for (int x = 0; x < 4; ++x)
+#pragma unroll
+                    for (int y = 0; y < 4; ++y) acc[x][y] = fmaf(vi[x], vc[y], acc[x][y]);
+            }
+#pragma unroll
+            for (int x = 0; x < 4; ++x)
+#pragma unroll
+                for (int y = 0; y < 4; ++y)
+                    if (i0 + x < kb && c0 + y <= i0 + x) A[i0 + x][c0 + y] -= acc[x][y];
         }
         __syncthreads();
     }
-    for (int e = tid; e < kb * kb; e += B) {
+    for (int e = tid; e < kb * kb; e += 512) {
         const int i = e / kb, j = e - i * kb;
         if (j <= i) G[(size_t)(k0 + i) * R + k0 + j] = A[i][j];
     }
-}
-
-// L21 = A21 L11^-T, 32 rows per block, thread per row.
-template <int PB>
-__global__ void trsm_panel_wide_kernel(float* G, int R, int k0, int kb) {
-    extern __shared__ __align__(16) unsigned char dsm[];
-    float (*L)[PB + 1] = reinterpret_cast<float (*)[PB + 1]>(dsm);
-    float (*X)[PB + 1] = L + PB;
-    const int tid = threadIdx.x, B = blockDim.x;
-    const int row0 = k0 + kb + 32 * blockIdx.x;
-    const int rows = R - row0 < 32 ? R - row0 : 32;
-    for (int e = tid; e < kb * kb; e += B) {
-        const int i = e / kb, j = e - i * kb;
-        L[i][j] = j <= i ? G[(size_t)(k0 + i) * R + k0 + j] : 0.f;
-    }
-    for (int e = tid; e < rows * kb; e += B) {
-        const int i = e / kb, j = e - i * kb;
-        X[i][j] = G[(size_t)(row0 + i) * R + k0 + j];
-    }
-    __shared__ float Linvd[PB];
-    for (int c = tid; c < kb; c += B) Linvd[c] = 1.f / G[(size_t)(k0 + c) * R + k0 + c];
-    __syncthreads();
-    if (tid < rows) {
-        // forward substitution along the row, four independent partial sums per column
-        for (int c = 0; c < kb; ++c) {
-            float s0 = X[tid][c], s1 = 0.f, s2 = 0.f, s3 = 0.f;
-            int cc = 0;
-            for (; cc + 3 < c; cc += 4) {
-                s0 -= X[tid][cc] * L[c][cc];
-                s1 -= X[tid][cc + 1] * L[c][cc + 1];
-                s2 -= X[tid][cc + 2] * L[c][cc + 2];
-                s3 -= X[tid][cc + 3] * L[c][cc + 3];
+    if (!want_inv) return;
+    // inverses of the four diagonal 32 x 32 blocks (needs kb = PB): warp d, lane c solves
+    // L_dd x = e_c; entries above the diagonal come out zero
+    if (warp < 4) {
+        const int d = warp, c = lane;
+        float x[SUB];
+#pragma unroll
+        for (int i = 0; i < SUB; ++i) {
+            float s0 = i == c ? 1.f : 0.f, s1 = 0.f;
+#pragma unroll
+            for (int k = 0; k < i; k += 2) {
+                s0 = fmaf(-A[d * SUB + i][d * SUB + k], x[k], s0);
+                if (k + 1 < i) s1 = fmaf(-A[d * SUB + i][d * SUB + k + 1], x[k + 1], s1);
             }
-            for (; cc < c; ++cc) s0 -= X[tid][cc] * L[c][cc];
-            X[tid][c] = ((s0 + s1) + (s2 + s3)) * Linvd[c];
+            x[i] = (s0 + s1) * invd[d * SUB + i];
         }
-    }
-    __syncthreads();
-    for (int e = tid; e < rows * kb; e += B) {
-        const int i = e / kb, j = e - i * kb;
-        G[(size_t)(row0 + i) * R + k0 + j] = X[i][j];
+#pragma unroll
+        for (int i = 0; i < SUB; ++i) Dinv[(d * SUB + i) * SUB + c] = x[i];
     }
 }
 
-// A22 -= L21 L21^T on lower 128 x 128 tiles, 8 x 8 outputs per thread, K in chunks of 32.
-__global__ void __launch_bounds__(256) syrk128_kernel(float* G, int R, int k0, int kb, int t0) {
-    constexpr int TS = 128, KC = 32;
-    __shared__ __align__(16) float As[KC][TS + 4];
-    __shared__ __align__(16) float Bs[KC][TS + 4];
+// L21 = A21 L11^-T for 64 panel rows per block (256 threads): 32-column block substitution,
+// X_d = (A_d - sum_{e<d} X_e L_de^T) Dinv_d^T.  Writes L21 (FP32) into G and the BF16 hi/lo
+// operand tiles of the trailing update (rows at or beyond R as zeros).
+__global__ void __launch_bounds__(256) trsm_pack_kernel(float* G, int R, int k0, const float* Dinv,
+                                                        unsigned char* Lp) {
+    extern __shared__ __align__(16) unsigned char dsm[];
+    float (*X)[AS] = reinterpret_cast<float (*)[AS]>(dsm);                                 // 64 rows
+    float (*L)[AS] = reinterpret_cast<float (*)[AS]>(dsm + sizeof(float) * 64 * AS);      // L11
+    float (*D)[SUB + 4] = reinterpret_cast<float (*)[SUB + 4]>(dsm + sizeof(float) * (64 + PB) * AS);
+    const int tid = threadIdx.x;
+    const int t0 = k0 + PB;
+    const int r0 = blockIdx.x * 64;
+    for (int e = tid; e < 64 * (PB / 4); e += 256) {
+        const int r = e / (PB / 4), c4 = (e % (PB / 4)) * 4;
+        const int g = t0 + r0 + r;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (g < R) {
+            const float* src = G + (size_t)g * R + k0 + c4;
+            v = make_float4(src[0], src[1], src[2], src[3]);
+        }
+        *reinterpret_cast<float4*>(&X[r][c4]) = v;
+    }
+    for (int e = tid; e < PB * (PB / 4); e += 256) {
+        const int r = e / (PB / 4), c4 = (e % (PB / 4)) * 4;
+        const float* src = G + (size_t)(k0 + r) * R + k0 + c4;
+        *reinterpret_cast<float4*>(&L[r][c4]) = make_float4(src[0], src[1], src[2], src[3]);
+    }
+    for (int e = tid; e < 4 * SUB * SUB; e += 256) D[e / SUB][e % SUB] = Dinv[e];
+    __syncthreads();
+    // thread: row r = tid / 4, columns cq*8 .. cq*8+7 of the current 32-column block
+    const int r = tid >> 2, cq = tid & 3;
+    for (int d = 0; d < 4; ++d) {
+        const int cb = d * SUB + cq * 8;
+        float y[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) y[j] = X[r][cb + j];
+        for (int k = 0; k < d * SUB; k += 4) {
+            const float4 xv = *reinterpret_cast<const float4*>(&X[r][k]);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const float4 lv = *reinterpret_cast<const float4*>(&L[cb + j][k]);
+                y[j] = fmaf(-xv.x, lv.x, y[j]);
+                y[j] = fmaf(-xv.y, lv.y, y[j]);
+                y[j] = fmaf(-xv.z, lv.z, y[j]);
+                y[j] = fmaf(-xv.w, lv.w, y[j]);
+            }
+        }
+        // the 32 Y values of row r for block d are spread over the 4 threads of the quad
+        __syncthreads();   // every thread has read X's block d before it is overwritten
+#pragma unroll
+        for (int j = 0; j < 8; ++j) X[r][cb + j] = y[j];
+        __syncthreads();
+        float xo[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) xo[j] = 0.f;
+        for (int t = 0; t < SUB; t += 4) {
+            const float4 yv = *reinterpret_cast<const float4*>(&X[r][d * SUB + t]);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const float4 dv = *reinterpret_cast<const float4*>(&D[d * SUB + cq * 8 + j][t]);
+                xo[j] = fmaf(yv.x, dv.x, xo[j]);
+                xo[j] = fmaf(yv.y, dv.y, xo[j]);
+                xo[j] = fmaf(yv.z, dv.z, xo[j]);
+                xo[j] = fmaf(yv.w, dv.w, xo[j]);
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < 8; ++j) X[r][cb + j] = xo[j];
+        __syncthreads();
+    }
+    // write L21 to G and the packed operand rows
+    const int g = t0 + r0 + r;
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+        const int c0 = h * SUB + cq * 8;
+        float v[8], lo[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) v[j] = g < R ? X[r][c0 + j] : 0.f;
+        if (g < R) {
+            float* dst = G + (size_t)g * R + k0 + c0;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) dst[j] = v[j];
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j) lo[j] = v[j] - __bfloat162float(__float2bfloat16_rn(v[j]));
+        const int pr = r0 + r;
+        unsigned char* tile = Lp + (size_t)(pr >> 7) * kTileBytes;
+        const uint32_t off = packed_off(pr & 127, c0);
+        *reinterpret_cast<uint4*>(tile + off) =
+            make_uint4(pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]), pack_bf16x2(v[4], v[5]), pack_bf16x2(v[6], v[7]));
+        *reinterpret_cast<uint4*>(tile + kPartBytes + off) = make_uint4(
+            pack_bf16x2(lo[0], lo[1]), pack_bf16x2(lo[2], lo[3]), pack_bf16x2(lo[4], lo[5]), pack_bf16x2(lo[6], lo[7]));
+    }
+}
+
+// A22 -= L21_i L21_j^T for one lower 128 x 128 tile (ti >= tj) of the trailing matrix that
+// starts at row/column t0.  256 threads: warps w and w+4 own TMEM lanes 32(w%4).. and columns
+// 64(w/4) ..; each thread reads its 64 G entries into registers first, so the HBM reads
+// overlap the operand copies and the MMAs; thread 0 moves the operands (two K-halves, bulk
+// copies) and issues the MMAs.
+__global__ void __launch_bounds__(256) syrk_tc_kernel(float* G, int R, int t0, const unsigned char* Lp, int* err) {
+    extern __shared__ unsigned char syrk_raw[];
+    unsigned char* sm = reinterpret_cast<unsigned char*>(((uintptr_t)syrk_raw + 127) & ~(uintptr_t)127);
+    __shared__ __align__(8) uint64_t bar_load, bar_half, bar_done;
+    __shared__ uint32_t tmem_slot;
+    __shared__ int issue_ok;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const long long b = blockIdx.x;
     int ti = (int)((sqrtf(8.f * (float)b + 1.f) - 1.f) * 0.5f);
     while ((long long)(ti + 1) * (ti + 2) / 2 <= b) ++ti;
     while ((long long)ti * (ti + 1) / 2 > b) --ti;
     const int tj = (int)(b - (long long)ti * (ti + 1) / 2);
-    const int r0 = t0 + ti * TS, c0 = t0 + tj * TS;
-    const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
-    const bool vec = (R & 3) == 0 && (k0 & 3) == 0;
-    float acc[8][8];
+    const bool diag = ti == tj;
+
+    if (warp == 0) tc::tmem_alloc(&tmem_slot, 128);
+    if (tid == 0) {
+        tc::mbar_init(&bar_load, 1);
+        tc::mbar_init(&bar_half, 1);
+        tc::mbar_init(&bar_done, 1);
+        tc::fence_mbar_init();
+    }
+    // this thread's G entries: row grow, columns gcol0 .. gcol0+63
+    const int grow = t0 + ti * 128 + (warp & 3) * 32 + lane;
+    const int gcol0 = t0 + tj * 128 + (warp >> 2) * 64;
+    const bool vec = (R & 3) == 0;
+    float gv[64];
+    if (grow < R) {
+        const float* src = G + (size_t)grow * R + gcol0;
+        if (vec && gcol0 + 64 <= R) {
 #pragma unroll
-    for (int i = 0; i < 8; ++i)
+            for (int e = 0; e < 64; e += 4) {
+                const float4 x = *reinterpret_cast<const float4*>(src + e);
+                gv[e] = x.x;
+                gv[e + 1] = x.y;
+                gv[e + 2] = x.z;
+                gv[e + 3] = x.w;
+            }
+        } else {
 #pragma unroll
-        for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
-    for (int tb = 0; tb < kb; tb += KC) {
-        __syncthreads();
-#pragma unroll
-        for (int l = 0; l < 4; ++l) {
-            const int e = tid + l * 256;
-            const int row = e >> 3, c4 = (e & 7) * 4;
-            float va[4] = {0.f, 0.f, 0.f, 0.f}, vb[4] = {0.f, 0.f, 0.f, 0.f};
-            const int ga = r0 + row, gb = c0 + row, kk = tb + c4;
-            if (vec && kk + 3 < kb) {
-                if (ga < R) {
-                    const float4 x = *reinterpret_cast<const float4*>(G + (size_t)ga * R + k0 + kk);
-                    va[0] = x.x; va[1] = x.y; va[2] = x.z; va[3] = x.w;
+            for (int e = 0; e < 64; ++e) gv[e] = gcol0 + e < R ? src[e] : 0.f;
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = tmem_slot;
+
+    if (tid == 0) {
+        int ok = 1;
+        const unsigned char* srcA = Lp + (size_t)ti * kTileBytes;
+        const unsigned char* srcB = Lp + (size_t)tj * kTileBytes;
+        const uint32_t a_base = tc::smem_u32(sm);
+        const uint32_t b_base = diag ? a_base : a_base + kHalfBytes;
+        constexpr uint32_t SBO = (128 / 16) * 128;
+        constexpr uint32_t idesc = tc::idesc_bf16(128, 128);
+        for (int h = 0; h < 2; ++h) {
+            if (h == 1) {
+                // the first half's MMAs must have read shared memory before it is refilled
+                tc::mma_commit(&bar_half);
+                if (!tc::mbar_wait(&bar_half, 0u, kCholWaitLimit)) {
+                    ok = 0;
+                    atomicOr(err, 1);
+                    break;
                 }
-                if (gb < R) {
-                    const float4 x = *reinterpret_cast<const float4*>(G + (size_t)gb * R + k0 + kk);
-                    vb[0] = x.x; vb[1] = x.y; vb[2] = x.z; vb[3] = x.w;
-                }
+            }
+            tc::mbar_arrive_expect_tx(&bar_load, diag ? kHalfBytes : 2 * kHalfBytes);
+            tc::bulk_g2s(sm, srcA + h * kHalfBytes, kHalfBytes, &bar_load);
+            if (!diag) tc::bulk_g2s(sm + kHalfBytes, srcB + h * kHalfBytes, kHalfBytes, &bar_load);
+            if (!tc::mbar_wait(&bar_load, (uint32_t)h, kCholWaitLimit)) {
+                ok = 0;
+                atomicOr(err, 2);
+                // the copies may still be in flight: give them one more bounded wait
+                if (!tc::mbar_wait(&bar_load, (uint32_t)h, kCholWaitLimit)) atomicOr(err, 8);
+                break;
+            }
+            tc::fence_after_sync();
+#pragma unroll
+            for (int ks = 0; ks < 4; ++ks) {
+                const uint32_t ko = ks * 256;
+                const uint64_t ah = tc::make_desc(a_base + ko, 128, SBO);
+                const uint64_t al = tc::make_desc(a_base + kPartBytes + ko, 128, SBO);
+                const uint64_t bh = tc::make_desc(b_base + ko, 128, SBO);
+                const uint64_t bl = tc::make_desc(b_base + kPartBytes + ko, 128, SBO);
+                tc::mma_bf16(tmem, ah, bh, idesc, (h | ks) ? 1u : 0u);
+                tc::mma_bf16(tmem, ah, bl, idesc, 1u);
+                tc::mma_bf16(tmem, al, bh, idesc, 1u);
+            }
+        }
+        issue_ok = ok;
+        tc::mma_commit(&bar_done);     // every MMA issued by this thread (possibly none)
+    }
+    const bool done = tc::mbar_wait(&bar_done, 0u, kCholWaitLimit);
+    if (!done) atomicOr(err, 4);
+    tc::fence_after_sync();
+    const int all_ok = __syncthreads_and(done ? 1 : 0) && issue_ok;
+    if (all_ok) {
+        const uint32_t taddr = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)((warp >> 2) * 64);
+#pragma unroll
+        for (int c0 = 0; c0 < 64; c0 += 16) {
+            float v[16];
+            tc::tmem_ld16(taddr + (uint32_t)c0, v);
+            tc::tmem_wait_ld();
+#pragma unroll
+            for (int e = 0; e < 16; ++e) gv[c0 + e] -= v[e];
+        }
+        if (grow < R) {
+            float* dst = G + (size_t)grow * R + gcol0;
+            if (vec && !diag && gcol0 + 64 <= R) {
+#pragma unroll
+                for (int e = 0; e < 64; e += 4)
+                    *reinterpret_cast<float4*>(dst + e) = make_float4(gv[e], gv[e + 1], gv[e + 2], gv[e + 3]);
             } else {
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    if (kk + q < kb) {
-                        if (ga < R) va[q] = G[(size_t)ga * R + k0 + kk + q];
-                        if (gb < R) vb[q] = G[(size_t)gb * R + k0 + kk + q];
-                    }
-                }
-            }
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                As[c4 + q][row] = va[q];
-                Bs[c4 + q][row] = vb[q];
+                for (int e = 0; e < 64; ++e)
+                    if (gcol0 + e < R && gcol0 + e <= grow) dst[e] = gv[e];
             }
         }
-        __syncthreads();
-#pragma unroll 4
-        for (int k = 0; k < KC; ++k) {
-            const float4 a0 = *reinterpret_cast<const float4*>(&As[k][ty * 8]);
-            const float4 a1 = *reinterpret_cast<const float4*>(&As[k][ty * 8 + 4]);
-            const float4 b0 = *reinterpret_cast<const float4*>(&Bs[k][tx * 8]);
-            const float4 b1 = *reinterpret_cast<const float4*>(&Bs[k][tx * 8 + 4]);
-            const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-            const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
-#pragma unroll
-            for (int i = 0; i < 8; ++i)
-#pragma unroll
-                for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
-        }
     }
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        const int gi = r0 + ty * 8 + i;
-        if (gi >= R) continue;
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const int gj = c0 + tx * 8 + j;
-            if (gj < R && gj <= gi) G[(size_t)gi * R + gj] -= acc[i][j];
-        }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, 128);
+}
+
+// FP32 factorisation; ws: pivot floors (R floats), the diagonal-block inverses, the packed
+// operand tiles.  The pivot flag goes to d_flag[0], an expired device wait to d_flag[1].
+static fst_status cholesky_lower_tc(float* G, int R, int* d_flag, const float* floors, unsigned char* ws_tail,
+                                    cudaStream_t s) {
+    float* Dinv = reinterpret_cast<float*>(ws_tail);
+    unsigned char* Lp = ws_tail + 4 * SUB * SUB * sizeof(float);
+    const size_t potrf_smem = sizeof(float) * (PB * AS + SUB * PB);
+    const size_t trsm_smem = sizeof(float) * ((64 + PB) * AS + 4 * SUB * (SUB + 4));
+    const size_t syrk_smem = 2 * kHalfBytes + 128;
+    FST_CUDA(cudaFuncSetAttribute(potrf_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)potrf_smem));
+    FST_CUDA(cudaFuncSetAttribute(trsm_pack_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)trsm_smem));
+    FST_CUDA(cudaFuncSetAttribute(syrk_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)syrk_smem));
+    for (int k0 = 0; k0 < R; k0 += PB) {
+        const int kb = R - k0 < PB ? R - k0 : PB;
+        const int rest = R - k0 - kb;
+        potrf_inv_kernel<<<1, 512, potrf_smem, s>>>(G, R, k0, kb, d_flag, floors, Dinv, rest > 0 ? 1 : 0);
+        FST_CHECK_LAUNCH();
+        if (rest <= 0) break;
+        const int nt = (rest + PB - 1) / PB;
+        trsm_pack_kernel<<<2 * nt, 256, trsm_smem, s>>>(G, R, k0, Dinv, Lp);
+        FST_CHECK_LAUNCH();
+        syrk_tc_kernel<<<(unsigned)((long long)nt * (nt + 1) / 2), 256, syrk_smem, s>>>(G, R, k0 + PB, Lp,
+                                                                                        d_flag + 1);
+        FST_CHECK_LAUNCH();
     }
+    return FST_OK;
 }
 
 template <typename T>
-fst_status cholesky_lower(T* G, int R, int* d_flag, cudaStream_t s) {
-    // d_flag points at two ints of scratch: the flag, then room for the pivot floor
-    T* floor_p = reinterpret_cast<T*>(d_flag + 2);
-    pivot_floor_kernel<T><<<1, 256, 0, s>>>(G, R, floor_p);
+fst_status cholesky_lower(T* G, int R, int* d_flag, DevBuf& ws, cudaStream_t s) {
+    // ws: per-column pivot floors, then (FP32) the panel scratch of the tensor-core path
+    const size_t floor_bytes = ((size_t)R * sizeof(T) + 255) / 256 * 256;
+    const size_t tail = sizeof(T) == 4 ? 4 * SUB * SUB * sizeof(float) + (size_t)((R + PB - 1) / PB) * kTileBytes : 0;
+    FST_TRY(ws.ensure(floor_bytes + tail));
+    T* floors = ws.as<T>();
+    pivot_floor_kernel<T><<<(R + 255) / 256 < 1024 ? (R + 255) / 256 : 1024, 256, 0, s>>>(G, R, floors);
     FST_CHECK_LAUNCH();
-    if (sizeof(T) == 4) {
-        constexpr int PB = 128;
-        float* Gf = reinterpret_cast<float*>(G);
-        const float* fl = reinterpret_cast<const float*>(floor_p);
-        const size_t diag_smem = (size_t)PB * (PB + 1) * sizeof(float);
-        const size_t trsm_smem = (size_t)(PB + 32) * (PB + 1) * sizeof(float);
-        FST_CUDA(cudaFuncSetAttribute(potrf_diag_wide_kernel<PB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)diag_smem));
-        FST_CUDA(cudaFuncSetAttribute(trsm_panel_wide_kernel<PB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)trsm_smem));
-        for (int k0 = 0; k0 < R; k0 += PB) {
-            const int kb = R - k0 < PB ? R - k0 : PB;
-            potrf_diag_wide_kernel<PB><<<1, 512, diag_smem, s>>>(Gf, R, k0, kb, d_flag, fl);
-            FST_CHECK_LAUNCH();
-            const int t0 = k0 + kb;
-            const int rest = R - t0;
-            if (rest <= 0) break;
-            trsm_panel_wide_kernel<PB><<<(rest + 31) / 32, 128, trsm_smem, s>>>(Gf, R, k0, kb);
-            FST_CHECK_LAUNCH();
-            const long long nt = (rest + 127) / 128;
-            syrk128_kernel<<<(unsigned)(nt * (nt + 1) / 2), 256, 0, s>>>(Gf, R, k0, kb, t0);
-            FST_CHECK_LAUNCH();
-        }
-        return FST_OK;
-    }
+    if (sizeof(T) == 4)
+        return cholesky_lower_tc(reinterpret_cast<float*>(G), R, d_flag, reinterpret_cast<const float*>(floors),
+                                 ws.as<unsigned char>() + floor_bytes, s);
     const size_t trsm_smem = 2 * NB * (NB + 1) * sizeof(T);
     FST_CUDA(cudaFuncSetAttribute(trsm_panel_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)trsm_smem));
     for (int k0 = 0; k0 < R; k0 += NB) {
         const int kb = R - k0 < NB ? R - k0 : NB;
-        potrf_diag_kernel<T><<<1, 256, 0, s>>>(G, R, k0, kb, d_flag, floor_p);
+        potrf_diag_kernel<T><<<1, 256, 0, s>>>(G, R, k0, kb, d_flag, floors);
         FST_CHECK_LAUNCH();
         const int t0 = k0 + kb;
         const int rest = R - t0;
@@ -390,63 +619,145 @@ __global__ void invert_diag_kernel(const T* L, int R, T* Linv) {
     }
 }
 
-// Forward step for diagonal block b: every block forms x_b = Linv_bb xin_b, block 0 stores it
-// in y; rows below block b (64 per block, a warp per row) subtract L_{i,b} x_b from xin.
-template <typename T>
-__global__ void __launch_bounds__(256) fwd_step_kernel(const T* L, const T* Linv, int R, int b, T* xin, T* y) {
-    __shared__ T xs[NB], xb[NB];
-    const int k0 = b * NB, kb = R - k0 < NB ? R - k0 : NB;
-    for (int i = threadIdx.x; i < NB; i += blockDim.x) xs[i] = i < kb ? xin[k0 + i] : T(0);
-    __syncthreads();
-    const T* Li = Linv + (size_t)b * NB * NB;
-    {
-        // x_b = Linv_bb xs: four threads per row, 16 contiguous entries each (coalesced)
-        const int i = threadIdx.x >> 2, part = threadIdx.x & 3;
-        T s = T(0);
-#pragma unroll
-        for (int c = 0; c < NB / 4; ++c) s += Li[i * NB + part * (NB / 4) + c] * xs[part * (NB / 4) + c];
-        s += __shfl_xor_sync(0xffffffffu, s, 1);
-        s += __shfl_xor_sync(0xffffffffu, s, 2);
-        if (part == 0) xb[i] = s;
-    }
-    __syncthreads();
-    if (blockIdx.x == 0)
-        for (int i = threadIdx.x; i < kb; i += blockDim.x) y[k0 + i] = xb[i];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int r0 = k0 + kb + blockIdx.x * NB;
-    for (int rr = warp; rr < NB; rr += blockDim.x >> 5) {
-        const int i = r0 + rr;
-        if (i >= R) break;
-        T s = T(0);
-        for (int c = lane; c < kb; c += 32) s += L[(size_t)i * R + k0 + c] * xb[c];
-        for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) xin[i] -= s;
-    }
+// One direction of x <- L^-T L^-1 x in a single launch.  Block row i (64 rows) is solved
+// by one block: forward, y_i = Linv_ii (b_i - sum_{j<i} L_ij y_j); backward (TRANS),
+// x_i = Linv_ii^T (y_i - sum_{j>i} L_ji^T x_j).  Blocks take block rows in solve order
+// from a ticket counter, so a block only waits for rows already taken by running blocks
+// (no deadlock whatever the residency).  A finished row publishes its values, then its
+// ready flag; every wait on a flag is bounded, and on expiry the block records an error
+// and still publishes (so the rows after it do not all wait out their own limits).
+// sync: [0] error word, [1] ticket, [2 + i] ready flag of block row i (zeroed before).
+constexpr long long kSolveWaitLimit = 2000000000LL;
+
+__device__ __forceinline__ int ld_acquire(const int* p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release(int* p, int v) {
+    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// Backward step for block b: x_b = Linv_bb^T yin_b stored in out; rows above subtract
-// L_{b,i}^T x_b from yin (thread per row, coalesced along i).
-template <typename T>
-__global__ void __launch_bounds__(256) bwd_step_kernel(const T* L, const T* Linv, int R, int b, T* yin, T* out) {
-    __shared__ T ys[NB], xb[NB];
-    const int k0 = b * NB, kb = R - k0 < NB ? R - k0 : NB;
-    for (int i = threadIdx.x; i < NB; i += blockDim.x) ys[i] = i < kb ? yin[k0 + i] : T(0);
+template <typename T, bool TRANS>
+__global__ void __launch_bounds__(256) trsv_kernel(const T* __restrict__ L, const T* __restrict__ Linv, int R,
+                                                   int nblk, const T* bin, T* out, int* sync) {
+    __shared__ T lis[NB][NB + 1];   // Linv of the diagonal block
+    __shared__ T red[4][NB];
+    __shared__ T vs[NB];
+    __shared__ int s_ticket, s_known;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid == 0) s_ticket = atomicAdd(&sync[1], 1);
     __syncthreads();
-    const T* Li = Linv + (size_t)b * NB * NB;
-    for (int i = threadIdx.x; i < NB; i += blockDim.x) {
-        T s = T(0);
-        for (int c = 0; c < NB; ++c) s += Li[c * NB + i] * ys[c];
-        xb[i] = s;
+    const int t = s_ticket;
+    const int i = TRANS ? nblk - 1 - t : t;
+    const int k0 = i * NB, kb = R - k0 < NB ? R - k0 : NB;
+    {
+        const T* Li = Linv + (size_t)i * NB * NB;
+        for (int e = tid; e < NB * NB; e += 256) lis[e / NB][e % NB] = Li[e];
+    }
+    // tile mappings (both coalesced along a row of L):
+    //   forward, tile (i, j): warp w owns rows 8w .. 8w+7, lane l columns l and l + 32;
+    //   backward, tile (j, i): thread owns column c = tid % 64 and rows 16 q .. 16 q + 15
+    const int q = tid >> 6, c = tid & 63;
+    T acc[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) acc[u] = T(0);
+    const int* ready = sync + 2;
+    const int ntiles = TRANS ? nblk - 1 - i : i;
+    if (tid == 0) s_known = 0;
+    __syncthreads();
+    int known = 0;   // tiles 0 .. known-1 (in solve order) have published values
+    for (int n = 0; n < ntiles; ++n) {
+        const int j = TRANS ? nblk - 1 - n : n;
+        const int j0 = j * NB;
+        T lv[16];
+        if (TRANS) {
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+                const int row = j0 + q * 16 + u, col = k0 + c;
+                lv[u] = (row < R && col < R) ? L[(size_t)row * R + col] : T(0);
+            }
+        } else {
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int row = k0 + warp * 8 + u;
+                const bool rok = row < R;
+                lv[2 * u] = (rok && j0 + lane < R) ? L[(size_t)row * R + j0 + lane] : T(0);
+                lv[2 * u + 1] = (rok && j0 + lane + 32 < R) ? L[(size_t)row * R + j0 + lane + 32] : T(0);
+            }
+        }
+        if (n >= known) {
+            if (tid == 0) {
+                const long long t0 = clock64();
+                bool timed_out = false;
+                while (ld_acquire(&ready[j]) == 0) {
+                    if (clock64() - t0 > kSolveWaitLimit) {
+                        timed_out = true;
+                        break;
+                    }
+                }
+                if (timed_out) atomicOr(&sync[0], 1);
+                // count the further rows already published
+                int k = n + 1;
+                while (k < ntiles && ld_acquire(&ready[TRANS ? nblk - 1 - k : k]) != 0) ++k;
+                s_known = k;
+            }
+            __syncthreads();
+            known = s_known;
+            __syncthreads();   // every thread has read s_known before thread 0 may rewrite it
+        }
+        const T* xj = out + j0;
+        if (TRANS) {
+            T sacc = T(0);
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+                const int a = q * 16 + u;
+                sacc += lv[u] * (j0 + a < R ? __ldcg(xj + a) : T(0));
+            }
+            acc[0] += sacc;
+        } else {
+            const T x0 = j0 + lane < R ? __ldcg(xj + lane) : T(0);
+            const T x1 = j0 + lane + 32 < R ? __ldcg(xj + lane + 32) : T(0);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) acc[u] += lv[2 * u] * x0 + lv[2 * u + 1] * x1;
+        }
+    }
+    // combine the partial sums of each row (forward: across the warp) / column (backward)
+    if (TRANS) {
+        red[q][c] = acc[0];
+    } else {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            T v = acc[u];
+#pragma unroll
+            for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0) red[0][warp * 8 + u] = v;
+        }
     }
     __syncthreads();
-    if (blockIdx.x == 0)
-        for (int i = threadIdx.x; i < kb; i += blockDim.x) out[k0 + i] = xb[i];
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < k0) {
-        T s = T(0);
-        for (int c = 0; c < kb; ++c) s += L[(size_t)(k0 + c) * R + i] * xb[c];
-        yin[i] -= s;
+    if (tid < NB) {
+        const T sum = TRANS ? (red[0][tid] + red[1][tid]) + (red[2][tid] + red[3][tid]) : red[0][tid];
+        vs[tid] = tid < kb ? __ldcg(bin + k0 + tid) - sum : T(0);
     }
+    __syncthreads();
+    // out_i = Linv_ii v (forward) or Linv_ii^T v (backward): thread (q, c) sums 16 terms
+    {
+        T s2 = T(0);
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+            const int a = q * 16 + u;
+            s2 += (TRANS ? lis[a][c] : lis[c][a]) * vs[a];
+        }
+        red[q][c] = s2;
+    }
+    __syncthreads();
+    if (tid < kb) {
+        const T v = (red[0][tid] + red[1][tid]) + (red[2][tid] + red[3][tid]);
+        __stcg(out + k0 + tid, v);
+        __threadfence();
+    }
+    __syncthreads();
+    if (tid == 0) st_release((int*)&ready[i], 1);
 }
 
 template <typename T>
@@ -457,27 +768,22 @@ fst_status chol_invert_diag(const T* L, int R, T* Linv, cudaStream_t s) {
     return FST_OK;
 }
 
-// x <- L^-T L^-1 x (x and y: R values of T; y is scratch).
+// x <- L^-T L^-1 x (x and y: R values of T; y is scratch; sync: 2 + nblk ints whose
+// first is the error word, left as it is).
 template <typename T>
-fst_status chol_solve(const T* L, const T* Linv, int R, T* x, T* y, cudaStream_t s) {
+fst_status chol_solve(const T* L, const T* Linv, int R, T* x, T* y, int* sync, cudaStream_t s) {
     const int nblk = (R + NB - 1) / NB;
-    for (int b = 0; b < nblk; ++b) {
-        const int rest = R - (b + 1) * NB;
-        const int grid = rest > 0 ? (rest + NB - 1) / NB : 1;
-        fwd_step_kernel<T><<<grid, 256, 0, s>>>(L, Linv, R, b, x, y);
-        FST_CHECK_LAUNCH();
-    }
-    for (int b = nblk - 1; b >= 0; --b) {
-        const int k0 = b * NB;
-        const int grid = k0 > 0 ? (k0 + 255) / 256 : 1;
-        bwd_step_kernel<T><<<grid, 256, 0, s>>>(L, Linv, R, b, y, x);
-        FST_CHECK_LAUNCH();
-    }
+    FST_CUDA(cudaMemsetAsync(sync + 1, 0, (size_t)(nblk + 1) * sizeof(int), s));
+    trsv_kernel<T, false><<<nblk, 256, 0, s>>>(L, Linv, R, nblk, x, y, sync);
+    FST_CHECK_LAUNCH();
+    FST_CUDA(cudaMemsetAsync(sync + 1, 0, (size_t)(nblk + 1) * sizeof(int), s));
+    trsv_kernel<T, true><<<nblk, 256, 0, s>>>(L, Linv, R, nblk, y, x, sync);
+    FST_CHECK_LAUNCH();
     return FST_OK;
 }
 
-template fst_status cholesky_lower<float>(float*, int, int*, cudaStream_t);
-template fst_status cholesky_lower<double>(double*, int, int*, cudaStream_t);
+template fst_status cholesky_lower<float>(float*, int, int*, DevBuf&, cudaStream_t);
+template fst_status cholesky_lower<double>(double*, int, int*, DevBuf&, cudaStream_t);
 template <typename T>
 fst_status chol_solve_graph(SolveGraph& g, const T* L, const T* Linv, int R, T* x, T* y, cudaStream_t s) {
     if (!g.exec || g.L != L || g.Linv != Linv || g.x != x || g.R != R || g.elem != (int)sizeof(T)) {
@@ -487,9 +793,12 @@ fst_status chol_solve_graph(SolveGraph& g, const T* L, const T* Linv, int R, T* 
             g.exec = nullptr;
         }
         if (!g.cap) FST_CUDA(cudaStreamCreateWithFlags(&g.cap, cudaStreamNonBlocking));
+        FST_TRY(g.sync.ensure(sizeof(int) * (size_t)(R / NB + 4)));
+        FST_CUDA(cudaMemsetAsync(g.sync.ptr, 0, sizeof(int), s));
+        FST_CUDA(cudaStreamSynchronize(s));
         FST_CUDA(cudaStreamBeginCapture(g.cap, cudaStreamCaptureModeThreadLocal));
         const uint64_t before = fst_kernel_launches();
-        fst_status st = chol_solve<T>(L, Linv, R, x, y, g.cap);
+        fst_status st = chol_solve<T>(L, Linv, R, x, y, g.sync.as<int>(), g.cap);
         cudaGraph_t graph = nullptr;
         cudaError_t e = cudaStreamEndCapture(g.cap, &graph);
         if (st != FST_OK) {
@@ -518,7 +827,39 @@ template fst_status chol_solve_graph<double>(SolveGraph&, const double*, const d
 
 template fst_status chol_invert_diag<float>(const float*, int, float*, cudaStream_t);
 template fst_status chol_invert_diag<double>(const double*, int, double*, cudaStream_t);
-template fst_status chol_solve<float>(const float*, const float*, int, float*, float*, cudaStream_t);
-template fst_status chol_solve<double>(const double*, const double*, int, double*, double*, cudaStream_t);
+template fst_status chol_solve<float>(const float*, const float*, int, float*, float*, int*, cudaStream_t);
+template fst_status chol_solve<double>(const double*, const double*, int, double*, double*, int*, cudaStream_t);
 
 }  // namespace fst
+
+extern "C" fst_status fst_cholesky_f32(float* G, int32_t R, fst_stream stream) {
+    using namespace fst;
+    FST_REQUIRE(G != nullptr && R > 0, "G is NULL or R <= 0");
+    int dev = 0;
+    FST_CUDA(cudaGetDevice(&dev));
+    FST_REQUIRE(pointer_device(G) == dev, "G must be device memory");
+    cudaStream_t s = (cudaStream_t)stream;
+    DevBuf flag, ws;
+    struct Release {
+        DevBuf *a, *b;
+        ~Release() {
+            a->release();
+            b->release();
+        }
+    } rel{&flag, &ws};
+    FST_TRY(flag.ensure(4 * sizeof(int)));
+    FST_CUDA(cudaMemsetAsync(flag.ptr, 0, 2 * sizeof(int), s));
+    FST_TRY(cholesky_lower<float>(G, R, flag.as<int>(), ws, s));
+    int h[2] = {0, 0};
+    FST_CUDA(cudaMemcpyAsync(h, flag.ptr, sizeof h, cudaMemcpyDeviceToHost, s));
+    FST_CUDA(cudaStreamSynchronize(s));
+    if (h[1]) {
+        set_error("Cholesky: a bounded device wait expired (code %d)", h[1]);
+        return FST_ETIMEOUT;
+    }
+    if (h[0]) {
+        set_error("matrix is not positive definite in FP32 (pivot below 16 eps max diag)");
+        return FST_ENOTSPD;
+    }
+    return FST_OK;
+}

@@ -68,12 +68,13 @@ struct SolveGraph {
     void* x = nullptr;
     int R = 0, elem = 0;
     uint64_t nodes = 0;
+    DevBuf sync;                 // error word, ticket, ready flags of the one-launch solves
     void release();
 };
 
 // Scratch of the refit, kept inside the model between calls.
 struct RefitScratch {
-    DevBuf idx, U[3], b, G, G64, res, g, z, delta, alpha, norms, flag, Linv, xw, yw, pcg;
+    DevBuf idx, U[3], b, G, G64, res, g, z, delta, alpha, norms, flag, Linv, xw, yw, pcg, chol_ws;
     SolveGraph solve;
 };
 
@@ -142,11 +143,11 @@ fst_status gram_tc_launch(const fst_model* m, const float* U1, const float* U2, 
 
 // Cholesky and triangular solves (chol.cu).
 template <typename T>
-fst_status cholesky_lower(T* G, int R, int* d_flag, cudaStream_t s);
+fst_status cholesky_lower(T* G, int R, int* d_flag, DevBuf& ws, cudaStream_t s);
 template <typename T>
 fst_status chol_invert_diag(const T* L, int R, T* Linv, cudaStream_t s);   // 64x64 diagonal blocks
 template <typename T>
-fst_status chol_solve(const T* L, const T* Linv, int R, T* x, T* y, cudaStream_t s);  // x <- (L L^T)^-1 x
+fst_status chol_solve(const T* L, const T* Linv, int R, T* x, T* y, int* sync, cudaStream_t s);  // x <- (L L^T)^-1 x
 // The same through a CUDA graph captured on first use for (L, Linv, x, y, R) and replayed.
 template <typename T>
 fst_status chol_solve_graph(SolveGraph& g, const T* L, const T* Linv, int R, T* x, T* y, cudaStream_t s);

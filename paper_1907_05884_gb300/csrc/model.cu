@@ -29,6 +29,7 @@ void SolveGraph::release() {
     x = nullptr;
     R = elem = 0;
     nodes = 0;
+    sync.release();
 }
 
 void set_error(const char* fmt, ...) {

@@ -246,6 +246,15 @@ __global__ void __launch_bounds__(128) residual_kernel(const T* __restrict__ U1,
     }
 }
 
+// Relative diagonal shift of the preconditioner's matrix, G_jj <- (1 + delta) G_jj: the
+// factor of G + delta diag(G) still preconditions the conjugate gradients, which solve the
+// unshifted normal equations.
+constexpr float kPrecondShift = 2.44140625e-4f;   // 2^-12
+__global__ void shift_diag_kernel(float* G, int R, float delta) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < R; i += gridDim.x * blockDim.x)
+        G[(size_t)i * R + i] *= 1.f + delta;
+}
+
 // out[k] = sum_i x_k[i] * y_k[i] for k < nd (out zeroed by the caller)
 __global__ void dots_kernel(const double* x0, const double* y0, const double* x1, const double* y1, int n, int nd,
                             double* out) {
@@ -455,26 +464,33 @@ static fst_status refit_impl(fst_model* M, const T* xyz, const T* u, int64_t Q, 
     }
     FST_TRY(launch_atr<T>(M, Uc, rv, m, g, s));
 
-    // 3-4. Gram and Cholesky in the working precision (or FP64 when asked / on failure)
+    // 3-4. Gram and Cholesky in the working precision; if the FP32 factorisation of a
+    // TF32 / BF16 Gram fails, the BF16x3 Gram (near-FP32 products) is tried next, then FP64
     bool use64 = fp64 || force64;
+    fst_prec gram_prec = prec;
+    bool shift = false;
     void* Lp = nullptr;
-    for (int attempt = 0; attempt < 2; ++attempt) {
-        FST_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), s));
+    for (int attempt = 0; attempt < 4; ++attempt) {
+        FST_CUDA(cudaMemsetAsync(flag, 0, 2 * sizeof(int), s));
         if (!use64) {
             FST_TRY(W.G.ensure(sizeof(float) * (size_t)R * R));
             float* G = W.G.as<float>();
-            if (prec == FST_FP32) {
+            if (gram_prec == FST_FP32) {
                 FST_TRY(launch_gram_simt<float>(M, reinterpret_cast<const float* const*>(Uc), m, G, s));
             } else {
                 fst_status gst = gram_tc_launch(M, reinterpret_cast<const float*>(Uc[0]),
                                                 reinterpret_cast<const float*>(Uc[1]),
-                                                reinterpret_cast<const float*>(Uc[2]), m, G, prec, s);
+                                                reinterpret_cast<const float*>(Uc[2]), m, G, gram_prec, s);
                 if (gst == FST_EUNSUPPORTED)   // r3 < 4: the CUDA-core Gram
                     gst = launch_gram_simt<float>(M, reinterpret_cast<const float* const*>(Uc), m, G, s);
                 FST_TRY(gst);
             }
             r.ms_gram += tm.stop();
-            FST_TRY(cholesky_lower<float>(G, R, flag, s));
+            if (shift) {
+                shift_diag_kernel<<<grid_for(R, 256), 256, 0, s>>>(G, R, kPrecondShift);
+                FST_CHECK_LAUNCH();
+            }
+            FST_TRY(cholesky_lower<float>(G, R, flag, W.chol_ws, s));
             Lp = G;
         } else {
             FST_TRY(W.G64.ensure(sizeof(double) * (size_t)R * R));
@@ -496,7 +512,7 @@ static fst_status refit_impl(fst_model* M, const T* xyz, const T* u, int64_t Q, 
             }
             FST_TRY(launch_gram_simt<double>(M, U64, m, G, s));
             r.ms_gram += tm.stop();
-            FST_TRY(cholesky_lower<double>(G, R, flag, s));
+            FST_TRY(cholesky_lower<double>(G, R, flag, W.chol_ws, s));
             Lp = G;
         }
         if (use64) {
@@ -506,18 +522,31 @@ static fst_status refit_impl(fst_model* M, const T* xyz, const T* u, int64_t Q, 
             FST_TRY(W.Linv.ensure(sizeof(float) * (size_t)((R + 63) / 64) * 64 * 64));
             FST_TRY(chol_invert_diag<float>(static_cast<const float*>(Lp), R, W.Linv.as<float>(), s));
         }
-        int hflag = 0;
-        FST_CUDA(cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+        int hflag[2] = {0, 0};
+        FST_CUDA(cudaMemcpyAsync(hflag, flag, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
         FST_CUDA(cudaStreamSynchronize(s));
         r.ms_cholesky += tm.stop();
-        if (!hflag) break;
+        if (hflag[1]) {
+            set_error("Cholesky: a bounded device wait expired (code %d)", hflag[1]);
+            if (rep) *rep = r;
+            return FST_ETIMEOUT;
+        }
+        if (!hflag[0]) break;
         if (use64) {
             set_error("normal matrix is not positive definite in FP64 (rank-deficient sample)");
             if (rep) *rep = r;
             return FST_ENOTSPD;
         }
-        use64 = true;
-        r.fallback_fp64 = 1;
+        if (gram_prec == FST_TF32 || gram_prec == FST_BF16) {
+            gram_prec = FST_BF16X3;
+            r.fallback_bf16x3 = 1;
+        } else if (!shift && gram_prec != FST_FP32) {
+            shift = true;
+            r.shifted_preconditioner = 1;
+        } else {
+            use64 = true;
+            r.fallback_fp64 = 1;
+        }
     }
 
     // the preconditioner solve runs in the factor's precision on a working copy
@@ -542,6 +571,8 @@ static fst_status refit_impl(fst_model* M, const T* xyz, const T* u, int64_t Q, 
         FST_CHECK_LAUNCH();
         return FST_OK;
     };
+    // the one-launch triangular solves report expired waits in their error word
+    if (W.solve.sync.ptr) FST_CUDA(cudaMemsetAsync(W.solve.sync.ptr, 0, sizeof(int), s));
     // alpha_0 = G^-1 h
     FST_CUDA(cudaMemcpyAsync(alpha, g, sizeof(double) * R, cudaMemcpyDeviceToDevice, s));
     FST_TRY(solve(alpha));
@@ -611,6 +642,16 @@ static fst_status refit_impl(fst_model* M, const T* xyz, const T* u, int64_t Q, 
         if (!converged && isfinite(last) && last <= floor_ok) converged = true;
     }
     r.ms_refine = tm.stop();
+    {
+        int serr = 0;
+        FST_CUDA(cudaMemcpyAsync(&serr, W.solve.sync.ptr, sizeof(int), cudaMemcpyDeviceToHost, s));
+        FST_CUDA(cudaStreamSynchronize(s));
+        if (serr) {
+            set_error("triangular solve: a bounded device wait expired");
+            if (rep) *rep = r;
+            return FST_ETIMEOUT;
+        }
+    }
     r.refine_steps = steps;
     r.last_rel_update = last;
     if (!converged && max_refine > 0) {

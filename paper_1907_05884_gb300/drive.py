@@ -17,7 +17,10 @@ import numpy as np
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("what", choices=["gram", "eval", "refit", "sample", "batch", "serve"])
+    ap.add_argument("what", choices=["gram", "eval", "refit", "sample", "batch", "serve", "fit"])
+    ap.add_argument("--grid", type=int, default=64)
+    ap.add_argument("--frac", type=float, default=0.05)
+    ap.add_argument("--eps", type=float, default=1e-3)
     ap.add_argument("--queries", type=int, default=2000)
     ap.add_argument("--q-lo", type=float, default=1e5)
     ap.add_argument("--q-hi", type=float, default=2e6)
@@ -39,6 +42,8 @@ def main():
         return batch(args)
     if args.what == "serve":
         return serve_loads(args)
+    if args.what == "fit":
+        return fit(args)
     model = synth.random_model(tuple(args.ranks), (args.degree,) * 3, seed=4, orthonormal=True)
     M = fst.Model(model)
     Q = max(args.n, 2 * args.m)
@@ -112,6 +117,34 @@ def batch(args):
               f"plan_ms={tp:.3f} ({total / tp / 1e3:.1f} Mpoints/s) graph_ms={tg:.3f} "
               f"({total / tg / 1e3:.1f} Mpoints/s) per_instance_ms={ts:.3f} ({total / ts / 1e3:.1f} Mpoints/s)",
               flush=True)
+
+
+def fit(args):
+    """Construction workload: --n scattered points (70% uniform, 30% in a band) of a sum of
+    20 Gaussians plus noise; grid --grid^3, rank caps --ranks, degree --degree, a --frac
+    subset interpolated, refit on ceil(8 R) rows in --prec."""
+    import json
+    import torch
+    from paper_1907_05884_gb300 import fst, synth
+    xyz_np = synth.points(args.n, seed=5, clustered=0.3).astype(np.float32)
+    u_np, _ = synth.field_values(xyz_np.astype(np.float64), synth.field_spec(6, 20), seed=7)
+    xyz = torch.from_numpy(xyz_np).cuda()
+    u = torch.from_numpy(u_np.astype(np.float32)).cuda()
+    for r in range(args.reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        M, rep = fst.fit(xyz, u, grid=(args.grid,) * 3, sample_frac=args.frac, eps=args.eps,
+                         max_rank=tuple(args.ranks), max_degree=args.degree, oversample=8.0, seed=11 + r,
+                         prec=args.prec)
+        e1.record()
+        torch.cuda.synchronize()
+        ref = u[:1 << 20]
+        pred = M.eval(xyz[:, :1 << 20].contiguous(), prec="fp32")
+        rel = float(torch.linalg.norm(pred - ref) / torch.linalg.norm(ref))
+        print(json.dumps({"fit_ms": e0.elapsed_time(e1), "rel_l2_first_1M": rel, **{
+            k: v for k, v in rep.items() if k != "refit"}, "refit": {k: rep["refit"][k] for k in (
+                "refine_steps", "ms_gram", "ms_cholesky", "ms_refine", "fallback_bf16x3", "shifted_preconditioner",
+                "fallback_fp64")}}), flush=True)
 
 
 def serve_loads(args):

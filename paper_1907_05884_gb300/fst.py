@@ -47,12 +47,40 @@ class RefitOpts(C.Structure):
 
 class RefitReport(C.Structure):
     _fields_ = [("m", C.c_int64), ("refine_steps", C.c_int32), ("fallback_fp64", C.c_int32),
+                ("fallback_bf16x3", C.c_int32), ("shifted_preconditioner", C.c_int32),
                 ("first_rel_change", C.c_double), ("last_rel_update", C.c_double),
                 ("ms_sample", C.c_double), ("ms_factors", C.c_double), ("ms_gram", C.c_double),
                 ("ms_cholesky", C.c_double), ("ms_refine", C.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class FitParams(C.Structure):
+    _fields_ = [("grid", C.c_int32 * 3), ("sample_frac", C.c_double), ("eps", C.c_double),
+                ("max_rank", C.c_int32 * 3), ("max_degree", C.c_int32), ("fixed_rank", C.c_int32),
+                ("oversample", C.c_double), ("seed", C.c_uint64), ("grid_values", C.c_void_p)]
+
+
+class FitReport(C.Structure):
+    _fields_ = [("r", C.c_int32 * 3), ("r_hosvd", C.c_int32 * 3), ("nnz", C.c_int32 * 3),
+                ("fill_sweeps", C.c_int32),
+                ("eig_sweeps", C.c_int32 * 3), ("n_interp", C.c_int64), ("m", C.c_int64),
+                ("compression_ratio", C.c_double), ("ms_interp", C.c_double), ("ms_hosvd", C.c_double),
+                ("ms_sparse", C.c_double), ("ms_refit", C.c_double), ("refit", RefitReport)]
+
+    def as_dict(self):
+        d = {}
+        for f, _ in self._fields_:
+            v = getattr(self, f)
+            d[f] = v.as_dict() if f == "refit" else (tuple(v) if f in ("r", "r_hosvd", "nnz", "eig_sweeps") else v)
+        return d
+
+
+class FitTrace(C.Structure):
+    _fields_ = [("grid_values", C.c_void_p), ("eigvals", C.c_void_p * 3), ("W", C.c_void_p * 3),
+                ("core_hosvd", C.c_void_p), ("col_nnz", C.c_void_p), ("col_loo", C.c_void_p),
+                ("col_kept", C.c_void_p)]
 
 
 def _load():
@@ -83,6 +111,8 @@ def _load():
         "fst_refit": (I32, [P, P, P, I64, P, I64, U64, I32, P, P, P]),
         "fst_refit_f64": (I32, [P, P, P, I64, P, I64, U64, P, P, P]),
         "fst_normal_matrix": (I32, [P, P, P, I64, P, I64, I32, P, P, P]),
+        "fst_fit": (I32, [P, P, I64, P, P, P, I32, P, P, P, P, P]),
+        "fst_cholesky_f32": (I32, [P, I32, P]),
         "fst_status_str": (C.c_char_p, [I32]),
         "fst_last_error": (C.c_char_p, []),
         "fst_build_info": (C.c_char_p, []),
@@ -235,6 +265,80 @@ class Model:
                                  C.c_uint64(seed & 0xFFFFFFFFFFFFFFFF), PREC[prec], C.byref(opts),
                                  C.byref(rep), _stream(stream)))
         return rep.as_dict()
+
+
+def fit(xyz, u, grid=(32, 32, 32), sample_frac: float = 0.05, eps: float = 1e-3, max_rank=(8, 8, 8),
+        max_degree: int = 15, oversample: float = 4.0, seed: int = 1, fixed_rank: bool = False,
+        prec: str = "fp32", lo=None, hi=None, grid_values=None, trace: bool = False,
+        max_refine: int = 32, refine_tol: float = 0.0, stream=None):
+    """Algorithm 1 and the core refit (fst_fit).  xyz (3, Q) and u (Q,): CUDA float32 tensors.
+    Returns (Model, report dict) or, with trace=True, (Model, report dict, trace dict)."""
+    import torch
+    assert xyz.is_cuda and xyz.dtype == torch.float32 and xyz.is_contiguous() and xyz.shape[0] == 3
+    assert u.is_cuda and u.dtype == torch.float32 and u.is_contiguous()
+    Q = xyz.shape[1]
+    prm = FitParams()
+    for k in range(3):
+        prm.grid[k] = int(grid[k])
+        prm.max_rank[k] = int(max_rank[k])
+    prm.sample_frac, prm.eps, prm.max_degree = float(sample_frac), float(eps), int(max_degree)
+    prm.fixed_rank, prm.oversample, prm.seed = int(bool(fixed_rank)), float(oversample), seed & 0xFFFFFFFFFFFFFFFF
+    keep = []
+    if grid_values is not None:
+        gv = np.ascontiguousarray(np.asarray(grid_values, dtype=np.float64).reshape(-1))
+        assert gv.size == int(np.prod(grid))
+        keep.append(gv)
+        prm.grid_values = gv.ctypes.data
+    box = []
+    for v in (lo, hi):
+        if v is None:
+            box.append(None)
+        else:
+            a = np.ascontiguousarray(np.asarray(v, dtype=np.float64))
+            keep.append(a)
+            box.append(a.ctypes.data)
+    opts = RefitOpts(int(max_refine), float(refine_tol), 0)
+    rep = FitReport()
+    tr, bufs = None, None
+    if trace:
+        G = [int(g) for g in grid]
+        bufs = {"grid_values": np.zeros(G), "eigvals": [np.zeros(g) for g in G],
+                "W": [np.zeros(g * int(mr)) for g, mr in zip(G, max_rank)],
+                "core_hosvd": np.zeros(int(np.prod(max_rank))), "col_nnz": np.zeros(int(sum(max_rank)), np.int32),
+                "col_loo": np.zeros(int(sum(max_rank))), "col_kept": np.zeros(int(sum(max_rank)), np.int32)}
+        tr = FitTrace()
+        tr.grid_values = bufs["grid_values"].ctypes.data
+        for k in range(3):
+            tr.eigvals[k] = bufs["eigvals"][k].ctypes.data
+            tr.W[k] = bufs["W"][k].ctypes.data
+        tr.core_hosvd = bufs["core_hosvd"].ctypes.data
+        tr.col_nnz = bufs["col_nnz"].ctypes.data
+        tr.col_loo = bufs["col_loo"].ctypes.data
+        tr.col_kept = bufs["col_kept"].ctypes.data
+    h = C.c_void_p()
+    _check(lib.fst_fit(_dptr(xyz), _dptr(u), Q, box[0], box[1], C.byref(prm), PREC[prec], C.byref(opts),
+                       C.byref(tr) if tr is not None else None, C.byref(rep), C.byref(h), _stream(stream)))
+    model = Model(_handle=h)
+    d = rep.as_dict()
+    if not trace:
+        return model, d
+    r = d["r_hosvd"]
+    ncol = sum(r)
+    t = {"grid_values": bufs["grid_values"], "eigvals": bufs["eigvals"],
+         "W": [bufs["W"][k][:G[k] * r[k]].reshape(G[k], r[k]) for k in range(3)],
+         "core_hosvd": bufs["core_hosvd"][:r[0] * r[1] * r[2]].reshape(r),
+         "col_nnz": bufs["col_nnz"][:ncol].copy(), "col_loo": bufs["col_loo"][:ncol].copy(),
+         "col_kept": bufs["col_kept"][:ncol].copy()}
+    return model, d, t
+
+
+def cholesky_f32(G, stream=None):
+    """In-place lower Cholesky factor of a CUDA float32 (R, R) SPD matrix (fst_cholesky_f32)."""
+    import torch
+    assert G.is_cuda and G.dtype == torch.float32 and G.is_contiguous() and G.dim() == 2
+    assert G.shape[0] == G.shape[1]
+    _check(lib.fst_cholesky_f32(_dptr(G), int(G.shape[0]), _stream(stream)))
+    return G
 
 
 def normal_matrix(model: "Model", xyz, u, idx, prec: str = "tf32", with_h: bool = True, stream=None):
