@@ -187,9 +187,19 @@ __global__ void __launch_bounds__(512) potrf_inv_kernel(float* G, int R, int k0,
     float (*P)[PB] = reinterpret_cast<float (*)[PB]>(dsm + sizeof(float) * PB * AS);   // P[k][row]
     __shared__ float invd[PB];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    for (int e = tid; e < PB * PB; e += 512) {
-        const int i = e >> 7, j = e & (PB - 1);
-        A[i][j] = (i < kb && j <= i) ? G[(size_t)(k0 + i) * R + k0 + j] : 0.f;
+    {
+        // all 32 loads of a thread in flight at once
+        float v[PB * PB / 512];
+#pragma unroll
+        for (int u = 0; u < PB * PB / 512; ++u) {
+            const int e = tid + u * 512, i = e >> 7, j = e & (PB - 1);
+            v[u] = (i < kb && j <= i) ? G[(size_t)(k0 + i) * R + k0 + j] : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < PB * PB / 512; ++u) {
+            const int e = tid + u * 512;
+            A[e >> 7][e & (PB - 1)] = v[u];
+        }
     }
     __syncthreads();
     for (int sb = 0; sb < kb; sb += SUB) {
@@ -198,17 +208,20 @@ __global__ void __launch_bounds__(512) potrf_inv_kernel(float* G, int R, int k0,
             // (a) 32 x 32 diagonal block in registers: lane i holds row sb + i (padded rows
             // beyond kb are identity rows)
             float a[SUB];
-            float dinv = 1.f;
+            float dinv = 1.f, piv = 1.f;
+            const float fl = lane < w ? floors[k0 + sb + lane] : 0.f;
 #pragma unroll
             for (int c = 0; c < SUB; ++c)
                 a[c] = lane < w ? (c <= lane ? A[sb + lane][sb + c] : 0.f) : (c == lane ? 1.f : 0.f);
 #pragma unroll 32
             for (int j = 0; j < SUB; ++j) {
                 const float d = __shfl_sync(0xffffffffu, a[j], j);
-                if (lane == 0 && j < w && !(d > floors[k0 + sb + j])) atomicOr(flag, 1);
                 const float sq = sqrtf(d);
                 const float inv = 1.f / sq;
-                if (lane == j) dinv = inv;
+                if (lane == j) {
+                    dinv = inv;
+                    piv = d;
+                }
                 a[j] = lane == j ? sq : (lane > j ? a[j] * inv : a[j]);
 #pragma unroll 31
                 for (int c = j + 1; c < SUB; ++c) {
@@ -216,6 +229,8 @@ __global__ void __launch_bounds__(512) potrf_inv_kernel(float* G, int R, int k0,
                     if (lane >= c) a[c] = fmaf(-a[j], lcj, a[c]);
                 }
             }
+            // the pivot test after the chain: no global load inside it
+            if (lane < w && !(piv > fl)) atomicOr(flag, 1);
             if (lane < w) {
 #pragma unroll
                 for (int c = 0; c < SUB; ++c) {
@@ -319,45 +334,60 @@ __global__ void __launch_bounds__(256) trsm_pack_kernel(float* G, int R, int k0,
     const int tid = threadIdx.x;
     const int t0 = k0 + PB;
     const int r0 = blockIdx.x * 64;
-    for (int e = tid; e < 64 * (PB / 4); e += 256) {
-        const int r = e / (PB / 4), c4 = (e % (PB / 4)) * 4;
-        const int g = t0 + r0 + r;
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (g < R) {
+    const bool vec = (R & 3) == 0;
+    {
+        // the 64 panel rows and L11: every load of a thread in flight at once
+        float4 xv[64 * (PB / 4) / 256], lv4[PB * (PB / 4) / 256];
+#pragma unroll
+        for (int u = 0; u < 64 * (PB / 4) / 256; ++u) {
+            const int e = tid + u * 256, r = e / (PB / 4), c4 = (e % (PB / 4)) * 4;
+            const int g = t0 + r0 + r;
             const float* src = G + (size_t)g * R + k0 + c4;
-            v = make_float4(src[0], src[1], src[2], src[3]);
+            xv[u] = g >= R ? make_float4(0.f, 0.f, 0.f, 0.f)
+                           : vec ? *reinterpret_cast<const float4*>(src) : make_float4(src[0], src[1], src[2], src[3]);
         }
-        *reinterpret_cast<float4*>(&X[r][c4]) = v;
-    }
-    for (int e = tid; e < PB * (PB / 4); e += 256) {
-        const int r = e / (PB / 4), c4 = (e % (PB / 4)) * 4;
-        const float* src = G + (size_t)(k0 + r) * R + k0 + c4;
-        *reinterpret_cast<float4*>(&L[r][c4]) = make_float4(src[0], src[1], src[2], src[3]);
+#pragma unroll
+        for (int u = 0; u < PB * (PB / 4) / 256; ++u) {
+            const int e = tid + u * 256, r = e / (PB / 4), c4 = (e % (PB / 4)) * 4;
+            const float* src = G + (size_t)(k0 + r) * R + k0 + c4;
+            lv4[u] = vec ? *reinterpret_cast<const float4*>(src) : make_float4(src[0], src[1], src[2], src[3]);
+        }
+#pragma unroll
+        for (int u = 0; u < 64 * (PB / 4) / 256; ++u) {
+            const int e = tid + u * 256;
+            *reinterpret_cast<float4*>(&X[e / (PB / 4)][(e % (PB / 4)) * 4]) = xv[u];
+        }
+#pragma unroll
+        for (int u = 0; u < PB * (PB / 4) / 256; ++u) {
+            const int e = tid + u * 256;
+            *reinterpret_cast<float4*>(&L[e / (PB / 4)][(e % (PB / 4)) * 4]) = lv4[u];
+        }
     }
     for (int e = tid; e < 4 * SUB * SUB; e += 256) D[e / SUB][e % SUB] = Dinv[e];
     __syncthreads();
-    // thread: row r = tid / 4, columns cq*8 .. cq*8+7 of the current 32-column block
+    // thread: row r = tid / 4 and the 8 columns cq + 4 j of the current 32-column block
+    // (interleaved, so the four threads of a row read four consecutive L rows: no bank
+    // conflicts)
     const int r = tid >> 2, cq = tid & 3;
     for (int d = 0; d < 4; ++d) {
-        const int cb = d * SUB + cq * 8;
+        const int cb = d * SUB + cq;
         float y[8];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) y[j] = X[r][cb + j];
+        for (int j = 0; j < 8; ++j) y[j] = X[r][cb + 4 * j];
         for (int k = 0; k < d * SUB; k += 4) {
-            const float4 xv = *reinterpret_cast<const float4*>(&X[r][k]);
+            const float4 xk = *reinterpret_cast<const float4*>(&X[r][k]);
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
-                const float4 lv = *reinterpret_cast<const float4*>(&L[cb + j][k]);
-                y[j] = fmaf(-xv.x, lv.x, y[j]);
-                y[j] = fmaf(-xv.y, lv.y, y[j]);
-                y[j] = fmaf(-xv.z, lv.z, y[j]);
-                y[j] = fmaf(-xv.w, lv.w, y[j]);
+                const float4 lk = *reinterpret_cast<const float4*>(&L[cb + 4 * j][k]);
+                y[j] = fmaf(-xk.x, lk.x, y[j]);
+                y[j] = fmaf(-xk.y, lk.y, y[j]);
+                y[j] = fmaf(-xk.z, lk.z, y[j]);
+                y[j] = fmaf(-xk.w, lk.w, y[j]);
             }
         }
-        // the 32 Y values of row r for block d are spread over the 4 threads of the quad
         __syncthreads();   // every thread has read X's block d before it is overwritten
 #pragma unroll
-        for (int j = 0; j < 8; ++j) X[r][cb + j] = y[j];
+        for (int j = 0; j < 8; ++j) X[r][cb + 4 * j] = y[j];
         __syncthreads();
         float xo[8];
 #pragma unroll
@@ -366,7 +396,7 @@ __global__ void __launch_bounds__(256) trsm_pack_kernel(float* G, int R, int k0,
             const float4 yv = *reinterpret_cast<const float4*>(&X[r][d * SUB + t]);
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
-                const float4 dv = *reinterpret_cast<const float4*>(&D[d * SUB + cq * 8 + j][t]);
+                const float4 dv = *reinterpret_cast<const float4*>(&D[cb + 4 * j][t]);
                 xo[j] = fmaf(yv.x, dv.x, xo[j]);
                 xo[j] = fmaf(yv.y, dv.y, xo[j]);
                 xo[j] = fmaf(yv.z, dv.z, xo[j]);
@@ -375,7 +405,7 @@ __global__ void __launch_bounds__(256) trsm_pack_kernel(float* G, int R, int k0,
         }
         __syncthreads();
 #pragma unroll
-        for (int j = 0; j < 8; ++j) X[r][cb + j] = xo[j];
+        for (int j = 0; j < 8; ++j) X[r][cb + 4 * j] = xo[j];
         __syncthreads();
     }
     // write L21 to G and the packed operand rows
@@ -667,10 +697,9 @@ __global__ void __launch_bounds__(256) trsv_kernel(const T* __restrict__ L, cons
     if (tid == 0) s_known = 0;
     __syncthreads();
     int known = 0;   // tiles 0 .. known-1 (in solve order) have published values
-    for (int n = 0; n < ntiles; ++n) {
-        const int j = TRANS ? nblk - 1 - n : n;
-        const int j0 = j * NB;
-        T lv[16];
+    // this thread's 16 entries of tile n: (i, j) forward, (j, i) backward
+    auto load_tile = [&](int n, T (&lv)[16]) {
+        const int j0 = (TRANS ? nblk - 1 - n : n) * NB;
         if (TRANS) {
 #pragma unroll
             for (int u = 0; u < 16; ++u) {
@@ -686,8 +715,45 @@ __global__ void __launch_bounds__(256) trsv_kernel(const T* __restrict__ L, cons
                 lv[2 * u + 1] = (rok && j0 + lane + 32 < R) ? L[(size_t)row * R + j0 + lane + 32] : T(0);
             }
         }
+    };
+    auto accum_tile = [&](int n, const T (&lv)[16]) {
+        const int j0 = (TRANS ? nblk - 1 - n : n) * NB;
+        const T* xj = out + j0;
+        if (TRANS) {
+            T sacc = T(0);
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+                const int a = q * 16 + u;
+                sacc += lv[u] * (j0 + a < R ? __ldcg(xj + a) : T(0));
+            }
+            acc[0] += sacc;
+        } else {
+            const T x0 = j0 + lane < R ? __ldcg(xj + lane) : T(0);
+            const T x1 = j0 + lane + 32 < R ? __ldcg(xj + lane + 32) : T(0);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) acc[u] += lv[2 * u] * x0 + lv[2 * u + 1] * x1;
+        }
+    };
+    for (int n = 0; n < ntiles;) {
+        if (n + 4 <= known) {
+            // four published tiles: all their loads in flight together
+            T l0[16], l1[16], l2[16], l3[16];
+            load_tile(n, l0);
+            load_tile(n + 1, l1);
+            load_tile(n + 2, l2);
+            load_tile(n + 3, l3);
+            accum_tile(n, l0);
+            accum_tile(n + 1, l1);
+            accum_tile(n + 2, l2);
+            accum_tile(n + 3, l3);
+            n += 4;
+            continue;
+        }
+        T lv[16];
+        load_tile(n, lv);   // issued before the wait: L does not depend on it
         if (n >= known) {
             if (tid == 0) {
+                const int j = TRANS ? nblk - 1 - n : n;
                 const long long t0 = clock64();
                 bool timed_out = false;
                 while (ld_acquire(&ready[j]) == 0) {
@@ -706,21 +772,8 @@ __global__ void __launch_bounds__(256) trsv_kernel(const T* __restrict__ L, cons
             known = s_known;
             __syncthreads();   // every thread has read s_known before thread 0 may rewrite it
         }
-        const T* xj = out + j0;
-        if (TRANS) {
-            T sacc = T(0);
-#pragma unroll
-            for (int u = 0; u < 16; ++u) {
-                const int a = q * 16 + u;
-                sacc += lv[u] * (j0 + a < R ? __ldcg(xj + a) : T(0));
-            }
-            acc[0] += sacc;
-        } else {
-            const T x0 = j0 + lane < R ? __ldcg(xj + lane) : T(0);
-            const T x1 = j0 + lane + 32 < R ? __ldcg(xj + lane + 32) : T(0);
-#pragma unroll
-            for (int u = 0; u < 8; ++u) acc[u] += lv[2 * u] * x0 + lv[2 * u + 1] * x1;
-        }
+        accum_tile(n, lv);
+        ++n;
     }
     // combine the partial sums of each row (forward: across the warp) / column (backward)
     if (TRANS) {

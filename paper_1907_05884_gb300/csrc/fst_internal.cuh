@@ -140,6 +140,13 @@ fst_status eval_tc_launch(fst_model* m, const float* xyz, int64_t n, float* out,
 // Tensor-core Gram (gram_tc.cu): lower triangle of G = A^T A, FP32 accumulation.
 fst_status gram_tc_launch(const fst_model* m, const float* U1, const float* U2, const float* U3,
                           int64_t mrows, float* G, fst_prec prec, cudaStream_t s);
+// The same G from a packed BF16 / TF32 / BF16 hi+lo copy of the Khatri-Rao operand
+// (gram_pk.cu); FST_ENOMEM if that copy cannot be allocated.
+fst_status gram_pk_launch(const fst_model* m, const float* U1, const float* U2, const float* U3, int64_t rows,
+                          float* G, fst_prec prec, cudaStream_t s);
+// PT[(i r2 + j) mpad + q] = w1_i(q) w2_j(q), U3T[k mpad + q] = w3_k(q), zero for q >= m.
+fst_status pair_products(const float* U1, const float* U2, const float* U3, int64_t m, int64_t mpad, int r1, int r2,
+                         int r3, float* PT, float* U3T, cudaStream_t s);
 
 // Cholesky and triangular solves (chol.cu).
 template <typename T>

@@ -461,6 +461,15 @@ GramErr g_gram_err[64];
 
 }  // namespace
 
+fst_status pair_products(const float* U1, const float* U2, const float* U3, int64_t m, int64_t mpad, int r1, int r2,
+                         int r3, float* PT, float* U3T, cudaStream_t s) {
+    int grid = (int)((mpad + 255) / 256);
+    if (grid > 8 * sm_count()) grid = 8 * sm_count();
+    pair_products_kernel<<<grid, 256, 0, s>>>(U1, U2, U3, m, mpad, r1, r2, r3, PT, U3T);
+    FST_CHECK_LAUNCH();
+    return FST_OK;
+}
+
 fst_status gram_tc_launch(const fst_model* M, const float* U1, const float* U2, const float* U3, int64_t m,
                           float* G, fst_prec prec, cudaStream_t s) {
     int dev = 0;
@@ -480,12 +489,7 @@ fst_status gram_tc_launch(const fst_model* M, const float* U1, const float* U2, 
     FST_TRY(ge.u3t.ensure(sizeof(float) * (size_t)r3 * mpad));
     float* PT = ge.pt.as<float>();
     float* U3T = ge.u3t.as<float>();
-    {
-        int grid = (int)((mpad + 255) / 256);
-        if (grid > 8 * sm_count()) grid = 8 * sm_count();
-        pair_products_kernel<<<grid, 256, 0, s>>>(U1, U2, U3, m, mpad, r1, r2, r3, PT, U3T);
-        FST_CHECK_LAUNCH();
-    }
+    FST_TRY(pair_products(U1, U2, U3, m, mpad, r1, r2, r3, PT, U3T, s));
     fst_status st;
     switch (prec) {
         case FST_TF32: st = launch<kTF32>(PT, U3T, m, mpad, r1, r2, r3, G, err, s); break;

@@ -406,6 +406,17 @@ static fst_status launch_gram_simt(const fst_model* M, const T* const U[3], int6
     return FST_OK;
 }
 
+// Tensor-core Gram: from the packed Khatri-Rao operand; without memory for the packed copy,
+// the kernel that generates the operand on the fly; for r3 < 4 there, the CUDA-core Gram.
+static fst_status gram_tensor(const fst_model* M, const float* const U[3], int64_t m, float* G, fst_prec prec,
+                              cudaStream_t s) {
+    fst_status st = gram_pk_launch(M, U[0], U[1], U[2], m, G, prec, s);
+    if (st != FST_ENOMEM) return st;
+    st = gram_tc_launch(M, U[0], U[1], U[2], m, G, prec, s);
+    if (st == FST_EUNSUPPORTED) st = launch_gram_simt<float>(M, U, m, G, s);
+    return st;
+}
+
 // Working precision T for factors, Gram and Cholesky; FP64 vectors and refinement.
 template <typename T>
 static fst_status refit_impl(fst_model* M, const T* xyz, const T* u, int64_t Q, const int64_t* idx_in, int64_t m,
@@ -478,12 +489,7 @@ static fst_status refit_impl(fst_model* M, const T* xyz, const T* u, int64_t Q, 
             if (gram_prec == FST_FP32) {
                 FST_TRY(launch_gram_simt<float>(M, reinterpret_cast<const float* const*>(Uc), m, G, s));
             } else {
-                fst_status gst = gram_tc_launch(M, reinterpret_cast<const float*>(Uc[0]),
-                                                reinterpret_cast<const float*>(Uc[1]),
-                                                reinterpret_cast<const float*>(Uc[2]), m, G, gram_prec, s);
-                if (gst == FST_EUNSUPPORTED)   // r3 < 4: the CUDA-core Gram
-                    gst = launch_gram_simt<float>(M, reinterpret_cast<const float* const*>(Uc), m, G, s);
-                FST_TRY(gst);
+                FST_TRY(gram_tensor(M, reinterpret_cast<const float* const*>(Uc), m, G, gram_prec, s));
             }
             r.ms_gram += tm.stop();
             if (shift) {
@@ -762,9 +768,7 @@ extern "C" fst_status fst_normal_matrix(const fst_model* M, const float* xyz, co
     if (prec == FST_FP32) {
         FST_TRY(launch_gram_simt<float>(M, Uc, m, G, s));
     } else {
-        fst_status gst = gram_tc_launch(M, Uc[0], Uc[1], Uc[2], m, G, prec, s);
-        if (gst == FST_EUNSUPPORTED) gst = launch_gram_simt<float>(M, Uc, m, G, s);   // r3 < 4
-        FST_TRY(gst);
+        FST_TRY(gram_tensor(M, Uc, m, G, prec, s));
     }
     if (h) {
         FST_TRY(W.res.ensure(sizeof(double) * (size_t)m));

@@ -3,7 +3,7 @@
     python -m paper_1907_05884_gb300.drive gram  --prec bf16   --m 16384
     python -m paper_1907_05884_gb300.drive eval  --prec bf16x3 --n 4194304
     python -m paper_1907_05884_gb300.drive refit --prec bf16   --n 1048576
-    python -m paper_1907_05884_gb300.drive chol  --prec fp32
+    python -m paper_1907_05884_gb300.drive chol  --m 110592
 
 The model has ranks 24^3 and Legendre degree 31 with orthonormal factor functions (unless
 --ranks/--degree say otherwise); each call is repeated --reps times and timed with CUDA events.
@@ -17,7 +17,7 @@ import numpy as np
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("what", choices=["gram", "eval", "refit", "sample", "batch", "serve", "fit"])
+    ap.add_argument("what", choices=["gram", "eval", "refit", "sample", "batch", "serve", "fit", "chol"])
     ap.add_argument("--grid", type=int, default=64)
     ap.add_argument("--frac", type=float, default=0.05)
     ap.add_argument("--eps", type=float, default=1e-3)
@@ -62,6 +62,12 @@ def main():
             fst.normal_matrix(M, xyz, u, idx, prec=args.prec, with_h=False)
         elif args.what == "eval":
             M.eval(xyz[:, :args.n].contiguous() if Q != args.n else xyz, prec=args.prec, out=out[:args.n])
+        elif args.what == "chol":
+            # G = A^T A of the sampled rows (BF16 Gram), then the FP32 factorisation alone
+            G, _ = fst.normal_matrix(M, xyz, u, idx, prec="bf16", with_h=False)
+            torch.cuda.synchronize()
+            e0.record()
+            fst.cholesky_f32(G)
         elif args.what == "refit":
             rep = M.refit(xyz, u, args.m, seed=9, prec=args.prec)
             extra = f" {rep}"
