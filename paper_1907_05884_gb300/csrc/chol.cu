@@ -653,28 +653,65 @@ __global__ void invert_diag_kernel(const T* L, int R, T* Linv) {
 // by one block: forward, y_i = Linv_ii (b_i - sum_{j<i} L_ij y_j); backward (TRANS),
 // x_i = Linv_ii^T (y_i - sum_{j>i} L_ji^T x_j).  Blocks take block rows in solve order
 // from a ticket counter, so a block only waits for rows already taken by running blocks
-// (no deadlock whatever the residency).  A finished row publishes its values, then its
-// ready flag; every wait on a flag is bounded, and on expiry the block records an error
-// and still publishes (so the rows after it do not all wait out their own limits).
-// sync: [0] error word, [1] ticket, [2 + i] ready flag of block row i (zeroed before).
+// (no deadlock whatever the residency).  The output vector is filled with an all-ones bit
+// pattern (a NaN that arithmetic never produces) before the launch; a value is published
+// by one relaxed store and a consumer spins on exactly the values it needs until they
+// differ from that pattern, so there are no flags, fences or block-wide barriers on the
+// chain.  Every spin is bounded; on expiry the block records an error in sync[0] and goes
+// on with what it read (the rows after it then finish without waiting out their own
+// limits).  sync: [0] error word, [1] ticket (zeroed before the launch).
 constexpr long long kSolveWaitLimit = 2000000000LL;
 
-__device__ __forceinline__ int ld_acquire(const int* p) {
-    int v;
-    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+__device__ __forceinline__ bool unpublished(float v) { return __float_as_uint(v) == 0xffffffffu; }
+__device__ __forceinline__ bool unpublished(double v) {
+    return (unsigned long long)__double_as_longlong(v) == 0xffffffffffffffffull;
+}
+__device__ __forceinline__ float ld_relaxed(const float* p) {
+    float v;
+    asm volatile("ld.relaxed.gpu.global.f32 %0, [%1];" : "=f"(v) : "l"(p) : "memory");
     return v;
 }
-__device__ __forceinline__ void st_release(int* p, int v) {
-    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+__device__ __forceinline__ double ld_relaxed(const double* p) {
+    double v;
+    asm volatile("ld.relaxed.gpu.global.f64 %0, [%1];" : "=d"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_relaxed(float* p, float v) {
+    asm volatile("st.relaxed.gpu.global.f32 [%0], %1;" ::"l"(p), "f"(v) : "memory");
+}
+__device__ __forceinline__ void st_relaxed(double* p, double v) {
+    asm volatile("st.relaxed.gpu.global.f64 [%0], %1;" ::"l"(p), "d"(v) : "memory");
+}
+// a computed value never takes the unpublished pattern
+template <typename T>
+__device__ __forceinline__ T publishable(T v) {
+    return unpublished(v) ? (T)NAN : v;
 }
 
+// wait for p to be published (bounded); returns the value
+template <typename T>
+__device__ __forceinline__ T wait_value(const T* p, int* err) {
+    T v = ld_relaxed(p);
+    if (!unpublished(v)) return v;
+    const long long t0 = clock64();
+    while (unpublished(v = ld_relaxed(p))) {
+        if (clock64() - t0 > kSolveWaitLimit) {
+            atomicOr(err, 1);
+            return T(0);
+        }
+    }
+    return v;
+}
+
+// M is L (forward) or L^T (backward, TRANS), both row-major: block row i reads the tiles
+// M[i-block][j-block] for j < i (forward) or j > i (backward) along its own rows.
 template <typename T, bool TRANS>
-__global__ void __launch_bounds__(256) trsv_kernel(const T* __restrict__ L, const T* __restrict__ Linv, int R,
+__global__ void __launch_bounds__(256) trsv_kernel(const T* __restrict__ M, const T* __restrict__ Linv, int R,
                                                    int nblk, const T* bin, T* out, int* sync) {
     __shared__ T lis[NB][NB + 1];   // Linv of the diagonal block
-    __shared__ T red[4][NB];
+    __shared__ T red[8][NB];
     __shared__ T vs[NB];
-    __shared__ int s_ticket, s_known;
+    __shared__ int s_ticket;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (tid == 0) s_ticket = atomicAdd(&sync[1], 1);
     __syncthreads();
@@ -685,133 +722,98 @@ __global__ void __launch_bounds__(256) trsv_kernel(const T* __restrict__ L, cons
         const T* Li = Linv + (size_t)i * NB * NB;
         for (int e = tid; e < NB * NB; e += 256) lis[e / NB][e % NB] = Li[e];
     }
-    // tile mappings (both coalesced along a row of L):
-    //   forward, tile (i, j): warp w owns rows 8w .. 8w+7, lane l columns l and l + 32;
-    //   backward, tile (j, i): thread owns column c = tid % 64 and rows 16 q .. 16 q + 15
-    const int q = tid >> 6, c = tid & 63;
+    // tile mapping (coalesced along the rows of M): warp w owns rows 8w .. 8w+7 of the
+    // block row, lane l the columns l and l + 32 of the tile
     T acc[8];
 #pragma unroll
     for (int u = 0; u < 8; ++u) acc[u] = T(0);
-    const int* ready = sync + 2;
     const int ntiles = TRANS ? nblk - 1 - i : i;
-    if (tid == 0) s_known = 0;
-    __syncthreads();
-    int known = 0;   // tiles 0 .. known-1 (in solve order) have published values
-    // this thread's 16 entries of tile n: (i, j) forward, (j, i) backward
     auto load_tile = [&](int n, T (&lv)[16]) {
         const int j0 = (TRANS ? nblk - 1 - n : n) * NB;
-        if (TRANS) {
-#pragma unroll
-            for (int u = 0; u < 16; ++u) {
-                const int row = j0 + q * 16 + u, col = k0 + c;
-                lv[u] = (row < R && col < R) ? L[(size_t)row * R + col] : T(0);
-            }
-        } else {
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const int row = k0 + warp * 8 + u;
-                const bool rok = row < R;
-                lv[2 * u] = (rok && j0 + lane < R) ? L[(size_t)row * R + j0 + lane] : T(0);
-                lv[2 * u + 1] = (rok && j0 + lane + 32 < R) ? L[(size_t)row * R + j0 + lane + 32] : T(0);
-            }
-        }
-    };
-    auto accum_tile = [&](int n, const T (&lv)[16]) {
-        const int j0 = (TRANS ? nblk - 1 - n : n) * NB;
-        const T* xj = out + j0;
-        if (TRANS) {
-            T sacc = T(0);
-#pragma unroll
-            for (int u = 0; u < 16; ++u) {
-                const int a = q * 16 + u;
-                sacc += lv[u] * (j0 + a < R ? __ldcg(xj + a) : T(0));
-            }
-            acc[0] += sacc;
-        } else {
-            const T x0 = j0 + lane < R ? __ldcg(xj + lane) : T(0);
-            const T x1 = j0 + lane + 32 < R ? __ldcg(xj + lane + 32) : T(0);
-#pragma unroll
-            for (int u = 0; u < 8; ++u) acc[u] += lv[2 * u] * x0 + lv[2 * u + 1] * x1;
-        }
-    };
-    for (int n = 0; n < ntiles;) {
-        if (n + 4 <= known) {
-            // four published tiles: all their loads in flight together
-            T l0[16], l1[16], l2[16], l3[16];
-            load_tile(n, l0);
-            load_tile(n + 1, l1);
-            load_tile(n + 2, l2);
-            load_tile(n + 3, l3);
-            accum_tile(n, l0);
-            accum_tile(n + 1, l1);
-            accum_tile(n + 2, l2);
-            accum_tile(n + 3, l3);
-            n += 4;
-            continue;
-        }
-        T lv[16];
-        load_tile(n, lv);   // issued before the wait: L does not depend on it
-        if (n >= known) {
-            if (tid == 0) {
-                const int j = TRANS ? nblk - 1 - n : n;
-                const long long t0 = clock64();
-                bool timed_out = false;
-                while (ld_acquire(&ready[j]) == 0) {
-                    if (clock64() - t0 > kSolveWaitLimit) {
-                        timed_out = true;
-                        break;
-                    }
-                }
-                if (timed_out) atomicOr(&sync[0], 1);
-                // count the further rows already published
-                int k = n + 1;
-                while (k < ntiles && ld_acquire(&ready[TRANS ? nblk - 1 - k : k]) != 0) ++k;
-                s_known = k;
-            }
-            __syncthreads();
-            known = s_known;
-            __syncthreads();   // every thread has read s_known before thread 0 may rewrite it
-        }
-        accum_tile(n, lv);
-        ++n;
-    }
-    // combine the partial sums of each row (forward: across the warp) / column (backward)
-    if (TRANS) {
-        red[q][c] = acc[0];
-    } else {
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
-            T v = acc[u];
-#pragma unroll
-            for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-            if (lane == 0) red[0][warp * 8 + u] = v;
+            const int row = k0 + warp * 8 + u;
+            const bool rok = row < R;
+            lv[2 * u] = (rok && j0 + lane < R) ? M[(size_t)row * R + j0 + lane] : T(0);
+            lv[2 * u + 1] = (rok && j0 + lane + 32 < R) ? M[(size_t)row * R + j0 + lane + 32] : T(0);
         }
+    };
+    T lv[16], ln[16];
+    if (ntiles > 0) load_tile(0, lv);
+    for (int n = 0; n < ntiles; ++n) {
+        if (n + 1 < ntiles) load_tile(n + 1, ln);   // the next tile's loads fly during this one
+        const int j0 = (TRANS ? nblk - 1 - n : n) * NB;
+        const T* xj = out + j0;
+        // both values in one batch of L2 loads; spin only on one not yet published
+        T x0 = j0 + lane < R ? __ldcg(xj + lane) : T(0);
+        T x1 = j0 + lane + 32 < R ? __ldcg(xj + lane + 32) : T(0);
+        if (unpublished(x0)) x0 = wait_value(xj + lane, sync);
+        if (unpublished(x1)) x1 = wait_value(xj + lane + 32, sync);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) acc[u] += lv[2 * u] * x0 + lv[2 * u + 1] * x1;
+#pragma unroll
+        for (int u = 0; u < 16; ++u) lv[u] = ln[u];
+    }
+    // row sums across the warp
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+        T v = acc[u];
+#pragma unroll
+        for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) red[0][warp * 8 + u] = v;
     }
     __syncthreads();
-    if (tid < NB) {
-        const T sum = TRANS ? (red[0][tid] + red[1][tid]) + (red[2][tid] + red[3][tid]) : red[0][tid];
-        vs[tid] = tid < kb ? __ldcg(bin + k0 + tid) - sum : T(0);
-    }
+    if (tid < NB) vs[tid] = tid < kb ? bin[k0 + tid] - red[0][tid] : T(0);
     __syncthreads();
     // out_i = Linv_ii v (forward) or Linv_ii^T v (backward): thread (q, c) sums 16 terms
     {
+        const int q = tid >> 6, c = tid & 63;
         T s2 = T(0);
 #pragma unroll
         for (int u = 0; u < 16; ++u) {
             const int a = q * 16 + u;
             s2 += (TRANS ? lis[a][c] : lis[c][a]) * vs[a];
         }
-        red[q][c] = s2;
+        red[4 + q][c] = s2;
     }
     __syncthreads();
     if (tid < kb) {
-        const T v = (red[0][tid] + red[1][tid]) + (red[2][tid] + red[3][tid]);
-        __stcg(out + k0 + tid, v);
-        __threadfence();
+        const T v = (red[4][tid] + red[5][tid]) + (red[6][tid] + red[7][tid]);
+        st_relaxed(out + k0 + tid, publishable(v));
+    }
+}
+
+// LT = L^T on the lower triangle's 32 x 32 tiles (the strict upper blocks of LT that the
+// backward solve reads are all written).
+template <typename T>
+__global__ void transpose_lower_kernel(const T* __restrict__ L, int R, T* __restrict__ LT) {
+    __shared__ T tl[32][33];
+    const long long b = blockIdx.x;
+    int ti = (int)((sqrt(8.0 * (double)b + 1.0) - 1.0) * 0.5);
+    while ((long long)(ti + 1) * (ti + 2) / 2 <= b) ++ti;
+    while ((long long)ti * (ti + 1) / 2 > b) --ti;
+    const int tj = (int)(b - (long long)ti * (ti + 1) / 2);
+    const int r0 = ti * 32, c0 = tj * 32, x = threadIdx.x;
+    for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+        const int row = r0 + y, col = c0 + x;
+        tl[y][x] = (row < R && col < R) ? L[(size_t)row * R + col] : T(0);
     }
     __syncthreads();
-    if (tid == 0) st_release((int*)&ready[i], 1);
+    for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+        const int row = c0 + y, col = r0 + x;
+        if (row < R && col < R) LT[(size_t)row * R + col] = tl[x][y];
+    }
 }
+
+template <typename T>
+fst_status chol_transpose(const T* L, int R, T* LT, cudaStream_t s) {
+    const long long nt = (R + 31) / 32;
+    transpose_lower_kernel<T><<<(unsigned)(nt * (nt + 1) / 2), dim3(32, 8), 0, s>>>(L, R, LT);
+    FST_CHECK_LAUNCH();
+    return FST_OK;
+}
+template fst_status chol_transpose<float>(const float*, int, float*, cudaStream_t);
+template fst_status chol_transpose<double>(const double*, int, double*, cudaStream_t);
 
 template <typename T>
 fst_status chol_invert_diag(const T* L, int R, T* Linv, cudaStream_t s) {
@@ -821,16 +823,19 @@ fst_status chol_invert_diag(const T* L, int R, T* Linv, cudaStream_t s) {
     return FST_OK;
 }
 
-// x <- L^-T L^-1 x (x and y: R values of T; y is scratch; sync: 2 + nblk ints whose
-// first is the error word, left as it is).
+// x <- L^-T L^-1 x (x and y: R values of T; y is scratch; LT = L^T; sync: 2 ints, the first
+// the error word, left as it is).  The output of each direction is filled with the all-ones
+// pattern first (both memsets and both kernels are captured by chol_solve_graph).
 template <typename T>
-fst_status chol_solve(const T* L, const T* Linv, int R, T* x, T* y, int* sync, cudaStream_t s) {
+fst_status chol_solve(const T* L, const T* LT, const T* Linv, int R, T* x, T* y, int* sync, cudaStream_t s) {
     const int nblk = (R + NB - 1) / NB;
-    FST_CUDA(cudaMemsetAsync(sync + 1, 0, (size_t)(nblk + 1) * sizeof(int), s));
+    FST_CUDA(cudaMemsetAsync(sync + 1, 0, sizeof(int), s));
+    FST_CUDA(cudaMemsetAsync(y, 0xff, sizeof(T) * (size_t)R, s));
     trsv_kernel<T, false><<<nblk, 256, 0, s>>>(L, Linv, R, nblk, x, y, sync);
     FST_CHECK_LAUNCH();
-    FST_CUDA(cudaMemsetAsync(sync + 1, 0, (size_t)(nblk + 1) * sizeof(int), s));
-    trsv_kernel<T, true><<<nblk, 256, 0, s>>>(L, Linv, R, nblk, y, x, sync);
+    FST_CUDA(cudaMemsetAsync(sync + 1, 0, sizeof(int), s));
+    FST_CUDA(cudaMemsetAsync(x, 0xff, sizeof(T) * (size_t)R, s));
+    trsv_kernel<T, true><<<nblk, 256, 0, s>>>(LT, Linv, R, nblk, y, x, sync);
     FST_CHECK_LAUNCH();
     return FST_OK;
 }
@@ -838,20 +843,21 @@ fst_status chol_solve(const T* L, const T* Linv, int R, T* x, T* y, int* sync, c
 template fst_status cholesky_lower<float>(float*, int, int*, DevBuf&, cudaStream_t);
 template fst_status cholesky_lower<double>(double*, int, int*, DevBuf&, cudaStream_t);
 template <typename T>
-fst_status chol_solve_graph(SolveGraph& g, const T* L, const T* Linv, int R, T* x, T* y, cudaStream_t s) {
-    if (!g.exec || g.L != L || g.Linv != Linv || g.x != x || g.R != R || g.elem != (int)sizeof(T)) {
+fst_status chol_solve_graph(SolveGraph& g, const T* L, const T* LT, const T* Linv, int R, T* x, T* y,
+                            cudaStream_t s) {
+    if (!g.exec || g.L != L || g.LT != LT || g.Linv != Linv || g.x != x || g.R != R || g.elem != (int)sizeof(T)) {
         if (g.exec) {
             FST_CUDA(cudaStreamSynchronize(s));
             cudaGraphExecDestroy(g.exec);
             g.exec = nullptr;
         }
         if (!g.cap) FST_CUDA(cudaStreamCreateWithFlags(&g.cap, cudaStreamNonBlocking));
-        FST_TRY(g.sync.ensure(sizeof(int) * (size_t)(R / NB + 4)));
+        FST_TRY(g.sync.ensure(4 * sizeof(int)));
         FST_CUDA(cudaMemsetAsync(g.sync.ptr, 0, sizeof(int), s));
         FST_CUDA(cudaStreamSynchronize(s));
         FST_CUDA(cudaStreamBeginCapture(g.cap, cudaStreamCaptureModeThreadLocal));
         const uint64_t before = fst_kernel_launches();
-        fst_status st = chol_solve<T>(L, Linv, R, x, y, g.sync.as<int>(), g.cap);
+        fst_status st = chol_solve<T>(L, LT, Linv, R, x, y, g.sync.as<int>(), g.cap);
         cudaGraph_t graph = nullptr;
         cudaError_t e = cudaStreamEndCapture(g.cap, &graph);
         if (st != FST_OK) {
@@ -864,6 +870,7 @@ fst_status chol_solve_graph(SolveGraph& g, const T* L, const T* Linv, int R, T* 
         if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate", __FILE__, __LINE__);
         g.nodes = fst_kernel_launches() - before;
         g.L = L;
+        g.LT = LT;
         g.Linv = Linv;
         g.x = x;
         g.R = R;
@@ -874,14 +881,16 @@ fst_status chol_solve_graph(SolveGraph& g, const T* L, const T* Linv, int R, T* 
     return FST_OK;
 }
 
-template fst_status chol_solve_graph<float>(SolveGraph&, const float*, const float*, int, float*, float*, cudaStream_t);
-template fst_status chol_solve_graph<double>(SolveGraph&, const double*, const double*, int, double*, double*,
-                                             cudaStream_t);
+template fst_status chol_solve_graph<float>(SolveGraph&, const float*, const float*, const float*, int, float*,
+                                            float*, cudaStream_t);
+template fst_status chol_solve_graph<double>(SolveGraph&, const double*, const double*, const double*, int, double*,
+                                             double*, cudaStream_t);
 
 template fst_status chol_invert_diag<float>(const float*, int, float*, cudaStream_t);
 template fst_status chol_invert_diag<double>(const double*, int, double*, cudaStream_t);
-template fst_status chol_solve<float>(const float*, const float*, int, float*, float*, int*, cudaStream_t);
-template fst_status chol_solve<double>(const double*, const double*, int, double*, double*, int*, cudaStream_t);
+template fst_status chol_solve<float>(const float*, const float*, const float*, int, float*, float*, int*, cudaStream_t);
+template fst_status chol_solve<double>(const double*, const double*, const double*, int, double*, double*, int*,
+                                       cudaStream_t);
 
 }  // namespace fst
 

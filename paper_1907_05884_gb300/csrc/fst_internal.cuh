@@ -64,6 +64,7 @@ struct SolveGraph {
     cudaGraphExec_t exec = nullptr;
     cudaStream_t cap = nullptr;
     const void* L = nullptr;
+    const void* LT = nullptr;
     const void* Linv = nullptr;
     void* x = nullptr;
     int R = 0, elem = 0;
@@ -74,7 +75,7 @@ struct SolveGraph {
 
 // Scratch of the refit, kept inside the model between calls.
 struct RefitScratch {
-    DevBuf idx, U[3], b, G, G64, res, g, z, delta, alpha, norms, flag, Linv, xw, yw, pcg, chol_ws;
+    DevBuf idx, U[3], b, G, G64, res, g, z, delta, alpha, norms, flag, Linv, LT, xw, yw, pcg, chol_ws;
     SolveGraph solve;
 };
 
@@ -154,9 +155,13 @@ fst_status cholesky_lower(T* G, int R, int* d_flag, DevBuf& ws, cudaStream_t s);
 template <typename T>
 fst_status chol_invert_diag(const T* L, int R, T* Linv, cudaStream_t s);   // 64x64 diagonal blocks
 template <typename T>
-fst_status chol_solve(const T* L, const T* Linv, int R, T* x, T* y, int* sync, cudaStream_t s);  // x <- (L L^T)^-1 x
+fst_status chol_solve(const T* L, const T* LT, const T* Linv, int R, T* x, T* y, int* sync, cudaStream_t s);  // x <- (L L^T)^-1 x
 // The same through a CUDA graph captured on first use for (L, Linv, x, y, R) and replayed.
 template <typename T>
-fst_status chol_solve_graph(SolveGraph& g, const T* L, const T* Linv, int R, T* x, T* y, cudaStream_t s);
+fst_status chol_solve_graph(SolveGraph& g, const T* L, const T* LT, const T* Linv, int R, T* x, T* y,
+                            cudaStream_t s);
+// LT = L^T (the strict upper blocks used by the backward solve)
+template <typename T>
+fst_status chol_transpose(const T* L, int R, T* LT, cudaStream_t s);
 
 }  // namespace fst

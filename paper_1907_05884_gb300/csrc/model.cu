@@ -25,7 +25,7 @@ void SolveGraph::release() {
     if (cap) cudaStreamDestroy(cap);
     exec = nullptr;
     cap = nullptr;
-    L = Linv = nullptr;
+    L = LT = Linv = nullptr;
     x = nullptr;
     R = elem = 0;
     nodes = 0;
@@ -124,6 +124,8 @@ static void free_device(fst_model* m) {
     s.norms.release();
     s.flag.release();
     s.Linv.release();
+    s.LT.release();
+    s.chol_ws.release();
     s.xw.release();
     s.yw.release();
     s.pcg.release();

@@ -137,49 +137,85 @@ __global__ void __launch_bounds__(256) gram_simt_kernel(const T* __restrict__ U1
 }
 
 // ------------------------------------------------------------------ A^T r and b - A alpha
-// g += A^T r over a chunk of rows per block: thread per (i,j) pair, r3 accumulators,
-// rows staged through shared memory; partial sums added to g with FP64 atomics.
-template <typename T, int R3M>
+// Partial sums of g = A^T r over a chunk of rows per block: each thread owns three (i,j)
+// pairs and their r3 accumulators (so every w3 row read feeds 3 r3 products); rows are
+// staged through shared memory.  Block b writes its R partial sums to part[b * R ..];
+// sum_partials_kernel adds them in FP64 (deterministic, no atomics).
+template <typename T, int R3M, int PPT>
 __global__ void __launch_bounds__(256) atr_kernel(const T* __restrict__ U1, const T* __restrict__ U2,
                                                   const T* __restrict__ U3, const double* __restrict__ rv,
                                                   int64_t m, int r1, int r2, int r3, int64_t rows_per_block,
-                                                  double* g) {
-    constexpr int S = 32;
+                                                  double* __restrict__ part) {
+    constexpr int S = 64;
     __shared__ T u1s[S][FST_MAX_RANK + 1], u2s[S][FST_MAX_RANK + 1];
     __shared__ __align__(16) T u3s[S][R3M];
     __shared__ T rs[S];
     const int64_t lo = (int64_t)blockIdx.x * rows_per_block;
     const int64_t hi = lo + rows_per_block < m ? lo + rows_per_block : m;
     const int npairs = r1 * r2;
-    for (int p0 = 0; p0 < npairs; p0 += blockDim.x) {
-        const int p = p0 + threadIdx.x;
-        const int i = p < npairs ? p / r2 : 0, j = p < npairs ? p % r2 : 0;
-        T acc[R3M];
+    double* out = part + (size_t)blockIdx.x * npairs * r3;
+    for (int p0 = 0; p0 < npairs; p0 += PPT * blockDim.x) {
+        int pi[PPT], pj[PPT];
 #pragma unroll
-        for (int k = 0; k < R3M; ++k) acc[k] = T(0);
+        for (int p = 0; p < PPT; ++p) {
+            const int pair = p0 + threadIdx.x + p * blockDim.x;
+            pi[p] = pair < npairs ? pair / r2 : 0;
+            pj[p] = pair < npairs ? pair % r2 : 0;
+        }
+        T acc[PPT][R3M];
+#pragma unroll
+        for (int p = 0; p < PPT; ++p)
+#pragma unroll
+            for (int k = 0; k < R3M; ++k) acc[p][k] = T(0);
         for (int64_t s0 = lo; s0 < hi; s0 += S) {
             __syncthreads();
+            // staging unrolled so that a thread's loads are in flight together
+#pragma unroll 8
             for (int e = threadIdx.x; e < S * FST_MAX_RANK; e += blockDim.x) {
                 const int ss = e / FST_MAX_RANK, c = e - ss * FST_MAX_RANK;
                 const int64_t s = s0 + ss;
                 const bool ok = s < hi;
-                if (c < r1) u1s[ss][c] = ok ? U1[s * r1 + c] : T(0);
-                if (c < r2) u2s[ss][c] = ok ? U2[s * r2 + c] : T(0);
-                if (c < R3M) u3s[ss][c] = (ok && c < r3) ? U3[s * r3 + c] : T(0);
-                if (c == 0) rs[ss] = ok ? (T)rv[s] : T(0);
+                const T a = (ok && c < r1) ? U1[s * r1 + c] : T(0);
+                const T b = (ok && c < r2) ? U2[s * r2 + c] : T(0);
+                const T w = (ok && c < r3) ? U3[s * r3 + c] : T(0);
+                const T rr = (ok && c == 0) ? (T)rv[s] : T(0);
+                if (c < r1) u1s[ss][c] = a;
+                if (c < r2) u2s[ss][c] = b;
+                if (c < R3M) u3s[ss][c] = w;
+                if (c == 0) rs[ss] = rr;
             }
             __syncthreads();
-            if (p < npairs) {
-#pragma unroll 4
-                for (int ss = 0; ss < S; ++ss) {
-                    const T c = rs[ss] * u1s[ss][i] * u2s[ss][j];
+#pragma unroll 2
+            for (int ss = 0; ss < S; ++ss) {
+                T w3[R3M];
 #pragma unroll
-                    for (int k = 0; k < R3M; ++k) acc[k] = fma(c, u3s[ss][k], acc[k]);
+                for (int k = 0; k < R3M; k += 4) load4(&u3s[ss][k], w3[k], w3[k + 1], w3[k + 2], w3[k + 3]);
+                const T r = rs[ss];
+#pragma unroll
+                for (int p = 0; p < PPT; ++p) {
+                    const T c = r * u1s[ss][pi[p]] * u2s[ss][pj[p]];
+#pragma unroll
+                    for (int k = 0; k < R3M; ++k) acc[p][k] = fma(c, w3[k], acc[p][k]);
                 }
             }
         }
-        if (p < npairs)
-            for (int k = 0; k < r3; ++k) atomicAdd(&g[(size_t)p * r3 + k], (double)acc[k]);
+#pragma unroll
+        for (int p = 0; p < PPT; ++p) {
+            const int pair = p0 + threadIdx.x + p * blockDim.x;
+            if (pair < npairs) {
+#pragma unroll
+                for (int k = 0; k < R3M; ++k)
+                    if (k < r3) out[(size_t)pair * r3 + k] = (double)acc[p][k];
+            }
+        }
+    }
+}
+
+__global__ void sum_partials_kernel(const double* __restrict__ part, int nparts, int R, double* __restrict__ g) {
+    for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < R; a += gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int b = 0; b < nparts; ++b) s += part[(size_t)b * R + a];
+        g[a] = s;
     }
 }
 
@@ -361,18 +397,51 @@ static fst_status launch_factors(const fst_model* M, const T* xyz, int64_t Q, co
     return FST_OK;
 }
 
+struct AtrScratch {
+    std::mutex mu;
+    DevBuf part;
+};
+static AtrScratch g_atr[64];
+
 template <typename T>
 static fst_status launch_atr(const fst_model* M, const T* const U[3], const double* rv, int64_t m, double* g,
                              cudaStream_t s) {
     const int r1 = M->r[0], r2 = M->r[1], r3 = M->r[2];
-    FST_CUDA(cudaMemsetAsync(g, 0, sizeof(double) * (size_t)M->R(), s));
-    const int64_t rows_per_block = 1024;
-    const unsigned grid = (unsigned)((m + rows_per_block - 1) / rows_per_block);
-    if (grid == 0) return FST_OK;
-    if (r3 <= 8) atr_kernel<T, 8><<<grid, 256, 0, s>>>(U[0], U[1], U[2], rv, m, r1, r2, r3, rows_per_block, g);
-    else if (r3 <= 16) atr_kernel<T, 16><<<grid, 256, 0, s>>>(U[0], U[1], U[2], rv, m, r1, r2, r3, rows_per_block, g);
-    else if (r3 <= 24) atr_kernel<T, 24><<<grid, 256, 0, s>>>(U[0], U[1], U[2], rv, m, r1, r2, r3, rows_per_block, g);
-    else atr_kernel<T, 32><<<grid, 256, 0, s>>>(U[0], U[1], U[2], rv, m, r1, r2, r3, rows_per_block, g);
+    const int R = M->R();
+    if (m <= 0) {
+        FST_CUDA(cudaMemsetAsync(g, 0, sizeof(double) * (size_t)R, s));
+        return FST_OK;
+    }
+    // pairs per thread: as many as the registers allow (3 x r3 <= 24 accumulators in FP32)
+    const int ppt = sizeof(T) == 8 ? 1 : (r3 <= 24 ? 3 : 2);
+    int threads = ((r1 * r2 + ppt - 1) / ppt + 31) / 32 * 32;
+    if (threads > 256) threads = 256;
+    int64_t nparts = 2LL * sm_count();
+    int64_t rows_per_block = ((m + nparts - 1) / nparts + 31) / 32 * 32;
+    nparts = (m + rows_per_block - 1) / rows_per_block;
+    int dev = 0;
+    FST_CUDA(cudaGetDevice(&dev));
+    AtrScratch& as = g_atr[dev & 63];
+    std::lock_guard<std::mutex> lk(as.mu);
+    FST_TRY(as.part.ensure(sizeof(double) * (size_t)nparts * R));
+    double* part = as.part.as<double>();
+    const unsigned grid = (unsigned)nparts;
+#define FST_ATR(R3V, PPTV) \
+    atr_kernel<T, R3V, PPTV><<<grid, threads, 0, s>>>(U[0], U[1], U[2], rv, m, r1, r2, r3, rows_per_block, part)
+    if (sizeof(T) == 8) {
+        if (r3 <= 8) FST_ATR(8, 1);
+        else if (r3 <= 16) FST_ATR(16, 1);
+        else if (r3 <= 24) FST_ATR(24, 1);
+        else FST_ATR(32, 1);
+    } else {
+        if (r3 <= 8) FST_ATR(8, 3);
+        else if (r3 <= 16) FST_ATR(16, 3);
+        else if (r3 <= 24) FST_ATR(24, 3);
+        else FST_ATR(32, 2);
+    }
+#undef FST_ATR
+    FST_CHECK_LAUNCH();
+    sum_partials_kernel<<<(R + 255) / 256, 256, 0, s>>>(part, (int)nparts, R, g);
     FST_CHECK_LAUNCH();
     return FST_OK;
 }
@@ -524,9 +593,13 @@ static fst_status refit_impl(fst_model* M, const T* xyz, const T* u, int64_t Q, 
         if (use64) {
             FST_TRY(W.Linv.ensure(sizeof(double) * (size_t)((R + 63) / 64) * 64 * 64));
             FST_TRY(chol_invert_diag<double>(static_cast<const double*>(Lp), R, W.Linv.as<double>(), s));
+            FST_TRY(W.LT.ensure(sizeof(double) * (size_t)R * R));
+            FST_TRY(chol_transpose<double>(static_cast<const double*>(Lp), R, W.LT.as<double>(), s));
         } else {
             FST_TRY(W.Linv.ensure(sizeof(float) * (size_t)((R + 63) / 64) * 64 * 64));
             FST_TRY(chol_invert_diag<float>(static_cast<const float*>(Lp), R, W.Linv.as<float>(), s));
+            FST_TRY(W.LT.ensure(sizeof(float) * (size_t)R * R));
+            FST_TRY(chol_transpose<float>(static_cast<const float*>(Lp), R, W.LT.as<float>(), s));
         }
         int hflag[2] = {0, 0};
         FST_CUDA(cudaMemcpyAsync(hflag, flag, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -563,7 +636,8 @@ static fst_status refit_impl(fst_model* M, const T* xyz, const T* u, int64_t Q, 
         if (use64) {
             double* xw = W.xw.as<double>();
             FST_CUDA(cudaMemcpyAsync(xw, x, sizeof(double) * R, cudaMemcpyDeviceToDevice, s));
-            FST_TRY(chol_solve_graph<double>(W.solve, static_cast<const double*>(Lp), W.Linv.as<double>(), R, xw,
+            FST_TRY(chol_solve_graph<double>(W.solve, static_cast<const double*>(Lp), W.LT.as<double>(),
+                                             W.Linv.as<double>(), R, xw,
                                              W.yw.as<double>(), s));
             FST_CUDA(cudaMemcpyAsync(x, xw, sizeof(double) * R, cudaMemcpyDeviceToDevice, s));
             return FST_OK;
@@ -571,7 +645,8 @@ static fst_status refit_impl(fst_model* M, const T* xyz, const T* u, int64_t Q, 
         float* xw = W.xw.as<float>();
         from_double_kernel<float><<<grid, 256, 0, s>>>(x, xw, R);
         FST_CHECK_LAUNCH();
-        FST_TRY(chol_solve_graph<float>(W.solve, static_cast<const float*>(Lp), W.Linv.as<float>(), R, xw,
+        FST_TRY(chol_solve_graph<float>(W.solve, static_cast<const float*>(Lp), W.LT.as<float>(), W.Linv.as<float>(),
+                                        R, xw,
                                         W.yw.as<float>(), s));
         to_double_kernel<float><<<grid, 256, 0, s>>>(xw, x, R);
         FST_CHECK_LAUNCH();
