@@ -177,9 +177,14 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
     return lo | (hi << 16);
 }
 
-// Diagonal block [k0, k0+kb) factored in place (L11 written to G).  With want_inv, the
-// inverses of its four 32 x 32 diagonal blocks go to Dinv (4 x 32 x 32, row-major).
-// 512 threads; dynamic shared memory: A (PB x AS) and the transposed sub-panel P (SUB x PB).
+// Diagonal block [k0, k0+kb) factored in place (L11 written to G) in FS-wide sub-panels:
+// (a) a warp factors the FS x FS block in registers (shuffles), (b) the rows below solve
+// against it (thread per row), (c) the rest of the block takes a register-tiled rank-FS
+// update.  With want_inv, the inverses of the four 32 x 32 diagonal blocks of L11 go to
+// Dinv (4 x 32 x 32, row-major).  512 threads; dynamic shared memory: A (PB x AS) and the
+// transposed sub-panel P (FS x PB), reused for the inverses (4 x 32 x 32 floats).
+constexpr int FS = 16;
+static_assert(FS * PB <= 4 * SUB * SUB, "the sub-panel buffer is reused for the diagonal inverses");
 __global__ void __launch_bounds__(512) potrf_inv_kernel(float* G, int R, int k0, int kb, int* flag,
                                                         const float* floors, float* Dinv, int want_inv) {
     extern __shared__ __align__(16) unsigned char dsm[];
@@ -202,19 +207,20 @@ __global__ void __launch_bounds__(512) potrf_inv_kernel(float* G, int R, int k0,
         }
     }
     __syncthreads();
-    for (int sb = 0; sb < kb; sb += SUB) {
-        const int w = kb - sb < SUB ? kb - sb : SUB;
+    for (int sb = 0; sb < kb; sb += FS) {
+        const int w = kb - sb < FS ? kb - sb : FS;
         if (warp == 0) {
-            // (a) 32 x 32 diagonal block in registers: lane i holds row sb + i (padded rows
-            // beyond kb are identity rows)
-            float a[SUB];
+            // (a) FS x FS diagonal block in registers: lane i < FS holds row sb + i (padded
+            // rows beyond kb are identity rows; lanes >= FS idle along)
+            const int li = lane < FS ? lane : FS - 1;
+            float a[FS];
             float dinv = 1.f, piv = 1.f;
             const float fl = lane < w ? floors[k0 + sb + lane] : 0.f;
 #pragma unroll
-            for (int c = 0; c < SUB; ++c)
-                a[c] = lane < w ? (c <= lane ? A[sb + lane][sb + c] : 0.f) : (c == lane ? 1.f : 0.f);
-#pragma unroll 32
-            for (int j = 0; j < SUB; ++j) {
+            for (int c = 0; c < FS; ++c)
+                a[c] = li < w ? (c <= li ? A[sb + li][sb + c] : 0.f) : (c == li ? 1.f : 0.f);
+#pragma unroll 16
+            for (int j = 0; j < FS; ++j) {
                 const float d = __shfl_sync(0xffffffffu, a[j], j);
                 const float sq = sqrtf(d);
                 const float inv = 1.f / sq;
@@ -223,8 +229,8 @@ __global__ void __launch_bounds__(512) potrf_inv_kernel(float* G, int R, int k0,
                     piv = d;
                 }
                 a[j] = lane == j ? sq : (lane > j ? a[j] * inv : a[j]);
-#pragma unroll 31
-                for (int c = j + 1; c < SUB; ++c) {
+#pragma unroll 15
+                for (int c = j + 1; c < FS; ++c) {
                     const float lcj = __shfl_sync(0xffffffffu, a[j], c);
                     if (lane >= c) a[c] = fmaf(-a[j], lcj, a[c]);
                 }
@@ -233,7 +239,7 @@ __global__ void __launch_bounds__(512) potrf_inv_kernel(float* G, int R, int k0,
             if (lane < w && !(piv > fl)) atomicOr(flag, 1);
             if (lane < w) {
 #pragma unroll
-                for (int c = 0; c < SUB; ++c) {
+                for (int c = 0; c < FS; ++c) {
                     const float v = c <= lane ? a[c] : 0.f;
                     A[sb + lane][sb + c] = v;
                     P[c][sb + lane] = v;
@@ -246,11 +252,11 @@ __global__ void __launch_bounds__(512) potrf_inv_kernel(float* G, int R, int k0,
         // (b) rows below the sub-block: x = a L_sub^-T, thread per row
         if (tid < nb) {
             const int i = below + tid;
-            float x[SUB];
+            float x[FS];
 #pragma unroll
-            for (int c = 0; c < SUB; ++c) x[c] = A[i][sb + c];
+            for (int c = 0; c < FS; ++c) x[c] = A[i][sb + c];
 #pragma unroll
-            for (int c = 0; c < SUB; ++c) {
+            for (int c = 0; c < FS; ++c) {
                 float s0 = x[c], s1 = 0.f;
 #pragma unroll
                 for (int k = 0; k < c; k += 2) {
@@ -260,13 +266,13 @@ __global__ void __launch_bounds__(512) potrf_inv_kernel(float* G, int R, int k0,
                 x[c] = (s0 + s1) * invd[sb + c];
             }
 #pragma unroll
-            for (int c = 0; c < SUB; ++c) {
+            for (int c = 0; c < FS; ++c) {
                 A[i][sb + c] = x[c];
                 P[c][i] = x[c];
             }
         }
         __syncthreads();
-        // (c) rank-32 update of the rest of the block, 4 x 4 lower tiles per thread
+        // (c) rank-FS update of the rest of the block, 4 x 4 lower tiles per thread
         const int nt4 = (nb + 3) >> 2;
         for (int t = tid; t < nt4 * (nt4 + 1) / 2; t += 512) {
             int ti = (int)((sqrtf(8.f * (float)t + 1.f) - 1.f) * 0.5f);
@@ -279,8 +285,8 @@ __global__ void __launch_bounds__(512) potrf_inv_kernel(float* G, int R, int k0,
             for (int x = 0; x < 4; ++x)
 #pragma unroll
                 for (int y = 0; y < 4; ++y) acc[x][y] = 0.f;
-#pragma unroll 8
-            for (int k = 0; k < SUB; ++k) {
+#pragma unroll
+            for (int k = 0; k < FS; ++k) {
                 const float4 pi = *reinterpret_cast<const float4*>(&P[k][i0]);
                 const float4 pc = *reinterpret_cast<const float4*>(&P[k][c0]);
                 const float vi[4] = {pi.x, pi.y, pi.z, pi.w}, vc[4] = {pc.x, pc.y, pc.z, pc.w};
@@ -303,22 +309,23 @@ __global__ void __launch_bounds__(512) potrf_inv_kernel(float* G, int R, int k0,
     }
     if (!want_inv) return;
     // inverses of the four diagonal 32 x 32 blocks (needs kb = PB): warp d, lane c solves
-    // L_dd x = e_c; entries above the diagonal come out zero
+    // L_dd x = e_c with x in shared memory (P reused, column c per lane: rolled loops);
+    // entries above the diagonal come out zero
     if (warp < 4) {
-        const int d = warp, c = lane;
-        float x[SUB];
-#pragma unroll
+        const int d = warp, c = lane, o = d * SUB;
+        float* X = &P[0][0] + d * SUB * SUB;        // [i][c] for this block
         for (int i = 0; i < SUB; ++i) {
             float s0 = i == c ? 1.f : 0.f, s1 = 0.f;
-#pragma unroll
-            for (int k = 0; k < i; k += 2) {
-                s0 = fmaf(-A[d * SUB + i][d * SUB + k], x[k], s0);
-                if (k + 1 < i) s1 = fmaf(-A[d * SUB + i][d * SUB + k + 1], x[k + 1], s1);
+            int k = 0;
+            for (; k + 1 < i; k += 2) {
+                s0 = fmaf(-A[o + i][o + k], X[k * SUB + c], s0);
+                s1 = fmaf(-A[o + i][o + k + 1], X[(k + 1) * SUB + c], s1);
             }
-            x[i] = (s0 + s1) * invd[d * SUB + i];
+            if (k < i) s0 = fmaf(-A[o + i][o + k], X[k * SUB + c], s0);
+            const float xi = (s0 + s1) * invd[o + i];
+            X[i * SUB + c] = xi;
+            Dinv[(o + i) * SUB + c] = xi;
         }
-#pragma unroll
-        for (int i = 0; i < SUB; ++i) Dinv[(d * SUB + i) * SUB + c] = x[i];
     }
 }
 
@@ -433,132 +440,201 @@ __global__ void __launch_bounds__(256) trsm_pack_kernel(float* G, int R, int k0,
     }
 }
 
-// A22 -= L21_i L21_j^T for one lower 128 x 128 tile (ti >= tj) of the trailing matrix that
-// starts at row/column t0.  256 threads: warps w and w+4 own TMEM lanes 32(w%4).. and columns
-// 64(w/4) ..; each thread reads its 64 G entries into registers first, so the HBM reads
-// overlap the operand copies and the MMAs; thread 0 moves the operands (two K-halves, bulk
-// copies) and issues the MMAs.
-__global__ void __launch_bounds__(256) syrk_tc_kernel(float* G, int R, int t0, const unsigned char* Lp, int* err) {
-    extern __shared__ unsigned char syrk_raw[];
-    unsigned char* sm = reinterpret_cast<unsigned char*>(((uintptr_t)syrk_raw + 127) & ~(uintptr_t)127);
-    __shared__ __align__(8) uint64_t bar_load, bar_half, bar_done;
-    __shared__ uint32_t tmem_slot;
-    __shared__ int issue_ok;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const long long b = blockIdx.x;
-    int ti = (int)((sqrtf(8.f * (float)b + 1.f) - 1.f) * 0.5f);
-    while ((long long)(ti + 1) * (ti + 2) / 2 <= b) ++ti;
-    while ((long long)ti * (ti + 1) / 2 > b) --ti;
-    const int tj = (int)(b - (long long)ti * (ti + 1) / 2);
-    const bool diag = ti == tj;
+// A22 -= L21_i L21_j^T over the lower 128 x 128 tiles (ti >= tj) of the trailing matrix
+// that starts at row/column t0.  Persistent: one CTA per SM walks tiles blockIdx.x,
+// blockIdx.x + gridDim.x, ...  Warp 8 (one thread) moves the operands through a ring of
+// kSyrkStages stages, one K-half of A and B (hi and lo) per stage, with bulk copies; warp 9
+// (one thread) issues the MMAs into one of two 128-column TMEM accumulators; warps 0-7 read
+// their 64 G entries of the tile into registers first, then take the accumulator
+// (warp w: lanes 32(w%4).., columns 64(w/4)..), subtract and store -- so the G traffic of a
+// tile overlaps the copies and MMAs of the next.
+constexpr int kSyrkStages = 3;
+constexpr int kSyrkThreads = 10 * 32;
+__device__ __forceinline__ void lower_tile(long long t, int& ti, int& tj) {
+    int x = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+    while ((long long)(x + 1) * (x + 2) / 2 <= t) ++x;
+    while ((long long)x * (x + 1) / 2 > t) --x;
+    ti = x;
+    tj = (int)(t - (long long)x * (x + 1) / 2);
+}
 
-    if (warp == 0) tc::tmem_alloc(&tmem_slot, 128);
+__global__ void __launch_bounds__(kSyrkThreads, 1)
+syrk_tc_kernel(float* G, int R, int t0, int nt, const unsigned char* Lp, int* err) {
+    extern __shared__ unsigned char syrk_raw[];
+    unsigned char* sm = reinterpret_cast<unsigned char*>(((uintptr_t)syrk_raw + 1023) & ~(uintptr_t)1023);
+    uint64_t* full = reinterpret_cast<uint64_t*>(sm + kSyrkStages * 2 * kHalfBytes);
+    uint64_t* empty = full + kSyrkStages;
+    uint64_t* tfull = empty + kSyrkStages;
+    uint64_t* tempty = tfull + 2;
+    uint64_t* drain = tempty + 2;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const long long ntiles = (long long)nt * (nt + 1) / 2;
+
+    if (warp == 0) tc::tmem_alloc(tmem_slot, 256);
     if (tid == 0) {
-        tc::mbar_init(&bar_load, 1);
-        tc::mbar_init(&bar_half, 1);
-        tc::mbar_init(&bar_done, 1);
-        tc::fence_mbar_init();
-    }
-    // this thread's G entries: row grow, columns gcol0 .. gcol0+63
-    const int grow = t0 + ti * 128 + (warp & 3) * 32 + lane;
-    const int gcol0 = t0 + tj * 128 + (warp >> 2) * 64;
-    const bool vec = (R & 3) == 0;
-    float gv[64];
-    if (grow < R) {
-        const float* src = G + (size_t)grow * R + gcol0;
-        if (vec && gcol0 + 64 <= R) {
-#pragma unroll
-            for (int e = 0; e < 64; e += 4) {
-                const float4 x = *reinterpret_cast<const float4*>(src + e);
-                gv[e] = x.x;
-                gv[e + 1] = x.y;
-                gv[e + 2] = x.z;
-                gv[e + 3] = x.w;
-            }
-        } else {
-#pragma unroll
-            for (int e = 0; e < 64; ++e) gv[e] = gcol0 + e < R ? src[e] : 0.f;
+        for (int s = 0; s < kSyrkStages; ++s) {
+            tc::mbar_init(&full[s], 1);
+            tc::mbar_init(&empty[s], 1);
         }
+        for (int b = 0; b < 2; ++b) {
+            tc::mbar_init(&tfull[b], 1);
+            tc::mbar_init(&tempty[b], 8);
+        }
+        tc::mbar_init(drain, 1);
+        *abort_flag = 0;
+        tc::fence_mbar_init();
     }
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
-    const uint32_t tmem = tmem_slot;
+    const uint32_t tmem = *tmem_slot;
+    auto fail = [&](int code) {
+        *abort_flag = 1;
+        atomicOr(err, code);
+    };
 
-    if (tid == 0) {
-        int ok = 1;
-        const unsigned char* srcA = Lp + (size_t)ti * kTileBytes;
-        const unsigned char* srcB = Lp + (size_t)tj * kTileBytes;
-        const uint32_t a_base = tc::smem_u32(sm);
-        const uint32_t b_base = diag ? a_base : a_base + kHalfBytes;
-        constexpr uint32_t SBO = (128 / 16) * 128;
-        constexpr uint32_t idesc = tc::idesc_bf16(128, 128);
-        for (int h = 0; h < 2; ++h) {
-            if (h == 1) {
-                // the first half's MMAs must have read shared memory before it is refilled
-                tc::mma_commit(&bar_half);
-                if (!tc::mbar_wait(&bar_half, 0u, kCholWaitLimit)) {
-                    ok = 0;
-                    atomicOr(err, 1);
-                    break;
+    if (warp == 8) {
+        // ---------------------------------------------------------------- producer
+        if (lane == 0) {
+            int it = 0;
+            for (long long t = blockIdx.x; t < ntiles && !*abort_flag; t += gridDim.x) {
+                int ti, tj;
+                lower_tile(t, ti, tj);
+                const bool diag = ti == tj;
+                for (int h = 0; h < 2; ++h, ++it) {
+                    const int s = it % kSyrkStages;
+                    const uint32_t ph = (uint32_t)((it / kSyrkStages) & 1);
+                    if (!tc::mbar_wait(&empty[s], ph ^ 1u, kCholWaitLimit)) {
+                        fail(1);
+                        break;
+                    }
+                    unsigned char* st = sm + s * 2 * kHalfBytes;
+                    tc::mbar_arrive_expect_tx(&full[s], diag ? kHalfBytes : 2 * kHalfBytes);
+                    tc::bulk_g2s(st, Lp + (size_t)ti * kTileBytes + h * kHalfBytes, kHalfBytes, &full[s]);
+                    if (!diag)
+                        tc::bulk_g2s(st + kHalfBytes, Lp + (size_t)tj * kTileBytes + h * kHalfBytes, kHalfBytes,
+                                     &full[s]);
                 }
             }
-            tc::mbar_arrive_expect_tx(&bar_load, diag ? kHalfBytes : 2 * kHalfBytes);
-            tc::bulk_g2s(sm, srcA + h * kHalfBytes, kHalfBytes, &bar_load);
-            if (!diag) tc::bulk_g2s(sm + kHalfBytes, srcB + h * kHalfBytes, kHalfBytes, &bar_load);
-            if (!tc::mbar_wait(&bar_load, (uint32_t)h, kCholWaitLimit)) {
-                ok = 0;
-                atomicOr(err, 2);
-                // the copies may still be in flight: give them one more bounded wait
-                if (!tc::mbar_wait(&bar_load, (uint32_t)h, kCholWaitLimit)) atomicOr(err, 8);
+        }
+    } else if (warp == 9) {
+        // ---------------------------------------------------------------- MMA issuer
+        if (lane == 0) {
+            constexpr uint32_t SBO = (128 / 16) * 128;
+            constexpr uint32_t idesc = tc::idesc_bf16(128, 128);
+            int it = 0, n = 0;
+            bool issued = false;
+            for (long long t = blockIdx.x; t < ntiles && !*abort_flag; t += gridDim.x, ++n) {
+                int ti, tj;
+                lower_tile(t, ti, tj);
+                const bool diag = ti == tj;
+                const int b = n & 1;
+                if (!tc::mbar_wait(&tempty[b], (uint32_t)((n >> 1) & 1) ^ 1u, kCholWaitLimit)) {
+                    fail(2);
+                    break;
+                }
+                tc::fence_after_sync();
+                bool ok = true;
+                for (int h = 0; h < 2; ++h, ++it) {
+                    const int s = it % kSyrkStages;
+                    const uint32_t ph = (uint32_t)((it / kSyrkStages) & 1);
+                    if (!tc::mbar_wait(&full[s], ph, kCholWaitLimit)) {
+                        fail(4);
+                        ok = false;
+                        break;
+                    }
+                    tc::fence_after_sync();
+                    const uint32_t a_base = tc::smem_u32(sm + s * 2 * kHalfBytes);
+                    const uint32_t b_base = diag ? a_base : a_base + kHalfBytes;
+                    const uint32_t d = tmem + (uint32_t)(b * 128);
+#pragma unroll
+                    for (int ks = 0; ks < 4; ++ks) {
+                        const uint32_t ko = ks * 256;
+                        const uint64_t ah = tc::make_desc(a_base + ko, 128, SBO);
+                        const uint64_t al = tc::make_desc(a_base + kPartBytes + ko, 128, SBO);
+                        const uint64_t bh = tc::make_desc(b_base + ko, 128, SBO);
+                        const uint64_t bl = tc::make_desc(b_base + kPartBytes + ko, 128, SBO);
+                        tc::mma_bf16(d, ah, bh, idesc, (h | ks) ? 1u : 0u);
+                        tc::mma_bf16(d, ah, bl, idesc, 1u);
+                        tc::mma_bf16(d, al, bh, idesc, 1u);
+                    }
+                    tc::mma_commit(&empty[s]);
+                    issued = true;
+                }
+                if (!ok) break;
+                tc::mma_commit(&tfull[b]);
+            }
+            if (issued) {
+                // every MMA of this CTA completes before tensor memory is released
+                tc::mma_commit(drain);
+                if (!tc::mbar_wait(drain, 0u, kCholWaitLimit)) atomicOr(err, 16);
+            }
+        }
+    } else {
+        // ---------------------------------------------------------------- epilogue
+        const bool vec = (R & 3) == 0;
+        int n = 0;
+        for (long long t = blockIdx.x; t < ntiles && !*abort_flag; t += gridDim.x, ++n) {
+            int ti, tj;
+            lower_tile(t, ti, tj);
+            const bool diag = ti == tj;
+            const int grow = t0 + ti * 128 + (warp & 3) * 32 + lane;
+            const int gcol0 = t0 + tj * 128 + (warp >> 2) * 64;
+            float gv[64];
+            if (grow < R) {
+                const float* src = G + (size_t)grow * R + gcol0;
+                if (vec && gcol0 + 64 <= R) {
+#pragma unroll
+                    for (int e = 0; e < 64; e += 4) {
+                        const float4 x = *reinterpret_cast<const float4*>(src + e);
+                        gv[e] = x.x;
+                        gv[e + 1] = x.y;
+                        gv[e + 2] = x.z;
+                        gv[e + 3] = x.w;
+                    }
+                } else {
+#pragma unroll
+                    for (int e = 0; e < 64; ++e) gv[e] = gcol0 + e < R ? src[e] : 0.f;
+                }
+            }
+            const int b = n & 1;
+            if (!tc::mbar_wait(&tfull[b], (uint32_t)((n >> 1) & 1), kCholWaitLimit)) {
+                fail(8);
                 break;
             }
             tc::fence_after_sync();
+            const uint32_t taddr = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(b * 128 + (warp >> 2) * 64);
 #pragma unroll
-            for (int ks = 0; ks < 4; ++ks) {
-                const uint32_t ko = ks * 256;
-                const uint64_t ah = tc::make_desc(a_base + ko, 128, SBO);
-                const uint64_t al = tc::make_desc(a_base + kPartBytes + ko, 128, SBO);
-                const uint64_t bh = tc::make_desc(b_base + ko, 128, SBO);
-                const uint64_t bl = tc::make_desc(b_base + kPartBytes + ko, 128, SBO);
-                tc::mma_bf16(tmem, ah, bh, idesc, (h | ks) ? 1u : 0u);
-                tc::mma_bf16(tmem, ah, bl, idesc, 1u);
-                tc::mma_bf16(tmem, al, bh, idesc, 1u);
+            for (int c0 = 0; c0 < 64; c0 += 16) {
+                float v[16];
+                tc::tmem_ld16(taddr + (uint32_t)c0, v);
+                tc::tmem_wait_ld();
+#pragma unroll
+                for (int e = 0; e < 16; ++e) gv[c0 + e] -= v[e];
             }
-        }
-        issue_ok = ok;
-        tc::mma_commit(&bar_done);     // every MMA issued by this thread (possibly none)
-    }
-    const bool done = tc::mbar_wait(&bar_done, 0u, kCholWaitLimit);
-    if (!done) atomicOr(err, 4);
-    tc::fence_after_sync();
-    const int all_ok = __syncthreads_and(done ? 1 : 0) && issue_ok;
-    if (all_ok) {
-        const uint32_t taddr = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)((warp >> 2) * 64);
+            tc::fence_before_sync();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(&tempty[b]);
+            if (grow < R) {
+                float* dst = G + (size_t)grow * R + gcol0;
+                if (vec && !diag && gcol0 + 64 <= R) {
 #pragma unroll
-        for (int c0 = 0; c0 < 64; c0 += 16) {
-            float v[16];
-            tc::tmem_ld16(taddr + (uint32_t)c0, v);
-            tc::tmem_wait_ld();
+                    for (int e = 0; e < 64; e += 4)
+                        *reinterpret_cast<float4*>(dst + e) = make_float4(gv[e], gv[e + 1], gv[e + 2], gv[e + 3]);
+                } else {
 #pragma unroll
-            for (int e = 0; e < 16; ++e) gv[c0 + e] -= v[e];
-        }
-        if (grow < R) {
-            float* dst = G + (size_t)grow * R + gcol0;
-            if (vec && !diag && gcol0 + 64 <= R) {
-#pragma unroll
-                for (int e = 0; e < 64; e += 4)
-                    *reinterpret_cast<float4*>(dst + e) = make_float4(gv[e], gv[e + 1], gv[e + 2], gv[e + 3]);
-            } else {
-#pragma unroll
-                for (int e = 0; e < 64; ++e)
-                    if (gcol0 + e < R && gcol0 + e <= grow) dst[e] = gv[e];
+                    for (int e = 0; e < 64; ++e)
+                        if (gcol0 + e < R && gcol0 + e <= grow) dst[e] = gv[e];
+                }
             }
         }
     }
     tc::fence_before_sync();
     __syncthreads();
-    if (warp == 0) tc::tmem_dealloc(tmem, 128);
+    tc::fence_after_sync();
+    if (warp == 0) tc::tmem_dealloc(tmem, 256);
 }
 
 // FP32 factorisation; ws: pivot floors (R floats), the diagonal-block inverses, the packed
@@ -567,9 +643,9 @@ static fst_status cholesky_lower_tc(float* G, int R, int* d_flag, const float* f
                                     cudaStream_t s) {
     float* Dinv = reinterpret_cast<float*>(ws_tail);
     unsigned char* Lp = ws_tail + 4 * SUB * SUB * sizeof(float);
-    const size_t potrf_smem = sizeof(float) * (PB * AS + SUB * PB);
+    const size_t potrf_smem = sizeof(float) * (PB * AS + 4 * SUB * SUB);   // P: FS x PB, then the inverses
     const size_t trsm_smem = sizeof(float) * ((64 + PB) * AS + 4 * SUB * (SUB + 4));
-    const size_t syrk_smem = 2 * kHalfBytes + 128;
+    const size_t syrk_smem = kSyrkStages * 2 * kHalfBytes + 1024 + 1024;
     FST_CUDA(cudaFuncSetAttribute(potrf_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)potrf_smem));
     FST_CUDA(cudaFuncSetAttribute(trsm_pack_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)trsm_smem));
     FST_CUDA(cudaFuncSetAttribute(syrk_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)syrk_smem));
@@ -582,8 +658,9 @@ static fst_status cholesky_lower_tc(float* G, int R, int* d_flag, const float* f
         const int nt = (rest + PB - 1) / PB;
         trsm_pack_kernel<<<2 * nt, 256, trsm_smem, s>>>(G, R, k0, Dinv, Lp);
         FST_CHECK_LAUNCH();
-        syrk_tc_kernel<<<(unsigned)((long long)nt * (nt + 1) / 2), 256, syrk_smem, s>>>(G, R, k0 + PB, Lp,
-                                                                                        d_flag + 1);
+        const long long ntiles = (long long)nt * (nt + 1) / 2;
+        const int grid = ntiles < sm_count() ? (int)ntiles : sm_count();
+        syrk_tc_kernel<<<grid, kSyrkThreads, syrk_smem, s>>>(G, R, k0 + PB, nt, Lp, d_flag + 1);
         FST_CHECK_LAUNCH();
     }
     return FST_OK;
