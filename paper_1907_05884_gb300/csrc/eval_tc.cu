@@ -20,6 +20,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <array>
 #include <memory>
 #include <vector>
 
@@ -40,18 +41,33 @@ constexpr long long kWaitLimitE = 2000000000LL;
 enum EMode { eTF32 = 0, eBF16 = 1, eBF16X3 = 2 };
 
 __host__ __device__ constexpr int jc_for(int r3p) { return 256 / r3p; }
+// factor-step variant: contraction chunks of 160 columns, factor blocks at TMEM column 160
+__host__ __device__ constexpr int jc3_for(int r3p) { return 160 / r3p; }
+constexpr int kUCol = 160;
+constexpr int kFacRows = 32;           // N of the factor MMA (ranks padded to 32)
+constexpr int kBarBytes = 1024;
 
-// Host-side description of the shared-memory image of C_(1).
+// Host-side description of the shared-memory image of C_(1) (and, for the factor-step
+// variant, of the three factor coefficient matrices behind it).
 struct CoreImage {
     int mode, r3p, jc, nc, ncp, kp, kb, nchunks, parts;
     size_t chunk_bytes, bytes;
+    bool tc3 = false;
+    int kpf = 0;                 // Legendre K of the factor MMA (multiple of 16)
+    size_t fac_off = 0, fac_bytes = 0;
 };
 
-CoreImage core_image_shape(const fst_model* m, int mode, int r3p) {
+int kpf_of(const fst_model* m) {
+    const int pe = std::max(m->p_eff[0], std::max(m->p_eff[1], m->p_eff[2]));
+    return std::max(16, (pe + 15) / 16 * 16);
+}
+
+CoreImage core_image_shape(const fst_model* m, int mode, int r3p, bool tc3 = false) {
     CoreImage c;
     c.mode = mode;
     c.r3p = r3p;
-    c.jc = jc_for(r3p);
+    c.tc3 = tc3;
+    c.jc = tc3 ? jc3_for(r3p) : jc_for(r3p);
     c.nc = c.jc * r3p;
     c.ncp = (c.nc + 15) / 16 * 16;
     const int gran = mode == eTF32 ? 8 : 16;
@@ -61,7 +77,27 @@ CoreImage core_image_shape(const fst_model* m, int mode, int r3p) {
     c.parts = mode == eBF16X3 ? 2 : 1;
     c.chunk_bytes = (size_t)c.ncp * c.kb;
     c.bytes = c.chunk_bytes * c.nchunks * c.parts;
+    if (tc3) {
+        c.kpf = kpf_of(m);
+        c.fac_off = (c.bytes + 1023) & ~(size_t)1023;
+        c.fac_bytes = (size_t)3 * 2 * kFacRows * c.kpf * 2;
+        c.bytes = c.fac_off + c.fac_bytes;
+    }
     return c;
+}
+
+// Shared memory of a factor-step bucket with these largest images.
+size_t tc3_smem(size_t core_max, int kb_max, int kpf_max, int parts) {
+    return 1024 + kBarBytes + core_max + (size_t)kGroups * (2 * 128 * kpf_max * 2) +
+           (size_t)kGroups * parts * 128 * kb_max + 2 * (size_t)kpf_max * 4 + 16;
+}
+
+// The factor-step variant serves BF16 / BF16X3 contractions with degrees below 64 whose
+// images fit the shared memory.
+bool use_tc3(const fst_model* m, int mode, int r3p) {
+    if (mode == eTF32 || kpf_of(m) > 64) return false;
+    const CoreImage c = core_image_shape(m, mode, r3p, true);
+    return tc3_smem((c.bytes + 1023) & ~(size_t)1023, c.kb, c.kpf, c.parts) <= 227 * 1024;
 }
 
 uint16_t bf16_bits(float x) {
@@ -104,6 +140,25 @@ std::vector<unsigned char> build_core_image(const fst_model* m, const CoreImage&
                 }
             }
         }
+    if (c.tc3) {
+        // factor coefficient matrices with sqrt(2n+1) folded in: mode k, part (hi, lo), row j
+        // (rank, padded to 32), K = degree n (padded to kpf)
+        const int KPB = c.kpf * 2;
+        const size_t wbytes = (size_t)kFacRows * KPB;
+        for (int k = 0; k < 3; ++k) {
+            unsigned char* base = img.data() + c.fac_off + (size_t)k * 2 * wbytes;
+            for (int j = 0; j < m->r[k]; ++j)
+                for (int e = m->colptr[k][j]; e < m->colptr[k][j + 1]; ++e) {
+                    const int nn = m->rowidx[k][e];
+                    if (nn >= c.kpf) continue;
+                    const float w = (float)(m->val[k][e] * sqrt(2.0 * nn + 1.0));
+                    const uint32_t off = tc::kmajor_offset(j, nn * 2, KPB);
+                    const uint16_t hi = bf16_bits(w), lo = bf16_bits(w - bf16_val(w));
+                    memcpy(base + off, &hi, 2);
+                    memcpy(base + wbytes + off, &lo, 2);
+                }
+        }
+    }
     return img;
 }
 
@@ -112,6 +167,7 @@ struct TcItem {
     EvalArgs<float> a;
     const unsigned char* core_img;   // operand image of C_(1) (device)
     int img_bytes, nchunks, kp, tab_bytes;
+    int fac_off, kpf;                // factor-step variant: offset of the Wc images, Legendre K
     const float* xyz;
     float* out;
     long long n;
@@ -132,7 +188,6 @@ __device__ __forceinline__ uint32_t pack2_bf16(float a, float b) {
     return *reinterpret_cast<uint32_t*>(&h);
 }
 
-constexpr int kBarBytes = 1024;
 
 // Persistent kernel over a work list of units (instance, tile range).  Block b takes the
 // contiguous unit range [cta_start[b], cta_start[b+1]) (cut by estimated cost on the host);
@@ -402,6 +457,374 @@ eval_tc_kernel(const TcItem* __restrict__ items, const TcUnit* __restrict__ unit
     if (warp == 0) tc::tmem_dealloc(tmem, 512);
 }
 
+// ---------------------------------------------------------------- factor step on tcgen05
+// Variant for BF16 / BF16X3 contractions with degrees below 64: the factor values are an
+// MMA too.  Per 128-point tile and mode k the workers write the Legendre values
+// L_0..L_{KPF-1} of their point (zero from the mode's highest used degree on) as BF16
+// high and low parts (the A operand, 128 x KPF), the MMA thread forms
+// U_k = P_k Wc_k^T (N = 32, BF16x3 products) into tensor memory, and the workers read
+// U_1..U_3 back: w1 becomes the contraction's A operand, w2 and w3 stay in registers for
+// the Khatri-Rao epilogue as before.  Per group, TMEM columns [0, 160) hold contraction
+// chunks (JC3 whole j-slices) and [160, 256) the three factor blocks.  The MMA thread
+// serves whichever group has work ready (non-blocking barrier tests), so one group's
+// Legendre values overlap the other group's MMAs.
+
+template <int MODE, int R3P, int RM>
+__global__ void __launch_bounds__(kThreadsE, 1)
+eval_tc3_kernel(const TcItem* __restrict__ items, const TcUnit* __restrict__ units, const int* __restrict__ cta_start,
+                int core_max, int kb_max, int kpf_max, const float* __restrict__ xyz_ov, float* __restrict__ out_ov,
+                int* __restrict__ err) {
+    constexpr int JC = jc3_for(R3P);
+    constexpr int NC = JC * R3P;
+    constexpr int NCP = (NC + 15) / 16 * 16;
+    constexpr int MAXCH = (FST_MAX_RANK + JC - 1) / JC;
+    constexpr int PARTS = MODE == eBF16X3 ? 2 : 1;
+
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* smem = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
+    uint64_t* p_full = bars;                 // [2] workers -> MMA: Legendre tile written
+    uint64_t* p_empty = bars + 2;            // [2] MMA -> workers: Legendre tile consumed
+    uint64_t* u_full = bars + 4;             // [2] MMA -> workers: U_1..U_3 in TMEM
+    uint64_t* u_empty = bars + 6;            // [2] workers -> MMA: U read back
+    uint64_t* a_full = bars + 8;             // [2] workers -> MMA: w1 operand written
+    uint64_t* a_empty = bars + 10;           // [2] MMA -> workers: w1 operand consumed
+    uint64_t* d_full = bars + 12;            // [2] MMA -> workers: chunk in TMEM
+    uint64_t* d_empty = bars + 14;           // [2] workers -> MMA: chunk read
+    uint64_t* drain = bars + 16;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+    unsigned char* core = smem + kBarBytes;
+    const int pgroup = 2 * 128 * kpf_max * 2;                          // hi + lo Legendre tile
+    unsigned char* pbuf = core + core_max;
+    const int agroup = PARTS * 128 * kb_max;
+    unsigned char* abuf = pbuf + kGroups * pgroup;
+    float* fsm = reinterpret_cast<float*>(abuf + kGroups * agroup);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (warp == 0) tc::tmem_alloc(tmem_slot, 512);
+    if (tid == 0) {
+        for (int g = 0; g < kGroups; ++g) {
+            tc::mbar_init(&p_full[g], 4);
+            tc::mbar_init(&p_empty[g], 1);
+            tc::mbar_init(&u_full[g], 1);
+            tc::mbar_init(&u_empty[g], 4);
+            tc::mbar_init(&a_full[g], 4);
+            tc::mbar_init(&a_empty[g], 1);
+            tc::mbar_init(&d_full[g], 1);
+            tc::mbar_init(&d_empty[g], 4);
+        }
+        tc::mbar_init(drain, 1);
+        tc::fence_mbar_init();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *tmem_slot;
+
+    const int u0 = cta_start[blockIdx.x], u1 = cta_start[blockIdx.x + 1];
+    int cur = -1;
+    // per-role phase counters run across units
+    int lt = 0, pc = 0, cc = 0;                                          // worker group
+    int mpc[kGroups] = {0, 0}, mlt[kGroups] = {0, 0}, mcc[kGroups] = {0, 0};   // MMA thread
+    bool issued = false, dead = false;
+    float *ra = nullptr, *rb = nullptr;
+    for (int u = u0; u < u1; ++u) {
+        const TcUnit U = units[u];
+        const TcItem& I = items[U.item];
+        const EvalArgs<float>& a = I.a;
+        if (U.item != cur) {
+            // all MMAs of the previous instance completed before the workers' last waits
+            tc::fence_before_sync();
+            __syncthreads();
+            const uint4* src = reinterpret_cast<const uint4*>(I.core_img);
+            uint4* dst = reinterpret_cast<uint4*>(core);
+            for (int e = tid; e < I.img_bytes / 16; e += blockDim.x) dst[e] = src[e];
+            ra = fsm;
+            rb = ra + kpf_max;
+            for (int i = tid; i < kpf_max; i += blockDim.x) {
+                ra[i] = float(2 * i + 1) / float(i + 1);
+                rb[i] = float(i) / float(i + 1);
+            }
+            tc::fence_async_smem();
+            tc::fence_before_sync();
+            __syncthreads();
+            tc::fence_after_sync();
+            cur = U.item;
+        }
+        const int KB = I.kp * 2;                   // contraction K bytes (BF16)
+        const int SBO = (KB / 16) * 128;
+        const int abytes = 128 * KB;
+        const int KPB = I.kpf * 2;                 // Legendre row bytes (BF16)
+        const int r1 = a.r[0];
+        const int nch = I.nchunks;
+        const long long n = I.n;
+        if (warp < kWorkers) {
+            // -------------------------------------------------------------- workers
+            const int g = warp >> 2, sub = warp & 3, row = sub * 32 + lane;   // TMEM lane = row
+            unsigned char* P = pbuf + g * pgroup;
+            unsigned char* A = abuf + g * agroup;
+            const float* X = xyz_ov ? xyz_ov : I.xyz;
+            float nxt[3];
+            {
+                const long long q = (U.tile0 + g) * 128 + row;
+                const bool ok = U.tile0 + g < U.tile0 + U.ntiles && q < n;
+#pragma unroll
+                for (int k = 0; k < 3; ++k) nxt[k] = ok ? X[k * n + q] : 0.f;
+            }
+            const uint32_t tg = tmem + ((uint32_t)(sub * 32) << 16) + (uint32_t)(g * 256);
+            for (long long t = U.tile0 + g; t < U.tile0 + U.ntiles; t += kGroups, ++lt) {
+                const long long q = t * 128 + row;
+                const bool ok = q < n;
+                float tt[3];
+#pragma unroll
+                for (int k = 0; k < 3; ++k) tt[k] = fmaf(nxt[k], a.sc[k], a.of[k]);
+                {
+                    const long long q2 = q + kGroups * 128;
+                    const bool ok2 = t + kGroups < U.tile0 + U.ntiles && q2 < n;
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) nxt[k] = ok2 ? X[k * n + q2] : 0.f;
+                }
+                // Legendre tiles of the three modes, one after the other through P
+#pragma unroll 1
+                for (int k = 0; k < 3; ++k, ++pc) {
+                    if (!tc::mbar_wait(&p_empty[g], (uint32_t)(pc & 1) ^ 1u, kWaitLimitE)) {
+                        atomicOr(err, 32);
+                        dead = true;
+                    }
+                    if (!dead) {
+                        const float x = tt[k];
+                        const int pe = a.pe[k];
+                        float Lm = 1.f, L = x;
+#pragma unroll 1
+                        for (int c8 = 0; c8 < I.kpf / 8; ++c8) {
+                            float v[8];
+#pragma unroll
+                            for (int e = 0; e < 8; ++e) {
+                                const int d = c8 * 8 + e;
+                                float val;
+                                if (d == 0) {
+                                    val = 1.f;
+                                } else if (d == 1) {
+                                    val = x;
+                                } else {
+                                    const float Ln = ra[d - 1] * x * L - rb[d - 1] * Lm;
+                                    Lm = L;
+                                    L = Ln;
+                                    val = Ln;
+                                }
+                                v[e] = d < pe ? val : 0.f;
+                            }
+                            const uint32_t off = tc::kmajor_offset(row, c8 * 16, KPB);
+                            float l[8];
+#pragma unroll
+                            for (int e = 0; e < 8; ++e) l[e] = v[e] - __bfloat162float(__float2bfloat16_rn(v[e]));
+                            *reinterpret_cast<uint4*>(P + off) =
+                                make_uint4(pack2_bf16(v[0], v[1]), pack2_bf16(v[2], v[3]), pack2_bf16(v[4], v[5]),
+                                           pack2_bf16(v[6], v[7]));
+                            *reinterpret_cast<uint4*>(P + 128 * KPB + off) =
+                                make_uint4(pack2_bf16(l[0], l[1]), pack2_bf16(l[2], l[3]), pack2_bf16(l[4], l[5]),
+                                           pack2_bf16(l[6], l[7]));
+                        }
+                        tc::fence_async_smem();
+                    }
+                    __syncwarp();
+                    if (lane == 0) tc::mbar_arrive(&p_full[g]);
+                }
+                // U_1 back from tensor memory, straight into the contraction's A operand
+                if (!tc::mbar_wait(&u_full[g], (uint32_t)(lt & 1), kWaitLimitE)) {
+                    atomicOr(err, 64);
+                    dead = true;
+                }
+                tc::fence_after_sync();
+                if (!tc::mbar_wait(&a_empty[g], (uint32_t)(lt & 1) ^ 1u, kWaitLimitE)) {
+                    atomicOr(err, 1);
+                    dead = true;
+                }
+#pragma unroll
+                for (int h16 = 0; h16 < 2; ++h16) {
+                    float w1[16];
+                    tc::tmem_ld16(tg + kUCol + 16 * h16, w1);
+                    tc::tmem_wait_ld();
+                    if (!dead) {
+#pragma unroll
+                        for (int c2 = 0; c2 < 2; ++c2) {
+                            const int c16 = h16 * 2 + c2;
+                            if (c16 * 16 >= KB) break;
+                            const uint32_t off = tc::kmajor_offset(row, c16 * 16, KB);
+                            float hh[8], ll[8];
+#pragma unroll
+                            for (int e = 0; e < 8; ++e) {
+                                const int i = c16 * 8 + e;
+                                const float x = i < r1 ? w1[c2 * 8 + e] : 0.f;
+                                hh[e] = x;
+                                ll[e] = x - __bfloat162float(__float2bfloat16_rn(x));
+                            }
+                            *reinterpret_cast<uint4*>(A + off) =
+                                make_uint4(pack2_bf16(hh[0], hh[1]), pack2_bf16(hh[2], hh[3]),
+                                           pack2_bf16(hh[4], hh[5]), pack2_bf16(hh[6], hh[7]));
+                            if (MODE == eBF16X3)
+                                *reinterpret_cast<uint4*>(A + abytes + off) =
+                                    make_uint4(pack2_bf16(ll[0], ll[1]), pack2_bf16(ll[2], ll[3]),
+                                               pack2_bf16(ll[4], ll[5]), pack2_bf16(ll[6], ll[7]));
+                        }
+                    }
+                }
+                if (!dead) tc::fence_async_smem();
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(&a_full[g]);
+                // U_2, U_3 into registers for the epilogue
+                float u2[RM], u3[RM];
+#pragma unroll
+                for (int h = 0; h < RM; h += 16) {
+                    float v[16];
+                    tc::tmem_ld16(tg + kUCol + 32 + h, v);
+                    tc::tmem_wait_ld();
+#pragma unroll
+                    for (int e = 0; e < 16 && h + e < RM; ++e) u2[h + e] = v[e];
+                    tc::tmem_ld16(tg + kUCol + 64 + h, v);
+                    tc::tmem_wait_ld();
+#pragma unroll
+                    for (int e = 0; e < 16 && h + e < RM; ++e) u3[h + e] = h + e < a.r[2] ? v[e] : 0.f;
+                }
+                tc::fence_before_sync();
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(&u_empty[g]);
+                // Khatri-Rao epilogue, chunk by chunk
+                float f = 0.f;
+#pragma unroll
+                for (int ch = 0; ch < MAXCH; ++ch) {
+                    if (ch < nch) {
+                        if (!tc::mbar_wait(&d_full[g], (uint32_t)(cc & 1), kWaitLimitE)) {
+                            atomicOr(err, 2);
+                            dead = true;
+                        }
+                        tc::fence_after_sync();
+                        float s = 0.f;
+#pragma unroll
+                        for (int c0 = 0; c0 < NC; c0 += 16) {
+                            float v[16];
+                            tc::tmem_ld16(tg + c0, v);
+                            tc::tmem_wait_ld();
+#pragma unroll
+                            for (int e = 0; e < 16; ++e) {
+                                const int col = c0 + e;
+                                if (col < NC) {
+                                    const int jl = col / R3P, k = col % R3P;
+                                    s = fmaf(v[e], u3[k < RM ? k : 0], s);
+                                    if (k == R3P - 1) {
+                                        const int j = ch * JC + jl;
+                                        if (j < RM) f = fmaf(s, u2[j < RM ? j : 0], f);
+                                        s = 0.f;
+                                    }
+                                }
+                            }
+                        }
+                        tc::fence_before_sync();
+                        __syncwarp();
+                        if (lane == 0) tc::mbar_arrive(&d_empty[g]);
+                        ++cc;
+                    }
+                }
+                if (ok) (out_ov ? out_ov : I.out)[q] = f;
+            }
+        } else if (lane == 0 && !dead) {
+            // -------------------------------------------------------------- MMA issuer
+            constexpr uint32_t idesc_c = tc::idesc_bf16(128, NCP);
+            constexpr uint32_t idesc_f = tc::idesc_bf16(128, kFacRows);
+            const uint32_t core_u32 = tc::smem_u32(core);
+            const uint32_t chunk_bytes = (uint32_t)(NCP * KB);
+            const uint32_t SBOP = (uint32_t)(KPB / 16) * 128;
+            const uint32_t wbytes = (uint32_t)(kFacRows * KPB);      // one part of one mode
+            long long tnext[kGroups];
+            int stage[kGroups], ch[kGroups];
+            bool act[kGroups];
+#pragma unroll
+            for (int g = 0; g < kGroups; ++g) {
+                tnext[g] = U.tile0 + g;
+                act[g] = tnext[g] < U.tile0 + U.ntiles;
+                stage[g] = 0;
+                ch[g] = 0;
+            }
+            long long last = clock64();
+            while ((act[0] || act[1]) && !dead) {
+                bool progressed = false;
+#pragma unroll
+                for (int g = 0; g < kGroups; ++g) {
+                    if (!act[g]) continue;
+                    const uint32_t tg = tmem + (uint32_t)(g * 256);
+                    if (stage[g] < 3) {
+                        const int k = stage[g];
+                        if (!tc::mbar_try_wait(&p_full[g], (uint32_t)(mpc[g] & 1))) continue;
+                        if (k == 0 && !tc::mbar_try_wait(&u_empty[g], (uint32_t)(mlt[g] & 1) ^ 1u)) continue;
+                        tc::fence_after_sync();
+                        const uint32_t pa = tc::smem_u32(pbuf + g * pgroup);
+                        const uint32_t wb = core_u32 + (uint32_t)I.fac_off + (uint32_t)k * 2u * wbytes;
+                        const uint32_t d = tg + kUCol + 32u * k;
+                        for (int ks = 0; ks < I.kpf / 16; ++ks) {
+                            const uint32_t ko = ks * 256;
+                            const uint64_t ah = tc::make_desc(pa + ko, 128, SBOP);
+                            const uint64_t al = tc::make_desc(pa + 128 * KPB + ko, 128, SBOP);
+                            const uint64_t bh = tc::make_desc(wb + ko, 128, SBOP);
+                            const uint64_t bl = tc::make_desc(wb + wbytes + ko, 128, SBOP);
+                            tc::mma_bf16(d, ah, bh, idesc_f, ks > 0);
+                            tc::mma_bf16(d, ah, bl, idesc_f, 1u);
+                            tc::mma_bf16(d, al, bh, idesc_f, 1u);
+                        }
+                        tc::mma_commit(&p_empty[g]);
+                        issued = true;
+                        ++mpc[g];
+                        if (++stage[g] == 3) tc::mma_commit(&u_full[g]);
+                        progressed = true;
+                    } else {
+                        if (ch[g] == 0 && !tc::mbar_try_wait(&a_full[g], (uint32_t)(mlt[g] & 1))) continue;
+                        if (!tc::mbar_try_wait(&d_empty[g], (uint32_t)(mcc[g] & 1) ^ 1u)) continue;
+                        tc::fence_after_sync();
+                        const uint32_t abase = tc::smem_u32(abuf + g * agroup);
+                        const uint32_t bb = core_u32 + ch[g] * chunk_bytes;
+                        for (int ks = 0; ks < KB / 32; ++ks) {
+                            const uint32_t ko = ks * 256;
+                            const uint64_t ad = tc::make_desc(abase + ko, 128, SBO);
+                            const uint64_t bd = tc::make_desc(bb + ko, 128, SBO);
+                            tc::mma_bf16(tg, ad, bd, idesc_c, ks > 0);
+                            if (MODE == eBF16X3) {
+                                const uint64_t al = tc::make_desc(abase + abytes + ko, 128, SBO);
+                                const uint64_t bl = tc::make_desc(bb + nch * chunk_bytes + ko, 128, SBO);
+                                tc::mma_bf16(tg, ad, bl, idesc_c, 1u);
+                                tc::mma_bf16(tg, al, bd, idesc_c, 1u);
+                            }
+                        }
+                        tc::mma_commit(&d_full[g]);
+                        ++mcc[g];
+                        if (++ch[g] == nch) {
+                            tc::mma_commit(&a_empty[g]);
+                            ++mlt[g];
+                            ch[g] = 0;
+                            stage[g] = 0;
+                            tnext[g] += kGroups;
+                            act[g] = tnext[g] < U.tile0 + U.ntiles;
+                        }
+                        progressed = true;
+                    }
+                }
+                if (progressed) {
+                    last = clock64();
+                } else if (clock64() - last > kWaitLimitE) {
+                    atomicOr(err, 128);
+                    dead = true;
+                }
+            }
+        }
+    }
+    if (warp == kWorkers && lane == 0 && issued) {
+        tc::mma_commit(drain);
+        if (!tc::mbar_wait(drain, 0u, kWaitLimitE)) atomicOr(err, 16);
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (warp == 0) tc::tmem_dealloc(tmem, 512);
+}
+
 struct EvalErr {
     std::mutex mu;
     DevBuf flag;
@@ -420,6 +843,8 @@ int bucket8(int r) { return r <= 8 ? 8 : r <= 16 ? 16 : r <= 24 ? 24 : 32; }
 // One size class of a batch: instances sharing the (rank, r3) padding, one launch.
 struct Bucket {
     int mode = 0, r3p = 8, rm = 8;
+    bool tc3 = false;            // factor step on the tensor cores (eval_tc3_kernel)
+    int kpf_max = 16;
     std::vector<TcItem> items;
     std::vector<TcUnit> units;
     std::vector<int> cta_start;
@@ -434,15 +859,16 @@ fst_status build_buckets(const std::vector<HostItem>& hitems, int mode, std::vec
     const int PARTS = mode == eBF16X3 ? 2 : 1;
     const int sms = sm_count();
     std::vector<std::vector<size_t>> members;
-    std::vector<std::pair<int, int>> keys;
+    std::vector<std::array<int, 3>> keys;
     for (size_t i = 0; i < hitems.size(); ++i) {
         const fst_model* m = hitems[i].m;
         const int rm = bucket8(std::max(m->r[0], std::max(m->r[1], m->r[2])));
         const int r3p = std::min(bucket8(m->r[2]), rm);
+        const std::array<int, 3> key{rm, r3p, use_tc3(m, mode, r3p) ? 1 : 0};
         size_t b = 0;
-        while (b < keys.size() && keys[b] != std::make_pair(rm, r3p)) ++b;
+        while (b < keys.size() && keys[b] != key) ++b;
         if (b == keys.size()) {
-            keys.push_back({rm, r3p});
+            keys.push_back(key);
             members.emplace_back();
         }
         members[b].push_back(i);
@@ -450,14 +876,15 @@ fst_status build_buckets(const std::vector<HostItem>& hitems, int mode, std::vec
     for (size_t b = 0; b < keys.size(); ++b) {
         Bucket B;
         B.mode = mode;
-        B.rm = keys[b].first;
-        B.r3p = keys[b].second;
+        B.rm = keys[b][0];
+        B.r3p = keys[b][1];
+        B.tc3 = keys[b][2] != 0;
         std::vector<double> tile_cost;
         int tab_max = 0;
         for (size_t idx : members[b]) {
             fst_model* m = hitems[idx].m;
             FST_TRY(prepare_core_image(m, mode, B.r3p));
-            const CoreImage ci = core_image_shape(m, mode, B.r3p);
+            const CoreImage ci = core_image_shape(m, mode, B.r3p, B.tc3);
             TcItem it;
             it.a = make_args<float>(m);
             bind(it.a, m);
@@ -467,18 +894,24 @@ fst_status build_buckets(const std::vector<HostItem>& hitems, int mode, std::vec
             it.kp = ci.kp;
             it.tab_bytes = (int)((2 * (size_t)it.a.pm + (size_t)(it.a.pe[0] + it.a.pe[1] + it.a.pe[2]) * B.rm) * 4 +
                                  3 * it.a.pm);
+            it.fac_off = (int)ci.fac_off;
+            it.kpf = ci.kpf;
             it.xyz = hitems[idx].xyz;
             it.out = hitems[idx].out;
             it.n = hitems[idx].n;
             B.core_max = std::max(B.core_max, (int)((ci.bytes + 1023) & ~(size_t)1023));
             B.kb_max = std::max(B.kb_max, ci.kb);
+            B.kpf_max = std::max(B.kpf_max, ci.kpf);
             tab_max = std::max(tab_max, it.tab_bytes);
-            // per-tile cost: factor values (CUDA cores) + contraction and epilogue per chunk
-            tile_cost.push_back(1.0 + (double)B.rm * (it.a.pe[0] + it.a.pe[1] + it.a.pe[2]) / 64.0 +
-                                (double)ci.nchunks * ci.ncp * (PARTS == 2 ? 1.5 : 1.0) / 64.0);
+            // per-tile cost: factor values (CUDA cores, or Legendre tiles + factor MMAs) +
+            // contraction and epilogue per chunk
+            const double fac = B.tc3 ? 1.0 + 3.0 * ci.kpf / 32.0
+                                     : 1.0 + (double)B.rm * (it.a.pe[0] + it.a.pe[1] + it.a.pe[2]) / 64.0;
+            tile_cost.push_back(fac + (double)ci.nchunks * ci.ncp * (PARTS == 2 ? 1.5 : 1.0) / 64.0);
             B.items.push_back(it);
         }
-        B.smem = 1024 + kBarBytes + B.core_max + (size_t)kGroups * PARTS * 128 * B.kb_max + tab_max + 16;
+        B.smem = B.tc3 ? tc3_smem(B.core_max, B.kb_max, B.kpf_max, PARTS)
+                       : 1024 + kBarBytes + B.core_max + (size_t)kGroups * PARTS * 128 * B.kb_max + tab_max + 16;
         if (B.smem > 227 * 1024) {
             set_error("model too large for the tensor-core evaluator (%zu bytes of shared memory)", B.smem);
             return FST_EUNSUPPORTED;
@@ -560,7 +993,34 @@ fst_status launch_bucket_m(const Bucket& B, const unsigned char* dimg, int* err,
     return FST_EUNSUPPORTED;
 }
 
+template <int MODE, int R3P, int RM>
+fst_status launch_bucket_tc3_t(const Bucket& B, const unsigned char* dimg, int* err, cudaStream_t s, Overrides ov) {
+    auto kern = eval_tc3_kernel<MODE, R3P, RM>;
+    FST_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)B.smem));
+    kern<<<B.grid, kThreadsE, B.smem, s>>>(reinterpret_cast<const TcItem*>(dimg + B.items_off),
+                                           reinterpret_cast<const TcUnit*>(dimg + B.units_off),
+                                           reinterpret_cast<const int*>(dimg + B.cta_off), B.core_max, B.kb_max,
+                                           B.kpf_max, ov.xyz, ov.out, err);
+    FST_CHECK_LAUNCH();
+    return FST_OK;
+}
+
+template <int MODE>
+fst_status launch_bucket_tc3_m(const Bucket& B, const unsigned char* dimg, int* err, cudaStream_t s, Overrides ov) {
+#define FST_EB(R3, RMV) \
+    if (B.r3p == R3 && B.rm == RMV) return launch_bucket_tc3_t<MODE, R3, RMV>(B, dimg, err, s, ov);
+    FST_EB(8, 8) FST_EB(8, 16) FST_EB(16, 16) FST_EB(8, 24) FST_EB(16, 24) FST_EB(24, 24)
+    FST_EB(8, 32) FST_EB(16, 32) FST_EB(24, 32) FST_EB(32, 32)
+#undef FST_EB
+    set_error("no evaluator instance for r3 padding %d, rank bound %d", B.r3p, B.rm);
+    return FST_EUNSUPPORTED;
+}
+
 fst_status launch_bucket(const Bucket& B, const unsigned char* dimg, int* err, cudaStream_t s, Overrides ov) {
+    if (B.tc3) {
+        if (B.mode == eBF16) return launch_bucket_tc3_m<eBF16>(B, dimg, err, s, ov);
+        return launch_bucket_tc3_m<eBF16X3>(B, dimg, err, s, ov);
+    }
     switch (B.mode) {
         case eTF32: return launch_bucket_m<eTF32>(B, dimg, err, s, ov);
         case eBF16: return launch_bucket_m<eBF16>(B, dimg, err, s, ov);
@@ -587,8 +1047,9 @@ fst_status error_word(int** out) {
 
 // Tensor-core operand image of the core for (mode, r3 padding), cached in the model.
 fst_status prepare_core_image(fst_model* m, int mode, int r3p) {
-    const CoreImage ci = core_image_shape(m, mode, r3p);
-    const int kind = mode * 64 + r3p;
+    const bool tc3 = use_tc3(m, mode, r3p);
+    const CoreImage ci = core_image_shape(m, mode, r3p, tc3);
+    const int kind = (tc3 ? 512 : 0) + mode * 64 + r3p;
     if (m->tc_core_kind == kind && m->tc_core) return FST_OK;
     std::vector<unsigned char> img = build_core_image(m, ci);
     if (m->tc_core_bytes < img.size()) {
