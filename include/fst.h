@@ -147,10 +147,28 @@ fst_status fst_eval_plan_run(const fst_eval_plan* plan, fst_stream stream);
 void fst_eval_plan_free(fst_eval_plan* plan);   /* waits for the device (cudaFree) */
 
 /* Build, ahead of time, what fst_eval needs for a tensor-core precision (the core as
- * tensor-core operand tiles; rebuilt after the core changes).  fst_eval does this itself
- * on first use with a synchronous upload; call this first to keep fst_eval free of
- * allocation and synchronisation.  Synchronous. */
+ * tensor-core operand tiles; rebuilt after the core changes), autotuning the model's size
+ * class first if this device has not measured it (see fst_eval_autotune).  fst_eval does
+ * the image build itself on first use with a synchronous upload; call this first to keep
+ * fst_eval free of allocation and synchronisation.  Synchronous. */
 fst_status fst_eval_prepare(fst_model* model, fst_prec prec);
+
+/* Autotuner of the tensor-core evaluator.  For BF16 / BF16X3 two kernels can serve a model:
+ * factor values on the CUDA cores (FP32) with the core contraction on the tensor cores, or
+ * factor values on the tensor cores too (Legendre tiles x factor coefficients, BF16x3
+ * products; degrees below 64).  Per device and size class (precision, rank bound, r3
+ * padding, Legendre K) the library keeps the variant measured fastest; fst_eval_prepare
+ * measures a class the first time it sees it, and fst_eval, fst_eval_batched and plans use the
+ * table (an unmeasured class takes the tensor-core factor step where it is possible).
+ * fst_eval_autotune measures the model's class now on n_probe points of its box (one warm-up
+ * and three timed runs per variant, CUDA events), records the faster and returns the mean
+ * times (ms; both -1 when only the CUDA-core factor step can serve the class: nothing is
+ * timed) and the choice (0: factor values on the CUDA cores, 1: on the tensor cores).
+ * Synchronous.  fst_eval_autotune_set records a
+ * choice by hand (-1 forgets the class). */
+fst_status fst_eval_autotune(fst_model* model, fst_prec prec, int64_t n_probe, fst_stream stream,
+                             float* ms_cuda_core_factors, float* ms_tensor_core_factors, int32_t* choice);
+fst_status fst_eval_autotune_set(const fst_model* model, fst_prec prec, int32_t choice);
 
 /* Report (and clear) a bounded device wait that expired inside a tensor-core evaluation
  * on this device since the last check: FST_ETIMEOUT, else FST_OK.  Synchronises stream. */

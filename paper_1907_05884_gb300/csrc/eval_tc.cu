@@ -21,7 +21,9 @@
 
 #include <algorithm>
 #include <array>
+#include <map>
 #include <memory>
+#include <tuple>
 #include <vector>
 
 #include "basis.cuh"
@@ -56,6 +58,8 @@ struct CoreImage {
     int kpf = 0;                 // Legendre K of the factor MMA (multiple of 16)
     size_t fac_off = 0, fac_bytes = 0;
 };
+
+int bucket8(int r) { return r <= 8 ? 8 : r <= 16 ? 16 : r <= 24 ? 24 : 32; }
 
 int kpf_of(const fst_model* m) {
     const int pe = std::max(m->p_eff[0], std::max(m->p_eff[1], m->p_eff[2]));
@@ -92,12 +96,44 @@ size_t tc3_smem(size_t core_max, int kb_max, int kpf_max, int parts) {
            (size_t)kGroups * parts * 128 * kb_max + 2 * (size_t)kpf_max * 4 + 16;
 }
 
-// The factor-step variant serves BF16 / BF16X3 contractions with degrees below 64 whose
-// images fit the shared memory.
-bool use_tc3(const fst_model* m, int mode, int r3p) {
+// The factor-step variant can serve BF16 / BF16X3 contractions with degrees below 64
+// whose images fit the shared memory.
+bool tc3_feasible(const fst_model* m, int mode, int r3p) {
     if (mode == eTF32 || kpf_of(m) > 64) return false;
     const CoreImage c = core_image_shape(m, mode, r3p, true);
     return tc3_smem((c.bytes + 1023) & ~(size_t)1023, c.kb, c.kpf, c.parts) <= 227 * 1024;
+}
+
+// Autotune table: per device and size class (mode, rank bound, r3 padding, Legendre K) the
+// evaluator variant measured fastest (0: factor values on the CUDA cores, 1: on the tensor
+// cores).  Classes not measured take the factor-step variant when it is feasible.
+struct TuneKey {
+    int mode, rm, r3p, kpf;
+    bool operator<(const TuneKey& o) const {
+        return std::tie(mode, rm, r3p, kpf) < std::tie(o.mode, o.rm, o.r3p, o.kpf);
+    }
+};
+struct TuneTable {
+    std::mutex mu;
+    std::map<TuneKey, int> choice;
+};
+TuneTable g_tune[64];
+thread_local int t_force_variant = -1;   // set while the autotuner probes a variant
+
+TuneKey tune_key(const fst_model* m, int mode, int r3p) {
+    const int rm = bucket8(std::max(m->r[0], std::max(m->r[1], m->r[2])));
+    return TuneKey{mode, rm, r3p, kpf_of(m)};
+}
+
+bool use_tc3(const fst_model* m, int mode, int r3p) {
+    if (!tc3_feasible(m, mode, r3p)) return false;
+    if (t_force_variant >= 0) return t_force_variant == 1;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    TuneTable& T = g_tune[dev & 63];
+    std::lock_guard<std::mutex> lk(T.mu);
+    auto it = T.choice.find(tune_key(m, mode, r3p));
+    return it == T.choice.end() ? true : it->second == 1;
 }
 
 uint16_t bf16_bits(float x) {
@@ -838,7 +874,6 @@ struct HostItem {
     float* out;
 };
 
-int bucket8(int r) { return r <= 8 ? 8 : r <= 16 ? 16 : r <= 24 ? 24 : 32; }
 
 // One size class of a batch: instances sharing the (rank, r3) padding, one launch.
 struct Bucket {
@@ -888,7 +923,7 @@ fst_status build_buckets(const std::vector<HostItem>& hitems, int mode, std::vec
             TcItem it;
             it.a = make_args<float>(m);
             bind(it.a, m);
-            it.core_img = static_cast<const unsigned char*>(m->tc_core);
+            it.core_img = static_cast<const unsigned char*>(m->tc_core);   // this kind's image
             it.img_bytes = (int)ci.bytes;
             it.nchunks = ci.nchunks;
             it.kp = ci.kp;
@@ -1050,17 +1085,34 @@ fst_status prepare_core_image(fst_model* m, int mode, int r3p) {
     const bool tc3 = use_tc3(m, mode, r3p);
     const CoreImage ci = core_image_shape(m, mode, r3p, tc3);
     const int kind = (tc3 ? 512 : 0) + mode * 64 + r3p;
-    if (m->tc_core_kind == kind && m->tc_core) return FST_OK;
-    std::vector<unsigned char> img = build_core_image(m, ci);
-    if (m->tc_core_bytes < img.size()) {
-        if (m->tc_core) cudaFree(m->tc_core);
-        m->tc_core = nullptr;
-        m->tc_core_bytes = 0;
-        FST_CUDA(cudaMalloc(&m->tc_core, img.size()));
-        m->tc_core_bytes = img.size();
+    // the slot of this kind, else a stale or unused one, else the least recently built
+    fst_model::TcImage* slot = nullptr;
+    for (auto& t : m->tc_img)
+        if (t.kind == kind && t.ptr) {
+            m->tc_core = t.ptr;
+            return FST_OK;
+        }
+    for (auto& t : m->tc_img)
+        if (t.kind < 0) {
+            slot = &t;
+            break;
+        }
+    if (!slot) {
+        // every slot holds a live kind (8 kinds): wait for the device before replacing one
+        FST_CUDA(cudaDeviceSynchronize());
+        slot = &m->tc_img[0];
     }
-    FST_CUDA(cudaMemcpy(m->tc_core, img.data(), img.size(), cudaMemcpyHostToDevice));
-    m->tc_core_kind = kind;
+    std::vector<unsigned char> img = build_core_image(m, ci);
+    if (slot->bytes < img.size()) {
+        if (slot->ptr) cudaFree(slot->ptr);
+        slot->ptr = nullptr;
+        slot->bytes = 0;
+        FST_CUDA(cudaMalloc(&slot->ptr, img.size()));
+        slot->bytes = img.size();
+    }
+    FST_CUDA(cudaMemcpy(slot->ptr, img.data(), img.size(), cudaMemcpyHostToDevice));
+    slot->kind = kind;
+    m->tc_core = slot->ptr;
     ++m->tc_core_kind_version;
     return FST_OK;
 }
@@ -1194,6 +1246,113 @@ fst_status eval_tc_launch(fst_model* m, const float* xyz, int64_t n, float* out,
     return plan_run(P, s, ov);
 }
 
+// ---------------------------------------------------------------- autotuner
+// Probe points: n points spread over the model's box by a counter hash (splitmix64 finaliser
+// of the index), reproducible.
+__global__ void probe_points_kernel(float* xyz, int64_t n, float lo0, float lo1, float lo2, float hi0, float hi1,
+                                    float hi2) {
+    const float lo[3] = {lo0, lo1, lo2}, hi[3] = {hi0, hi1, hi2};
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        for (int k = 0; k < 3; ++k) {
+            uint64_t z = (uint64_t)(3 * i + k + 1) * 0x9E3779B97F4A7C15ull;
+            z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+            z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+            z ^= z >> 31;
+            const float u01 = (float)(z >> 40) * (1.0f / 16777216.0f);
+            xyz[k * n + i] = lo[k] + (hi[k] - lo[k]) * u01;
+        }
+}
+
+struct ProbeBufs {
+    std::mutex mu;
+    DevBuf xyz, out;
+};
+ProbeBufs g_probe[64];
+
+// Times both evaluator variants of the model's size class on n probe points (one warm-up and
+// three timed runs each, CUDA events) and records the faster in the table.  Synchronous.
+fst_status eval_autotune(fst_model* m, fst_prec prec, int64_t n, cudaStream_t s, float ms[2], int* choice) {
+    ms[0] = ms[1] = -1.f;
+    const int mode = mode_of(prec);
+    const int rm = bucket8(std::max(m->r[0], std::max(m->r[1], m->r[2])));
+    const int r3p = std::min(bucket8(m->r[2]), rm);
+    int dev = 0;
+    FST_CUDA(cudaGetDevice(&dev));
+    const TuneKey key = tune_key(m, mode, r3p);
+    if (!tc3_feasible(m, mode, r3p)) {
+        *choice = 0;
+    } else {
+        ProbeBufs& pb = g_probe[dev & 63];
+        std::lock_guard<std::mutex> lk(pb.mu);
+        FST_TRY(pb.xyz.ensure(sizeof(float) * 3 * (size_t)n));
+        FST_TRY(pb.out.ensure(sizeof(float) * (size_t)n));
+        float* xyz = pb.xyz.as<float>();
+        float* out = pb.out.as<float>();
+        probe_points_kernel<<<(unsigned)std::min<int64_t>((n + 255) / 256, 8LL * sm_count()), 256, 0, s>>>(
+            xyz, n, (float)m->lo[0], (float)m->lo[1], (float)m->lo[2], (float)m->hi[0], (float)m->hi[1],
+            (float)m->hi[2]);
+        FST_CHECK_LAUNCH();
+        cudaEvent_t e0, e1;
+        FST_CUDA(cudaEventCreate(&e0));
+        FST_CUDA(cudaEventCreate(&e1));
+        fst_status st = FST_OK;
+        for (int v = 0; v < 2 && st == FST_OK; ++v) {
+            t_force_variant = v;
+            fst_eval_plan* P = nullptr;
+            st = prepare_core_image(m, mode, r3p);
+            std::vector<HostItem> one{HostItem{m, xyz, (long long)n, out}};
+            if (st == FST_OK) st = plan_build(one, prec, &P);
+            if (st == FST_OK) st = plan_run(P, s);
+            if (st == FST_OK && cudaEventRecord(e0, s) != cudaSuccess) st = FST_ECUDA;
+            for (int r = 0; r < 3 && st == FST_OK; ++r) st = plan_run(P, s);
+            if (st == FST_OK && cudaEventRecord(e1, s) != cudaSuccess) st = FST_ECUDA;
+            if (st == FST_OK && cudaEventSynchronize(e1) != cudaSuccess) st = FST_ECUDA;
+            if (st == FST_OK) {
+                float t = 0.f;
+                cudaEventElapsedTime(&t, e0, e1);
+                ms[v] = t / 3.f;
+            }
+            if (P) plan_free(P);
+        }
+        t_force_variant = -1;
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (st == FST_ECUDA) set_error("autotune: CUDA event failure");
+        FST_TRY(st);
+        *choice = ms[1] < ms[0] ? 1 : 0;
+    }
+    {
+        TuneTable& T = g_tune[dev & 63];
+        std::lock_guard<std::mutex> lk(T.mu);
+        T.choice[key] = *choice;
+    }
+    return prepare_core_image(m, mode, r3p);   // the image of the chosen variant
+}
+
+bool tune_known(const fst_model* m, fst_prec prec) {
+    const int mode = mode_of(prec);
+    const int rm = bucket8(std::max(m->r[0], std::max(m->r[1], m->r[2])));
+    const int r3p = std::min(bucket8(m->r[2]), rm);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    TuneTable& T = g_tune[dev & 63];
+    std::lock_guard<std::mutex> lk(T.mu);
+    return T.choice.count(tune_key(m, mode, r3p)) != 0;
+}
+
+fst_status tune_set(const fst_model* m, fst_prec prec, int choice) {
+    const int mode = mode_of(prec);
+    const int rm = bucket8(std::max(m->r[0], std::max(m->r[1], m->r[2])));
+    const int r3p = std::min(bucket8(m->r[2]), rm);
+    int dev = 0;
+    FST_CUDA(cudaGetDevice(&dev));
+    TuneTable& T = g_tune[dev & 63];
+    std::lock_guard<std::mutex> lk(T.mu);
+    if (choice < 0) T.choice.erase(tune_key(m, mode, r3p));
+    else T.choice[tune_key(m, mode, r3p)] = choice;
+    return FST_OK;
+}
+
 // Device error word of the tensor-core evaluator (bounded waits that expired), read and
 // cleared by fst_eval_check.
 fst_status eval_tc_check(cudaStream_t s) {
@@ -1231,10 +1390,41 @@ extern "C" fst_status fst_eval_prepare(fst_model* m, fst_prec prec) {
     int rmax = m->r[0] > m->r[1] ? m->r[0] : m->r[1];
     rmax = m->r[2] > rmax ? m->r[2] : rmax;
     const int r3 = m->r[2];
-    const int r3p = r3 <= 8 ? 8 : r3 <= 16 ? 16 : r3 <= 24 ? 24 : 32;
-    (void)rmax;
-    (void)s;
+    const int r3p = std::min(r3 <= 8 ? 8 : r3 <= 16 ? 16 : r3 <= 24 ? 24 : 32, fst::bucket8(rmax));
+    if (!fst::tune_known(m, prec)) {
+        // first model of this size class on this device: measure the evaluator variants
+        float ms[2];
+        int choice = 0;
+        return fst::eval_autotune(m, prec, 1 << 18, s, ms, &choice);
+    }
     return fst::prepare_core_image(m, mode, r3p);
+}
+
+extern "C" fst_status fst_eval_autotune(fst_model* m, fst_prec prec, int64_t n_probe, fst_stream stream,
+                                        float* ms_cuda_core_factors, float* ms_tensor_core_factors,
+                                        int32_t* choice) {
+    FST_REQUIRE(m != nullptr, "model is NULL");
+    FST_REQUIRE(prec == FST_TF32 || prec == FST_BF16 || prec == FST_BF16X3,
+                "autotuning covers the tensor-core precisions TF32, BF16, BF16X3");
+    FST_REQUIRE(n_probe > 0, "n_probe must be positive");
+    int dev = 0;
+    FST_CUDA(cudaGetDevice(&dev));
+    FST_REQUIRE(dev == m->device, "model lives on device %d, current device is %d", m->device, dev);
+    std::lock_guard<std::mutex> lk(m->mu);
+    float ms[2];
+    int c = 0;
+    FST_TRY(fst::eval_autotune(m, prec, n_probe, (cudaStream_t)stream, ms, &c));
+    if (ms_cuda_core_factors) *ms_cuda_core_factors = ms[0];
+    if (ms_tensor_core_factors) *ms_tensor_core_factors = ms[1];
+    if (choice) *choice = c;
+    return FST_OK;
+}
+
+extern "C" fst_status fst_eval_autotune_set(const fst_model* m, fst_prec prec, int32_t choice) {
+    FST_REQUIRE(m != nullptr, "model is NULL");
+    FST_REQUIRE(prec == FST_TF32 || prec == FST_BF16 || prec == FST_BF16X3, "tensor-core precision expected");
+    FST_REQUIRE(choice >= -1 && choice <= 1, "choice must be -1 (forget), 0 or 1");
+    return fst::tune_set(m, prec, choice);
 }
 
 extern "C" fst_status fst_eval_batched(const fst_eval_item* items, int32_t count, fst_prec prec,

@@ -99,11 +99,17 @@ struct fst_model {
     double* alpha64 = nullptr;
     float* alpha32 = nullptr;
 
-    // tensor-core images of the core, built on demand (eval_tc.cu)
-    void* tc_core = nullptr;
-    size_t tc_core_bytes = 0;
-    int tc_core_kind = -1;
-    long long tc_core_kind_version = 0;
+    // tensor-core images of the core, built on demand (eval_tc.cu): one slot per kind
+    // (precision, evaluator variant, r3 padding), so preparing one kind never rewrites an
+    // image that a batch of another kind may still be reading
+    struct TcImage {
+        void* ptr = nullptr;
+        size_t bytes = 0;
+        int kind = -1;      // -1: stale (the core changed) or unused
+    };
+    TcImage tc_img[8];
+    const void* tc_core = nullptr;          // the image of the last prepared kind
+    long long tc_core_kind_version = 0;     // bumped whenever an image is (re)built
     // cached single-instance tensor-core work list (eval_tc.cu)
     fst_eval_plan* eval_plan = nullptr;
     long long eval_plan_n = -1, eval_plan_core = -1;

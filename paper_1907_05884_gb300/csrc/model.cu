@@ -102,14 +102,17 @@ static void free_device(fst_model* m) {
     }
     if (m->alpha64) cudaFree(m->alpha64);
     if (m->alpha32) cudaFree(m->alpha32);
-    if (m->tc_core) cudaFree(m->tc_core);
+    for (auto& t : m->tc_img) {
+        if (t.ptr) cudaFree(t.ptr);
+        t.ptr = nullptr;
+        t.bytes = 0;
+        t.kind = -1;
+    }
     if (m->eval_plan) plan_free(m->eval_plan);
     m->eval_plan = nullptr;
     m->alpha64 = nullptr;
     m->alpha32 = nullptr;
     m->tc_core = nullptr;
-    m->tc_core_bytes = 0;
-    m->tc_core_kind = -1;
     RefitScratch& s = m->rs;
     s.idx.release();
     for (int k = 0; k < 3; ++k) s.U[k].release();
@@ -133,7 +136,9 @@ static void free_device(fst_model* m) {
 }
 
 fst_status model_invalidate_tc(fst_model* m) {
-    m->tc_core_kind = -1;
+    // the core changed: every image is stale (its buffer is reused by the next build)
+    for (auto& t : m->tc_img) t.kind = -1;
+    ++m->tc_core_kind_version;
     return FST_OK;
 }
 

@@ -106,6 +106,8 @@ def _load():
         "fst_eval_plan_run": (I32, [P, P]),
         "fst_eval_plan_free": (None, [P]),
         "fst_eval_check": (I32, [P]),
+        "fst_eval_autotune": (I32, [P, I32, I64, P, P, P, P]),
+        "fst_eval_autotune_set": (I32, [P, I32, I32]),
         "fst_sample_rows": (I32, [U64, I64, I64, P, P]),
         "fst_sample_rows_static": (I32, [U64, I64, I64, P, P]),
         "fst_refit": (I32, [P, P, P, I64, P, I64, U64, I32, P, P, P]),
@@ -231,6 +233,18 @@ class Model:
 
     def prepare(self, prec: str):
         _check(lib.fst_eval_prepare(self._h, PREC[prec]))
+
+    def autotune(self, prec: str, n_probe: int = 1 << 18, stream=None):
+        """Measure this model's size class (fst_eval_autotune): returns
+        {"ms_cuda_core_factors", "ms_tensor_core_factors", "choice"}."""
+        a, b, c = C.c_float(), C.c_float(), C.c_int32()
+        _check(lib.fst_eval_autotune(self._h, PREC[prec], int(n_probe), _stream(stream), C.byref(a), C.byref(b),
+                                     C.byref(c)))
+        return {"ms_cuda_core_factors": a.value, "ms_tensor_core_factors": b.value, "choice": c.value}
+
+    def set_variant(self, prec: str, choice: int):
+        """Record the evaluator variant of this model's size class by hand (-1 forgets it)."""
+        _check(lib.fst_eval_autotune_set(self._h, PREC[prec], int(choice)))
 
     def eval_f64(self, xyz, out=None, stream=None):
         import torch
