@@ -250,6 +250,29 @@ fst_status fst_refit(fst_model* model, const float* xyz, const float* u, int64_t
                      const int64_t* idx, int64_t m, uint64_t seed, fst_prec prec,
                      const fst_refit_opts* opts, fst_refit_report* report, fst_stream stream);
 
+/* One refit instance of a batch: a model (each item a different model), its points (device,
+ * 3Q floats SoA) and values (device, Q floats), and the rows to draw (fst_sample_rows with
+ * `seed`, m >= R). */
+typedef struct {
+    fst_model* model;
+    const float* xyz;
+    const float* u;
+    int64_t Q;
+    int64_t m;
+    uint64_t seed;
+} fst_refit_item;
+
+/* Refit many models -- uneven ranks and point counts -- concurrently: `streams` (1..64) worker
+ * host threads, each with its own non-blocking CUDA stream of the current device, take the
+ * items in order and run fst_refit on them, so the launches of different instances overlap on
+ * the GPU (small instances do not fill it alone).  Every result equals that of fst_refit on
+ * the item (the same kernels, rows and arithmetic).  reports: host array of count entries, or
+ * NULL.  The inputs must be complete when the call starts (its streams do not wait on any of
+ * the caller's).  Synchronous: returns after every refit has finished; on failure returns the
+ * status of the first failed item (the others still ran).  Two items naming one model: EINVAL. */
+fst_status fst_refit_batched(const fst_refit_item* items, int32_t count, fst_prec prec,
+                             const fst_refit_opts* opts, int32_t streams, fst_refit_report* reports);
+
 /* The normal equations of the sampled problem alone (eq. rand_core restricted to the
  * rows idx): G = A^T A (device, R x R FP32 row-major; the lower triangle is written,
  * the upper triangle is unspecified) with A_{s,(i,j,k)} = w1_i w2_j w3_k at the points

@@ -646,9 +646,9 @@ static fst_status cholesky_lower_tc(float* G, int R, int* d_flag, const float* f
     const size_t potrf_smem = sizeof(float) * (PB * AS + 4 * SUB * SUB);   // P: FS x PB, then the inverses
     const size_t trsm_smem = sizeof(float) * ((64 + PB) * AS + 4 * SUB * (SUB + 4));
     const size_t syrk_smem = kSyrkStages * 2 * kHalfBytes + 1024 + 1024;
-    FST_CUDA(cudaFuncSetAttribute(potrf_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)potrf_smem));
-    FST_CUDA(cudaFuncSetAttribute(trsm_pack_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)trsm_smem));
-    FST_CUDA(cudaFuncSetAttribute(syrk_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)syrk_smem));
+    FST_TRY(allow_smem(potrf_inv_kernel, potrf_smem));
+    FST_TRY(allow_smem(trsm_pack_kernel, trsm_smem));
+    FST_TRY(allow_smem(syrk_tc_kernel, syrk_smem));
     for (int k0 = 0; k0 < R; k0 += PB) {
         const int kb = R - k0 < PB ? R - k0 : PB;
         const int rest = R - k0 - kb;
@@ -679,8 +679,7 @@ fst_status cholesky_lower(T* G, int R, int* d_flag, DevBuf& ws, cudaStream_t s) 
         return cholesky_lower_tc(reinterpret_cast<float*>(G), R, d_flag, reinterpret_cast<const float*>(floors),
                                  ws.as<unsigned char>() + floor_bytes, s);
     const size_t trsm_smem = 2 * NB * (NB + 1) * sizeof(T);
-    FST_CUDA(cudaFuncSetAttribute(trsm_panel_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)trsm_smem));
+    FST_TRY(allow_smem(trsm_panel_kernel<T>, trsm_smem));
     for (int k0 = 0; k0 < R; k0 += NB) {
         const int kb = R - k0 < NB ? R - k0 : NB;
         potrf_diag_kernel<T><<<1, 256, 0, s>>>(G, R, k0, kb, d_flag, floors);

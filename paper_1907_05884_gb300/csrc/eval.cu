@@ -135,7 +135,7 @@ static fst_status launch_rm(const EvalArgs<T>& a, const T* xyz, int64_t n, T* ou
         set_error("model too large for the CUDA-core evaluator (%zu bytes of shared memory)", smem);
         return FST_EUNSUPPORTED;
     }
-    FST_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    FST_TRY(allow_smem(kern, smem));
     int per_sm = 0;
     FST_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, B, smem));
     if (per_sm < 1) per_sm = 1;

@@ -1008,7 +1008,7 @@ struct Overrides {
 template <int MODE, int R3P, int RM>
 fst_status launch_bucket_t(const Bucket& B, const unsigned char* dimg, int* err, cudaStream_t s, Overrides ov) {
     auto kern = eval_tc_kernel<MODE, R3P, RM>;
-    FST_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)B.smem));
+    FST_TRY(allow_smem(kern, B.smem));
     kern<<<B.grid, kThreadsE, B.smem, s>>>(reinterpret_cast<const TcItem*>(dimg + B.items_off),
                                            reinterpret_cast<const TcUnit*>(dimg + B.units_off),
                                            reinterpret_cast<const int*>(dimg + B.cta_off), B.core_max, B.kb_max,
@@ -1031,7 +1031,7 @@ fst_status launch_bucket_m(const Bucket& B, const unsigned char* dimg, int* err,
 template <int MODE, int R3P, int RM>
 fst_status launch_bucket_tc3_t(const Bucket& B, const unsigned char* dimg, int* err, cudaStream_t s, Overrides ov) {
     auto kern = eval_tc3_kernel<MODE, R3P, RM>;
-    FST_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)B.smem));
+    FST_TRY(allow_smem(kern, B.smem));
     kern<<<B.grid, kThreadsE, B.smem, s>>>(reinterpret_cast<const TcItem*>(dimg + B.items_off),
                                            reinterpret_cast<const TcUnit*>(dimg + B.units_off),
                                            reinterpret_cast<const int*>(dimg + B.cta_off), B.core_max, B.kb_max,

@@ -936,7 +936,7 @@ extern "C" fst_status fst_fit(const float* xyz, const float* u, int64_t Q, const
     FST_TRY(sc.get(&loo_d, ncols));
     FST_CUDA(cudaMemcpyAsync(jobs_d, jobs.data(), ncols * sizeof(LarsJob), cudaMemcpyHostToDevice, s));
     const size_t lsm = 2 * (size_t)kLarsMaxP * kLarsMaxP * sizeof(double);
-    FST_CUDA(cudaFuncSetAttribute(lars_loo_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lsm));
+    FST_TRY(allow_smem(lars_loo_kernel, lsm));
     lars_loo_kernel<<<ncols, kLarsThreads, lsm, s>>>(jobs_d, rows_d, coef_d, nnz_d, loo_d);
     FST_CHECK_LAUNCH();
     std::vector<int32_t> rows_h((size_t)ncols * kLarsMaxP), nnz_h(ncols);

@@ -59,6 +59,59 @@ struct DevBuf {
     template <typename T> T* as() const { return static_cast<T*>(ptr); }
 };
 
+// Per-device scratch that refits of different models on different streams may need at the
+// same time (the Gram's operand copies).  A caller leases the first slot nobody holds (one
+// caller alone always gets slot 0), its stream waits on the device for the slot's previous
+// user, and the lease records the caller's use once its work is enqueued; the host holds the
+// slot only while enqueueing.  Growing a buffer first waits for the previous user to finish.
+constexpr int kScratchSlots = 4;
+struct ScratchSlot {
+    std::mutex mu;
+    DevBuf buf[3];
+    cudaEvent_t done = nullptr;
+    bool used = false;
+};
+struct ScratchPool {
+    ScratchSlot slot[kScratchSlots];
+};
+class SlotLease {
+  public:
+    explicit SlotLease(ScratchPool& pool) {
+        for (int i = 0; i < kScratchSlots && !sl_; ++i)
+            if (pool.slot[i].mu.try_lock()) sl_ = &pool.slot[i];
+        if (!sl_) {
+            pool.slot[0].mu.lock();
+            sl_ = &pool.slot[0];
+        }
+    }
+    // a lease that began records its use even when the caller gave up half-way, since
+    // some of its work may already be enqueued
+    ~SlotLease() {
+        if (began_) {
+            if (cudaEventRecord(sl_->done, s_) == cudaSuccess) sl_->used = true;
+        }
+        sl_->mu.unlock();
+    }
+    SlotLease(const SlotLease&) = delete;
+    SlotLease& operator=(const SlotLease&) = delete;
+    fst_status begin(cudaStream_t s) {
+        if (!sl_->done) FST_CUDA(cudaEventCreateWithFlags(&sl_->done, cudaEventDisableTiming));
+        if (sl_->used) FST_CUDA(cudaStreamWaitEvent(s, sl_->done, 0));
+        s_ = s;
+        began_ = true;
+        return FST_OK;
+    }
+    fst_status ensure(int i, size_t bytes) {
+        if (bytes > sl_->buf[i].bytes && sl_->used) FST_CUDA(cudaEventSynchronize(sl_->done));
+        return sl_->buf[i].ensure(bytes);
+    }
+    template <typename T> T* as(int i) const { return sl_->buf[i].as<T>(); }
+  private:
+    ScratchSlot* sl_ = nullptr;
+    cudaStream_t s_ = nullptr;
+    bool began_ = false;
+};
+
 // A captured triangular-solve sequence (chol.cu), replayed with one graph launch.
 struct SolveGraph {
     cudaGraphExec_t exec = nullptr;
@@ -75,7 +128,8 @@ struct SolveGraph {
 
 // Scratch of the refit, kept inside the model between calls.
 struct RefitScratch {
-    DevBuf idx, U[3], b, G, G64, res, g, z, delta, alpha, norms, flag, Linv, LT, xw, yw, pcg, chol_ws;
+    DevBuf idx, U[3], b, G, G64, res, g, z, delta, alpha, norms, flag, Linv, LT, xw, yw, pcg, chol_ws, atr_part,
+        gram_err;
     SolveGraph solve;
 };
 
@@ -128,6 +182,15 @@ void plan_free(fst_eval_plan* p);
 // Device upload of the derived layouts after the host copy changed.
 fst_status model_upload_core(fst_model* m);
 fst_status model_invalidate_tc(fst_model* m);
+
+// Raise a kernel's dynamic shared-memory limit on the current device to at least `bytes`.
+// The limit is a property of the function, not of a launch, and it only grows here, so
+// launches from host threads on different streams never lower it under one another.
+fst_status allow_dynamic_smem(const void* func, size_t bytes);
+template <typename K>
+fst_status allow_smem(K* kernel, size_t bytes) {
+    return allow_dynamic_smem(reinterpret_cast<const void*>(kernel), bytes);
+}
 
 // Number of SMs of the current device (cached).
 int sm_count();

@@ -286,36 +286,33 @@ gram_pk_kernel(const unsigned char* __restrict__ pk, int R, int nrt, int nkc, fl
     if (warp == 0) tc::tmem_dealloc(tmem, 512);
 }
 
-struct PkScratch {
-    std::mutex mu;
-    DevBuf flag, pt, u3t, packed;
-};
-PkScratch g_pk[64];
+ScratchPool g_pk[64];   // per device: PT, U3T, the packed operand
 
 template <int MODE>
 fst_status pack_and_multiply(const float* PT, const float* U3T, int64_t m, int64_t mpad, int r3, int R,
-                             DevBuf& packed, float* G, int* err, cudaStream_t s) {
+                             SlotLease& lease, float* G, int* err, cudaStream_t s) {
     using C = PCfg<MODE>;
     const int nrt = 2 * ((R + 255) / 256);
     const int nkc = (int)((m + C::KT - 1) / C::KT);
     const size_t bytes = (size_t)C::PLANES * nkc * nrt * C::TILE;
-    FST_TRY(packed.ensure(bytes));
+    FST_TRY(lease.ensure(2, bytes));
+    unsigned char* packed = lease.as<unsigned char>(2);
     {
         const int64_t total = (int64_t)nkc * nrt * 128 * C::NCH;
         int64_t grid = (total + 255) / 256;
         if (grid > 16LL * sm_count()) grid = 16LL * sm_count();
         pack_kr_kernel<MODE><<<(unsigned)grid, 256, 0, s>>>(PT, U3T, mpad, r3, R, nrt, nkc,
-                                                            packed.as<unsigned char>());
+                                                            packed);
         FST_CHECK_LAUNCH();
     }
     auto kern = gram_pk_kernel<MODE>;
     const size_t smem = kStagesP * kStageBytesP + 1024 + 1024;
-    FST_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    FST_TRY(allow_smem(kern, smem));
     const long long nT = nrt / 2;
     const long long ntiles = nT * (nT + 1) / 2;
     int grid = sm_count();
     if (ntiles < grid) grid = (int)ntiles;
-    kern<<<grid, kThreadsP, smem, s>>>(packed.as<unsigned char>(), R, nrt, nkc, G, err);
+    kern<<<grid, kThreadsP, smem, s>>>(packed, R, nrt, nkc, G, err);
     FST_CHECK_LAUNCH();
     return FST_OK;
 }
@@ -329,29 +326,33 @@ fst_status gram_pk_launch(const fst_model* M, const float* U1, const float* U2, 
                           float* G, fst_prec prec, cudaStream_t s) {
     int dev = 0;
     FST_CUDA(cudaGetDevice(&dev));
-    PkScratch& ps = g_pk[dev & 63];
-    std::lock_guard<std::mutex> lk(ps.mu);
-    FST_TRY(ps.flag.ensure(sizeof(int)));
-    int* err = ps.flag.as<int>();
-    FST_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
-    const int r1 = M->r[0], r2 = M->r[1], r3 = M->r[2];
-    const int R = r1 * r2 * r3;
-    const int64_t mpad = (m + 63) / 64 * 64;
-    FST_TRY(ps.pt.ensure(sizeof(float) * (size_t)r1 * r2 * mpad));
-    FST_TRY(ps.u3t.ensure(sizeof(float) * (size_t)r3 * mpad));
-    float* PT = ps.pt.as<float>();
-    float* U3T = ps.u3t.as<float>();
-    FST_TRY(pair_products(U1, U2, U3, m, mpad, r1, r2, r3, PT, U3T, s));
-    fst_status st;
-    switch (prec) {
-        case FST_TF32: st = pack_and_multiply<pTF32>(PT, U3T, m, mpad, r3, R, ps.packed, G, err, s); break;
-        case FST_BF16: st = pack_and_multiply<pBF16>(PT, U3T, m, mpad, r3, R, ps.packed, G, err, s); break;
-        case FST_BF16X3: st = pack_and_multiply<pBF16X3>(PT, U3T, m, mpad, r3, R, ps.packed, G, err, s); break;
-        default:
-            set_error("packed Gram takes TF32, BF16 or BF16X3");
-            return FST_EINVAL;
-    }
-    if (st != FST_OK) return st;
+    // the error word is the model's (the caller holds the model's lock)
+    DevBuf& eb = const_cast<fst_model*>(M)->rs.gram_err;
+    FST_TRY(eb.ensure(sizeof(int)));
+    int* err = eb.as<int>();
+    {
+        SlotLease lease(g_pk[dev & 63]);
+        FST_TRY(lease.begin(s));
+        FST_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
+        const int r1 = M->r[0], r2 = M->r[1], r3 = M->r[2];
+        const int R = r1 * r2 * r3;
+        const int64_t mpad = (m + 63) / 64 * 64;
+        FST_TRY(lease.ensure(0, sizeof(float) * (size_t)r1 * r2 * mpad));
+        FST_TRY(lease.ensure(1, sizeof(float) * (size_t)r3 * mpad));
+        float* PT = lease.as<float>(0);
+        float* U3T = lease.as<float>(1);
+        FST_TRY(pair_products(U1, U2, U3, m, mpad, r1, r2, r3, PT, U3T, s));
+        fst_status st;
+        switch (prec) {
+            case FST_TF32: st = pack_and_multiply<pTF32>(PT, U3T, m, mpad, r3, R, lease, G, err, s); break;
+            case FST_BF16: st = pack_and_multiply<pBF16>(PT, U3T, m, mpad, r3, R, lease, G, err, s); break;
+            case FST_BF16X3: st = pack_and_multiply<pBF16X3>(PT, U3T, m, mpad, r3, R, lease, G, err, s); break;
+            default:
+                set_error("packed Gram takes TF32, BF16 or BF16X3");
+                return FST_EINVAL;
+        }
+        if (st != FST_OK) return st;
+    }   // the lease records this stream's use of the slot
     int herr = 0;
     FST_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
     FST_CUDA(cudaStreamSynchronize(s));

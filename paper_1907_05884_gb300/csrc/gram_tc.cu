@@ -442,7 +442,7 @@ fst_status launch(const float* PT, const float* U3T, int64_t m, int64_t mpad, in
         set_error("tensor-core Gram: ranks need %zu bytes of shared memory", smem);
         return FST_EUNSUPPORTED;
     }
-    FST_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    FST_TRY(allow_smem(kern, smem));
     const int R = r1 * r2 * r3;
     const long long nT = (R + kTile - 1) / kTile;
     const long long ntiles = nT * (nT + 1) / 2;
@@ -453,11 +453,7 @@ fst_status launch(const float* PT, const float* U3T, int64_t m, int64_t mpad, in
     return FST_OK;
 }
 
-struct GramErr {
-    std::mutex mu;
-    DevBuf flag, pt, u3t;
-};
-GramErr g_gram_err[64];
+ScratchPool g_gram_tc[64];   // per device: PT, U3T
 
 }  // namespace
 
@@ -474,32 +470,36 @@ fst_status gram_tc_launch(const fst_model* M, const float* U1, const float* U2, 
                           float* G, fst_prec prec, cudaStream_t s) {
     int dev = 0;
     FST_CUDA(cudaGetDevice(&dev));
-    GramErr& ge = g_gram_err[dev & 63];
-    std::lock_guard<std::mutex> lk(ge.mu);
-    FST_TRY(ge.flag.ensure(sizeof(int)));
-    int* err = ge.flag.as<int>();
-    FST_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
     const int r1 = M->r[0], r2 = M->r[1], r3 = M->r[2];
     if (r3 < 4) {
         set_error("tensor-core Gram needs r3 >= 4");
         return FST_EUNSUPPORTED;
     }
-    const int64_t mpad = (m + 63) / 64 * 64;
-    FST_TRY(ge.pt.ensure(sizeof(float) * (size_t)r1 * r2 * mpad));
-    FST_TRY(ge.u3t.ensure(sizeof(float) * (size_t)r3 * mpad));
-    float* PT = ge.pt.as<float>();
-    float* U3T = ge.u3t.as<float>();
-    FST_TRY(pair_products(U1, U2, U3, m, mpad, r1, r2, r3, PT, U3T, s));
-    fst_status st;
-    switch (prec) {
-        case FST_TF32: st = launch<kTF32>(PT, U3T, m, mpad, r1, r2, r3, G, err, s); break;
-        case FST_BF16: st = launch<kBF16>(PT, U3T, m, mpad, r1, r2, r3, G, err, s); break;
-        case FST_BF16X3: st = launch<kBF16X3>(PT, U3T, m, mpad, r1, r2, r3, G, err, s); break;
-        default:
-            set_error("tensor-core Gram takes TF32, BF16 or BF16X3");
-            return FST_EINVAL;
-    }
-    if (st != FST_OK) return st;
+    // the error word is the model's (the caller holds the model's lock)
+    DevBuf& eb = const_cast<fst_model*>(M)->rs.gram_err;
+    FST_TRY(eb.ensure(sizeof(int)));
+    int* err = eb.as<int>();
+    {
+        SlotLease lease(g_gram_tc[dev & 63]);
+        FST_TRY(lease.begin(s));
+        FST_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
+        const int64_t mpad = (m + 63) / 64 * 64;
+        FST_TRY(lease.ensure(0, sizeof(float) * (size_t)r1 * r2 * mpad));
+        FST_TRY(lease.ensure(1, sizeof(float) * (size_t)r3 * mpad));
+        float* PT = lease.as<float>(0);
+        float* U3T = lease.as<float>(1);
+        FST_TRY(pair_products(U1, U2, U3, m, mpad, r1, r2, r3, PT, U3T, s));
+        fst_status st;
+        switch (prec) {
+            case FST_TF32: st = launch<kTF32>(PT, U3T, m, mpad, r1, r2, r3, G, err, s); break;
+            case FST_BF16: st = launch<kBF16>(PT, U3T, m, mpad, r1, r2, r3, G, err, s); break;
+            case FST_BF16X3: st = launch<kBF16X3>(PT, U3T, m, mpad, r1, r2, r3, G, err, s); break;
+            default:
+                set_error("tensor-core Gram takes TF32, BF16 or BF16X3");
+                return FST_EINVAL;
+        }
+        if (st != FST_OK) return st;
+    }   // the lease records this stream's use of the slot
     int herr = 0;
     FST_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
     FST_CUDA(cudaStreamSynchronize(s));

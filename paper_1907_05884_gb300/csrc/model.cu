@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <atomic>
+#include <map>
 #include <memory>
 
 #include "fst_internal.cuh"
@@ -44,6 +45,19 @@ void set_error(const char* fmt, ...) {
 fst_status cuda_fail(cudaError_t e, const char* what, const char* file, int line) {
     set_error("%s failed: %s (%s:%d)", what, cudaGetErrorString(e), file, line);
     return e == cudaErrorMemoryAllocation ? FST_ENOMEM : FST_ECUDA;
+}
+
+fst_status allow_dynamic_smem(const void* func, size_t bytes) {
+    static std::mutex mu;
+    static std::map<std::pair<int, const void*>, size_t> limit;
+    int dev = 0;
+    FST_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(mu);
+    size_t& cur = limit[{dev, func}];
+    if (bytes <= cur) return FST_OK;
+    FST_CUDA(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    cur = bytes;
+    return FST_OK;
 }
 
 fst_status DevBuf::ensure(size_t need) {
@@ -129,6 +143,8 @@ static void free_device(fst_model* m) {
     s.Linv.release();
     s.LT.release();
     s.chol_ws.release();
+    s.atr_part.release();
+    s.gram_err.release();
     s.xw.release();
     s.yw.release();
     s.pcg.release();

@@ -17,6 +17,9 @@
 #include <math.h>
 
 #include <vector>
+#include <thread>
+#include <string>
+#include <atomic>
 
 #include "basis.cuh"
 
@@ -291,11 +294,14 @@ __global__ void shift_diag_kernel(float* G, int R, float delta) {
         G[(size_t)i * R + i] *= 1.f + delta;
 }
 
-// out[k] = sum_i x_k[i] * y_k[i] for k < nd (out zeroed by the caller)
-__global__ void dots_kernel(const double* x0, const double* y0, const double* x1, const double* y1, int n, int nd,
-                            double* out) {
+// out[k] = sum_i x_k[i] * y_k[i] for k < nd, by one block in a fixed order, so that a refit
+// repeats bit for bit (the step lengths of the conjugate gradients depend on these sums)
+constexpr int kDotThreads = 1024;
+__global__ void __launch_bounds__(kDotThreads) dots_kernel(const double* x0, const double* y0, const double* x1,
+                                                           const double* y1, int n, int nd, double* out) {
+    __shared__ double red[2][kDotThreads / 32];
     double a0 = 0.0, a1 = 0.0;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    for (int i = threadIdx.x; i < n; i += kDotThreads) {
         a0 += x0[i] * y0[i];
         if (nd > 1) a1 += x1[i] * y1[i];
     }
@@ -303,9 +309,23 @@ __global__ void dots_kernel(const double* x0, const double* y0, const double* x1
         a0 += __shfl_xor_sync(0xffffffffu, a0, o);
         a1 += __shfl_xor_sync(0xffffffffu, a1, o);
     }
-    if ((threadIdx.x & 31) == 0) {
-        atomicAdd(&out[0], a0);
-        if (nd > 1) atomicAdd(&out[1], a1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) {
+        red[0][warp] = a0;
+        red[1][warp] = a1;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        a0 = red[0][lane];
+        a1 = red[1][lane];
+        for (int o = 16; o; o >>= 1) {
+            a0 += __shfl_xor_sync(0xffffffffu, a0, o);
+            a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+        }
+        if (lane == 0) {
+            out[0] = a0;
+            if (nd > 1) out[1] = a1;
+        }
     }
 }
 
@@ -325,25 +345,6 @@ template <typename T>
 __global__ void from_double_kernel(const double* src, T* dst, int64_t n) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         dst[i] = (T)src[i];
-}
-
-// alpha += delta; norms[0] += ||delta||^2, norms[1] += ||alpha||^2 (norms zeroed by the caller)
-__global__ void axpy_norms_kernel(double* alpha, const double* delta, int n, double* norms) {
-    double d2 = 0.0, a2 = 0.0;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const double a = alpha[i] + delta[i];
-        alpha[i] = a;
-        d2 += delta[i] * delta[i];
-        a2 += a * a;
-    }
-    for (int o = 16; o; o >>= 1) {
-        d2 += __shfl_xor_sync(0xffffffffu, d2, o);
-        a2 += __shfl_xor_sync(0xffffffffu, a2, o);
-    }
-    if ((threadIdx.x & 31) == 0) {
-        atomicAdd(&norms[0], d2);
-        atomicAdd(&norms[1], a2);
-    }
 }
 
 // ------------------------------------------------------------------ driver
@@ -388,7 +389,7 @@ static fst_status launch_factors(const fst_model* M, const T* xyz, int64_t Q, co
 #define FST_FACT(RMV)                                                                                      \
     {                                                                                                      \
         auto kern = sampled_factors_kernel<T, RMV>;                                                        \
-        FST_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));      \
+        FST_TRY(allow_smem(kern, smem));      \
         kern<<<grid_for(m, 128), 128, smem, s>>>(a, xyz, Q, idx, m, u, U[0], U[1], U[2], bvec);           \
     }
     if (RMb == 8) FST_FACT(8) else if (RMb == 16) FST_FACT(16) else if (RMb == 24) FST_FACT(24) else FST_FACT(32)
@@ -396,12 +397,6 @@ static fst_status launch_factors(const fst_model* M, const T* xyz, int64_t Q, co
     FST_CHECK_LAUNCH();
     return FST_OK;
 }
-
-struct AtrScratch {
-    std::mutex mu;
-    DevBuf part;
-};
-static AtrScratch g_atr[64];
 
 template <typename T>
 static fst_status launch_atr(const fst_model* M, const T* const U[3], const double* rv, int64_t m, double* g,
@@ -419,12 +414,11 @@ static fst_status launch_atr(const fst_model* M, const T* const U[3], const doub
     int64_t nparts = 2LL * sm_count();
     int64_t rows_per_block = ((m + nparts - 1) / nparts + 31) / 32 * 32;
     nparts = (m + rows_per_block - 1) / rows_per_block;
-    int dev = 0;
-    FST_CUDA(cudaGetDevice(&dev));
-    AtrScratch& as = g_atr[dev & 63];
-    std::lock_guard<std::mutex> lk(as.mu);
-    FST_TRY(as.part.ensure(sizeof(double) * (size_t)nparts * R));
-    double* part = as.part.as<double>();
+    // per-model scratch (the caller holds the model's lock), so refits of different models on
+    // different streams never share it
+    DevBuf& pb = const_cast<fst_model*>(M)->rs.atr_part;
+    FST_TRY(pb.ensure(sizeof(double) * (size_t)nparts * R));
+    double* part = pb.as<double>();
     const unsigned grid = (unsigned)nparts;
 #define FST_ATR(R3V, PPTV) \
     atr_kernel<T, R3V, PPTV><<<grid, threads, 0, s>>>(U[0], U[1], U[2], rv, m, r1, r2, r3, rows_per_block, part)
@@ -456,7 +450,7 @@ static fst_status launch_residual(const fst_model* M, const T* const U[3], const
 #define FST_RES(V)                                                                                          \
     {                                                                                                       \
         auto kern = residual_kernel<T, V>;                                                                  \
-        FST_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));       \
+        FST_TRY(allow_smem(kern, smem));       \
         kern<<<grid, 128, smem, s>>>(U[0], U[1], U[2], bvec, alpha, m, r1, r2, r3, scale, rv);              \
     }
     if (R3M == 8) FST_RES(8) else if (R3M == 16) FST_RES(16) else if (R3M == 24) FST_RES(24) else FST_RES(32)
@@ -673,8 +667,7 @@ static fst_status refit_impl(fst_model* M, const T* xyz, const T* u, int64_t Q, 
     const int vgrid = grid_for(R, 256, 2);
     auto dots = [&](const double* x0, const double* y0, const double* x1, const double* y1, int nd,
                     double* hout) -> fst_status {
-        FST_CUDA(cudaMemsetAsync(norms, 0, 2 * sizeof(double), s));
-        dots_kernel<<<vgrid, 256, 0, s>>>(x0, y0, x1, y1, R, nd, norms);
+        dots_kernel<<<1, kDotThreads, 0, s>>>(x0, y0, x1, y1, R, nd, norms);
         FST_CHECK_LAUNCH();
         FST_CUDA(cudaMemcpyAsync(hout, norms, nd * sizeof(double), cudaMemcpyDeviceToHost, s));
         FST_CUDA(cudaStreamSynchronize(s));
@@ -806,6 +799,59 @@ extern "C" fst_status fst_refit(fst_model* model, const float* xyz, const float*
     FST_REQUIRE(prec == FST_FP32 || prec == FST_TF32 || prec == FST_BF16 || prec == FST_BF16X3,
                 "fst_refit takes FP32/TF32/BF16/BF16X3; use fst_refit_f64 for FP64");
     return refit_entry<float>(model, xyz, u, Q, idx, m, seed, prec, opts, report, (cudaStream_t)stream);
+}
+
+// Many refits at once: `streams` worker threads, each with its own non-blocking stream, take
+// the items in order and refit them, so the launches of different instances overlap on the
+// device.  Every per-model scratch is private to its model; the per-device scratch the refit
+// shares (the sampler's, the packed Gram operand) is ordered across streams on the device.
+extern "C" fst_status fst_refit_batched(const fst_refit_item* items, int32_t count, fst_prec prec,
+                                        const fst_refit_opts* opts, int32_t streams, fst_refit_report* reports) {
+    FST_REQUIRE(count >= 0 && (count == 0 || items != nullptr), "items is NULL");
+    FST_REQUIRE(prec == FST_FP32 || prec == FST_TF32 || prec == FST_BF16 || prec == FST_BF16X3,
+                "fst_refit_batched takes FP32/TF32/BF16/BF16X3");
+    FST_REQUIRE(streams >= 1 && streams <= 64, "streams must be in 1..64");
+    for (int i = 0; i < count; ++i)
+        for (int j = 0; j < i; ++j)
+            FST_REQUIRE(items[i].model != items[j].model, "items %d and %d refit the same model", j, i);
+    if (count == 0) return FST_OK;
+    int dev = 0;
+    FST_CUDA(cudaGetDevice(&dev));
+    const int nw = streams < count ? streams : count;
+    std::atomic<int> next{0};
+    std::vector<fst_status> status(count, FST_OK);
+    std::vector<std::string> errors(count);
+    std::vector<std::thread> workers;
+    workers.reserve(nw);
+    for (int w = 0; w < nw; ++w) {
+        workers.emplace_back([&, w]() {
+            (void)w;
+            if (cudaSetDevice(dev) != cudaSuccess) {
+                for (int i; (i = next.fetch_add(1)) < count;) status[i] = FST_ECUDA;
+                return;
+            }
+            cudaStream_t s = nullptr;
+            if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+                for (int i; (i = next.fetch_add(1)) < count;) status[i] = FST_ECUDA;
+                return;
+            }
+            for (int i; (i = next.fetch_add(1)) < count;) {
+                const fst_refit_item& it = items[i];
+                status[i] = fst_refit(it.model, it.xyz, it.u, it.Q, nullptr, it.m, it.seed, prec, opts,
+                                      reports ? &reports[i] : nullptr, (fst_stream)s);
+                if (status[i] != FST_OK) errors[i] = fst_last_error();
+            }
+            cudaStreamSynchronize(s);
+            cudaStreamDestroy(s);
+        });
+    }
+    for (auto& t : workers) t.join();
+    for (int i = 0; i < count; ++i)
+        if (status[i] != FST_OK) {
+            set_error("item %d: %s", i, errors[i].c_str());
+            return status[i];
+        }
+    return FST_OK;
 }
 
 extern "C" fst_status fst_refit_f64(fst_model* model, const double* xyz, const double* u, int64_t Q,

@@ -181,10 +181,14 @@ __global__ void iota_kernel(int64_t* idx, int64_t n) {
         idx[i] = i;
 }
 
-// Per-device scratch of the sampler (state, histogram, block counts).
+// Per-device scratch of the sampler (state, histogram, block counts).  Calls on different
+// streams are ordered on the device through `done` (the event after the last user's kernels),
+// so two samplers never share the scratch at the same time; no host synchronisation.
 struct SampleScratch {
     std::mutex mu;
     DevBuf state, hist, counts;
+    cudaEvent_t done = nullptr;
+    bool used = false;
 };
 static SampleScratch g_sample_scratch[64];
 
@@ -202,6 +206,13 @@ fst_status sample_rows(uint64_t seed, int64_t Q, int64_t m, int64_t* idx, cudaSt
     FST_REQUIRE(dev >= 0 && dev < 64, "device ordinal %d out of range", dev);
     SampleScratch& sc = g_sample_scratch[dev];
     std::lock_guard<std::mutex> lk(sc.mu);
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    FST_CUDA(cudaStreamIsCapturing(s, &cap));
+    const bool capturing = cap != cudaStreamCaptureStatusNone;   // no cross-stream ordering inside a capture
+    if (!capturing) {
+        if (!sc.done) FST_CUDA(cudaEventCreateWithFlags(&sc.done, cudaEventDisableTiming));
+        if (sc.used) FST_CUDA(cudaStreamWaitEvent(s, sc.done, 0));
+    }
     const int sms = sm_count();
     int64_t nblocks = (Q + 8191) / 8192;
     if (nblocks < 1) nblocks = 1;
@@ -230,6 +241,10 @@ fst_status sample_rows(uint64_t seed, int64_t Q, int64_t m, int64_t* idx, cudaSt
     compact_write_kernel<<<(unsigned)nblocks, kCompactBlock, 0, s>>>(seed, Q, rows_per_block, st, counts,
                                                                       idx, m);
     FST_CHECK_LAUNCH();
+    if (!capturing) {
+        FST_CUDA(cudaEventRecord(sc.done, s));
+        sc.used = true;
+    }
     return FST_OK;
 }
 

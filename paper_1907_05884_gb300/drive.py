@@ -18,7 +18,7 @@ import numpy as np
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("what", choices=["gram", "eval", "refit", "sample", "batch", "serve", "fit", "chol",
-                                     "precision", "plain"])
+                                     "precision", "plain", "refit-batch"])
     ap.add_argument("--grid", type=int, default=64)
     ap.add_argument("--frac", type=float, default=0.05)
     ap.add_argument("--eps", type=float, default=1e-3)
@@ -32,6 +32,7 @@ def main():
     ap.add_argument("--ranks", type=int, nargs=3, default=[24, 24, 24])
     ap.add_argument("--degree", type=int, default=31)
     ap.add_argument("--reps", type=int, default=2)
+    ap.add_argument("--streams", type=int, nargs="+", default=[1, 2, 4, 8])
     args = ap.parse_args()
 
     import torch
@@ -41,6 +42,8 @@ def main():
 
     if args.what == "batch":
         return batch(args)
+    if args.what == "refit-batch":
+        return refit_batch(args)
     if args.what == "serve":
         return serve_loads(args)
     if args.what == "fit":
@@ -128,6 +131,50 @@ def batch(args):
               f"plan_ms={tp:.3f} ({total / tp / 1e3:.1f} Mpoints/s) graph_ms={tg:.3f} "
               f"({total / tg / 1e3:.1f} Mpoints/s) per_instance_ms={ts:.3f} ({total / ts / 1e3:.1f} Mpoints/s)",
               flush=True)
+
+
+def refit_batch(args):
+    """Batched refits over the batching workload's instances (ranks U{4..24} per mode, point
+    counts log-uniform in [--q-lo, --q-hi], m = 8R rows each): one fst_refit_batched call on S
+    streams against one fst_refit per instance, one after another."""
+    import time
+    import torch
+    from paper_1907_05884_gb300 import fst, synth
+    table = synth.batch_instances(n_fields=max(1, args.instances // 8), n_steps=8, q_lo=args.q_lo,
+                                  q_hi=args.q_hi)[:args.instances]
+    models, xs, us, ms, seeds = [], [], [], [], []
+    g = torch.Generator(device="cuda")
+    g.manual_seed(11)
+    for inst in table:
+        m = synth.random_model(inst["r"], (args.degree,) * 3, seed=inst["seed"] % (1 << 31), density=0.6,
+                               orthonormal=True)
+        models.append(fst.Model(m))
+        x = torch.rand((3, inst["Q"]), device="cuda", generator=g) * 2 - 1
+        xs.append(x.contiguous())
+        # a smooth synthetic field of the coordinates
+        us.append((torch.exp(-2 * (x * x).sum(0)) + 0.3 * torch.sin(3 * x[0]) * x[1]).contiguous())
+        ms.append(min(8 * m.R, inst["Q"]))
+        seeds.append(inst["seed"])
+    rows = sum(ms)
+    torch.cuda.synchronize()
+    for r in range(args.reps):
+        # wall-clock on both sides: the batched call runs on several streams of its own
+        torch.cuda.synchronize()
+        h0 = time.perf_counter()
+        reps = [Mi.refit(x, u, mm, seed=sd, prec=args.prec) for Mi, x, u, mm, sd in zip(models, xs, us, ms, seeds)]
+        torch.cuda.synchronize()
+        seq = (time.perf_counter() - h0) * 1e3
+        phases = {k: sum(rp[k] for rp in reps) for k in ("ms_sample", "ms_factors", "ms_gram", "ms_cholesky",
+                                                          "ms_refine")}
+        line = (f"refit-batch instances={len(models)} rows={rows} prec={args.prec} sequential_ms={seq:.2f} "
+                + " ".join(f"{k}={v:.1f}" for k, v in phases.items()))
+        for S in args.streams:
+            torch.cuda.synchronize()
+            h0 = time.perf_counter()
+            fst.refit_batched(models, xs, us, ms, seeds, prec=args.prec, streams=S)
+            torch.cuda.synchronize()
+            line += f" streams{S}_ms={(time.perf_counter() - h0) * 1e3:.2f}"
+        print(line, flush=True)
 
 
 def fit(args):

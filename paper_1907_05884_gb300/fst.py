@@ -56,6 +56,11 @@ class RefitReport(C.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class RefitItem(C.Structure):
+    _fields_ = [("model", C.c_void_p), ("xyz", C.c_void_p), ("u", C.c_void_p), ("Q", C.c_int64),
+                ("m", C.c_int64), ("seed", C.c_uint64)]
+
+
 class FitParams(C.Structure):
     _fields_ = [("grid", C.c_int32 * 3), ("sample_frac", C.c_double), ("eps", C.c_double),
                 ("max_rank", C.c_int32 * 3), ("max_degree", C.c_int32), ("fixed_rank", C.c_int32),
@@ -112,6 +117,7 @@ def _load():
         "fst_sample_rows_static": (I32, [U64, I64, I64, P, P]),
         "fst_refit": (I32, [P, P, P, I64, P, I64, U64, I32, P, P, P]),
         "fst_refit_f64": (I32, [P, P, P, I64, P, I64, U64, P, P, P]),
+        "fst_refit_batched": (I32, [P, I32, I32, P, I32, P]),
         "fst_normal_matrix": (I32, [P, P, P, I64, P, I64, I32, P, P, P]),
         "fst_fit": (I32, [P, P, I64, P, P, P, I32, P, P, P, P, P]),
         "fst_cholesky_f32": (I32, [P, I32, P]),
@@ -279,6 +285,24 @@ class Model:
                                  C.c_uint64(seed & 0xFFFFFFFFFFFFFFFF), PREC[prec], C.byref(opts),
                                  C.byref(rep), _stream(stream)))
         return rep.as_dict()
+
+
+def refit_batched(models, xyzs, us, ms, seeds, prec: str = "bf16", streams: int = 4, max_refine: int = 32,
+                  refine_tol: float = 0.0):
+    """fst_refit_batched: refit every model on its own points concurrently on `streams` streams.
+    Returns the reports (dicts)."""
+    import torch
+    n = len(models)
+    arr = (RefitItem * max(n, 1))()
+    for i, (M, x, u, m, sd) in enumerate(zip(models, xyzs, us, ms, seeds)):
+        assert x.is_cuda and x.dtype == torch.float32 and x.is_contiguous() and x.shape[0] == 3
+        assert u.is_cuda and u.dtype == torch.float32 and u.is_contiguous()
+        arr[i] = RefitItem(M._h, x.data_ptr(), u.data_ptr(), x.shape[1], int(m), int(sd) & 0xFFFFFFFFFFFFFFFF)
+    reps = (RefitReport * max(n, 1))()
+    opts = RefitOpts(int(max_refine), float(refine_tol), 0)
+    torch.cuda.synchronize()     # the library's streams do not wait on the caller's
+    _check(lib.fst_refit_batched(arr, n, PREC[prec], C.byref(opts), int(streams), reps))
+    return [reps[i].as_dict() for i in range(n)]
 
 
 def fit(xyz, u, grid=(32, 32, 32), sample_frac: float = 0.05, eps: float = 1e-3, max_rank=(8, 8, 8),
