@@ -458,8 +458,25 @@ __device__ __forceinline__ void lower_tile(long long t, int& ti, int& tj) {
     tj = (int)(t - (long long)x * (x + 1) / 2);
 }
 
+// Tile t of the lower trapezoid of an nt x nt tile grid cut to its first ncol tile columns:
+// the ncol (ncol + 1) / 2 tiles of the leading triangle, then ncol tiles per further row.
+__device__ __forceinline__ void trapezoid_tile(long long t, int ncol, int& ti, int& tj) {
+    const long long tri = (long long)ncol * (ncol + 1) / 2;
+    if (t < tri) {
+        lower_tile(t, ti, tj);
+    } else {
+        const long long u = t - tri;
+        ti = ncol + (int)(u / ncol);
+        tj = (int)(u % ncol);
+    }
+}
+
+// npan panels of 128 columns each make the K = 128 npan of the update; panel p's packed
+// rows start 128 (npan - 1 - p) rows above t0 (each panel was packed from the row after its
+// own diagonal block), at Lp + p * pstride.
 __global__ void __launch_bounds__(kSyrkThreads, 1)
-syrk_tc_kernel(float* G, int R, int t0, int nt, const unsigned char* Lp, int* err) {
+syrk_tc_kernel(float* G, int R, int t0, int nt, int ncol, const unsigned char* Lp, size_t pstride, int npan,
+               int* err) {
     extern __shared__ unsigned char syrk_raw[];
     unsigned char* sm = reinterpret_cast<unsigned char*>(((uintptr_t)syrk_raw + 1023) & ~(uintptr_t)1023);
     uint64_t* full = reinterpret_cast<uint64_t*>(sm + kSyrkStages * 2 * kHalfBytes);
@@ -470,7 +487,8 @@ syrk_tc_kernel(float* G, int R, int t0, int nt, const unsigned char* Lp, int* er
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const long long ntiles = (long long)nt * (nt + 1) / 2;
+    const long long ntiles = (long long)ncol * (ncol + 1) / 2 + (long long)(nt - ncol) * ncol;
+    const int nh = 2 * npan;   // K-halves of 64 per tile
 
     if (warp == 0) tc::tmem_alloc(tmem_slot, 256);
     if (tid == 0) {
@@ -501,21 +519,22 @@ syrk_tc_kernel(float* G, int R, int t0, int nt, const unsigned char* Lp, int* er
             int it = 0;
             for (long long t = blockIdx.x; t < ntiles && !*abort_flag; t += gridDim.x) {
                 int ti, tj;
-                lower_tile(t, ti, tj);
+                trapezoid_tile(t, ncol, ti, tj);
                 const bool diag = ti == tj;
-                for (int h = 0; h < 2; ++h, ++it) {
+                for (int h = 0; h < nh; ++h, ++it) {
                     const int s = it % kSyrkStages;
                     const uint32_t ph = (uint32_t)((it / kSyrkStages) & 1);
                     if (!tc::mbar_wait(&empty[s], ph ^ 1u, kCholWaitLimit)) {
                         fail(1);
                         break;
                     }
+                    const int pan = h >> 1, up = npan - 1 - pan;
+                    const unsigned char* src = Lp + (size_t)pan * pstride + (size_t)(h & 1) * kHalfBytes;
                     unsigned char* st = sm + s * 2 * kHalfBytes;
                     tc::mbar_arrive_expect_tx(&full[s], diag ? kHalfBytes : 2 * kHalfBytes);
-                    tc::bulk_g2s(st, Lp + (size_t)ti * kTileBytes + h * kHalfBytes, kHalfBytes, &full[s]);
+                    tc::bulk_g2s(st, src + (size_t)(ti + up) * kTileBytes, kHalfBytes, &full[s]);
                     if (!diag)
-                        tc::bulk_g2s(st + kHalfBytes, Lp + (size_t)tj * kTileBytes + h * kHalfBytes, kHalfBytes,
-                                     &full[s]);
+                        tc::bulk_g2s(st + kHalfBytes, src + (size_t)(tj + up) * kTileBytes, kHalfBytes, &full[s]);
                 }
             }
         }
@@ -528,7 +547,7 @@ syrk_tc_kernel(float* G, int R, int t0, int nt, const unsigned char* Lp, int* er
             bool issued = false;
             for (long long t = blockIdx.x; t < ntiles && !*abort_flag; t += gridDim.x, ++n) {
                 int ti, tj;
-                lower_tile(t, ti, tj);
+                trapezoid_tile(t, ncol, ti, tj);
                 const bool diag = ti == tj;
                 const int b = n & 1;
                 if (!tc::mbar_wait(&tempty[b], (uint32_t)((n >> 1) & 1) ^ 1u, kCholWaitLimit)) {
@@ -537,7 +556,7 @@ syrk_tc_kernel(float* G, int R, int t0, int nt, const unsigned char* Lp, int* er
                 }
                 tc::fence_after_sync();
                 bool ok = true;
-                for (int h = 0; h < 2; ++h, ++it) {
+                for (int h = 0; h < nh; ++h, ++it) {
                     const int s = it % kSyrkStages;
                     const uint32_t ph = (uint32_t)((it / kSyrkStages) & 1);
                     if (!tc::mbar_wait(&full[s], ph, kCholWaitLimit)) {
@@ -556,7 +575,7 @@ syrk_tc_kernel(float* G, int R, int t0, int nt, const unsigned char* Lp, int* er
                         const uint64_t al = tc::make_desc(a_base + kPartBytes + ko, 128, SBO);
                         const uint64_t bh = tc::make_desc(b_base + ko, 128, SBO);
                         const uint64_t bl = tc::make_desc(b_base + kPartBytes + ko, 128, SBO);
-                        tc::mma_bf16(d, ah, bh, idesc, (h | ks) ? 1u : 0u);
+                        tc::mma_bf16(d, ah, bh, idesc, (h > 0 || ks > 0) ? 1u : 0u);
                         tc::mma_bf16(d, ah, bl, idesc, 1u);
                         tc::mma_bf16(d, al, bh, idesc, 1u);
                     }
@@ -578,7 +597,7 @@ syrk_tc_kernel(float* G, int R, int t0, int nt, const unsigned char* Lp, int* er
         int n = 0;
         for (long long t = blockIdx.x; t < ntiles && !*abort_flag; t += gridDim.x, ++n) {
             int ti, tj;
-            lower_tile(t, ti, tj);
+            trapezoid_tile(t, ncol, ti, tj);
             const bool diag = ti == tj;
             const int grow = t0 + ti * 128 + (warp & 3) * 32 + lane;
             const int gcol0 = t0 + tj * 128 + (warp >> 2) * 64;
@@ -637,31 +656,61 @@ syrk_tc_kernel(float* G, int R, int t0, int nt, const unsigned char* Lp, int* er
     if (warp == 0) tc::tmem_dealloc(tmem, 256);
 }
 
-// FP32 factorisation; ws: pivot floors (R floats), the diagonal-block inverses, the packed
-// operand tiles.  The pivot flag goes to d_flag[0], an expired device wait to d_flag[1].
+// FP32 factorisation in super-panels of kSuperPanels 128-column panels.  Per panel: factor
+// the diagonal block, solve and pack the panel below it, and update only the columns of the
+// rest of the super-panel (K = 128); after the super-panel, one update of the whole trailing
+// matrix with K = 128 kSuperPanels from the panels' packed operands.  The trailing matrix is
+// read and written once per super-panel instead of once per panel.
+// ws: pivot floors (R floats), the diagonal-block inverses, kSuperPanels packed operands of
+// ceil(R / 128) tiles each.  The pivot flag goes to d_flag[0], an expired device wait to d_flag[1].
+constexpr int kSuperPanels = 4;
+static size_t packed_panel_bytes(int R) { return (size_t)((R + PB - 1) / PB) * kTileBytes; }
+
+static fst_status syrk_tc(float* G, int R, int t0, int nt, int ncol, const unsigned char* Lp, size_t pstride,
+                          int npan, int* err, size_t smem, cudaStream_t s) {
+    const long long ntiles = (long long)ncol * (ncol + 1) / 2 + (long long)(nt - ncol) * ncol;
+    const int grid = ntiles < sm_count() ? (int)ntiles : sm_count();
+    syrk_tc_kernel<<<grid, kSyrkThreads, smem, s>>>(G, R, t0, nt, ncol, Lp, pstride, npan, err);
+    FST_CHECK_LAUNCH();
+    return FST_OK;
+}
+
 static fst_status cholesky_lower_tc(float* G, int R, int* d_flag, const float* floors, unsigned char* ws_tail,
                                     cudaStream_t s) {
     float* Dinv = reinterpret_cast<float*>(ws_tail);
     unsigned char* Lp = ws_tail + 4 * SUB * SUB * sizeof(float);
+    const size_t pstride = packed_panel_bytes(R);
     const size_t potrf_smem = sizeof(float) * (PB * AS + 4 * SUB * SUB);   // P: FS x PB, then the inverses
     const size_t trsm_smem = sizeof(float) * ((64 + PB) * AS + 4 * SUB * (SUB + 4));
     const size_t syrk_smem = kSyrkStages * 2 * kHalfBytes + 1024 + 1024;
     FST_TRY(allow_smem(potrf_inv_kernel, potrf_smem));
     FST_TRY(allow_smem(trsm_pack_kernel, trsm_smem));
     FST_TRY(allow_smem(syrk_tc_kernel, syrk_smem));
-    for (int k0 = 0; k0 < R; k0 += PB) {
-        const int kb = R - k0 < PB ? R - k0 : PB;
-        const int rest = R - k0 - kb;
-        potrf_inv_kernel<<<1, 512, potrf_smem, s>>>(G, R, k0, kb, d_flag, floors, Dinv, rest > 0 ? 1 : 0);
-        FST_CHECK_LAUNCH();
-        if (rest <= 0) break;
-        const int nt = (rest + PB - 1) / PB;
-        trsm_pack_kernel<<<2 * nt, 256, trsm_smem, s>>>(G, R, k0, Dinv, Lp);
-        FST_CHECK_LAUNCH();
-        const long long ntiles = (long long)nt * (nt + 1) / 2;
-        const int grid = ntiles < sm_count() ? (int)ntiles : sm_count();
-        syrk_tc_kernel<<<grid, kSyrkThreads, syrk_smem, s>>>(G, R, k0 + PB, nt, Lp, d_flag + 1);
-        FST_CHECK_LAUNCH();
+    constexpr int SBW = kSuperPanels * PB;
+    for (int K0 = 0; K0 < R; K0 += SBW) {
+        int npan = 0;
+        for (int p = 0; p < kSuperPanels; ++p) {
+            const int k0 = K0 + p * PB;
+            if (k0 >= R) break;
+            const int kb = R - k0 < PB ? R - k0 : PB;
+            const int rest = R - k0 - kb;
+            potrf_inv_kernel<<<1, 512, potrf_smem, s>>>(G, R, k0, kb, d_flag, floors, Dinv, rest > 0 ? 1 : 0);
+            FST_CHECK_LAUNCH();
+            if (rest <= 0) return FST_OK;
+            ++npan;
+            const int nt = (rest + PB - 1) / PB;
+            unsigned char* Lpp = Lp + (size_t)p * pstride;
+            trsm_pack_kernel<<<2 * nt, 256, trsm_smem, s>>>(G, R, k0, Dinv, Lpp);
+            FST_CHECK_LAUNCH();
+            // the columns of the super-panel right of this panel
+            int ncol = (K0 + SBW - (k0 + PB)) / PB;
+            if (ncol > nt) ncol = nt;
+            if (ncol > 0) FST_TRY(syrk_tc(G, R, k0 + PB, nt, ncol, Lpp, pstride, 1, d_flag + 1, syrk_smem, s));
+        }
+        const int T0 = K0 + npan * PB;
+        if (T0 >= R) break;
+        const int nt = (R - T0 + PB - 1) / PB;
+        FST_TRY(syrk_tc(G, R, T0, nt, nt, Lp, pstride, npan, d_flag + 1, syrk_smem, s));
     }
     return FST_OK;
 }
@@ -670,7 +719,7 @@ template <typename T>
 fst_status cholesky_lower(T* G, int R, int* d_flag, DevBuf& ws, cudaStream_t s) {
     // ws: per-column pivot floors, then (FP32) the panel scratch of the tensor-core path
     const size_t floor_bytes = ((size_t)R * sizeof(T) + 255) / 256 * 256;
-    const size_t tail = sizeof(T) == 4 ? 4 * SUB * SUB * sizeof(float) + (size_t)((R + PB - 1) / PB) * kTileBytes : 0;
+    const size_t tail = sizeof(T) == 4 ? 4 * SUB * SUB * sizeof(float) + kSuperPanels * packed_panel_bytes(R) : 0;
     FST_TRY(ws.ensure(floor_bytes + tail));
     T* floors = ws.as<T>();
     pivot_floor_kernel<T><<<(R + 255) / 256 < 1024 ? (R + 255) / 256 : 1024, 256, 0, s>>>(G, R, floors);
