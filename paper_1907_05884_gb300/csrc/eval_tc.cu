@@ -224,6 +224,15 @@ __device__ __forceinline__ uint32_t pack2_bf16(float a, float b) {
     return *reinterpret_cast<uint32_t*>(&h);
 }
 
+// BF16 hi and lo words of the pair (a, b): hi = bf16(a, b), lo = bf16(a - hi_a, b - hi_b);
+// the differences are exact in FP32 and taken two at a time.
+__device__ __forceinline__ void split2_bf16(float a, float b, uint32_t& hi, uint32_t& lo) {
+    hi = pack2_bf16(a, b);
+    const float2 h = make_float2(__uint_as_float(hi << 16), __uint_as_float(hi & 0xffff0000u));
+    const float2 l = __ffma2_rn(h, make_float2(-1.f, -1.f), make_float2(a, b));
+    lo = pack2_bf16(l.x, l.y);
+}
+
 
 // Persistent kernel over a work list of units (instance, tile range).  Block b takes the
 // contiguous unit range [cta_start[b], cta_start[b+1]) (cut by estimated cost on the host);
@@ -373,30 +382,31 @@ eval_tc_kernel(const TcItem* __restrict__ items, const TcUnit* __restrict__ unit
                             }
                             *reinterpret_cast<uint4*>(A + off) = make_uint4(v4[0], v4[1], v4[2], v4[3]);
                         } else {
-                            float h[8], l[8];
+                            float h[8];
 #pragma unroll
                             for (int e = 0; e < 8; ++e) {
                                 const int i = c16 * 8 + e;
-                                const float x = (i < RM && i < r1) ? w[0][i < RM ? i : 0] : 0.f;
-                                h[e] = x;
-                                l[e] = x - __bfloat162float(__float2bfloat16_rn(x));
+                                h[e] = (i < RM && i < r1) ? w[0][i < RM ? i : 0] : 0.f;
                             }
-                            *reinterpret_cast<uint4*>(A + off) =
-                                make_uint4(pack2_bf16(h[0], h[1]), pack2_bf16(h[2], h[3]),
-                                           pack2_bf16(h[4], h[5]), pack2_bf16(h[6], h[7]));
+                            uint32_t hw[4], lw[4];
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) split2_bf16(h[2 * e], h[2 * e + 1], hw[e], lw[e]);
+                            *reinterpret_cast<uint4*>(A + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
                             if (MODE == eBF16X3)
-                                *reinterpret_cast<uint4*>(A + abytes + off) =
-                                    make_uint4(pack2_bf16(l[0], l[1]), pack2_bf16(l[2], l[3]),
-                                               pack2_bf16(l[4], l[5]), pack2_bf16(l[6], l[7]));
+                                *reinterpret_cast<uint4*>(A + abytes + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
                         }
                     }
                     tc::fence_async_smem();
                 }
                 __syncwarp();
                 if (lane == 0) tc::mbar_arrive(&a_full[g]);
-                // Khatri-Rao epilogue, chunk by chunk
-                float f = 0.f;
                 const uint32_t tbase = tmem + ((uint32_t)(sub * 32) << 16) + (uint32_t)(g * 256);
+                // Khatri-Rao epilogue, chunk by chunk: per j-slice s_j = sum_k T_(j,k) w3_k in
+                // packed pairs of k (two independent accumulators), then f += s_j w2_j
+                float2 u3p[RM / 2];
+#pragma unroll
+                for (int e = 0; e < RM / 2; ++e) u3p[e] = make_float2(u3[2 * e], u3[2 * e + 1]);
+                float f = 0.f;
 #pragma unroll
                 for (int ch = 0; ch < MAXCH; ++ch) {
                     if (ch < nch) {
@@ -405,22 +415,30 @@ eval_tc_kernel(const TcItem* __restrict__ items, const TcUnit* __restrict__ unit
                             dead = true;
                         }
                         tc::fence_after_sync();
-                        float s = 0.f;
+                        float2 sa = make_float2(0.f, 0.f), sb = make_float2(0.f, 0.f);
 #pragma unroll
-                        for (int c0 = 0; c0 < NC; c0 += 16) {
-                            float v[16];
-                            tc::tmem_ld16(tbase + c0, v);
+                        for (int c0 = 0; c0 < NC; c0 += 48) {
+                            float v[3][16];
+#pragma unroll
+                            for (int b = 0; b < 3; ++b)
+                                if (c0 + 16 * b < NC) tc::tmem_ld16(tbase + c0 + 16 * b, v[b]);
                             tc::tmem_wait_ld();
 #pragma unroll
-                            for (int e = 0; e < 16; ++e) {
+                            for (int e = 0; e < 48; e += 2) {
                                 const int col = c0 + e;
                                 if (col < NC) {
                                     const int jl = col / R3P, k = col % R3P;
-                                    s = fmaf(v[e], u3[k], s);
-                                    if (k == R3P - 1) {
+                                    const float2 vv = make_float2(v[e / 16][e % 16], v[e / 16][e % 16 + 1]);
+                                    const float2 ww = u3p[k / 2 < RM / 2 ? k / 2 : 0];
+                                    if ((k & 2) == 0)
+                                        sa = __ffma2_rn(vv, ww, sa);
+                                    else
+                                        sb = __ffma2_rn(vv, ww, sb);
+                                    if (k == R3P - 2) {
                                         const int j = ch * JC + jl;
-                                        if (j < RM) f = fmaf(s, u2[j < RM ? j : 0], f);
-                                        s = 0.f;
+                                        if (j < RM) f = fmaf((sa.x + sa.y) + (sb.x + sb.y), u2[j < RM ? j : 0], f);
+                                        sa = make_float2(0.f, 0.f);
+                                        sb = make_float2(0.f, 0.f);
                                     }
                                 }
                             }
@@ -630,9 +648,12 @@ eval_tc3_kernel(const TcItem* __restrict__ items, const TcUnit* __restrict__ uni
                     if (!dead) {
                         const float x = tt[k];
                         const int pe = a.pe[k];
+                        // L_d = ((2d - 1) x L_{d-1} - (d - 1) L_{d-2}) / d, with the
+                        // coefficients folded into the unrolled code (degree < 64)
                         float Lm = 1.f, L = x;
-#pragma unroll 1
-                        for (int c8 = 0; c8 < I.kpf / 8; ++c8) {
+#pragma unroll
+                        for (int c8 = 0; c8 < 8; ++c8) {
+                            if (c8 * 8 >= I.kpf) break;
                             float v[8];
 #pragma unroll
                             for (int e = 0; e < 8; ++e) {
@@ -643,7 +664,8 @@ eval_tc3_kernel(const TcItem* __restrict__ items, const TcUnit* __restrict__ uni
                                 } else if (d == 1) {
                                     val = x;
                                 } else {
-                                    const float Ln = ra[d - 1] * x * L - rb[d - 1] * Lm;
+                                    const float ca = float(2 * d - 1) / float(d), cb = float(d - 1) / float(d);
+                                    const float Ln = ca * x * L - cb * Lm;
                                     Lm = L;
                                     L = Ln;
                                     val = Ln;
@@ -651,15 +673,11 @@ eval_tc3_kernel(const TcItem* __restrict__ items, const TcUnit* __restrict__ uni
                                 v[e] = d < pe ? val : 0.f;
                             }
                             const uint32_t off = tc::kmajor_offset(row, c8 * 16, KPB);
-                            float l[8];
+                            uint32_t hw[4], lw[4];
 #pragma unroll
-                            for (int e = 0; e < 8; ++e) l[e] = v[e] - __bfloat162float(__float2bfloat16_rn(v[e]));
-                            *reinterpret_cast<uint4*>(P + off) =
-                                make_uint4(pack2_bf16(v[0], v[1]), pack2_bf16(v[2], v[3]), pack2_bf16(v[4], v[5]),
-                                           pack2_bf16(v[6], v[7]));
-                            *reinterpret_cast<uint4*>(P + 128 * KPB + off) =
-                                make_uint4(pack2_bf16(l[0], l[1]), pack2_bf16(l[2], l[3]), pack2_bf16(l[4], l[5]),
-                                           pack2_bf16(l[6], l[7]));
+                            for (int e = 0; e < 4; ++e) split2_bf16(v[2 * e], v[2 * e + 1], hw[e], lw[e]);
+                            *reinterpret_cast<uint4*>(P + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+                            *reinterpret_cast<uint4*>(P + 128 * KPB + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
                         }
                         tc::fence_async_smem();
                     }
@@ -687,21 +705,18 @@ eval_tc3_kernel(const TcItem* __restrict__ items, const TcUnit* __restrict__ uni
                             const int c16 = h16 * 2 + c2;
                             if (c16 * 16 >= KB) break;
                             const uint32_t off = tc::kmajor_offset(row, c16 * 16, KB);
-                            float hh[8], ll[8];
+                            float hh[8];
 #pragma unroll
                             for (int e = 0; e < 8; ++e) {
                                 const int i = c16 * 8 + e;
-                                const float x = i < r1 ? w1[c2 * 8 + e] : 0.f;
-                                hh[e] = x;
-                                ll[e] = x - __bfloat162float(__float2bfloat16_rn(x));
+                                hh[e] = i < r1 ? w1[c2 * 8 + e] : 0.f;
                             }
-                            *reinterpret_cast<uint4*>(A + off) =
-                                make_uint4(pack2_bf16(hh[0], hh[1]), pack2_bf16(hh[2], hh[3]),
-                                           pack2_bf16(hh[4], hh[5]), pack2_bf16(hh[6], hh[7]));
+                            uint32_t hw[4], lw[4];
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) split2_bf16(hh[2 * e], hh[2 * e + 1], hw[e], lw[e]);
+                            *reinterpret_cast<uint4*>(A + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
                             if (MODE == eBF16X3)
-                                *reinterpret_cast<uint4*>(A + abytes + off) =
-                                    make_uint4(pack2_bf16(ll[0], ll[1]), pack2_bf16(ll[2], ll[3]),
-                                               pack2_bf16(ll[4], ll[5]), pack2_bf16(ll[6], ll[7]));
+                                *reinterpret_cast<uint4*>(A + abytes + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
                         }
                     }
                 }
@@ -710,22 +725,29 @@ eval_tc3_kernel(const TcItem* __restrict__ items, const TcUnit* __restrict__ uni
                 if (lane == 0) tc::mbar_arrive(&a_full[g]);
                 // U_2, U_3 into registers for the epilogue
                 float u2[RM], u3[RM];
+                {
+                    constexpr int NU = (RM + 15) / 16;
+                    float v2[NU][16], v3[NU][16];
 #pragma unroll
-                for (int h = 0; h < RM; h += 16) {
-                    float v[16];
-                    tc::tmem_ld16(tg + kUCol + 32 + h, v);
+                    for (int h = 0; h < NU; ++h) {
+                        tc::tmem_ld16(tg + kUCol + 32 + 16 * h, v2[h]);
+                        tc::tmem_ld16(tg + kUCol + 64 + 16 * h, v3[h]);
+                    }
                     tc::tmem_wait_ld();
 #pragma unroll
-                    for (int e = 0; e < 16 && h + e < RM; ++e) u2[h + e] = v[e];
-                    tc::tmem_ld16(tg + kUCol + 64 + h, v);
-                    tc::tmem_wait_ld();
-#pragma unroll
-                    for (int e = 0; e < 16 && h + e < RM; ++e) u3[h + e] = h + e < a.r[2] ? v[e] : 0.f;
+                    for (int e = 0; e < RM; ++e) {
+                        u2[e] = v2[e / 16][e % 16];
+                        u3[e] = e < a.r[2] ? v3[e / 16][e % 16] : 0.f;
+                    }
                 }
                 tc::fence_before_sync();
                 __syncwarp();
                 if (lane == 0) tc::mbar_arrive(&u_empty[g]);
-                // Khatri-Rao epilogue, chunk by chunk
+                // Khatri-Rao epilogue, chunk by chunk: per j-slice s_j = sum_k T_(j,k) w3_k in
+                // packed pairs of k (two independent accumulators), then f += s_j w2_j
+                float2 u3p[RM / 2];
+#pragma unroll
+                for (int e = 0; e < RM / 2; ++e) u3p[e] = make_float2(u3[2 * e], u3[2 * e + 1]);
                 float f = 0.f;
 #pragma unroll
                 for (int ch = 0; ch < MAXCH; ++ch) {
@@ -735,22 +757,30 @@ eval_tc3_kernel(const TcItem* __restrict__ items, const TcUnit* __restrict__ uni
                             dead = true;
                         }
                         tc::fence_after_sync();
-                        float s = 0.f;
+                        float2 sa = make_float2(0.f, 0.f), sb = make_float2(0.f, 0.f);
 #pragma unroll
-                        for (int c0 = 0; c0 < NC; c0 += 16) {
-                            float v[16];
-                            tc::tmem_ld16(tg + c0, v);
+                        for (int c0 = 0; c0 < NC; c0 += 48) {
+                            float v[3][16];
+#pragma unroll
+                            for (int b = 0; b < 3; ++b)
+                                if (c0 + 16 * b < NC) tc::tmem_ld16(tg + c0 + 16 * b, v[b]);
                             tc::tmem_wait_ld();
 #pragma unroll
-                            for (int e = 0; e < 16; ++e) {
+                            for (int e = 0; e < 48; e += 2) {
                                 const int col = c0 + e;
                                 if (col < NC) {
                                     const int jl = col / R3P, k = col % R3P;
-                                    s = fmaf(v[e], u3[k < RM ? k : 0], s);
-                                    if (k == R3P - 1) {
+                                    const float2 vv = make_float2(v[e / 16][e % 16], v[e / 16][e % 16 + 1]);
+                                    const float2 ww = u3p[k / 2 < RM / 2 ? k / 2 : 0];
+                                    if ((k & 2) == 0)
+                                        sa = __ffma2_rn(vv, ww, sa);
+                                    else
+                                        sb = __ffma2_rn(vv, ww, sb);
+                                    if (k == R3P - 2) {
                                         const int j = ch * JC + jl;
-                                        if (j < RM) f = fmaf(s, u2[j < RM ? j : 0], f);
-                                        s = 0.f;
+                                        if (j < RM) f = fmaf((sa.x + sa.y) + (sb.x + sb.y), u2[j < RM ? j : 0], f);
+                                        sa = make_float2(0.f, 0.f);
+                                        sb = make_float2(0.f, 0.f);
                                     }
                                 }
                             }
