@@ -45,7 +45,6 @@ enum EMode { eTF32 = 0, eBF16 = 1, eBF16X3 = 2 };
 __host__ __device__ constexpr int jc_for(int r3p) { return 256 / r3p; }
 // factor-step variant: contraction chunks of 160 columns, factor blocks at TMEM column 160
 __host__ __device__ constexpr int jc3_for(int r3p) { return 160 / r3p; }
-constexpr int kUCol = 160;
 constexpr int kFacRows = 32;           // N of the factor MMA (ranks padded to 32)
 constexpr int kBarBytes = 1024;
 
@@ -91,9 +90,16 @@ CoreImage core_image_shape(const fst_model* m, int mode, int r3p, bool tc3 = fal
 }
 
 // Shared memory of a factor-step bucket with these largest images.
+// One worker group's operand buffer: the Legendre tile (BF16 hi + lo, 128 x KPF), later
+// overwritten by the w1 operand (parts x 128 x KB).
+__host__ __device__ inline size_t tc3_group_bytes(int kb_max, int kpf_max, int parts) {
+    const size_t p = (size_t)2 * 128 * kpf_max * 2, w = (size_t)parts * 128 * kb_max;
+    return p > w ? p : w;
+}
+// Shared memory of a factor-step bucket: barriers, the core and factor images, and one
+// operand buffer for each of the three worker groups.
 size_t tc3_smem(size_t core_max, int kb_max, int kpf_max, int parts) {
-    return 1024 + kBarBytes + core_max + (size_t)kGroups * (2 * 128 * kpf_max * 2) +
-           (size_t)kGroups * parts * 128 * kb_max + 2 * (size_t)kpf_max * 4 + 16;
+    return 1024 + kBarBytes + core_max + 3 * tc3_group_bytes(kb_max, kpf_max, parts);
 }
 
 // The factor-step variant can serve BF16 / BF16X3 contractions with degrees below 64
@@ -177,17 +183,20 @@ std::vector<unsigned char> build_core_image(const fst_model* m, const CoreImage&
             }
         }
     if (c.tc3) {
-        // factor coefficient matrices with sqrt(2n+1) folded in: mode k, part (hi, lo), row j
+        // factor coefficient matrices with sqrt(2n+1) and the leading coefficient k_n of L_n
+        // folded in (the kernel's Legendre tiles hold L_n / k_n): mode k, part (hi, lo), row j
         // (rank, padded to 32), K = degree n (padded to kpf)
         const int KPB = c.kpf * 2;
         const size_t wbytes = (size_t)kFacRows * KPB;
+        std::vector<double> lead(c.kpf, 1.0);     // k_n = prod_{i <= n} (2i - 1) / i
+        for (int nn = 1; nn < c.kpf; ++nn) lead[nn] = lead[nn - 1] * (2.0 * nn - 1.0) / nn;
         for (int k = 0; k < 3; ++k) {
             unsigned char* base = img.data() + c.fac_off + (size_t)k * 2 * wbytes;
             for (int j = 0; j < m->r[k]; ++j)
                 for (int e = m->colptr[k][j]; e < m->colptr[k][j + 1]; ++e) {
                     const int nn = m->rowidx[k][e];
                     if (nn >= c.kpf) continue;
-                    const float w = (float)(m->val[k][e] * sqrt(2.0 * nn + 1.0));
+                    const float w = (float)(m->val[k][e] * sqrt(2.0 * nn + 1.0) * lead[nn]);
                     const uint32_t off = tc::kmajor_offset(j, nn * 2, KPB);
                     const uint16_t hi = bf16_bits(w), lo = bf16_bits(w - bf16_val(w));
                     memcpy(base + off, &hi, 2);
@@ -513,18 +522,45 @@ eval_tc_kernel(const TcItem* __restrict__ items, const TcUnit* __restrict__ unit
 
 // ---------------------------------------------------------------- factor step on tcgen05
 // Variant for BF16 / BF16X3 contractions with degrees below 64: the factor values are an
-// MMA too.  Per 128-point tile and mode k the workers write the Legendre values
-// L_0..L_{KPF-1} of their point (zero from the mode's highest used degree on) as BF16
-// high and low parts (the A operand, 128 x KPF), the MMA thread forms
-// U_k = P_k Wc_k^T (N = 32, BF16x3 products) into tensor memory, and the workers read
-// U_1..U_3 back: w1 becomes the contraction's A operand, w2 and w3 stay in registers for
-// the Khatri-Rao epilogue as before.  Per group, TMEM columns [0, 160) hold contraction
-// chunks (JC3 whole j-slices) and [160, 256) the three factor blocks.  The MMA thread
-// serves whichever group has work ready (non-blocking barrier tests), so one group's
-// Legendre values overlap the other group's MMAs.
+// MMA too.  Three groups of four warps, each on its own 128-point tiles (thread = point =
+// TMEM lane); within a group everything runs in order and one thread of the group's first
+// warp issues the group's MMAs:
+//   * per mode k the workers write the monic Legendre values q_0..q_{KPF-1} of their point
+//     (zero from the mode's highest used degree on) as BF16 high and low parts (A operand,
+//     128 x KPF), and U_k = P_k Wc_k^T (N = 32, BF16x3 products) goes to tensor memory;
+//   * the workers read U_1..U_3 back: w1 becomes the contraction's A operand (written over
+//     the Legendre buffer, which is free by then), w2 and w3 stay in registers;
+//   * T = U1 C_(1) is formed in chunks of JC3 whole j-slices into the same 160 tensor-memory
+//     columns of the group (the U blocks are read by then), and each chunk is reduced
+//     against w2 and w3 (the Khatri-Rao epilogue) before the next is issued.
+// The three groups interleave on the SM's four schedulers, so one group's CUDA-core work
+// overlaps the others' MMAs.  Every wait is bounded.
+constexpr int kGroups3 = 3;
+constexpr int kThreads3 = kGroups3 * 4 * 32;
+constexpr int kGroupCols3 = 160;
+constexpr int kEpiBatch = 3;       // 16-column TMEM reads in flight per wait in the epilogue
+
+// N (a multiple of 8) consecutive TMEM columns of this warp's lanes into v; complete after
+// tc::tmem_wait_ld()
+template <int N>
+__device__ __forceinline__ void tmem_ld_cols(uint32_t taddr, float* v) {
+#pragma unroll
+    for (int h = 0; h + 16 <= N; h += 16) {
+        float t[16];
+        tc::tmem_ld16(taddr + h, t);
+#pragma unroll
+        for (int e = 0; e < 16; ++e) v[h + e] = t[e];
+    }
+    if (N % 16) {
+        float t[8];
+        tc::tmem_ld8(taddr + N / 16 * 16, t);
+#pragma unroll
+        for (int e = 0; e < 8; ++e) v[N / 16 * 16 + e] = t[e];
+    }
+}
 
 template <int MODE, int R3P, int RM>
-__global__ void __launch_bounds__(kThreadsE, 1)
+__global__ void __launch_bounds__(kThreads3, 1)
 eval_tc3_kernel(const TcItem* __restrict__ items, const TcUnit* __restrict__ units, const int* __restrict__ cta_start,
                 int core_max, int kb_max, int kpf_max, const float* __restrict__ xyz_ov, float* __restrict__ out_ov,
                 int* __restrict__ err) {
@@ -532,73 +568,75 @@ eval_tc3_kernel(const TcItem* __restrict__ items, const TcUnit* __restrict__ uni
     constexpr int NC = JC * R3P;
     constexpr int NCP = (NC + 15) / 16 * 16;
     constexpr int MAXCH = (FST_MAX_RANK + JC - 1) / JC;
-    constexpr int PARTS = MODE == eBF16X3 ? 2 : 1;
+    static_assert(NCP <= kGroupCols3, "a chunk fits the group's tensor-memory columns");
 
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
-    uint64_t* p_full = bars;                 // [2] workers -> MMA: Legendre tile written
-    uint64_t* p_empty = bars + 2;            // [2] MMA -> workers: Legendre tile consumed
-    uint64_t* u_full = bars + 4;             // [2] MMA -> workers: U_1..U_3 in TMEM
-    uint64_t* u_empty = bars + 6;            // [2] workers -> MMA: U read back
-    uint64_t* a_full = bars + 8;             // [2] workers -> MMA: w1 operand written
-    uint64_t* a_empty = bars + 10;           // [2] MMA -> workers: w1 operand consumed
-    uint64_t* d_full = bars + 12;            // [2] MMA -> workers: chunk in TMEM
-    uint64_t* d_empty = bars + 14;           // [2] workers -> MMA: chunk read
-    uint64_t* drain = bars + 16;
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+    uint64_t* w_bar = bars;                       // [3] the group's 4 warps -> issuer: operand written / chunk read
+    uint64_t* m_bar = bars + kGroups3;            // [3] MMA commit -> the group: MMAs of the step complete
+    uint64_t* drain = bars + 2 * kGroups3;        // [3]
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + kGroups3);
     unsigned char* core = smem + kBarBytes;
-    const int pgroup = 2 * 128 * kpf_max * 2;                          // hi + lo Legendre tile
-    unsigned char* pbuf = core + core_max;
-    const int agroup = PARTS * 128 * kb_max;
-    unsigned char* abuf = pbuf + kGroups * pgroup;
-    float* fsm = reinterpret_cast<float*>(abuf + kGroups * agroup);
+    const size_t gbytes = tc3_group_bytes(kb_max, kpf_max, MODE == eBF16X3 ? 2 : 1);
+    unsigned char* gbuf = core + core_max;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int g = warp >> 2, sub = warp & 3, row = sub * 32 + lane;   // TMEM lane = row
+    const bool issuer = sub == 0 && lane == 0;
     if (warp == 0) tc::tmem_alloc(tmem_slot, 512);
     if (tid == 0) {
-        for (int g = 0; g < kGroups; ++g) {
-            tc::mbar_init(&p_full[g], 4);
-            tc::mbar_init(&p_empty[g], 1);
-            tc::mbar_init(&u_full[g], 1);
-            tc::mbar_init(&u_empty[g], 4);
-            tc::mbar_init(&a_full[g], 4);
-            tc::mbar_init(&a_empty[g], 1);
-            tc::mbar_init(&d_full[g], 1);
-            tc::mbar_init(&d_empty[g], 4);
+        for (int e = 0; e < kGroups3; ++e) {
+            tc::mbar_init(&w_bar[e], 4);
+            tc::mbar_init(&m_bar[e], 1);
+            tc::mbar_init(&drain[e], 1);
         }
-        tc::mbar_init(drain, 1);
         tc::fence_mbar_init();
     }
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = *tmem_slot;
+    const uint32_t tcol = tmem + (uint32_t)(g * kGroupCols3);               // issuer's view
+    const uint32_t tg = tcol + ((uint32_t)(sub * 32) << 16);                // this warp's lanes
+    unsigned char* P = gbuf + (size_t)g * gbytes;                           // Legendre tile, then w1
+    const uint32_t p_u32 = tc::smem_u32(P);
+    const uint32_t core_u32 = tc::smem_u32(core);
 
     const int u0 = cta_start[blockIdx.x], u1 = cta_start[blockIdx.x + 1];
     int cur = -1;
-    // per-role phase counters run across units
-    int lt = 0, pc = 0, cc = 0;                                          // worker group
-    int mpc[kGroups] = {0, 0}, mlt[kGroups] = {0, 0}, mcc[kGroups] = {0, 0};   // MMA thread
+    int nw = 0, nm = 0;        // completed phases of w_bar[g] and m_bar[g]
     bool issued = false, dead = false;
-    float *ra = nullptr, *rb = nullptr;
+    auto wait = [&](uint64_t* bar, int& phase, int code) {
+        if (!dead && !tc::mbar_wait(bar, (uint32_t)(phase & 1), kWaitLimitE)) {
+            atomicOr(err, code);
+            dead = true;
+        }
+        ++phase;
+    };
+    // every warp of the group has written its rows of the operand (or read its TMEM lanes)
+    auto handoff = [&]() {
+        tc::fence_before_sync();
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(&w_bar[g]);
+    };
+    // the warp reconverges after the issuer's branch and agrees on `dead` (tcgen05.ld needs
+    // the whole warp)
+    auto converge = [&]() {
+        __syncwarp();
+        dead = __any_sync(0xffffffffu, dead);
+    };
     for (int u = u0; u < u1; ++u) {
         const TcUnit U = units[u];
         const TcItem& I = items[U.item];
         const EvalArgs<float>& a = I.a;
         if (U.item != cur) {
-            // all MMAs of the previous instance completed before the workers' last waits
+            // every MMA of the previous instance completed before its group's last wait
             tc::fence_before_sync();
             __syncthreads();
             const uint4* src = reinterpret_cast<const uint4*>(I.core_img);
             uint4* dst = reinterpret_cast<uint4*>(core);
             for (int e = tid; e < I.img_bytes / 16; e += blockDim.x) dst[e] = src[e];
-            ra = fsm;
-            rb = ra + kpf_max;
-            for (int i = tid; i < kpf_max; i += blockDim.x) {
-                ra[i] = float(2 * i + 1) / float(i + 1);
-                rb[i] = float(i) / float(i + 1);
-            }
             tc::fence_async_smem();
             tc::fence_before_sync();
             __syncthreads();
@@ -612,278 +650,215 @@ eval_tc3_kernel(const TcItem* __restrict__ items, const TcUnit* __restrict__ uni
         const int r1 = a.r[0];
         const int nch = I.nchunks;
         const long long n = I.n;
-        if (warp < kWorkers) {
-            // -------------------------------------------------------------- workers
-            const int g = warp >> 2, sub = warp & 3, row = sub * 32 + lane;   // TMEM lane = row
-            unsigned char* P = pbuf + g * pgroup;
-            unsigned char* A = abuf + g * agroup;
-            const float* X = xyz_ov ? xyz_ov : I.xyz;
-            float nxt[3];
+        const float* X = xyz_ov ? xyz_ov : I.xyz;
+        // issuer constants
+        constexpr uint32_t idesc_c = tc::idesc_bf16(128, NCP);
+        constexpr uint32_t idesc_f = tc::idesc_bf16(128, kFacRows);
+        const uint32_t chunk_bytes = (uint32_t)(NCP * KB);
+        const uint32_t SBOP = (uint32_t)(KPB / 16) * 128;
+        const uint32_t wbytes = (uint32_t)(kFacRows * KPB);      // one part of one mode
+        auto issue_chunk = [&](int ch) {
+            const uint32_t bb = core_u32 + ch * chunk_bytes;
+            for (int ks = 0; ks < KB / 32; ++ks) {
+                const uint32_t ko = ks * 256;
+                const uint64_t ad = tc::make_desc(p_u32 + ko, 128, SBO);
+                const uint64_t bd = tc::make_desc(bb + ko, 128, SBO);
+                tc::mma_bf16(tcol, ad, bd, idesc_c, ks > 0);
+                if (MODE == eBF16X3) {
+                    const uint64_t al = tc::make_desc(p_u32 + abytes + ko, 128, SBO);
+                    const uint64_t bl = tc::make_desc(bb + nch * chunk_bytes + ko, 128, SBO);
+                    tc::mma_bf16(tcol, ad, bl, idesc_c, 1u);
+                    tc::mma_bf16(tcol, al, bd, idesc_c, 1u);
+                }
+            }
+            tc::mma_commit(&m_bar[g]);
+            issued = true;
+        };
+
+        float nxt[3];
+        {
+            const long long q = (U.tile0 + g) * 128 + row;
+            const bool ok = U.tile0 + g < U.tile0 + U.ntiles && q < n;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) nxt[k] = ok ? X[k * n + q] : 0.f;
+        }
+        for (long long t = U.tile0 + g; t < U.tile0 + U.ntiles && !dead; t += kGroups3) {
+            const long long q = t * 128 + row;
+            const bool ok = q < n;
+            float tt[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) tt[k] = fmaf(nxt[k], a.sc[k], a.of[k]);
             {
-                const long long q = (U.tile0 + g) * 128 + row;
-                const bool ok = U.tile0 + g < U.tile0 + U.ntiles && q < n;
+                const long long q2 = q + kGroups3 * 128;
+                const bool ok2 = t + kGroups3 < U.tile0 + U.ntiles && q2 < n;
 #pragma unroll
-                for (int k = 0; k < 3; ++k) nxt[k] = ok ? X[k * n + q] : 0.f;
+                for (int k = 0; k < 3; ++k) nxt[k] = ok2 ? X[k * n + q2] : 0.f;
             }
-            const uint32_t tg = tmem + ((uint32_t)(sub * 32) << 16) + (uint32_t)(g * 256);
-            for (long long t = U.tile0 + g; t < U.tile0 + U.ntiles; t += kGroups, ++lt) {
-                const long long q = t * 128 + row;
-                const bool ok = q < n;
-                float tt[3];
-#pragma unroll
-                for (int k = 0; k < 3; ++k) tt[k] = fmaf(nxt[k], a.sc[k], a.of[k]);
-                {
-                    const long long q2 = q + kGroups * 128;
-                    const bool ok2 = t + kGroups < U.tile0 + U.ntiles && q2 < n;
-#pragma unroll
-                    for (int k = 0; k < 3; ++k) nxt[k] = ok2 ? X[k * n + q2] : 0.f;
-                }
-                // Legendre tiles of the three modes, one after the other through P
+            // Legendre tiles of the three modes, one after the other through P
 #pragma unroll 1
-                for (int k = 0; k < 3; ++k, ++pc) {
-                    if (!tc::mbar_wait(&p_empty[g], (uint32_t)(pc & 1) ^ 1u, kWaitLimitE)) {
-                        atomicOr(err, 32);
-                        dead = true;
-                    }
-                    if (!dead) {
-                        const float x = tt[k];
-                        const int pe = a.pe[k];
-                        // L_d = ((2d - 1) x L_{d-1} - (d - 1) L_{d-2}) / d, with the
-                        // coefficients folded into the unrolled code (degree < 64)
-                        float Lm = 1.f, L = x;
+            for (int k = 0; k < 3; ++k) {
+                const float x = tt[k];
+                const int pe = a.pe[k];
+                // monic Legendre polynomials q_d = L_d / k_d (k_d the leading coefficient of L_d,
+                // folded into the factor coefficients): q_d = x q_{d-1} - (d-1)^2 / ((2d-1)(2d-3))
+                // q_{d-2}, two operations a degree, constants folded into the unrolled code
+                float Lm = 1.f, L = x;
 #pragma unroll
-                        for (int c8 = 0; c8 < 8; ++c8) {
-                            if (c8 * 8 >= I.kpf) break;
-                            float v[8];
+                for (int c8 = 0; c8 < 8; ++c8) {
+                    if (c8 * 8 >= I.kpf) break;
+                    float v[8];
 #pragma unroll
-                            for (int e = 0; e < 8; ++e) {
-                                const int d = c8 * 8 + e;
-                                float val;
-                                if (d == 0) {
-                                    val = 1.f;
-                                } else if (d == 1) {
-                                    val = x;
-                                } else {
-                                    const float ca = float(2 * d - 1) / float(d), cb = float(d - 1) / float(d);
-                                    const float Ln = ca * x * L - cb * Lm;
-                                    Lm = L;
-                                    L = Ln;
-                                    val = Ln;
-                                }
-                                v[e] = d < pe ? val : 0.f;
-                            }
-                            const uint32_t off = tc::kmajor_offset(row, c8 * 16, KPB);
-                            uint32_t hw[4], lw[4];
-#pragma unroll
-                            for (int e = 0; e < 4; ++e) split2_bf16(v[2 * e], v[2 * e + 1], hw[e], lw[e]);
-                            *reinterpret_cast<uint4*>(P + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-                            *reinterpret_cast<uint4*>(P + 128 * KPB + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+                    for (int e = 0; e < 8; ++e) {
+                        const int d = c8 * 8 + e;
+                        float val;
+                        if (d == 0) {
+                            val = 1.f;
+                        } else if (d == 1) {
+                            val = x;
+                        } else {
+                            const float gd = float((d - 1) * (d - 1)) / float((2 * d - 1) * (2 * d - 3));
+                            const float Ln = fmaf(x, L, -gd * Lm);
+                            Lm = L;
+                            L = Ln;
+                            val = Ln;
                         }
-                        tc::fence_async_smem();
+                        v[e] = d < pe ? val : 0.f;
                     }
-                    __syncwarp();
-                    if (lane == 0) tc::mbar_arrive(&p_full[g]);
+                    const uint32_t off = tc::kmajor_offset(row, c8 * 16, KPB);
+                    uint32_t hw[4], lw[4];
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) split2_bf16(v[2 * e], v[2 * e + 1], hw[e], lw[e]);
+                    *reinterpret_cast<uint4*>(P + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+                    *reinterpret_cast<uint4*>(P + 128 * KPB + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
                 }
-                // U_1 back from tensor memory, straight into the contraction's A operand
-                if (!tc::mbar_wait(&u_full[g], (uint32_t)(lt & 1), kWaitLimitE)) {
-                    atomicOr(err, 64);
-                    dead = true;
+                tc::fence_async_smem();
+                handoff();
+                if (issuer) {
+                    wait(&w_bar[g], nw, 32);
+                    tc::fence_after_sync();
+                    const uint32_t wb = core_u32 + (uint32_t)I.fac_off + (uint32_t)k * 2u * wbytes;
+                    const uint32_t d = tcol + 32u * k;
+                    for (int ks = 0; ks < I.kpf / 16; ++ks) {
+                        const uint32_t ko = ks * 256;
+                        const uint64_t ah = tc::make_desc(p_u32 + ko, 128, SBOP);
+                        const uint64_t al = tc::make_desc(p_u32 + 128 * KPB + ko, 128, SBOP);
+                        const uint64_t bh = tc::make_desc(wb + ko, 128, SBOP);
+                        const uint64_t bl = tc::make_desc(wb + wbytes + ko, 128, SBOP);
+                        tc::mma_bf16(d, ah, bh, idesc_f, ks > 0);
+                        tc::mma_bf16(d, ah, bl, idesc_f, 1u);
+                        tc::mma_bf16(d, al, bh, idesc_f, 1u);
+                    }
+                    tc::mma_commit(&m_bar[g]);
+                    issued = true;
+                } else if (sub == 0) {
+                    ++nw;    // the issuer's lanes track the same phase count
                 }
+                wait(&m_bar[g], nm, 64);      // U_k in TMEM, P free
                 tc::fence_after_sync();
-                if (!tc::mbar_wait(&a_empty[g], (uint32_t)(lt & 1) ^ 1u, kWaitLimitE)) {
-                    atomicOr(err, 1);
-                    dead = true;
-                }
+                converge();
+            }
+            if (dead) break;
+            // U_1..U_3 back from tensor memory: w1 over P as the contraction's A operand,
+            // w2 and w3 into registers
+            float u2[RM], u3[RM];
+            {
+                float w1[RM];
+                tmem_ld_cols<RM>(tg + 0, w1);
+                tmem_ld_cols<RM>(tg + 32, u2);
+                tmem_ld_cols<RM>(tg + 64, u3);
+                tc::tmem_wait_ld();
 #pragma unroll
-                for (int h16 = 0; h16 < 2; ++h16) {
-                    float w1[16];
-                    tc::tmem_ld16(tg + kUCol + 16 * h16, w1);
-                    tc::tmem_wait_ld();
-                    if (!dead) {
+                for (int e = 0; e < RM; ++e) u3[e] = e < a.r[2] ? u3[e] : 0.f;
 #pragma unroll
-                        for (int c2 = 0; c2 < 2; ++c2) {
-                            const int c16 = h16 * 2 + c2;
-                            if (c16 * 16 >= KB) break;
-                            const uint32_t off = tc::kmajor_offset(row, c16 * 16, KB);
-                            float hh[8];
+                for (int c16 = 0; c16 < 4; ++c16) {
+                    if (c16 * 16 >= KB) break;
+                    const uint32_t off = tc::kmajor_offset(row, c16 * 16, KB);
+                    float hh[8];
 #pragma unroll
-                            for (int e = 0; e < 8; ++e) {
-                                const int i = c16 * 8 + e;
-                                hh[e] = i < r1 ? w1[c2 * 8 + e] : 0.f;
-                            }
-                            uint32_t hw[4], lw[4];
-#pragma unroll
-                            for (int e = 0; e < 4; ++e) split2_bf16(hh[2 * e], hh[2 * e + 1], hw[e], lw[e]);
-                            *reinterpret_cast<uint4*>(A + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-                            if (MODE == eBF16X3)
-                                *reinterpret_cast<uint4*>(A + abytes + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
-                        }
+                    for (int e = 0; e < 8; ++e) {
+                        const int i = c16 * 8 + e;
+                        hh[e] = i < r1 && i < RM ? w1[i < RM ? i : 0] : 0.f;
                     }
+                    uint32_t hw[4], lw[4];
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) split2_bf16(hh[2 * e], hh[2 * e + 1], hw[e], lw[e]);
+                    *reinterpret_cast<uint4*>(P + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+                    if (MODE == eBF16X3)
+                        *reinterpret_cast<uint4*>(P + abytes + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
                 }
-                if (!dead) tc::fence_async_smem();
-                __syncwarp();
-                if (lane == 0) tc::mbar_arrive(&a_full[g]);
-                // U_2, U_3 into registers for the epilogue
-                float u2[RM], u3[RM];
-                {
-                    constexpr int NU = (RM + 15) / 16;
-                    float v2[NU][16], v3[NU][16];
+            }
+            tc::fence_async_smem();
+            handoff();                         // w1 written, U read: chunk 0 may overwrite the U blocks
+            if (issuer) {
+                wait(&w_bar[g], nw, 1);
+                tc::fence_after_sync();
+                issue_chunk(0);
+            } else if (sub == 0) {
+                ++nw;
+            }
+            // Khatri-Rao epilogue, chunk by chunk: per j-slice s_j = sum_k T_(j,k) w3_k in packed
+            // pairs of k (two independent accumulators), then f += s_j w2_j
+            float2 u3p[RM / 2];
 #pragma unroll
-                    for (int h = 0; h < NU; ++h) {
-                        tc::tmem_ld16(tg + kUCol + 32 + 16 * h, v2[h]);
-                        tc::tmem_ld16(tg + kUCol + 64 + 16 * h, v3[h]);
-                    }
-                    tc::tmem_wait_ld();
+            for (int e = 0; e < RM / 2; ++e) u3p[e] = make_float2(u3[2 * e], u3[2 * e + 1]);
+            float f = 0.f;
+            // u2 slides down by JC a chunk, so the chunk loop needs no unrolling: w2_{ch JC + jl}
+            // is u2[jl] in chunk ch (zero past the rank bound)
+#pragma unroll 1
+            for (int ch = 0; ch < MAXCH; ++ch) {
+                if (ch < nch) {
+                    wait(&m_bar[g], nm, 2);
+                    tc::fence_after_sync();
+                    converge();
+                    if (dead) break;
+                    float2 sa = make_float2(0.f, 0.f), sb = make_float2(0.f, 0.f);
 #pragma unroll
-                    for (int e = 0; e < RM; ++e) {
-                        u2[e] = v2[e / 16][e % 16];
-                        u3[e] = e < a.r[2] ? v3[e / 16][e % 16] : 0.f;
-                    }
-                }
-                tc::fence_before_sync();
-                __syncwarp();
-                if (lane == 0) tc::mbar_arrive(&u_empty[g]);
-                // Khatri-Rao epilogue, chunk by chunk: per j-slice s_j = sum_k T_(j,k) w3_k in
-                // packed pairs of k (two independent accumulators), then f += s_j w2_j
-                float2 u3p[RM / 2];
+                    for (int c0 = 0; c0 < NC; c0 += 16 * kEpiBatch) {
+                        float v[kEpiBatch][16];
 #pragma unroll
-                for (int e = 0; e < RM / 2; ++e) u3p[e] = make_float2(u3[2 * e], u3[2 * e + 1]);
-                float f = 0.f;
+                        for (int b = 0; b < kEpiBatch; ++b)
+                            if (c0 + 16 * b < NC) tc::tmem_ld16(tg + c0 + 16 * b, v[b]);
+                        tc::tmem_wait_ld();
 #pragma unroll
-                for (int ch = 0; ch < MAXCH; ++ch) {
-                    if (ch < nch) {
-                        if (!tc::mbar_wait(&d_full[g], (uint32_t)(cc & 1), kWaitLimitE)) {
-                            atomicOr(err, 2);
-                            dead = true;
-                        }
-                        tc::fence_after_sync();
-                        float2 sa = make_float2(0.f, 0.f), sb = make_float2(0.f, 0.f);
-#pragma unroll
-                        for (int c0 = 0; c0 < NC; c0 += 48) {
-                            float v[3][16];
-#pragma unroll
-                            for (int b = 0; b < 3; ++b)
-                                if (c0 + 16 * b < NC) tc::tmem_ld16(tg + c0 + 16 * b, v[b]);
-                            tc::tmem_wait_ld();
-#pragma unroll
-                            for (int e = 0; e < 48; e += 2) {
-                                const int col = c0 + e;
-                                if (col < NC) {
-                                    const int jl = col / R3P, k = col % R3P;
-                                    const float2 vv = make_float2(v[e / 16][e % 16], v[e / 16][e % 16 + 1]);
-                                    const float2 ww = u3p[k / 2 < RM / 2 ? k / 2 : 0];
-                                    if ((k & 2) == 0)
-                                        sa = __ffma2_rn(vv, ww, sa);
-                                    else
-                                        sb = __ffma2_rn(vv, ww, sb);
-                                    if (k == R3P - 2) {
-                                        const int j = ch * JC + jl;
-                                        if (j < RM) f = fmaf((sa.x + sa.y) + (sb.x + sb.y), u2[j < RM ? j : 0], f);
-                                        sa = make_float2(0.f, 0.f);
-                                        sb = make_float2(0.f, 0.f);
-                                    }
+                        for (int e = 0; e < 16 * kEpiBatch; e += 2) {
+                            const int col = c0 + e;
+                            if (col < NC) {
+                                const int jl = col / R3P, k = col % R3P;
+                                const float2 vv = make_float2(v[e / 16][e % 16], v[e / 16][e % 16 + 1]);
+                                const float2 ww = u3p[k / 2 < RM / 2 ? k / 2 : 0];
+                                if ((k & 2) == 0)
+                                    sa = __ffma2_rn(vv, ww, sa);
+                                else
+                                    sb = __ffma2_rn(vv, ww, sb);
+                                if (k == R3P - 2) {
+                                    if (jl < RM) f = fmaf((sa.x + sa.y) + (sb.x + sb.y), u2[jl < RM ? jl : 0], f);
+                                    sa = make_float2(0.f, 0.f);
+                                    sb = make_float2(0.f, 0.f);
                                 }
                             }
                         }
-                        tc::fence_before_sync();
-                        __syncwarp();
-                        if (lane == 0) tc::mbar_arrive(&d_empty[g]);
-                        ++cc;
+                    }
+#pragma unroll
+                    for (int e = 0; e < RM; ++e) u2[e] = e + JC < RM ? u2[e + JC < RM ? e + JC : 0] : 0.f;
+                    if (ch + 1 < nch) {
+                        handoff();             // chunk read: the next one may overwrite it
+                        if (issuer) {
+                            wait(&w_bar[g], nw, 4);
+                            tc::fence_after_sync();
+                            issue_chunk(ch + 1);
+                        } else if (sub == 0) {
+                            ++nw;
+                        }
                     }
                 }
-                if (ok) (out_ov ? out_ov : I.out)[q] = f;
             }
-        } else if (lane == 0 && !dead) {
-            // -------------------------------------------------------------- MMA issuer
-            constexpr uint32_t idesc_c = tc::idesc_bf16(128, NCP);
-            constexpr uint32_t idesc_f = tc::idesc_bf16(128, kFacRows);
-            const uint32_t core_u32 = tc::smem_u32(core);
-            const uint32_t chunk_bytes = (uint32_t)(NCP * KB);
-            const uint32_t SBOP = (uint32_t)(KPB / 16) * 128;
-            const uint32_t wbytes = (uint32_t)(kFacRows * KPB);      // one part of one mode
-            long long tnext[kGroups];
-            int stage[kGroups], ch[kGroups];
-            bool act[kGroups];
-#pragma unroll
-            for (int g = 0; g < kGroups; ++g) {
-                tnext[g] = U.tile0 + g;
-                act[g] = tnext[g] < U.tile0 + U.ntiles;
-                stage[g] = 0;
-                ch[g] = 0;
-            }
-            long long last = clock64();
-            while ((act[0] || act[1]) && !dead) {
-                bool progressed = false;
-#pragma unroll
-                for (int g = 0; g < kGroups; ++g) {
-                    if (!act[g]) continue;
-                    const uint32_t tg = tmem + (uint32_t)(g * 256);
-                    if (stage[g] < 3) {
-                        const int k = stage[g];
-                        if (!tc::mbar_try_wait(&p_full[g], (uint32_t)(mpc[g] & 1))) continue;
-                        if (k == 0 && !tc::mbar_try_wait(&u_empty[g], (uint32_t)(mlt[g] & 1) ^ 1u)) continue;
-                        tc::fence_after_sync();
-                        const uint32_t pa = tc::smem_u32(pbuf + g * pgroup);
-                        const uint32_t wb = core_u32 + (uint32_t)I.fac_off + (uint32_t)k * 2u * wbytes;
-                        const uint32_t d = tg + kUCol + 32u * k;
-                        for (int ks = 0; ks < I.kpf / 16; ++ks) {
-                            const uint32_t ko = ks * 256;
-                            const uint64_t ah = tc::make_desc(pa + ko, 128, SBOP);
-                            const uint64_t al = tc::make_desc(pa + 128 * KPB + ko, 128, SBOP);
-                            const uint64_t bh = tc::make_desc(wb + ko, 128, SBOP);
-                            const uint64_t bl = tc::make_desc(wb + wbytes + ko, 128, SBOP);
-                            tc::mma_bf16(d, ah, bh, idesc_f, ks > 0);
-                            tc::mma_bf16(d, ah, bl, idesc_f, 1u);
-                            tc::mma_bf16(d, al, bh, idesc_f, 1u);
-                        }
-                        tc::mma_commit(&p_empty[g]);
-                        issued = true;
-                        ++mpc[g];
-                        if (++stage[g] == 3) tc::mma_commit(&u_full[g]);
-                        progressed = true;
-                    } else {
-                        if (ch[g] == 0 && !tc::mbar_try_wait(&a_full[g], (uint32_t)(mlt[g] & 1))) continue;
-                        if (!tc::mbar_try_wait(&d_empty[g], (uint32_t)(mcc[g] & 1) ^ 1u)) continue;
-                        tc::fence_after_sync();
-                        const uint32_t abase = tc::smem_u32(abuf + g * agroup);
-                        const uint32_t bb = core_u32 + ch[g] * chunk_bytes;
-                        for (int ks = 0; ks < KB / 32; ++ks) {
-                            const uint32_t ko = ks * 256;
-                            const uint64_t ad = tc::make_desc(abase + ko, 128, SBO);
-                            const uint64_t bd = tc::make_desc(bb + ko, 128, SBO);
-                            tc::mma_bf16(tg, ad, bd, idesc_c, ks > 0);
-                            if (MODE == eBF16X3) {
-                                const uint64_t al = tc::make_desc(abase + abytes + ko, 128, SBO);
-                                const uint64_t bl = tc::make_desc(bb + nch * chunk_bytes + ko, 128, SBO);
-                                tc::mma_bf16(tg, ad, bl, idesc_c, 1u);
-                                tc::mma_bf16(tg, al, bd, idesc_c, 1u);
-                            }
-                        }
-                        tc::mma_commit(&d_full[g]);
-                        ++mcc[g];
-                        if (++ch[g] == nch) {
-                            tc::mma_commit(&a_empty[g]);
-                            ++mlt[g];
-                            ch[g] = 0;
-                            stage[g] = 0;
-                            tnext[g] += kGroups;
-                            act[g] = tnext[g] < U.tile0 + U.ntiles;
-                        }
-                        progressed = true;
-                    }
-                }
-                if (progressed) {
-                    last = clock64();
-                } else if (clock64() - last > kWaitLimitE) {
-                    atomicOr(err, 128);
-                    dead = true;
-                }
-            }
+            if (ok && !dead) (out_ov ? out_ov : I.out)[q] = f;
         }
     }
-    if (warp == kWorkers && lane == 0 && issued) {
-        tc::mma_commit(drain);
-        if (!tc::mbar_wait(drain, 0u, kWaitLimitE)) atomicOr(err, 16);
+    if (issuer && issued) {
+        // every MMA of this group completes before tensor memory is released
+        tc::mma_commit(&drain[g]);
+        if (!tc::mbar_wait(&drain[g], 0u, kWaitLimitE)) atomicOr(err, 16);
     }
     tc::fence_before_sync();
     __syncthreads();
@@ -990,7 +965,7 @@ fst_status build_buckets(const std::vector<HostItem>& hitems, int mode, std::vec
         }
         if (total_tiles == 0) continue;
         long long run = (total_tiles + 4LL * sms - 1) / (4LL * sms);
-        if (run < 2) run = 2;
+        if (run < 3) run = 3;   // a unit feeds every worker group of a CTA
         std::vector<double> unit_cost;
         for (size_t i = 0; i < B.items.size(); ++i) {
             const long long nt = (B.items[i].n + 127) / 128;
@@ -1062,7 +1037,7 @@ template <int MODE, int R3P, int RM>
 fst_status launch_bucket_tc3_t(const Bucket& B, const unsigned char* dimg, int* err, cudaStream_t s, Overrides ov) {
     auto kern = eval_tc3_kernel<MODE, R3P, RM>;
     FST_TRY(allow_smem(kern, B.smem));
-    kern<<<B.grid, kThreadsE, B.smem, s>>>(reinterpret_cast<const TcItem*>(dimg + B.items_off),
+    kern<<<B.grid, kThreads3, B.smem, s>>>(reinterpret_cast<const TcItem*>(dimg + B.items_off),
                                            reinterpret_cast<const TcUnit*>(dimg + B.units_off),
                                            reinterpret_cast<const int*>(dimg + B.cta_off), B.core_max, B.kb_max,
                                            B.kpf_max, ov.xyz, ov.out, err);

@@ -33,6 +33,9 @@ def main():
     ap.add_argument("--degree", type=int, default=31)
     ap.add_argument("--reps", type=int, default=2)
     ap.add_argument("--streams", type=int, nargs="+", default=[1, 2, 4, 8])
+    ap.add_argument("--variant", type=int, default=-1,
+                    help="evaluator variant (0: factor values on the CUDA cores, 1: on the tensor cores); "
+                         "default: autotuned")
     args = ap.parse_args()
 
     import torch
@@ -61,6 +64,8 @@ def main():
     out = torch.empty(Q, device="cuda")
     idx = fst.sample_rows(8, Q, args.m)
     if args.what == "eval" and args.prec != "fp32":
+        if args.variant >= 0:
+            M.set_variant(args.prec, args.variant)
         M.prepare(args.prec)
     for r in range(args.reps):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
