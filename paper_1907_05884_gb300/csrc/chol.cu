@@ -774,6 +774,49 @@ __global__ void invert_diag_kernel(const T* L, int R, T* Linv) {
     }
 }
 
+// The link matrices of the triangular solves: the last dependency of block row i folded
+// into its diagonal solve, Kf_i = L_ii^-1 L_{i,i-1} (forward) and
+// Kb_i = L_ii^-T L_{i+1,i}^T (backward), so y_i = L_ii^-1 (b_i - sum_{j<i-1} L_ij y_j) - Kf_i y_{i-1}
+// and the chain from one block row to the next is one 64 x 64 product.
+template <typename T>
+__global__ void __launch_bounds__(256) link_blocks_kernel(const T* __restrict__ L, int R, const T* __restrict__ Linv,
+                                                          T* __restrict__ Kf, T* __restrict__ Kb) {
+    __shared__ T li[NB][NB + 1];
+    __shared__ T tl[NB][NB + 1];
+    const int i = blockIdx.x, nblk = gridDim.x, k0 = i * NB, tid = threadIdx.x;
+    for (int e = tid; e < NB * NB; e += 256) li[e / NB][e % NB] = Linv[(size_t)i * NB * NB + e];
+    if (i >= 1) {
+        // tl[k][c] = L[k0 + k][(i - 1) NB + c]
+        for (int e = tid; e < NB * NB; e += 256) {
+            const int k = e / NB, c = e % NB;
+            tl[k][c] = k0 + k < R ? L[(size_t)(k0 + k) * R + (i - 1) * NB + c] : T(0);
+        }
+        __syncthreads();
+        for (int e = tid; e < NB * NB; e += 256) {
+            const int r = e / NB, c = e % NB;
+            T acc = T(0);
+            for (int k = 0; k < NB; ++k) acc += li[r][k] * tl[k][c];
+            Kf[(size_t)i * NB * NB + e] = acc;
+        }
+        __syncthreads();
+    }
+    if (i + 1 < nblk) {
+        // tl[c][k] = L[(i + 1) NB + c][k0 + k]
+        for (int e = tid; e < NB * NB; e += 256) {
+            const int c = e / NB, k = e % NB;
+            const int row = (i + 1) * NB + c;
+            tl[c][k] = row < R ? L[(size_t)row * R + k0 + k] : T(0);
+        }
+        __syncthreads();
+        for (int e = tid; e < NB * NB; e += 256) {
+            const int r = e / NB, c = e % NB;
+            T acc = T(0);
+            for (int k = 0; k < NB; ++k) acc += li[k][r] * tl[c][k];
+            Kb[(size_t)i * NB * NB + e] = acc;
+        }
+    }
+}
+
 // One direction of x <- L^-T L^-1 x in a single launch.  Block row i (64 rows) is solved
 // by one block: forward, y_i = Linv_ii (b_i - sum_{j<i} L_ij y_j); backward (TRANS),
 // x_i = Linv_ii^T (y_i - sum_{j>i} L_ji^T x_j).  Blocks take block rows in solve order
@@ -830,12 +873,15 @@ __device__ __forceinline__ T wait_value(const T* p, int* err) {
 
 // M is L (forward) or L^T (backward, TRANS), both row-major: block row i reads the tiles
 // M[i-block][j-block] for j < i (forward) or j > i (backward) along its own rows.
+constexpr int kTrsvDepth = 4;
 template <typename T, bool TRANS>
-__global__ void __launch_bounds__(256) trsv_kernel(const T* __restrict__ M, const T* __restrict__ Linv, int R,
-                                                   int nblk, const T* bin, T* out, int* sync) {
+__global__ void __launch_bounds__(256) trsv_kernel(const T* __restrict__ M, const T* __restrict__ Linv,
+                                                   const T* __restrict__ K, int R, int nblk, const T* bin, T* out,
+                                                   int* sync) {
     __shared__ T lis[NB][NB + 1];   // Linv of the diagonal block
     __shared__ T red[8][NB];
     __shared__ T vs[NB];
+    __shared__ T xl[NB];            // the values of the last dependency
     __shared__ int s_ticket;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (tid == 0) s_ticket = atomicAdd(&sync[1], 1);
@@ -847,12 +893,22 @@ __global__ void __launch_bounds__(256) trsv_kernel(const T* __restrict__ M, cons
         const T* Li = Linv + (size_t)i * NB * NB;
         for (int e = tid; e < NB * NB; e += 256) lis[e / NB][e % NB] = Li[e];
     }
+    const int ntiles = TRANS ? nblk - 1 - i : i;   // block rows this one depends on
+    // the link matrix (thread (r, q): row r, columns 16q .. 16q + 15), loaded off the chain
+    const int lr = tid >> 2, lq = tid & 3;
+    T kr[16];
+    if (ntiles > 0) {
+        const T* Ki = K + (size_t)i * NB * NB + lr * NB + 16 * lq;
+#pragma unroll
+        for (int u = 0; u < 16; ++u) kr[u] = Ki[u];
+    }
     // tile mapping (coalesced along the rows of M): warp w owns rows 8w .. 8w+7 of the
-    // block row, lane l the columns l and l + 32 of the tile
+    // block row, lane l the columns l and l + 32 of the tile; every dependency but the
+    // last is summed here
     T acc[8];
 #pragma unroll
     for (int u = 0; u < 8; ++u) acc[u] = T(0);
-    const int ntiles = TRANS ? nblk - 1 - i : i;
+    const int nsum = ntiles - 1;
     auto load_tile = [&](int n, T (&lv)[16]) {
         const int j0 = (TRANS ? nblk - 1 - n : n) * NB;
 #pragma unroll
@@ -863,21 +919,29 @@ __global__ void __launch_bounds__(256) trsv_kernel(const T* __restrict__ M, cons
             lv[2 * u + 1] = (rok && j0 + lane + 32 < R) ? M[(size_t)row * R + j0 + lane + 32] : T(0);
         }
     };
-    T lv[16], ln[16];
-    if (ntiles > 0) load_tile(0, lv);
-    for (int n = 0; n < ntiles; ++n) {
-        if (n + 1 < ntiles) load_tile(n + 1, ln);   // the next tile's loads fly during this one
-        const int j0 = (TRANS ? nblk - 1 - n : n) * NB;
-        const T* xj = out + j0;
-        // both values in one batch of L2 loads; spin only on one not yet published
-        T x0 = j0 + lane < R ? __ldcg(xj + lane) : T(0);
-        T x1 = j0 + lane + 32 < R ? __ldcg(xj + lane + 32) : T(0);
-        if (unpublished(x0)) x0 = wait_value(xj + lane, sync);
-        if (unpublished(x1)) x1 = wait_value(xj + lane + 32, sync);
+    // a ring of kTrsvDepth tiles in registers: the loads of the next kTrsvDepth - 1 tiles fly
+    // while one is summed (late block rows stream many tiles)
+    T ring[kTrsvDepth][16];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) acc[u] += lv[2 * u] * x0 + lv[2 * u + 1] * x1;
+    for (int d = 0; d + 1 < kTrsvDepth; ++d)
+        if (d < nsum) load_tile(d, ring[d]);
+    for (int n0 = 0; n0 < nsum; n0 += kTrsvDepth) {
 #pragma unroll
-        for (int u = 0; u < 16; ++u) lv[u] = ln[u];
+        for (int d = 0; d < kTrsvDepth; ++d) {
+            const int n = n0 + d;
+            if (n < nsum) {
+                if (n + kTrsvDepth - 1 < nsum) load_tile(n + kTrsvDepth - 1, ring[(d + kTrsvDepth - 1) % kTrsvDepth]);
+                const int j0 = (TRANS ? nblk - 1 - n : n) * NB;
+                const T* xj = out + j0;
+                // both values in one batch of L2 loads; spin only on one not yet published
+                T x0 = j0 + lane < R ? __ldcg(xj + lane) : T(0);
+                T x1 = j0 + lane + 32 < R ? __ldcg(xj + lane + 32) : T(0);
+                if (unpublished(x0)) x0 = wait_value(xj + lane, sync);
+                if (unpublished(x1)) x1 = wait_value(xj + lane + 32, sync);
+#pragma unroll
+                for (int u = 0; u < 8; ++u) acc[u] += ring[d][2 * u] * x0 + ring[d][2 * u + 1] * x1;
+            }
+        }
     }
     // row sums across the warp
 #pragma unroll
@@ -890,7 +954,7 @@ __global__ void __launch_bounds__(256) trsv_kernel(const T* __restrict__ M, cons
     __syncthreads();
     if (tid < NB) vs[tid] = tid < kb ? bin[k0 + tid] - red[0][tid] : T(0);
     __syncthreads();
-    // out_i = Linv_ii v (forward) or Linv_ii^T v (backward): thread (q, c) sums 16 terms
+    // c_i = Linv_ii v (forward) or Linv_ii^T v (backward): thread (q, c) sums 16 terms
     {
         const int q = tid >> 6, c = tid & 63;
         T s2 = T(0);
@@ -902,9 +966,33 @@ __global__ void __launch_bounds__(256) trsv_kernel(const T* __restrict__ M, cons
         red[4 + q][c] = s2;
     }
     __syncthreads();
-    if (tid < kb) {
-        const T v = (red[4][tid] + red[5][tid]) + (red[6][tid] + red[7][tid]);
-        st_relaxed(out + k0 + tid, publishable(v));
+    if (ntiles == 0) {
+        if (tid < kb) {
+            const T v = (red[4][tid] + red[5][tid]) + (red[6][tid] + red[7][tid]);
+            st_relaxed(out + k0 + tid, publishable(v));
+        }
+        return;
+    }
+    // the last dependency: out_i = c_i - K_i x_last
+    if (warp == 0) {
+        const int j0 = (TRANS ? i + 1 : i - 1) * NB;
+        const T* xj = out + j0;
+        T x0 = j0 + lane < R ? __ldcg(xj + lane) : T(0);
+        T x1 = j0 + lane + 32 < R ? __ldcg(xj + lane + 32) : T(0);
+        if (unpublished(x0)) x0 = wait_value(xj + lane, sync);
+        if (unpublished(x1)) x1 = wait_value(xj + lane + 32, sync);
+        xl[lane] = x0;
+        xl[lane + 32] = x1;
+    }
+    __syncthreads();
+    T s3 = T(0);
+#pragma unroll
+    for (int u = 0; u < 16; ++u) s3 += kr[u] * xl[16 * lq + u];
+    s3 += __shfl_xor_sync(0xffffffffu, s3, 1);
+    s3 += __shfl_xor_sync(0xffffffffu, s3, 2);
+    if (lq == 0 && lr < kb) {
+        const T c = (red[4][lr] + red[5][lr]) + (red[6][lr] + red[7][lr]);
+        st_relaxed(out + k0 + lr, publishable(c - s3));
     }
 }
 
@@ -945,6 +1033,9 @@ fst_status chol_invert_diag(const T* L, int R, T* Linv, cudaStream_t s) {
     const int nblk = (R + NB - 1) / NB;
     invert_diag_kernel<T><<<nblk, NB, 0, s>>>(L, R, Linv);
     FST_CHECK_LAUNCH();
+    link_blocks_kernel<T><<<nblk, 256, 0, s>>>(L, R, Linv, Linv + (size_t)nblk * NB * NB,
+                                                 Linv + 2 * (size_t)nblk * NB * NB);
+    FST_CHECK_LAUNCH();
     return FST_OK;
 }
 
@@ -956,11 +1047,13 @@ fst_status chol_solve(const T* L, const T* LT, const T* Linv, int R, T* x, T* y,
     const int nblk = (R + NB - 1) / NB;
     FST_CUDA(cudaMemsetAsync(sync + 1, 0, sizeof(int), s));
     FST_CUDA(cudaMemsetAsync(y, 0xff, sizeof(T) * (size_t)R, s));
-    trsv_kernel<T, false><<<nblk, 256, 0, s>>>(L, Linv, R, nblk, x, y, sync);
+    const T* Kf = Linv + (size_t)nblk * NB * NB;
+    const T* Kb = Linv + 2 * (size_t)nblk * NB * NB;
+    trsv_kernel<T, false><<<nblk, 256, 0, s>>>(L, Linv, Kf, R, nblk, x, y, sync);
     FST_CHECK_LAUNCH();
     FST_CUDA(cudaMemsetAsync(sync + 1, 0, sizeof(int), s));
     FST_CUDA(cudaMemsetAsync(x, 0xff, sizeof(T) * (size_t)R, s));
-    trsv_kernel<T, true><<<nblk, 256, 0, s>>>(LT, Linv, R, nblk, y, x, sync);
+    trsv_kernel<T, true><<<nblk, 256, 0, s>>>(LT, Linv, Kb, R, nblk, y, x, sync);
     FST_CHECK_LAUNCH();
     return FST_OK;
 }

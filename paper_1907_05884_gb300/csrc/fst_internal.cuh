@@ -222,7 +222,7 @@ fst_status pair_products(const float* U1, const float* U2, const float* U3, int6
 template <typename T>
 fst_status cholesky_lower(T* G, int R, int* d_flag, DevBuf& ws, cudaStream_t s);
 template <typename T>
-fst_status chol_invert_diag(const T* L, int R, T* Linv, cudaStream_t s);   // 64x64 diagonal blocks
+fst_status chol_invert_diag(const T* L, int R, T* Linv, cudaStream_t s);   // 64x64 diagonal-block inverses, then the forward and backward link matrices (3 x ceil(R/64) x 64^2 values)
 template <typename T>
 fst_status chol_solve(const T* L, const T* LT, const T* Linv, int R, T* x, T* y, int* sync, cudaStream_t s);  // x <- (L L^T)^-1 x
 // The same through a CUDA graph captured on first use for (L, Linv, x, y, R) and replayed.

@@ -585,12 +585,12 @@ static fst_status refit_impl(fst_model* M, const T* xyz, const T* u, int64_t Q, 
             Lp = G;
         }
         if (use64) {
-            FST_TRY(W.Linv.ensure(sizeof(double) * (size_t)((R + 63) / 64) * 64 * 64));
+            FST_TRY(W.Linv.ensure(3 * sizeof(double) * (size_t)((R + 63) / 64) * 64 * 64));   // + link matrices
             FST_TRY(chol_invert_diag<double>(static_cast<const double*>(Lp), R, W.Linv.as<double>(), s));
             FST_TRY(W.LT.ensure(sizeof(double) * (size_t)R * R));
             FST_TRY(chol_transpose<double>(static_cast<const double*>(Lp), R, W.LT.as<double>(), s));
         } else {
-            FST_TRY(W.Linv.ensure(sizeof(float) * (size_t)((R + 63) / 64) * 64 * 64));
+            FST_TRY(W.Linv.ensure(3 * sizeof(float) * (size_t)((R + 63) / 64) * 64 * 64));   // + link matrices
             FST_TRY(chol_invert_diag<float>(static_cast<const float*>(Lp), R, W.Linv.as<float>(), s));
             FST_TRY(W.LT.ensure(sizeof(float) * (size_t)R * R));
             FST_TRY(chol_transpose<float>(static_cast<const float*>(Lp), R, W.LT.as<float>(), s));
