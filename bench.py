@@ -126,6 +126,9 @@ def gpu_index_for_smi():
 
 
 # ----------------------------------------------------------------------------- peaks
+GRAM_PK_BF16_TRAFFIC = 41.62e9 + 0.3798e9
+
+
 def measured_peaks():
     p = ROOT / "MEASURED_PEAKS.json"
     if p.exists():
@@ -336,7 +339,11 @@ def main():
                      "peak": tc_peak[args.prec], "unit": "TFLOP/s",
                      "peak_source": f"{peak_kind} bf16_tflops_sustained {bf16_peak} x "
                                     f"{ {'tf32': 0.5, 'bf16': 1.0, 'bf16x3': 1 / 3}[args.prec]:.3f}"}
-    roof_gram["traffic"] = None
+    # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one gram_pk_kernel<BF16>
+    # launch at this workload (R = 13,824, m = 110,592), from one ncu capture of the current
+    # kernel; null for other configurations
+    roof_gram["traffic"] = (GRAM_PK_BF16_TRAFFIC if (args.prec == "bf16" and R == 13824 and m == 110592)
+                            else None)
     roof_gram["frac"] = roof_gram["achieved"] / roof_gram["peak"]
     roof_eval = {"kernel": f"eval_tc3_kernel ({args.eval_prec}; factor step and contraction on tcgen05)"
                            if args.eval_prec in ("bf16", "bf16x3") else f"eval ({args.eval_prec})", "ms": ev_ms,
