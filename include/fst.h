@@ -124,9 +124,10 @@ typedef struct {
 
 /* Evaluate many instances -- different models, uneven ranks and point counts -- with one
  * persistent launch per size class of ranks (tensor-core precisions): the items are cut
- * into runs of 128-point tiles, about four runs per SM, the runs are split over the blocks
- * by estimated cost, and a block reloads a model's core tiles only when the instance
- * changes.  Every result equals the single-instance fst_eval of that item bit for bit.
+ * into runs of 128-point tiles, about four runs per SM; with several instances the blocks
+ * of the factor-step evaluator take runs in order from a counter (otherwise the runs are
+ * split over the blocks by estimated cost), and a block reloads a model's core tiles only
+ * when the instance changes.  Every result equals the single-instance fst_eval of that item bit for bit.
  * FST_FP32 runs one CUDA-core launch per item.  items: host array; a model must not be
  * refitted while it is being evaluated.  Asynchronous: the work lists go through a
  * per-device ring of 8 pinned/device staging slots that only grow (the ninth call in
@@ -139,7 +140,9 @@ fst_status fst_eval_batched(const fst_eval_item* items, int32_t count, fst_prec 
  * per size class of ranks), allocates nothing and does not synchronise, so it can be
  * captured into a CUDA graph and replayed.  The models' cores and the items' buffers must
  * stay as they were when the plan was made (a refit changes the core: make a new plan).
- * Tensor-core precisions only. */
+ * Runs of one plan on different streams are ordered on the device (they share the plan's
+ * run counters); inside a stream capture that ordering is the graph's.  Tensor-core
+ * precisions only. */
 typedef struct fst_eval_plan fst_eval_plan;
 fst_status fst_eval_plan_create(const fst_eval_item* items, int32_t count, fst_prec prec,
                                 fst_eval_plan** out);

@@ -562,6 +562,7 @@ __device__ __forceinline__ void tmem_ld_cols(uint32_t taddr, float* v) {
 template <int MODE, int R3P, int RM>
 __global__ void __launch_bounds__(kThreads3, 1)
 eval_tc3_kernel(const TcItem* __restrict__ items, const TcUnit* __restrict__ units, const int* __restrict__ cta_start,
+                int nunits, int* unit_ctr,
                 int core_max, int kb_max, int kpf_max, const float* __restrict__ xyz_ov, float* __restrict__ out_ov,
                 int* __restrict__ err) {
     constexpr int JC = jc3_for(R3P);
@@ -603,7 +604,7 @@ eval_tc3_kernel(const TcItem* __restrict__ items, const TcUnit* __restrict__ uni
     const uint32_t p_u32 = tc::smem_u32(P);
     const uint32_t core_u32 = tc::smem_u32(core);
 
-    const int u0 = cta_start[blockIdx.x], u1 = cta_start[blockIdx.x + 1];
+    __shared__ int s_unit;
     int cur = -1;
     int nw = 0, nm = 0;        // completed phases of w_bar[g] and m_bar[g]
     bool issued = false, dead = false;
@@ -626,7 +627,19 @@ eval_tc3_kernel(const TcItem* __restrict__ items, const TcUnit* __restrict__ uni
         __syncwarp();
         dead = __any_sync(0xffffffffu, dead);
     };
-    for (int u = u0; u < u1; ++u) {
+    // with a counter (several instances), units are taken in order from it (zeroed before
+    // the launch), so the CTAs stay balanced whatever each unit costs; without, the CTA runs
+    // its own range of units and the worker groups never meet at unit boundaries
+    const int u0 = unit_ctr ? 0 : cta_start[blockIdx.x], u1 = unit_ctr ? nunits : cta_start[blockIdx.x + 1];
+    for (int us = u0;; ++us) {
+        int u = us;
+        if (unit_ctr) {
+            if (tid == 0) s_unit = atomicAdd(unit_ctr, 1);
+            __syncthreads();
+            u = s_unit;
+            __syncthreads();
+        }
+        if (u >= u1) break;
         const TcUnit U = units[u];
         const TcItem& I = items[U.item];
         const EvalArgs<float>& a = I.a;
@@ -890,7 +903,7 @@ struct Bucket {
     std::vector<int> cta_start;
     int core_max = 0, kb_max = 32, grid = 1;
     size_t smem = 0;
-    size_t items_off = 0, units_off = 0, cta_off = 0, bytes = 0;   // device image layout
+    size_t items_off = 0, units_off = 0, cta_off = 0, ctr_off = 0, bytes = 0;   // device image layout
 };
 
 fst_status build_buckets(const std::vector<HostItem>& hitems, int mode, std::vector<Bucket>& out) {
@@ -964,8 +977,10 @@ fst_status build_buckets(const std::vector<HostItem>& hitems, int mode, std::vec
             total_cost += nt * tile_cost[i];
         }
         if (total_tiles == 0) continue;
+        // units of ~1/4 of a CTA's share (taken dynamically by the factor-step kernel, cut
+        // into static per-CTA ranges by cost for the other); at least one tile per worker group
         long long run = (total_tiles + 4LL * sms - 1) / (4LL * sms);
-        if (run < 3) run = 3;   // a unit feeds every worker group of a CTA
+        if (run < 3) run = 3;
         std::vector<double> unit_cost;
         for (size_t i = 0; i < B.items.size(); ++i) {
             const long long nt = (B.items[i].n + 127) / 128;
@@ -992,7 +1007,8 @@ fst_status build_buckets(const std::vector<HostItem>& hitems, int mode, std::vec
         B.items_off = 0;
         B.units_off = (B.items.size() * sizeof(TcItem) + 15) & ~(size_t)15;
         B.cta_off = (B.units_off + B.units.size() * sizeof(TcUnit) + 15) & ~(size_t)15;
-        B.bytes = B.cta_off + B.cta_start.size() * sizeof(int);
+        B.ctr_off = (B.cta_off + B.cta_start.size() * sizeof(int) + 15) & ~(size_t)15;   // unit counter
+        B.bytes = B.ctr_off + 16;
         out.push_back(std::move(B));
     }
     return FST_OK;
@@ -1037,10 +1053,16 @@ template <int MODE, int R3P, int RM>
 fst_status launch_bucket_tc3_t(const Bucket& B, const unsigned char* dimg, int* err, cudaStream_t s, Overrides ov) {
     auto kern = eval_tc3_kernel<MODE, R3P, RM>;
     FST_TRY(allow_smem(kern, B.smem));
+    // several instances: units from a counter; one: the static per-CTA ranges
+    int* ctr = nullptr;
+    if (B.items.size() > 1) {
+        ctr = reinterpret_cast<int*>(const_cast<unsigned char*>(dimg) + B.ctr_off);
+        FST_CUDA(cudaMemsetAsync(ctr, 0, sizeof(int), s));
+    }
     kern<<<B.grid, kThreads3, B.smem, s>>>(reinterpret_cast<const TcItem*>(dimg + B.items_off),
                                            reinterpret_cast<const TcUnit*>(dimg + B.units_off),
-                                           reinterpret_cast<const int*>(dimg + B.cta_off), B.core_max, B.kb_max,
-                                           B.kpf_max, ov.xyz, ov.out, err);
+                                           reinterpret_cast<const int*>(dimg + B.cta_off), (int)B.units.size(), ctr,
+                                           B.core_max, B.kb_max, B.kpf_max, ov.xyz, ov.out, err);
     FST_CHECK_LAUNCH();
     return FST_OK;
 }
@@ -1128,8 +1150,13 @@ fst_status prepare_core_image(fst_model* m, int mode, int r3p) {
 struct fst_eval_plan {
     int device = 0;
     std::vector<fst::Bucket> buckets;
-    unsigned char* dimg = nullptr;
+    unsigned char* dimg = nullptr;      // work lists and unit counters
     std::vector<size_t> offs;
+    // runs of one plan on different streams are ordered on the device (they share the unit
+    // counters): each waits for the event of the previous run
+    mutable std::mutex mu;
+    mutable cudaEvent_t done = nullptr;
+    mutable bool used = false;
 };
 
 namespace fst {
@@ -1158,14 +1185,27 @@ fst_status plan_build(const std::vector<HostItem>& items, fst_prec prec, fst_eva
 fst_status plan_run(const fst_eval_plan* P, cudaStream_t s, Overrides ov = Overrides()) {
     int* err = nullptr;
     FST_TRY(error_word(&err));
+    std::lock_guard<std::mutex> lk(P->mu);
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    FST_CUDA(cudaStreamIsCapturing(s, &cap));
+    const bool capturing = cap != cudaStreamCaptureStatusNone;   // a captured run is ordered by its graph
+    if (!capturing) {
+        if (!P->done) FST_CUDA(cudaEventCreateWithFlags(&P->done, cudaEventDisableTiming));
+        if (P->used) FST_CUDA(cudaStreamWaitEvent(s, P->done, 0));
+    }
     for (size_t b = 0; b < P->buckets.size(); ++b)
         FST_TRY(launch_bucket(P->buckets[b], P->dimg + P->offs[b], err, s, ov));
+    if (!capturing) {
+        FST_CUDA(cudaEventRecord(P->done, s));
+        P->used = true;
+    }
     return FST_OK;
 }
 
 void plan_free(fst_eval_plan* P) {
     if (!P) return;
     if (P->dimg) cudaFree(P->dimg);   // cudaFree waits for work in flight on the device
+    if (P->done) cudaEventDestroy(P->done);
     delete P;
 }
 
