@@ -873,7 +873,6 @@ __device__ __forceinline__ T wait_value(const T* p, int* err) {
 
 // M is L (forward) or L^T (backward, TRANS), both row-major: block row i reads the tiles
 // M[i-block][j-block] for j < i (forward) or j > i (backward) along its own rows.
-constexpr int kTrsvDepth = 4;
 template <typename T, bool TRANS>
 __global__ void __launch_bounds__(256) trsv_kernel(const T* __restrict__ M, const T* __restrict__ Linv,
                                                    const T* __restrict__ K, int R, int nblk, const T* bin, T* out,
@@ -921,6 +920,7 @@ __global__ void __launch_bounds__(256) trsv_kernel(const T* __restrict__ M, cons
     };
     // a ring of kTrsvDepth tiles in registers: the loads of the next kTrsvDepth - 1 tiles fly
     // while one is summed (late block rows stream many tiles)
+    constexpr int kTrsvDepth = sizeof(T) == 4 ? 8 : 4;
     T ring[kTrsvDepth][16];
 #pragma unroll
     for (int d = 0; d + 1 < kTrsvDepth; ++d)

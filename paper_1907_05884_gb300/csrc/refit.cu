@@ -226,8 +226,9 @@ __global__ void sum_partials_kernel(const double* __restrict__ part, int nparts,
 // product A alpha).  The sums over k and j run in T; for T = float alpha is split into
 // alpha_hi + alpha_lo (both FP32) so the core keeps its FP64 digits; the sum over i and the
 // subtraction from b run in FP64.
+constexpr int kMaxRank = FST_MAX_RANK;
 template <typename T, int R3M>
-__global__ void __launch_bounds__(128) residual_kernel(const T* __restrict__ U1, const T* __restrict__ U2,
+__global__ void __launch_bounds__(256) residual_kernel(const T* __restrict__ U1, const T* __restrict__ U2,
                                                        const T* __restrict__ U3, const T* __restrict__ bvec,
                                                        const double* __restrict__ alpha, int64_t m, int r1,
                                                        int r2, int r3, double scale, double* rv) {
@@ -244,40 +245,46 @@ __global__ void __launch_bounds__(128) residual_kernel(const T* __restrict__ U1,
     }
     __syncthreads();
     for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < m; s += (int64_t)gridDim.x * blockDim.x) {
-        T w3[R3M];
+        // the row's factor values in registers (w2 indexed by the unrolled j loop)
+        T w3[R3M], w2[kMaxRank];
 #pragma unroll
         for (int k = 0; k < R3M; ++k) w3[k] = k < r3 ? U3[s * r3 + k] : T(0);
+#pragma unroll
+        for (int j = 0; j < kMaxRank; ++j) w2[j] = j < r2 ? U2[s * r2 + j] : T(0);
         double f = 0.0;
         for (int i = 0; i < r1; ++i) {
             T si = T(0);
-            for (int j = 0; j < r2; ++j) {
-                const T* arow = As + (i * r2 + j) * R3M;
-                T t0 = T(0), t1 = T(0);
 #pragma unroll
-                for (int k = 0; k < R3M; k += 4) {
-                    T a0, a1, a2, a3;
-                    load4(arow + k, a0, a1, a2, a3);
-                    t0 = fma(a0, w3[k], t0);
-                    t1 = fma(a1, w3[k + 1], t1);
-                    t0 = fma(a2, w3[k + 2], t0);
-                    t1 = fma(a3, w3[k + 3], t1);
-                }
-                T t = t0 + t1;
-                if (kSplit) {
-                    const T* lrow = Al + (i * r2 + j) * R3M;
-                    T l0 = T(0), l1 = T(0);
+            for (int j = 0; j < kMaxRank; ++j) {
+                if (j < r2) {
+                    const T* arow = As + (i * r2 + j) * R3M;
+                    T t0 = T(0), t1 = T(0);
 #pragma unroll
                     for (int k = 0; k < R3M; k += 4) {
                         T a0, a1, a2, a3;
-                        load4(lrow + k, a0, a1, a2, a3);
-                        l0 = fma(a0, w3[k], l0);
-                        l1 = fma(a1, w3[k + 1], l1);
-                        l0 = fma(a2, w3[k + 2], l0);
-                        l1 = fma(a3, w3[k + 3], l1);
+                        load4(arow + k, a0, a1, a2, a3);
+                        t0 = fma(a0, w3[k], t0);
+                        t1 = fma(a1, w3[k + 1], t1);
+                        t0 = fma(a2, w3[k + 2], t0);
+                        t1 = fma(a3, w3[k + 3], t1);
                     }
-                    t += l0 + l1;
+                    T t = t0 + t1;
+                    if (kSplit) {
+                        const T* lrow = Al + (i * r2 + j) * R3M;
+                        T l0 = T(0), l1 = T(0);
+#pragma unroll
+                        for (int k = 0; k < R3M; k += 4) {
+                            T a0, a1, a2, a3;
+                            load4(lrow + k, a0, a1, a2, a3);
+                            l0 = fma(a0, w3[k], l0);
+                            l1 = fma(a1, w3[k + 1], l1);
+                            l0 = fma(a2, w3[k + 2], l0);
+                            l1 = fma(a3, w3[k + 3], l1);
+                        }
+                        t += l0 + l1;
+                    }
+                    si = fma(t, w2[j], si);
                 }
-                si = fma(t, U2[s * r2 + j], si);
             }
             f = fma((double)si, (double)U1[s * r1 + i], f);
         }
@@ -446,12 +453,13 @@ static fst_status launch_residual(const fst_model* M, const T* const U[3], const
     const int r1 = M->r[0], r2 = M->r[1], r3 = M->r[2];
     const int R3M = r3 <= 8 ? 8 : r3 <= 16 ? 16 : r3 <= 24 ? 24 : 32;
     const size_t smem = (size_t)r1 * r2 * R3M * sizeof(T) * (sizeof(T) == 4 ? 2 : 1);
-    const int grid = grid_for(m, 128, 4);
+    // 256 threads a block: two blocks (16 warps) fit beside the core's hi/lo copy at r = 24
+    const int grid = grid_for(m, 256, 2);
 #define FST_RES(V)                                                                                          \
     {                                                                                                       \
         auto kern = residual_kernel<T, V>;                                                                  \
-        FST_TRY(allow_smem(kern, smem));       \
-        kern<<<grid, 128, smem, s>>>(U[0], U[1], U[2], bvec, alpha, m, r1, r2, r3, scale, rv);              \
+        FST_TRY(allow_smem(kern, smem));                                                                    \
+        kern<<<grid, 256, smem, s>>>(U[0], U[1], U[2], bvec, alpha, m, r1, r2, r3, scale, rv);              \
     }
     if (R3M == 8) FST_RES(8) else if (R3M == 16) FST_RES(16) else if (R3M == 24) FST_RES(24) else FST_RES(32)
 #undef FST_RES
