@@ -876,7 +876,8 @@ __device__ __forceinline__ T wait_value(const T* p, int* err) {
 template <typename T, bool TRANS>
 __global__ void __launch_bounds__(256) trsv_kernel(const T* __restrict__ M, const T* __restrict__ Linv,
                                                    const T* __restrict__ K, int R, int nblk, const T* bin, T* out,
-                                                   int* sync) {
+                                                   int* sync, const int* stop) {
+    if (stop && *stop) return;   // the caller's iteration has already stopped (no block waits then)
     __shared__ T lis[NB][NB + 1];   // Linv of the diagonal block
     __shared__ T red[8][NB];
     __shared__ T vs[NB];
@@ -1043,17 +1044,18 @@ fst_status chol_invert_diag(const T* L, int R, T* Linv, cudaStream_t s) {
 // the error word, left as it is).  The output of each direction is filled with the all-ones
 // pattern first (both memsets and both kernels are captured by chol_solve_graph).
 template <typename T>
-fst_status chol_solve(const T* L, const T* LT, const T* Linv, int R, T* x, T* y, int* sync, cudaStream_t s) {
+fst_status chol_solve(const T* L, const T* LT, const T* Linv, int R, T* x, T* y, int* sync, cudaStream_t s,
+                      const int* stop) {
     const int nblk = (R + NB - 1) / NB;
     FST_CUDA(cudaMemsetAsync(sync + 1, 0, sizeof(int), s));
     FST_CUDA(cudaMemsetAsync(y, 0xff, sizeof(T) * (size_t)R, s));
     const T* Kf = Linv + (size_t)nblk * NB * NB;
     const T* Kb = Linv + 2 * (size_t)nblk * NB * NB;
-    trsv_kernel<T, false><<<nblk, 256, 0, s>>>(L, Linv, Kf, R, nblk, x, y, sync);
+    trsv_kernel<T, false><<<nblk, 256, 0, s>>>(L, Linv, Kf, R, nblk, x, y, sync, stop);
     FST_CHECK_LAUNCH();
     FST_CUDA(cudaMemsetAsync(sync + 1, 0, sizeof(int), s));
     FST_CUDA(cudaMemsetAsync(x, 0xff, sizeof(T) * (size_t)R, s));
-    trsv_kernel<T, true><<<nblk, 256, 0, s>>>(LT, Linv, Kb, R, nblk, y, x, sync);
+    trsv_kernel<T, true><<<nblk, 256, 0, s>>>(LT, Linv, Kb, R, nblk, y, x, sync, stop);
     FST_CHECK_LAUNCH();
     return FST_OK;
 }
@@ -1062,8 +1064,9 @@ template fst_status cholesky_lower<float>(float*, int, int*, DevBuf&, cudaStream
 template fst_status cholesky_lower<double>(double*, int, int*, DevBuf&, cudaStream_t);
 template <typename T>
 fst_status chol_solve_graph(SolveGraph& g, const T* L, const T* LT, const T* Linv, int R, T* x, T* y,
-                            cudaStream_t s) {
-    if (!g.exec || g.L != L || g.LT != LT || g.Linv != Linv || g.x != x || g.R != R || g.elem != (int)sizeof(T)) {
+                            cudaStream_t s, const int* stop) {
+    if (!g.exec || g.L != L || g.LT != LT || g.Linv != Linv || g.x != x || g.R != R || g.elem != (int)sizeof(T) ||
+        g.stop != stop) {
         if (g.exec) {
             FST_CUDA(cudaStreamSynchronize(s));
             cudaGraphExecDestroy(g.exec);
@@ -1075,7 +1078,7 @@ fst_status chol_solve_graph(SolveGraph& g, const T* L, const T* LT, const T* Lin
         FST_CUDA(cudaStreamSynchronize(s));
         FST_CUDA(cudaStreamBeginCapture(g.cap, cudaStreamCaptureModeThreadLocal));
         const uint64_t before = fst_kernel_launches();
-        fst_status st = chol_solve<T>(L, LT, Linv, R, x, y, g.sync.as<int>(), g.cap);
+        fst_status st = chol_solve<T>(L, LT, Linv, R, x, y, g.sync.as<int>(), g.cap, stop);
         cudaGraph_t graph = nullptr;
         cudaError_t e = cudaStreamEndCapture(g.cap, &graph);
         if (st != FST_OK) {
@@ -1093,6 +1096,7 @@ fst_status chol_solve_graph(SolveGraph& g, const T* L, const T* LT, const T* Lin
         g.x = x;
         g.R = R;
         g.elem = (int)sizeof(T);
+        g.stop = stop;
     }
     FST_CUDA(cudaGraphLaunch(g.exec, s));
     count_launches(g.nodes);
@@ -1100,15 +1104,16 @@ fst_status chol_solve_graph(SolveGraph& g, const T* L, const T* LT, const T* Lin
 }
 
 template fst_status chol_solve_graph<float>(SolveGraph&, const float*, const float*, const float*, int, float*,
-                                            float*, cudaStream_t);
+                                            float*, cudaStream_t, const int*);
 template fst_status chol_solve_graph<double>(SolveGraph&, const double*, const double*, const double*, int, double*,
-                                             double*, cudaStream_t);
+                                             double*, cudaStream_t, const int*);
 
 template fst_status chol_invert_diag<float>(const float*, int, float*, cudaStream_t);
 template fst_status chol_invert_diag<double>(const double*, int, double*, cudaStream_t);
-template fst_status chol_solve<float>(const float*, const float*, const float*, int, float*, float*, int*, cudaStream_t);
+template fst_status chol_solve<float>(const float*, const float*, const float*, int, float*, float*, int*, cudaStream_t,
+                                      const int*);
 template fst_status chol_solve<double>(const double*, const double*, const double*, int, double*, double*, int*,
-                                       cudaStream_t);
+                                       cudaStream_t, const int*);
 
 }  // namespace fst
 

@@ -120,6 +120,7 @@ struct SolveGraph {
     const void* LT = nullptr;
     const void* Linv = nullptr;
     void* x = nullptr;
+    const int* stop = nullptr;
     int R = 0, elem = 0;
     uint64_t nodes = 0;
     DevBuf sync;                 // error word, ticket, ready flags of the one-launch solves
@@ -129,7 +130,7 @@ struct SolveGraph {
 // Scratch of the refit, kept inside the model between calls.
 struct RefitScratch {
     DevBuf idx, U[3], b, G, G64, res, g, z, delta, alpha, norms, flag, Linv, LT, xw, yw, pcg, chol_ws, atr_part,
-        gram_err;
+        gram_err, pcg_state;
     SolveGraph solve;
 };
 
@@ -224,11 +225,12 @@ fst_status cholesky_lower(T* G, int R, int* d_flag, DevBuf& ws, cudaStream_t s);
 template <typename T>
 fst_status chol_invert_diag(const T* L, int R, T* Linv, cudaStream_t s);   // 64x64 diagonal-block inverses, then the forward and backward link matrices (3 x ceil(R/64) x 64^2 values)
 template <typename T>
-fst_status chol_solve(const T* L, const T* LT, const T* Linv, int R, T* x, T* y, int* sync, cudaStream_t s);  // x <- (L L^T)^-1 x
+fst_status chol_solve(const T* L, const T* LT, const T* Linv, int R, T* x, T* y, int* sync, cudaStream_t s,
+                      const int* stop = nullptr);  // x <- (L L^T)^-1 x; nothing when *stop is set
 // The same through a CUDA graph captured on first use for (L, Linv, x, y, R) and replayed.
 template <typename T>
 fst_status chol_solve_graph(SolveGraph& g, const T* L, const T* LT, const T* Linv, int R, T* x, T* y,
-                            cudaStream_t s);
+                            cudaStream_t s, const int* stop = nullptr);
 // LT = L^T (the strict upper blocks used by the backward solve)
 template <typename T>
 fst_status chol_transpose(const T* L, int R, T* LT, cudaStream_t s);

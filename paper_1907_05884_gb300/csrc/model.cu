@@ -145,6 +145,7 @@ static void free_device(fst_model* m) {
     s.chol_ws.release();
     s.atr_part.release();
     s.gram_err.release();
+    s.pcg_state.release();
     s.xw.release();
     s.yw.release();
     s.pcg.release();

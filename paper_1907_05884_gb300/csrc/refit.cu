@@ -148,7 +148,8 @@ template <typename T, int R3M, int PPT>
 __global__ void __launch_bounds__(256) atr_kernel(const T* __restrict__ U1, const T* __restrict__ U2,
                                                   const T* __restrict__ U3, const double* __restrict__ rv,
                                                   int64_t m, int r1, int r2, int r3, int64_t rows_per_block,
-                                                  double* __restrict__ part) {
+                                                  double* __restrict__ part, const int* stop) {
+    if (stop && *stop) return;
     constexpr int S = 64;
     __shared__ T u1s[S][FST_MAX_RANK + 1], u2s[S][FST_MAX_RANK + 1];
     __shared__ __align__(16) T u3s[S][R3M];
@@ -214,7 +215,9 @@ __global__ void __launch_bounds__(256) atr_kernel(const T* __restrict__ U1, cons
     }
 }
 
-__global__ void sum_partials_kernel(const double* __restrict__ part, int nparts, int R, double* __restrict__ g) {
+__global__ void sum_partials_kernel(const double* __restrict__ part, int nparts, int R, double* __restrict__ g,
+                                    const int* stop) {
+    if (stop && *stop) return;
     for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < R; a += gridDim.x * blockDim.x) {
         double s = 0.0;
         for (int b = 0; b < nparts; ++b) s += part[(size_t)b * R + a];
@@ -231,8 +234,10 @@ template <typename T, int R3M>
 __global__ void __launch_bounds__(256) residual_kernel(const T* __restrict__ U1, const T* __restrict__ U2,
                                                        const T* __restrict__ U3, const T* __restrict__ bvec,
                                                        const double* __restrict__ alpha, int64_t m, int r1,
-                                                       int r2, int r3, double scale, double* rv) {
+                                                       int r2, int r3, double scale, double* rv,
+                                                       const int* stop) {
     constexpr bool kSplit = sizeof(T) == 4;
+    if (stop && *stop) return;   // the conjugate gradients have stopped
     extern __shared__ __align__(16) unsigned char smem[];
     T* As = reinterpret_cast<T*>(smem);        // [r1*r2][R3M]
     T* Al = As + r1 * r2 * R3M;                // low parts (FP32 only)
@@ -336,10 +341,59 @@ __global__ void __launch_bounds__(kDotThreads) dots_kernel(const double* x0, con
     }
 }
 
-// y += a x, or (with xpby) y = x + b y
-__global__ void axpy_kernel(double* y, const double* x, double a, int n, int xpby) {
+// Scalars of the conjugate gradients, kept on the device so that iterations are launched
+// without a host round trip; stop: 1 converged, 2 broke down (not converged).
+struct PcgState {
+    double rz, ak, pp2, beta, last, prev;
+    int stop, steps;
+};
+
+__global__ void pcg_init_kernel(const double* __restrict__ norms, PcgState* st) {
+    st->rz = norms[0];
+    st->ak = st->pp2 = st->beta = st->last = st->prev = 0.0;
+    st->stop = 0;
+    st->steps = 0;
+}
+
+// after w = A^T A p: norms = (p.w, p.p); the step length
+__global__ void pcg_step_length_kernel(const double* __restrict__ norms, PcgState* st) {
+    if (st->stop) return;
+    const double pw = norms[0];
+    if (!(pw > 0.0) || !isfinite(st->rz)) {
+        st->stop = 2;
+        return;
+    }
+    st->ak = st->rz / pw;
+    st->pp2 = norms[1];
+}
+
+// after z = M^-1 r: norms = (r.z, alpha.alpha); the relative update and the stopping rule
+// (below tol, or no longer shrinking at a level below floor_ok), else the next direction's beta
+__global__ void pcg_step_end_kernel(const double* __restrict__ norms, PcgState* st, double tol, double floor_ok) {
+    if (st->stop) return;
+    st->steps += 1;
+    st->prev = st->last;
+    const double nx0 = norms[0], nx1 = norms[1];
+    const double last = nx1 > 0 ? fabs(st->ak) * sqrt(st->pp2 / nx1) : 0.0;
+    st->last = last;
+    if (!isfinite(last)) {
+        st->stop = 2;
+        return;
+    }
+    if (last <= tol || (st->steps >= 3 && last > 0.5 * st->prev && last <= floor_ok)) {
+        st->stop = 1;
+        return;
+    }
+    st->beta = nx0 / st->rz;
+    st->rz = nx0;
+}
+
+// alpha += ak p (which 0), r -= ak w (1), p = z + beta p (2), with the scalars of st
+__global__ void pcg_axpy_kernel(double* y, const double* x, const PcgState* st, int which, int n) {
+    if (st->stop) return;
+    const double a = which == 0 ? st->ak : which == 1 ? -st->ak : st->beta;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-        y[i] = xpby ? x[i] + a * y[i] : y[i] + a * x[i];
+        y[i] = which == 2 ? x[i] + a * y[i] : y[i] + a * x[i];
 }
 
 template <typename T>
@@ -407,7 +461,7 @@ static fst_status launch_factors(const fst_model* M, const T* xyz, int64_t Q, co
 
 template <typename T>
 static fst_status launch_atr(const fst_model* M, const T* const U[3], const double* rv, int64_t m, double* g,
-                             cudaStream_t s) {
+                             cudaStream_t s, const int* stop = nullptr) {
     const int r1 = M->r[0], r2 = M->r[1], r3 = M->r[2];
     const int R = M->R();
     if (m <= 0) {
@@ -428,7 +482,7 @@ static fst_status launch_atr(const fst_model* M, const T* const U[3], const doub
     double* part = pb.as<double>();
     const unsigned grid = (unsigned)nparts;
 #define FST_ATR(R3V, PPTV) \
-    atr_kernel<T, R3V, PPTV><<<grid, threads, 0, s>>>(U[0], U[1], U[2], rv, m, r1, r2, r3, rows_per_block, part)
+    atr_kernel<T, R3V, PPTV><<<grid, threads, 0, s>>>(U[0], U[1], U[2], rv, m, r1, r2, r3, rows_per_block, part, stop)
     if (sizeof(T) == 8) {
         if (r3 <= 8) FST_ATR(8, 1);
         else if (r3 <= 16) FST_ATR(16, 1);
@@ -442,14 +496,15 @@ static fst_status launch_atr(const fst_model* M, const T* const U[3], const doub
     }
 #undef FST_ATR
     FST_CHECK_LAUNCH();
-    sum_partials_kernel<<<(R + 255) / 256, 256, 0, s>>>(part, (int)nparts, R, g);
+    sum_partials_kernel<<<(R + 255) / 256, 256, 0, s>>>(part, (int)nparts, R, g, stop);
     FST_CHECK_LAUNCH();
     return FST_OK;
 }
 
 template <typename T>
 static fst_status launch_residual(const fst_model* M, const T* const U[3], const T* bvec, const double* alpha,
-                                  int64_t m, double* rv, cudaStream_t s, double scale = -1.0) {
+                                  int64_t m, double* rv, cudaStream_t s, double scale = -1.0,
+                                  const int* stop = nullptr) {
     const int r1 = M->r[0], r2 = M->r[1], r3 = M->r[2];
     const int R3M = r3 <= 8 ? 8 : r3 <= 16 ? 16 : r3 <= 24 ? 24 : 32;
     const size_t smem = (size_t)r1 * r2 * R3M * sizeof(T) * (sizeof(T) == 4 ? 2 : 1);
@@ -459,7 +514,7 @@ static fst_status launch_residual(const fst_model* M, const T* const U[3], const
     {                                                                                                       \
         auto kern = residual_kernel<T, V>;                                                                  \
         FST_TRY(allow_smem(kern, smem));                                                                    \
-        kern<<<grid, 256, smem, s>>>(U[0], U[1], U[2], bvec, alpha, m, r1, r2, r3, scale, rv);              \
+        kern<<<grid, 256, smem, s>>>(U[0], U[1], U[2], bvec, alpha, m, r1, r2, r3, scale, rv, stop);        \
     }
     if (R3M == 8) FST_RES(8) else if (R3M == 16) FST_RES(16) else if (R3M == 24) FST_RES(24) else FST_RES(32)
 #undef FST_RES
@@ -633,6 +688,13 @@ static fst_status refit_impl(fst_model* M, const T* xyz, const T* u, int64_t Q, 
     // the preconditioner solve runs in the factor's precision on a working copy
     FST_TRY(W.xw.ensure(sizeof(double) * (size_t)R));
     FST_TRY(W.yw.ensure(sizeof(double) * (size_t)R));
+    // the CG state (its stop word also gates the solves, so the captured solve graph is the
+    // same for every call); zeroed before the first solve
+    FST_TRY(W.pcg_state.ensure(sizeof(PcgState)));
+    PcgState* pst = W.pcg_state.as<PcgState>();
+    const int* stop = &pst->stop;
+    FST_CUDA(cudaMemsetAsync(pst, 0, sizeof(PcgState), s));
+    const int* solve_stop = stop;
     auto solve = [&](double* x) -> fst_status {
         const int grid = grid_for(R, 256, 2);
         if (use64) {
@@ -640,7 +702,7 @@ static fst_status refit_impl(fst_model* M, const T* xyz, const T* u, int64_t Q, 
             FST_CUDA(cudaMemcpyAsync(xw, x, sizeof(double) * R, cudaMemcpyDeviceToDevice, s));
             FST_TRY(chol_solve_graph<double>(W.solve, static_cast<const double*>(Lp), W.LT.as<double>(),
                                              W.Linv.as<double>(), R, xw,
-                                             W.yw.as<double>(), s));
+                                             W.yw.as<double>(), s, solve_stop));
             FST_CUDA(cudaMemcpyAsync(x, xw, sizeof(double) * R, cudaMemcpyDeviceToDevice, s));
             return FST_OK;
         }
@@ -649,7 +711,7 @@ static fst_status refit_impl(fst_model* M, const T* xyz, const T* u, int64_t Q, 
         FST_CHECK_LAUNCH();
         FST_TRY(chol_solve_graph<float>(W.solve, static_cast<const float*>(Lp), W.LT.as<float>(), W.Linv.as<float>(),
                                         R, xw,
-                                        W.yw.as<float>(), s));
+                                        W.yw.as<float>(), s, solve_stop));
         to_double_kernel<float><<<grid, 256, 0, s>>>(xw, x, R);
         FST_CHECK_LAUNCH();
         return FST_OK;
@@ -673,15 +735,17 @@ static fst_status refit_impl(fst_model* M, const T* xyz, const T* u, int64_t Q, 
     double* pp = zz + R;                 // search direction
     double* ww = pp + R;                 // A^T A p
     const int vgrid = grid_for(R, 256, 2);
-    auto dots = [&](const double* x0, const double* y0, const double* x1, const double* y1, int nd,
-                    double* hout) -> fst_status {
+    auto dots = [&](const double* x0, const double* y0, const double* x1, const double* y1, int nd) -> fst_status {
         dots_kernel<<<1, kDotThreads, 0, s>>>(x0, y0, x1, y1, R, nd, norms);
         FST_CHECK_LAUNCH();
-        FST_CUDA(cudaMemcpyAsync(hout, norms, nd * sizeof(double), cudaMemcpyDeviceToHost, s));
-        FST_CUDA(cudaStreamSynchronize(s));
         return FST_OK;
     };
-    double last = 0.0, prev = 0.0;
+    // iterations are launched kCheckEvery at a time; the host reads the state in between, and
+    // the kernels of iterations launched after the stop return at once
+    constexpr int kCheckEvery = 2;
+    PcgState hs;
+    memset(&hs, 0, sizeof hs);
+    double last = 0.0;
     int steps = 0;
     bool converged = max_refine <= 0;
     if (max_refine > 0) {
@@ -690,37 +754,35 @@ static fst_status refit_impl(fst_model* M, const T* xyz, const T* u, int64_t Q, 
         FST_CUDA(cudaMemcpyAsync(zz, rr, sizeof(double) * R, cudaMemcpyDeviceToDevice, s));
         FST_TRY(solve(zz));
         FST_CUDA(cudaMemcpyAsync(pp, zz, sizeof(double) * R, cudaMemcpyDeviceToDevice, s));
-        double rz[2];
-        FST_TRY(dots(rr, zz, alpha, alpha, 2, rz));
-        double rzv = rz[0];
+        FST_TRY(dots(rr, zz, alpha, alpha, 2));
+        pcg_init_kernel<<<1, 1, 0, s>>>(norms, pst);
+        FST_CHECK_LAUNCH();
         for (int it = 0; it < max_refine; ++it) {
-            FST_TRY(launch_residual<T>(M, Uc, nullptr, pp, m, rv, s, 1.0));   // q = A p
-            FST_TRY(launch_atr<T>(M, Uc, rv, m, ww, s));                      // w = A^T q
-            double pw[2];
-            FST_TRY(dots(pp, ww, pp, pp, 2, pw));
-            if (!(pw[0] > 0.0) || !isfinite(rzv)) break;
-            const double ak = rzv / pw[0];
-            axpy_kernel<<<vgrid, 256, 0, s>>>(alpha, pp, ak, R, 0);
+            FST_TRY(launch_residual<T>(M, Uc, nullptr, pp, m, rv, s, 1.0, stop));   // q = A p
+            FST_TRY(launch_atr<T>(M, Uc, rv, m, ww, s, stop));                      // w = A^T q
+            FST_TRY(dots(pp, ww, pp, pp, 2));
+            pcg_step_length_kernel<<<1, 1, 0, s>>>(norms, pst);
             FST_CHECK_LAUNCH();
-            axpy_kernel<<<vgrid, 256, 0, s>>>(rr, ww, -ak, R, 0);
+            pcg_axpy_kernel<<<vgrid, 256, 0, s>>>(alpha, pp, pst, 0, R);             // alpha += ak p
+            FST_CHECK_LAUNCH();
+            pcg_axpy_kernel<<<vgrid, 256, 0, s>>>(rr, ww, pst, 1, R);                // r -= ak w
             FST_CHECK_LAUNCH();
             FST_CUDA(cudaMemcpyAsync(zz, rr, sizeof(double) * R, cudaMemcpyDeviceToDevice, s));
             FST_TRY(solve(zz));
-            double nx[2];
-            FST_TRY(dots(rr, zz, alpha, alpha, 2, nx));
-            ++steps;
-            prev = last;
-            last = nx[1] > 0 ? fabs(ak) * sqrt(pw[1] / nx[1]) : 0.0;
-            if (!isfinite(last)) break;
-            if (last <= tol || (it >= 2 && last > 0.5 * prev && last <= floor_ok)) {
-                converged = true;
-                break;
-            }
-            const double beta = nx[0] / rzv;
-            rzv = nx[0];
-            axpy_kernel<<<vgrid, 256, 0, s>>>(pp, zz, beta, R, 1);          // p = z + beta p
+            FST_TRY(dots(rr, zz, alpha, alpha, 2));
+            pcg_step_end_kernel<<<1, 1, 0, s>>>(norms, pst, tol, floor_ok);
             FST_CHECK_LAUNCH();
+            pcg_axpy_kernel<<<vgrid, 256, 0, s>>>(pp, zz, pst, 2, R);                // p = z + beta p
+            FST_CHECK_LAUNCH();
+            if ((it + 1) % kCheckEvery == 0 || it + 1 == max_refine) {
+                FST_CUDA(cudaMemcpyAsync(&hs, pst, sizeof hs, cudaMemcpyDeviceToHost, s));
+                FST_CUDA(cudaStreamSynchronize(s));
+                if (hs.stop) break;
+            }
         }
+        steps = hs.steps;
+        last = hs.last;
+        converged = hs.stop == 1;
         if (!converged && isfinite(last) && last <= floor_ok) converged = true;
     }
     r.ms_refine = tm.stop();
