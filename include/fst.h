@@ -265,7 +265,8 @@ typedef struct {
     uint64_t seed;
 } fst_refit_item;
 
-/* Refit many models -- uneven ranks and point counts -- concurrently: `streams` (1..64) worker
+/* Refit many models (Sec. 5, eq. rand_core; Algorithm 2 per item) -- uneven ranks and point
+ * counts -- concurrently: `streams` (1..64) worker
  * host threads, each with its own non-blocking CUDA stream of the current device, take the
  * items in order and run fst_refit on them, so the launches of different instances overlap on
  * the GPU (small instances do not fill it alone).  Every result equals that of fst_refit on
