@@ -7,8 +7,9 @@ import, link or call it, and share no code with it.
 
 ``fst_oracle.c`` holds the evaluation (Sec. 2, eq. func_tuck / eq. sparse), the
 row sampler and the least-squares core refit (Sec. 5, eq. rand_core,
-Algorithm 2); ``fit.py`` holds the construction steps of Algorithm 1
-(interpolation, ST-HOSVD, sparse Legendre fit).  Parity status of each function
+Algorithm 2); ``mixing.py`` holds Algorithm 2's sign flip and fast mixing of the
+rows; ``fit.py`` holds the construction steps of Algorithm 1 (interpolation,
+ST-HOSVD, sparse Legendre fit).  Parity status of each function
 is stated in its docstring; every function here is pinned by a ``-m "not gpu"``
 test against closed forms, library routines or brute force, except where a
 docstring says "parity unpinned".
