@@ -277,6 +277,19 @@ typedef struct {
 fst_status fst_refit_batched(const fst_refit_item* items, int32_t count, fst_prec prec,
                              const fst_refit_opts* opts, int32_t streams, fst_refit_report* reports);
 
+/* Algorithm 2 with its mixing step (Sec. 5): the core minimising || S F D W alpha - S F D u ||
+ * over all Q points, W the Khatri-Rao rows of the points (eq. rand_core), D = diag(+-1) with
+ * D_q = -1 when bit 63 of the splitmix64 key of row q under seed_signs is set, F the
+ * normalised Walsh-Hadamard transform over the rows padded with zeros to N = 2^ceil(log2 Q)
+ * (the paper asks for a fast orthonormal mixing; this is the real one taken), and S the m rows
+ * of fst_sample_rows(seed_rows, N, m).  Mixing spreads the row leverage scores, so uniform
+ * sampling sees every direction of the design.  FP64 throughout, solved by the normal
+ * equations (Cholesky); F D W is materialised (N (R + 1) doubles of device memory), so this is
+ * for problems of that size.  xyz: device, 3Q doubles SoA; u: device, Q doubles; R <= m <= N
+ * (FST_ERANK below R).  Synchronous; the model's core is replaced. */
+fst_status fst_refit_mixed(fst_model* model, const double* xyz, const double* u, int64_t Q, int64_t m,
+                           uint64_t seed_signs, uint64_t seed_rows, fst_refit_report* report, fst_stream stream);
+
 /* The normal equations of the sampled problem alone (eq. rand_core restricted to the
  * rows idx): G = A^T A (device, R x R FP32 row-major; the lower triangle is written,
  * the upper triangle is unspecified) with A_{s,(i,j,k)} = w1_i w2_j w3_k at the points

@@ -130,7 +130,7 @@ struct SolveGraph {
 // Scratch of the refit, kept inside the model between calls.
 struct RefitScratch {
     DevBuf idx, U[3], b, G, G64, res, g, z, delta, alpha, norms, flag, Linv, LT, xw, yw, pcg, chol_ws, atr_part,
-        gram_err, pcg_state;
+        gram_err, pcg_state, mix;
     SolveGraph solve;
 };
 
@@ -191,6 +191,16 @@ fst_status allow_dynamic_smem(const void* func, size_t bytes);
 template <typename K>
 fst_status allow_smem(K* kernel, size_t bytes) {
     return allow_dynamic_smem(reinterpret_cast<const void*>(kernel), bytes);
+}
+
+// Key of row q under a seed: the (q+1)-th output of a splitmix64 stream started at the seed
+// (Steele, Lea, Flood, OOPSLA 2014).  The sampler keeps the rows with the smallest keys; the
+// mixed refit takes its random signs from the top bit.
+__host__ __device__ __forceinline__ uint64_t splitmix_key(uint64_t seed, uint64_t q) {
+    uint64_t z = seed + (q + 1ull) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
 }
 
 // Number of SMs of the current device (cached).

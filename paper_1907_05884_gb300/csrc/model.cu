@@ -146,6 +146,7 @@ static void free_device(fst_model* m) {
     s.atr_part.release();
     s.gram_err.release();
     s.pcg_state.release();
+    s.mix.release();
     s.xw.release();
     s.yw.release();
     s.pcg.release();

@@ -16,6 +16,7 @@
 // (FP64 G, FP64 Cholesky) is used.
 #include <math.h>
 
+#include <algorithm>
 #include <vector>
 #include <thread>
 #include <string>
@@ -928,6 +929,229 @@ extern "C" fst_status fst_refit_f64(fst_model* model, const double* xyz, const d
                                     const int64_t* idx, int64_t m, uint64_t seed, const fst_refit_opts* opts,
                                     fst_refit_report* report, fst_stream stream) {
     return refit_entry<double>(model, xyz, u, Q, idx, m, seed, FST_FP64, opts, report, (cudaStream_t)stream);
+}
+
+// ------------------------------------------------------------------ Algorithm 2 with mixing
+namespace fst {
+
+// Rows of the mixed system before the transform: WB[q] = D_q [w1 (x) w2 (x) w3 (y_q), u_q] for
+// q < Q (column (i r2 + j) r3 + k, then u), zero rows up to N; D_q = -1 when the top bit of
+// the row's key under the sign seed is set.
+__global__ void mix_rows_kernel(const double* __restrict__ U1, const double* __restrict__ U2,
+                                const double* __restrict__ U3, const double* __restrict__ b, int64_t Q, int64_t N,
+                                int r1, int r2, int r3, uint64_t seed, double* __restrict__ WB) {
+    const int R = r1 * r2 * r3, C = R + 1;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < N * C; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t q = e / C;
+        const int c = (int)(e - q * C);
+        double v = 0.0;
+        if (q < Q) {
+            if (c == R) {
+                v = b[q];
+            } else {
+                const int i = c / (r2 * r3), j = (c / r3) % r2, k = c % r3;
+                v = U1[q * r1 + i] * U2[q * r2 + j] * U3[q * r3 + k];
+            }
+            if (splitmix_key(seed, (uint64_t)q) >> 63) v = -v;
+        }
+        WB[e] = v;
+    }
+}
+
+// One stage of the normalised Walsh-Hadamard transform along the rows (stride h):
+// (a, b) -> (a + b, a - b) / sqrt(2) for rows i0 = (p / h) 2h + p % h and i0 + h.
+__global__ void fwht_stage_kernel(double* __restrict__ WB, int64_t N, int C, int64_t h) {
+    const double s = 0.70710678118654752440;
+    const int64_t pairs = N / 2;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < pairs * C;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p = e / C;
+        const int c = (int)(e - p * C);
+        const int64_t i0 = (p / h) * 2 * h + p % h, i1 = i0 + h;
+        const double a = WB[i0 * C + c], bb = WB[i1 * C + c];
+        WB[i0 * C + c] = (a + bb) * s;
+        WB[i1 * C + c] = (a - bb) * s;
+    }
+}
+
+// Lower triangle of E = A^T A over the sampled rows idx of WB (m x C, A = WB[idx]), in 32 x 32
+// tiles: E[0:R, 0:R] is G, row R holds h = A_u^T b.
+__global__ void __launch_bounds__(256) mixed_gram_kernel(const double* __restrict__ WB, int C,
+                                                         const int64_t* __restrict__ idx, int64_t m,
+                                                         double* __restrict__ E) {
+    __shared__ double a[32][33], bt[32][33];
+    int ti = 0;
+    {
+        const int t = blockIdx.x;
+        ti = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
+        while ((ti + 1) * (ti + 2) / 2 <= t) ++ti;
+        while (ti * (ti + 1) / 2 > t) --ti;
+    }
+    const int tj = blockIdx.x - ti * (ti + 1) / 2;
+    const int r0 = ti * 32, c0 = tj * 32;
+    const int tid = threadIdx.x, tr = tid >> 3, tc = (tid & 7) * 4;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int64_t s0 = 0; s0 < m; s0 += 32) {
+        for (int e = tid; e < 32 * 32; e += 256) {
+            const int rr = e >> 5, cc = e & 31;
+            const int64_t sidx = s0 + rr;
+            const double* row = sidx < m ? WB + idx[sidx] * (int64_t)C : nullptr;
+            a[rr][cc] = row && r0 + cc < C ? row[r0 + cc] : 0.0;
+            bt[rr][cc] = row && c0 + cc < C ? row[c0 + cc] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int k = 0; k < 32; ++k) {
+            const double x = a[k][tr];
+#pragma unroll
+            for (int y = 0; y < 4; ++y) acc[y] = fma(x, bt[k][tc + y], acc[y]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int y = 0; y < 4; ++y) {
+        const int r = r0 + tr, c = c0 + tc + y;
+        if (r < C && c < C && c <= r) E[(size_t)r * C + c] = acc[y];
+    }
+}
+
+// E (C x C lower) -> G (R x R lower) and h
+__global__ void split_gram_kernel(const double* __restrict__ E, int R, double* __restrict__ G, double* __restrict__ h) {
+    const int C = R + 1;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)R * R;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int r = (int)(e / R), c = (int)(e - (int64_t)r * R);
+        G[e] = c <= r ? E[(size_t)r * C + c] : 0.0;
+    }
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < R; c += gridDim.x * blockDim.x) h[c] = E[(size_t)R * C + c];
+}
+
+static fst_status refit_mixed_impl(fst_model* M, const double* xyz, const double* u, int64_t Q, int64_t m,
+                                   uint64_t seed_signs, uint64_t seed_rows, fst_refit_report* rep, cudaStream_t s) {
+    const int R = M->R();
+    const int C = R + 1;
+    int64_t N = 1;
+    while (N < Q) N *= 2;
+    RefitScratch& W = M->rs;
+    fst_refit_report r;
+    memset(&r, 0, sizeof r);
+    r.m = m;
+    EventTimer tm(s);
+    // 1. factor values of every point, the signed Khatri-Rao rows, the transform
+    FST_TRY(W.idx.ensure(sizeof(int64_t) * (size_t)Q));
+    int64_t* all = W.idx.as<int64_t>();
+    FST_TRY(sample_rows(0, Q, Q, all, s));       // m >= Q: every row, in order
+    double* U[3];
+    for (int k = 0; k < 3; ++k) {
+        FST_TRY(W.U[k].ensure(sizeof(double) * (size_t)Q * M->r[k]));
+        U[k] = W.U[k].as<double>();
+    }
+    FST_TRY(W.b.ensure(sizeof(double) * (size_t)Q));
+    FST_TRY(launch_factors<double>(M, xyz, Q, all, Q, u, U, W.b.as<double>(), s));
+    FST_TRY(W.mix.ensure(sizeof(double) * (size_t)N * C));
+    double* WB = W.mix.as<double>();
+    {
+        int64_t total = N * C;
+        int grid = (int)std::min<int64_t>((total + 255) / 256, 16LL * sm_count());
+        mix_rows_kernel<<<grid, 256, 0, s>>>(U[0], U[1], U[2], W.b.as<double>(), Q, N, M->r[0], M->r[1], M->r[2],
+                                             seed_signs, WB);
+        FST_CHECK_LAUNCH();
+        total = N / 2 * C;
+        grid = (int)std::min<int64_t>((total + 255) / 256, 16LL * sm_count());
+        for (int64_t h = 1; h < N; h *= 2) {
+            fwht_stage_kernel<<<grid < 1 ? 1 : grid, 256, 0, s>>>(WB, N, C, h);
+            FST_CHECK_LAUNCH();
+        }
+    }
+    r.ms_sample = tm.stop();
+    // 2. the sampled mixed rows and their normal equations
+    FST_TRY(W.res.ensure(sizeof(int64_t) * (size_t)m));
+    int64_t* idx = reinterpret_cast<int64_t*>(W.res.ptr);
+    FST_TRY(sample_rows(seed_rows, N, m, idx, s));
+    FST_TRY(W.G64.ensure(sizeof(double) * ((size_t)C * C + (size_t)R * R + R)));
+    double* E = W.G64.as<double>();
+    double* G = E + (size_t)C * C;
+    double* h = G + (size_t)R * R;
+    {
+        const int nt = (C + 31) / 32;
+        mixed_gram_kernel<<<nt * (nt + 1) / 2, 256, 0, s>>>(WB, C, idx, m, E);
+        FST_CHECK_LAUNCH();
+        split_gram_kernel<<<grid_for((int64_t)R * R, 256), 256, 0, s>>>(E, R, G, h);
+        FST_CHECK_LAUNCH();
+    }
+    r.ms_gram = tm.stop();
+    // 3. FP64 Cholesky and the two triangular solves: alpha = G^-1 h
+    FST_TRY(W.flag.ensure(4 * sizeof(int)));
+    int* flag = W.flag.as<int>();
+    FST_CUDA(cudaMemsetAsync(flag, 0, 2 * sizeof(int), s));
+    FST_TRY(cholesky_lower<double>(G, R, flag, W.chol_ws, s));
+    int hflag[2] = {0, 0};
+    FST_CUDA(cudaMemcpyAsync(hflag, flag, sizeof hflag, cudaMemcpyDeviceToHost, s));
+    FST_CUDA(cudaStreamSynchronize(s));
+    r.ms_cholesky = tm.stop();
+    if (hflag[1]) {
+        set_error("Cholesky: a bounded device wait expired (code %d)", hflag[1]);
+        if (rep) *rep = r;
+        return FST_ETIMEOUT;
+    }
+    if (hflag[0]) {
+        set_error("normal matrix of the mixed rows is not positive definite in FP64 (rank-deficient sample)");
+        if (rep) *rep = r;
+        return FST_ENOTSPD;
+    }
+    FST_TRY(W.Linv.ensure(3 * sizeof(double) * (size_t)((R + 63) / 64) * 64 * 64));
+    FST_TRY(chol_invert_diag<double>(G, R, W.Linv.as<double>(), s));
+    FST_TRY(W.LT.ensure(sizeof(double) * (size_t)R * R));
+    FST_TRY(chol_transpose<double>(G, R, W.LT.as<double>(), s));
+    FST_TRY(W.yw.ensure(sizeof(double) * (size_t)R));
+    FST_TRY(W.solve.sync.ensure(4 * sizeof(int)));
+    int* sync = W.solve.sync.as<int>();
+    FST_CUDA(cudaMemsetAsync(sync, 0, sizeof(int), s));
+    FST_TRY(chol_solve<double>(G, W.LT.as<double>(), W.Linv.as<double>(), R, h, W.yw.as<double>(), sync, s));
+    std::vector<double> ha(R);
+    int serr = 0;
+    FST_CUDA(cudaMemcpyAsync(ha.data(), h, sizeof(double) * R, cudaMemcpyDeviceToHost, s));
+    FST_CUDA(cudaMemcpyAsync(&serr, sync, sizeof(int), cudaMemcpyDeviceToHost, s));
+    FST_CUDA(cudaStreamSynchronize(s));
+    r.ms_refine = tm.stop();
+    if (serr) {
+        set_error("triangular solve: a bounded device wait expired");
+        if (rep) *rep = r;
+        return FST_ETIMEOUT;
+    }
+    for (int i = 0; i < R; ++i)
+        if (!isfinite(ha[i])) {
+            set_error("mixed refit produced a non-finite core");
+            if (rep) *rep = r;
+            return FST_ENOTSPD;
+        }
+    M->alpha = ha;
+    FST_TRY(model_upload_core(M));
+    if (rep) *rep = r;
+    return FST_OK;
+}
+
+}  // namespace fst
+
+extern "C" fst_status fst_refit_mixed(fst_model* model, const double* xyz, const double* u, int64_t Q, int64_t m,
+                                      uint64_t seed_signs, uint64_t seed_rows, fst_refit_report* report,
+                                      fst_stream stream) {
+    using namespace fst;
+    FST_REQUIRE(model != nullptr && xyz && u, "model, xyz or u is NULL");
+    FST_REQUIRE(Q > 0 && m > 0, "Q and m must be positive");
+    int64_t N = 1;
+    while (N < Q) N *= 2;
+    FST_REQUIRE(m <= N, "m = %lld exceeds the %lld mixed rows", (long long)m, (long long)N);
+    if (m < (int64_t)model->R()) {
+        set_error("m = %lld sampled rows < R = %d unknowns", (long long)m, model->R());
+        return FST_ERANK;
+    }
+    int dev = 0;
+    FST_CUDA(cudaGetDevice(&dev));
+    FST_REQUIRE(dev == model->device, "model lives on device %d, current device is %d", model->device, dev);
+    FST_REQUIRE(pointer_device(xyz) == dev && pointer_device(u) == dev, "xyz and u must be device memory");
+    std::lock_guard<std::mutex> lk(model->mu);
+    return refit_mixed_impl(model, xyz, u, Q, m, seed_signs, seed_rows, report, (cudaStream_t)stream);
 }
 
 // ------------------------------------------------------------------ normal matrix only

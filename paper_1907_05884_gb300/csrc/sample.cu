@@ -15,13 +15,6 @@
 
 namespace fst {
 
-__device__ __forceinline__ uint64_t splitmix_key(uint64_t seed, uint64_t q) {
-    uint64_t z = seed + (q + 1ull) * 0x9E3779B97F4A7C15ull;
-    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-    return z ^ (z >> 31);
-}
-
 struct SelectState {
     unsigned long long prefix;  // fixed high bits of the m-th smallest key
     unsigned long long mask;    // which bits of prefix are fixed

@@ -18,7 +18,7 @@ import numpy as np
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("what", choices=["gram", "eval", "refit", "sample", "batch", "serve", "fit", "chol",
-                                     "refit-batch"])
+                                     "refit-batch", "mixed"])
     ap.add_argument("--grid", type=int, default=64)
     ap.add_argument("--frac", type=float, default=0.05)
     ap.add_argument("--eps", type=float, default=1e-3)
@@ -47,6 +47,8 @@ def main():
         return batch(args)
     if args.what == "refit-batch":
         return refit_batch(args)
+    if args.what == "mixed":
+        return mixed(args)
     if args.what == "serve":
         return serve_loads(args)
     if args.what == "fit":
@@ -176,6 +178,52 @@ def refit_batch(args):
             torch.cuda.synchronize()
             line += f" streams{S}_ms={(time.perf_counter() - h0) * 1e3:.2f}"
         print(line, flush=True)
+
+
+def mixed(args):
+    """Algorithm 2 with and without its mixing step (Sec. 5; configuration-1 scale): --n points
+    (default 20,000; 90 % clustered in the band, so plain uniform sampling over-weights it) of a
+    sum of Gaussians, an orthonormal model of ranks --ranks (default 8^3) and degree --degree
+    (default 15).  For each m: the refit on m rows with mixing (fst_refit_mixed) and without
+    (fst_refit_f64 on m uniformly sampled points), and the change of the core when m grows by
+    R / 4 (the self-convergence of Fig. 5), each timed with CUDA events."""
+    import json
+    import torch
+    from paper_1907_05884_gb300 import fst, synth
+    Q = args.n if args.n != (1 << 22) else 20000
+    ranks = tuple(args.ranks) if tuple(args.ranks) != (24, 24, 24) else (8, 8, 8)
+    deg = args.degree if args.degree != 31 else 15
+    model = synth.random_model(ranks, (deg,) * 3, seed=51, density=0.8, orthonormal=True)
+    xyz_np = synth.points(Q, seed=52, clustered=0.9)
+    u_np, _ = synth.field_values(xyz_np, synth.field_spec(53, 5), seed=54)
+    xyz = torch.from_numpy(xyz_np).cuda()
+    u = torch.from_numpy(u_np).cuda()
+    R = model.R
+    M = fst.Model(model)
+    N = 1
+    while N < Q:
+        N *= 2
+    for mult in (1.25, 1.5, 2.0, 3.0, 4.0, 6.0, 8.0):
+        m1 = int(mult * R)
+        m2 = m1 + R // 4
+        if m2 > min(Q, N):
+            break
+        line = {"what": "mixed", "Q": Q, "N": N, "R": R, "m": m1}
+        for name, call in (("mixed", lambda mm: fst.refit_mixed(M, xyz, u, mm, 61, 62)),
+                           ("plain", lambda mm: M.refit(xyz, u, mm, seed=62, prec="fp64"))):
+            cores = []
+            for mm in (m1, m2):
+                M.set_core(model.alpha)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                call(mm)
+                e1.record()
+                torch.cuda.synchronize()
+                if mm == m1:
+                    line[f"{name}_ms"] = e0.elapsed_time(e1)
+                cores.append(M.read()["alpha"].ravel())
+            line[f"{name}_self_change"] = float(np.linalg.norm(cores[1] - cores[0]) / np.linalg.norm(cores[1]))
+        print(json.dumps(line), flush=True)
 
 
 def fit(args):

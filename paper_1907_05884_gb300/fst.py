@@ -118,6 +118,7 @@ def _load():
         "fst_refit": (I32, [P, P, P, I64, P, I64, U64, I32, P, P, P]),
         "fst_refit_f64": (I32, [P, P, P, I64, P, I64, U64, P, P, P]),
         "fst_refit_batched": (I32, [P, I32, I32, P, I32, P]),
+        "fst_refit_mixed": (I32, [P, P, P, I64, I64, U64, U64, P, P]),
         "fst_normal_matrix": (I32, [P, P, P, I64, P, I64, I32, P, P, P]),
         "fst_fit": (I32, [P, P, I64, P, P, P, I32, P, P, P, P, P]),
         "fst_cholesky_f32": (I32, [P, I32, P]),
@@ -285,6 +286,19 @@ class Model:
                                  C.c_uint64(seed & 0xFFFFFFFFFFFFFFFF), PREC[prec], C.byref(opts),
                                  C.byref(rep), _stream(stream)))
         return rep.as_dict()
+
+
+def refit_mixed(model, xyz, u, m: int, seed_signs: int, seed_rows: int, stream=None):
+    """fst_refit_mixed: Algorithm 2 with the sign flip and Walsh-Hadamard mixing over all Q rows
+    (FP64; xyz (3, Q) and u (Q,) float64 CUDA tensors).  Returns the report as a dict."""
+    import torch
+    assert xyz.is_cuda and xyz.dtype == torch.float64 and xyz.is_contiguous() and xyz.shape[0] == 3
+    assert u.is_cuda and u.dtype == torch.float64 and u.is_contiguous()
+    rep = RefitReport()
+    _check(lib.fst_refit_mixed(model._h, _dptr(xyz), _dptr(u), xyz.shape[1], int(m),
+                               C.c_uint64(seed_signs & 0xFFFFFFFFFFFFFFFF), C.c_uint64(seed_rows & 0xFFFFFFFFFFFFFFFF),
+                               C.byref(rep), _stream(stream)))
+    return rep.as_dict()
 
 
 def refit_batched(models, xyzs, us, ms, seeds, prec: str = "bf16", streams: int = 4, max_refine: int = 32,
