@@ -329,24 +329,30 @@ __global__ void __launch_bounds__(512) potrf_inv_kernel(float* G, int R, int k0,
     }
 }
 
-// L21 = A21 L11^-T for 64 panel rows per block (256 threads): 32-column block substitution,
-// X_d = (A_d - sum_{e<d} X_e L_de^T) Dinv_d^T.  Writes L21 (FP32) into G and the BF16 hi/lo
-// operand tiles of the trailing update (rows at or beyond R as zeros).
+// L21 = A21 L11^-T for kTrsmRows panel rows per block (256 threads): 32-column block
+// substitution, X_d = (A_d - sum_{e<d} X_e L_de^T) Dinv_d^T.  Writes L21 (FP32) into G and the
+// BF16 hi/lo operand tiles of the trailing update (rows at or beyond R as zeros).  Few rows a
+// block keep each block's chain short (the panel solve sits on the factorisation's critical
+// path) and spread the panel over more SMs.
+constexpr int kTrsmRows = 32;
+constexpr int kTrsmCQ = 256 / kTrsmRows;          // threads per row
+constexpr int kTrsmNJ = SUB / kTrsmCQ;            // columns of a 32-column block per thread
 __global__ void __launch_bounds__(256) trsm_pack_kernel(float* G, int R, int k0, const float* Dinv,
                                                         unsigned char* Lp) {
     extern __shared__ __align__(16) unsigned char dsm[];
-    float (*X)[AS] = reinterpret_cast<float (*)[AS]>(dsm);                                 // 64 rows
-    float (*L)[AS] = reinterpret_cast<float (*)[AS]>(dsm + sizeof(float) * 64 * AS);      // L11
-    float (*D)[SUB + 4] = reinterpret_cast<float (*)[SUB + 4]>(dsm + sizeof(float) * (64 + PB) * AS);
+    float (*X)[AS] = reinterpret_cast<float (*)[AS]>(dsm);                                        // panel rows
+    float (*L)[AS] = reinterpret_cast<float (*)[AS]>(dsm + sizeof(float) * kTrsmRows * AS);      // L11
+    float (*D)[SUB + 4] = reinterpret_cast<float (*)[SUB + 4]>(dsm + sizeof(float) * (kTrsmRows + PB) * AS);
     const int tid = threadIdx.x;
     const int t0 = k0 + PB;
-    const int r0 = blockIdx.x * 64;
+    const int r0 = blockIdx.x * kTrsmRows;
     const bool vec = (R & 3) == 0;
     {
-        // the 64 panel rows and L11: every load of a thread in flight at once
-        float4 xv[64 * (PB / 4) / 256], lv4[PB * (PB / 4) / 256];
+        // the panel rows and L11: every load of a thread in flight at once
+        constexpr int NX = kTrsmRows * (PB / 4) / 256, NL = PB * (PB / 4) / 256;
+        float4 xv[NX], lv4[NL];
 #pragma unroll
-        for (int u = 0; u < 64 * (PB / 4) / 256; ++u) {
+        for (int u = 0; u < NX; ++u) {
             const int e = tid + u * 256, r = e / (PB / 4), c4 = (e % (PB / 4)) * 4;
             const int g = t0 + r0 + r;
             const float* src = G + (size_t)g * R + k0 + c4;
@@ -354,38 +360,37 @@ __global__ void __launch_bounds__(256) trsm_pack_kernel(float* G, int R, int k0,
                            : vec ? *reinterpret_cast<const float4*>(src) : make_float4(src[0], src[1], src[2], src[3]);
         }
 #pragma unroll
-        for (int u = 0; u < PB * (PB / 4) / 256; ++u) {
+        for (int u = 0; u < NL; ++u) {
             const int e = tid + u * 256, r = e / (PB / 4), c4 = (e % (PB / 4)) * 4;
             const float* src = G + (size_t)(k0 + r) * R + k0 + c4;
             lv4[u] = vec ? *reinterpret_cast<const float4*>(src) : make_float4(src[0], src[1], src[2], src[3]);
         }
 #pragma unroll
-        for (int u = 0; u < 64 * (PB / 4) / 256; ++u) {
+        for (int u = 0; u < NX; ++u) {
             const int e = tid + u * 256;
             *reinterpret_cast<float4*>(&X[e / (PB / 4)][(e % (PB / 4)) * 4]) = xv[u];
         }
 #pragma unroll
-        for (int u = 0; u < PB * (PB / 4) / 256; ++u) {
+        for (int u = 0; u < NL; ++u) {
             const int e = tid + u * 256;
             *reinterpret_cast<float4*>(&L[e / (PB / 4)][(e % (PB / 4)) * 4]) = lv4[u];
         }
     }
     for (int e = tid; e < 4 * SUB * SUB; e += 256) D[e / SUB][e % SUB] = Dinv[e];
     __syncthreads();
-    // thread: row r = tid / 4 and the 8 columns cq + 4 j of the current 32-column block
-    // (interleaved, so the four threads of a row read four consecutive L rows: no bank
-    // conflicts)
-    const int r = tid >> 2, cq = tid & 3;
+    // thread: row r and the kTrsmNJ columns cq + kTrsmCQ j of the current 32-column block
+    // (interleaved, so the threads of a row read consecutive L rows: no bank conflicts)
+    const int r = tid / kTrsmCQ, cq = tid % kTrsmCQ;
     for (int d = 0; d < 4; ++d) {
         const int cb = d * SUB + cq;
-        float y[8];
+        float y[kTrsmNJ];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) y[j] = X[r][cb + 4 * j];
+        for (int j = 0; j < kTrsmNJ; ++j) y[j] = X[r][cb + kTrsmCQ * j];
         for (int k = 0; k < d * SUB; k += 4) {
             const float4 xk = *reinterpret_cast<const float4*>(&X[r][k]);
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const float4 lk = *reinterpret_cast<const float4*>(&L[cb + 4 * j][k]);
+            for (int j = 0; j < kTrsmNJ; ++j) {
+                const float4 lk = *reinterpret_cast<const float4*>(&L[cb + kTrsmCQ * j][k]);
                 y[j] = fmaf(-xk.x, lk.x, y[j]);
                 y[j] = fmaf(-xk.y, lk.y, y[j]);
                 y[j] = fmaf(-xk.z, lk.z, y[j]);
@@ -394,16 +399,16 @@ __global__ void __launch_bounds__(256) trsm_pack_kernel(float* G, int R, int k0,
         }
         __syncthreads();   // every thread has read X's block d before it is overwritten
 #pragma unroll
-        for (int j = 0; j < 8; ++j) X[r][cb + 4 * j] = y[j];
+        for (int j = 0; j < kTrsmNJ; ++j) X[r][cb + kTrsmCQ * j] = y[j];
         __syncthreads();
-        float xo[8];
+        float xo[kTrsmNJ];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) xo[j] = 0.f;
+        for (int j = 0; j < kTrsmNJ; ++j) xo[j] = 0.f;
         for (int t = 0; t < SUB; t += 4) {
             const float4 yv = *reinterpret_cast<const float4*>(&X[r][d * SUB + t]);
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const float4 dv = *reinterpret_cast<const float4*>(&D[cb + 4 * j][t]);
+            for (int j = 0; j < kTrsmNJ; ++j) {
+                const float4 dv = *reinterpret_cast<const float4*>(&D[cb + kTrsmCQ * j][t]);
                 xo[j] = fmaf(yv.x, dv.x, xo[j]);
                 xo[j] = fmaf(yv.y, dv.y, xo[j]);
                 xo[j] = fmaf(yv.z, dv.z, xo[j]);
@@ -412,14 +417,14 @@ __global__ void __launch_bounds__(256) trsm_pack_kernel(float* G, int R, int k0,
         }
         __syncthreads();
 #pragma unroll
-        for (int j = 0; j < 8; ++j) X[r][cb + 4 * j] = xo[j];
+        for (int j = 0; j < kTrsmNJ; ++j) X[r][cb + kTrsmCQ * j] = xo[j];
         __syncthreads();
     }
-    // write L21 to G and the packed operand rows
+    // write L21 to G and the packed operand rows: chunks of 8 columns, (PB / 8) / kTrsmCQ a thread
     const int g = t0 + r0 + r;
 #pragma unroll
-    for (int h = 0; h < 4; ++h) {
-        const int c0 = h * SUB + cq * 8;
+    for (int h = 0; h < PB / 8 / kTrsmCQ; ++h) {
+        const int c0 = (h * kTrsmCQ + cq) * 8;
         float v[8], lo[8];
 #pragma unroll
         for (int j = 0; j < 8; ++j) v[j] = g < R ? X[r][c0 + j] : 0.f;
@@ -681,7 +686,7 @@ static fst_status cholesky_lower_tc(float* G, int R, int* d_flag, const float* f
     unsigned char* Lp = ws_tail + 4 * SUB * SUB * sizeof(float);
     const size_t pstride = packed_panel_bytes(R);
     const size_t potrf_smem = sizeof(float) * (PB * AS + 4 * SUB * SUB);   // P: FS x PB, then the inverses
-    const size_t trsm_smem = sizeof(float) * ((64 + PB) * AS + 4 * SUB * (SUB + 4));
+    const size_t trsm_smem = sizeof(float) * ((kTrsmRows + PB) * AS + 4 * SUB * (SUB + 4));
     const size_t syrk_smem = kSyrkStages * 2 * kHalfBytes + 1024 + 1024;
     FST_TRY(allow_smem(potrf_inv_kernel, potrf_smem));
     FST_TRY(allow_smem(trsm_pack_kernel, trsm_smem));
@@ -700,7 +705,7 @@ static fst_status cholesky_lower_tc(float* G, int R, int* d_flag, const float* f
             ++npan;
             const int nt = (rest + PB - 1) / PB;
             unsigned char* Lpp = Lp + (size_t)p * pstride;
-            trsm_pack_kernel<<<2 * nt, 256, trsm_smem, s>>>(G, R, k0, Dinv, Lpp);
+            trsm_pack_kernel<<<(PB / kTrsmRows) * nt, 256, trsm_smem, s>>>(G, R, k0, Dinv, Lpp);
             FST_CHECK_LAUNCH();
             // the columns of the super-panel right of this panel
             int ncol = (K0 + SBW - (k0 + PB)) / PB;
