@@ -222,8 +222,10 @@ __global__ void __launch_bounds__(512) potrf_inv_kernel(float* G, int R, int k0,
 #pragma unroll 16
             for (int j = 0; j < FS; ++j) {
                 const float d = __shfl_sync(0xffffffffu, a[j], j);
-                const float sq = sqrtf(d);
-                const float inv = 1.f / sq;
+                // the pivot's reciprocal square root from the hardware approximation (a few
+                // ulp; the factor preconditions the conjugate gradients), its root as d / sqrt(d)
+                const float inv = rsqrtf(d);
+                const float sq = d * inv;
                 if (lane == j) {
                     dinv = inv;
                     piv = d;
