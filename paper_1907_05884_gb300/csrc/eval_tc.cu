@@ -90,16 +90,25 @@ CoreImage core_image_shape(const fst_model* m, int mode, int r3p, bool tc3 = fal
 }
 
 // Shared memory of a factor-step bucket with these largest images.
-// One worker group's operand buffer: the Legendre tile (BF16 hi + lo, 128 x KPF), later
-// overwritten by the w1 operand (parts x 128 x KB).
-__host__ __device__ inline size_t tc3_group_bytes(int kb_max, int kpf_max, int parts) {
-    const size_t p = (size_t)2 * 128 * kpf_max * 2, w = (size_t)parts * 128 * kb_max;
+// One worker group's operand buffers: the Legendre tile (BF16 hi + lo, 128 x KPF), later
+// overwritten by the w1 operand (parts x 128 x KB), and with nbuf = 2 a second Legendre tile,
+// so that two modes go to the tensor cores in one round trip.
+__host__ __device__ inline size_t tc3_pbytes(int kpf_max) { return (size_t)2 * 128 * kpf_max * 2; }
+__host__ __device__ inline size_t tc3_buf0_bytes(int kb_max, int kpf_max, int parts) {
+    const size_t p = tc3_pbytes(kpf_max), w = (size_t)parts * 128 * kb_max;
     return p > w ? p : w;
 }
-// Shared memory of a factor-step bucket: barriers, the core and factor images, and one
-// operand buffer for each of the three worker groups.
-size_t tc3_smem(size_t core_max, int kb_max, int kpf_max, int parts) {
-    return 1024 + kBarBytes + core_max + 3 * tc3_group_bytes(kb_max, kpf_max, parts);
+__host__ __device__ inline size_t tc3_group_bytes(int kb_max, int kpf_max, int parts, int nbuf) {
+    return tc3_buf0_bytes(kb_max, kpf_max, parts) + (nbuf == 2 ? tc3_pbytes(kpf_max) : 0);
+}
+// Shared memory of a factor-step bucket: barriers, the core and factor images, and the operand
+// buffers of the three worker groups.
+size_t tc3_smem(size_t core_max, int kb_max, int kpf_max, int parts, int nbuf) {
+    return 1024 + kBarBytes + core_max + 3 * tc3_group_bytes(kb_max, kpf_max, parts, nbuf);
+}
+// Two Legendre buffers per group when they fit.
+int tc3_nbuf(size_t core_max, int kb_max, int kpf_max, int parts) {
+    return tc3_smem(core_max, kb_max, kpf_max, parts, 2) <= 227 * 1024 ? 2 : 1;
 }
 
 // The factor-step variant can serve BF16 / BF16X3 contractions with degrees below 64
@@ -107,7 +116,7 @@ size_t tc3_smem(size_t core_max, int kb_max, int kpf_max, int parts) {
 bool tc3_feasible(const fst_model* m, int mode, int r3p) {
     if (mode == eTF32 || kpf_of(m) > 64) return false;
     const CoreImage c = core_image_shape(m, mode, r3p, true);
-    return tc3_smem((c.bytes + 1023) & ~(size_t)1023, c.kb, c.kpf, c.parts) <= 227 * 1024;
+    return tc3_smem((c.bytes + 1023) & ~(size_t)1023, c.kb, c.kpf, c.parts, 1) <= 227 * 1024;
 }
 
 // Autotune table: per device and size class (mode, rank bound, r3 padding, Legendre K) the
@@ -563,8 +572,8 @@ template <int MODE, int R3P, int RM>
 __global__ void __launch_bounds__(kThreads3, 1)
 eval_tc3_kernel(const TcItem* __restrict__ items, const TcUnit* __restrict__ units, const int* __restrict__ cta_start,
                 int nunits, int* unit_ctr,
-                int core_max, int kb_max, int kpf_max, const float* __restrict__ xyz_ov, float* __restrict__ out_ov,
-                int* __restrict__ err) {
+                int core_max, int kb_max, int kpf_max, int nbuf, const float* __restrict__ xyz_ov,
+                float* __restrict__ out_ov, int* __restrict__ err) {
     constexpr int JC = jc3_for(R3P);
     constexpr int NC = JC * R3P;
     constexpr int NCP = (NC + 15) / 16 * 16;
@@ -579,7 +588,8 @@ eval_tc3_kernel(const TcItem* __restrict__ items, const TcUnit* __restrict__ uni
     uint64_t* drain = bars + 2 * kGroups3;        // [3]
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + kGroups3);
     unsigned char* core = smem + kBarBytes;
-    const size_t gbytes = tc3_group_bytes(kb_max, kpf_max, MODE == eBF16X3 ? 2 : 1);
+    const size_t gbytes = tc3_group_bytes(kb_max, kpf_max, MODE == eBF16X3 ? 2 : 1, nbuf);
+    const uint32_t buf1 = (uint32_t)tc3_buf0_bytes(kb_max, kpf_max, MODE == eBF16X3 ? 2 : 1);
     unsigned char* gbuf = core + core_max;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -707,66 +717,79 @@ eval_tc3_kernel(const TcItem* __restrict__ items, const TcUnit* __restrict__ uni
 #pragma unroll
                 for (int k = 0; k < 3; ++k) nxt[k] = ok2 ? X[k * n + q2] : 0.f;
             }
-            // Legendre tiles of the three modes, one after the other through P
+            // Legendre tiles of the three modes: with two buffers modes 0 and 1 go to the tensor
+            // cores in one round trip and mode 2 in a second, else one mode a round trip
+            const int nsteps = nbuf == 2 ? 2 : 3;
 #pragma unroll 1
-            for (int k = 0; k < 3; ++k) {
-                const float x = tt[k];
-                const int pe = a.pe[k];
-                // monic Legendre polynomials q_d = L_d / k_d (k_d the leading coefficient of L_d,
-                // folded into the factor coefficients): q_d = x q_{d-1} - (d-1)^2 / ((2d-1)(2d-3))
-                // q_{d-2}, two operations a degree, constants folded into the unrolled code
-                float Lm = 1.f, L = x;
+            for (int st = 0; st < nsteps; ++st) {
+                const int kfirst = nbuf == 2 ? 2 * st : st;
+                const int kcount = nbuf == 2 && st == 0 ? 2 : 1;
+#pragma unroll 1
+                for (int kk = 0; kk < kcount; ++kk) {
+                    const int k = kfirst + kk;
+                    unsigned char* Pb = P + (kk ? buf1 : 0u);
+                    const float x = k == 0 ? tt[0] : k == 1 ? tt[1] : tt[2];
+                    const int pe = a.pe[k];
+                    // monic Legendre polynomials q_d = L_d / k_d (k_d the leading coefficient of L_d,
+                    // folded into the factor coefficients): q_d = x q_{d-1} - (d-1)^2 / ((2d-1)(2d-3))
+                    // q_{d-2}, two operations a degree, constants folded into the unrolled code
+                    float Lm = 1.f, L = x;
 #pragma unroll
-                for (int c8 = 0; c8 < 8; ++c8) {
-                    if (c8 * 8 >= I.kpf) break;
-                    float v[8];
+                    for (int c8 = 0; c8 < 8; ++c8) {
+                        if (c8 * 8 >= I.kpf) break;
+                        float v[8];
 #pragma unroll
-                    for (int e = 0; e < 8; ++e) {
-                        const int d = c8 * 8 + e;
-                        float val;
-                        if (d == 0) {
-                            val = 1.f;
-                        } else if (d == 1) {
-                            val = x;
-                        } else {
-                            const float gd = float((d - 1) * (d - 1)) / float((2 * d - 1) * (2 * d - 3));
-                            const float Ln = fmaf(x, L, -gd * Lm);
-                            Lm = L;
-                            L = Ln;
-                            val = Ln;
+                        for (int e = 0; e < 8; ++e) {
+                            const int d = c8 * 8 + e;
+                            float val;
+                            if (d == 0) {
+                                val = 1.f;
+                            } else if (d == 1) {
+                                val = x;
+                            } else {
+                                const float gd = float((d - 1) * (d - 1)) / float((2 * d - 1) * (2 * d - 3));
+                                const float Ln = fmaf(x, L, -gd * Lm);
+                                Lm = L;
+                                L = Ln;
+                                val = Ln;
+                            }
+                            v[e] = d < pe ? val : 0.f;
                         }
-                        v[e] = d < pe ? val : 0.f;
-                    }
-                    const uint32_t off = tc::kmajor_offset(row, c8 * 16, KPB);
-                    uint32_t hw[4], lw[4];
+                        const uint32_t off = tc::kmajor_offset(row, c8 * 16, KPB);
+                        uint32_t hw[4], lw[4];
 #pragma unroll
-                    for (int e = 0; e < 4; ++e) split2_bf16(v[2 * e], v[2 * e + 1], hw[e], lw[e]);
-                    *reinterpret_cast<uint4*>(P + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-                    *reinterpret_cast<uint4*>(P + 128 * KPB + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+                        for (int e = 0; e < 4; ++e) split2_bf16(v[2 * e], v[2 * e + 1], hw[e], lw[e]);
+                        *reinterpret_cast<uint4*>(Pb + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+                        *reinterpret_cast<uint4*>(Pb + 128 * KPB + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+                    }
                 }
                 tc::fence_async_smem();
                 handoff();
                 if (issuer) {
                     wait(&w_bar[g], nw, 32);
                     tc::fence_after_sync();
-                    const uint32_t wb = core_u32 + (uint32_t)I.fac_off + (uint32_t)k * 2u * wbytes;
-                    const uint32_t d = tcol + 32u * k;
-                    for (int ks = 0; ks < I.kpf / 16; ++ks) {
-                        const uint32_t ko = ks * 256;
-                        const uint64_t ah = tc::make_desc(p_u32 + ko, 128, SBOP);
-                        const uint64_t al = tc::make_desc(p_u32 + 128 * KPB + ko, 128, SBOP);
-                        const uint64_t bh = tc::make_desc(wb + ko, 128, SBOP);
-                        const uint64_t bl = tc::make_desc(wb + wbytes + ko, 128, SBOP);
-                        tc::mma_bf16(d, ah, bh, idesc_f, ks > 0);
-                        tc::mma_bf16(d, ah, bl, idesc_f, 1u);
-                        tc::mma_bf16(d, al, bh, idesc_f, 1u);
+                    for (int kk = 0; kk < kcount; ++kk) {
+                        const int k = kfirst + kk;
+                        const uint32_t pa = p_u32 + (kk ? buf1 : 0u);
+                        const uint32_t wb = core_u32 + (uint32_t)I.fac_off + (uint32_t)k * 2u * wbytes;
+                        const uint32_t d = tcol + 32u * k;
+                        for (int ks = 0; ks < I.kpf / 16; ++ks) {
+                            const uint32_t ko = ks * 256;
+                            const uint64_t ah = tc::make_desc(pa + ko, 128, SBOP);
+                            const uint64_t al = tc::make_desc(pa + 128 * KPB + ko, 128, SBOP);
+                            const uint64_t bh = tc::make_desc(wb + ko, 128, SBOP);
+                            const uint64_t bl = tc::make_desc(wb + wbytes + ko, 128, SBOP);
+                            tc::mma_bf16(d, ah, bh, idesc_f, ks > 0);
+                            tc::mma_bf16(d, ah, bl, idesc_f, 1u);
+                            tc::mma_bf16(d, al, bh, idesc_f, 1u);
+                        }
                     }
                     tc::mma_commit(&m_bar[g]);
                     issued = true;
                 } else if (sub == 0) {
                     ++nw;    // the issuer's lanes track the same phase count
                 }
-                wait(&m_bar[g], nm, 64);      // U_k in TMEM, P free
+                wait(&m_bar[g], nm, 64);      // the step's U blocks in TMEM, the buffers free
                 tc::fence_after_sync();
                 converge();
             }
@@ -898,6 +921,7 @@ struct Bucket {
     int mode = 0, r3p = 8, rm = 8;
     bool tc3 = false;            // factor step on the tensor cores (eval_tc3_kernel)
     int kpf_max = 16;
+    int nbuf = 1;                // Legendre buffers per worker group (factor-step variant)
     std::vector<TcItem> items;
     std::vector<TcUnit> units;
     std::vector<int> cta_start;
@@ -963,7 +987,8 @@ fst_status build_buckets(const std::vector<HostItem>& hitems, int mode, std::vec
             tile_cost.push_back(fac + (double)ci.nchunks * ci.ncp * (PARTS == 2 ? 1.5 : 1.0) / 64.0);
             B.items.push_back(it);
         }
-        B.smem = B.tc3 ? tc3_smem(B.core_max, B.kb_max, B.kpf_max, PARTS)
+        if (B.tc3) B.nbuf = tc3_nbuf(B.core_max, B.kb_max, B.kpf_max, PARTS);
+        B.smem = B.tc3 ? tc3_smem(B.core_max, B.kb_max, B.kpf_max, PARTS, B.nbuf)
                        : 1024 + kBarBytes + B.core_max + (size_t)kGroups * PARTS * 128 * B.kb_max + tab_max + 16;
         if (B.smem > 227 * 1024) {
             set_error("model too large for the tensor-core evaluator (%zu bytes of shared memory)", B.smem);
@@ -1062,7 +1087,7 @@ fst_status launch_bucket_tc3_t(const Bucket& B, const unsigned char* dimg, int* 
     kern<<<B.grid, kThreads3, B.smem, s>>>(reinterpret_cast<const TcItem*>(dimg + B.items_off),
                                            reinterpret_cast<const TcUnit*>(dimg + B.units_off),
                                            reinterpret_cast<const int*>(dimg + B.cta_off), (int)B.units.size(), ctr,
-                                           B.core_max, B.kb_max, B.kpf_max, ov.xyz, ov.out, err);
+                                           B.core_max, B.kb_max, B.kpf_max, B.nbuf, ov.xyz, ov.out, err);
     FST_CHECK_LAUNCH();
     return FST_OK;
 }
