@@ -111,10 +111,10 @@ int tc3_nbuf(size_t core_max, int kb_max, int kpf_max, int parts) {
     return tc3_smem(core_max, kb_max, kpf_max, parts, 2) <= 227 * 1024 ? 2 : 1;
 }
 
-// The factor-step variant can serve BF16 / BF16X3 contractions with degrees below 64
+// The factor-step variant can serve contractions (TF32, BF16, BF16X3) with degrees below 64
 // whose images fit the shared memory.
 bool tc3_feasible(const fst_model* m, int mode, int r3p) {
-    if (mode == eTF32 || kpf_of(m) > 64) return false;
+    if (kpf_of(m) > 64) return false;
     const CoreImage c = core_image_shape(m, mode, r3p, true);
     return tc3_smem((c.bytes + 1023) & ~(size_t)1023, c.kb, c.kpf, c.parts, 1) <= 227 * 1024;
 }
@@ -666,7 +666,7 @@ eval_tc3_kernel(const TcItem* __restrict__ items, const TcUnit* __restrict__ uni
             tc::fence_after_sync();
             cur = U.item;
         }
-        const int KB = I.kp * 2;                   // contraction K bytes (BF16)
+        const int KB = I.kp * (MODE == eTF32 ? 4 : 2);   // contraction K bytes
         const int SBO = (KB / 16) * 128;
         const int abytes = 128 * KB;
         const int KPB = I.kpf * 2;                 // Legendre row bytes (BF16)
@@ -675,7 +675,7 @@ eval_tc3_kernel(const TcItem* __restrict__ items, const TcUnit* __restrict__ uni
         const long long n = I.n;
         const float* X = xyz_ov ? xyz_ov : I.xyz;
         // issuer constants
-        constexpr uint32_t idesc_c = tc::idesc_bf16(128, NCP);
+        constexpr uint32_t idesc_c = MODE == eTF32 ? tc::idesc_tf32(128, NCP) : tc::idesc_bf16(128, NCP);
         constexpr uint32_t idesc_f = tc::idesc_bf16(128, kFacRows);
         const uint32_t chunk_bytes = (uint32_t)(NCP * KB);
         const uint32_t SBOP = (uint32_t)(KPB / 16) * 128;
@@ -686,6 +686,10 @@ eval_tc3_kernel(const TcItem* __restrict__ items, const TcUnit* __restrict__ uni
                 const uint32_t ko = ks * 256;
                 const uint64_t ad = tc::make_desc(p_u32 + ko, 128, SBO);
                 const uint64_t bd = tc::make_desc(bb + ko, 128, SBO);
+                if (MODE == eTF32) {
+                    tc::mma_tf32(tcol, ad, bd, idesc_c, ks > 0);
+                    continue;
+                }
                 tc::mma_bf16(tcol, ad, bd, idesc_c, ks > 0);
                 if (MODE == eBF16X3) {
                     const uint64_t al = tc::make_desc(p_u32 + abytes + ko, 128, SBO);
@@ -805,6 +809,21 @@ eval_tc3_kernel(const TcItem* __restrict__ items, const TcUnit* __restrict__ uni
                 tc::tmem_wait_ld();
 #pragma unroll
                 for (int e = 0; e < RM; ++e) u3[e] = e < a.r[2] ? u3[e] : 0.f;
+                if (MODE == eTF32) {
+                    // TF32 operand: four elements a 16-byte chunk
+#pragma unroll
+                    for (int c16 = 0; c16 < 8; ++c16) {
+                        if (c16 * 16 >= KB) break;
+                        const uint32_t off = tc::kmajor_offset(row, c16 * 16, KB);
+                        uint32_t v4[4];
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const int i = c16 * 4 + e;
+                            v4[e] = tf32_dev(i < r1 && i < RM ? w1[i < RM ? i : 0] : 0.f);
+                        }
+                        *reinterpret_cast<uint4*>(P + off) = make_uint4(v4[0], v4[1], v4[2], v4[3]);
+                    }
+                } else
 #pragma unroll
                 for (int c16 = 0; c16 < 4; ++c16) {
                     if (c16 * 16 >= KB) break;
@@ -1105,6 +1124,7 @@ fst_status launch_bucket_tc3_m(const Bucket& B, const unsigned char* dimg, int* 
 
 fst_status launch_bucket(const Bucket& B, const unsigned char* dimg, int* err, cudaStream_t s, Overrides ov) {
     if (B.tc3) {
+        if (B.mode == eTF32) return launch_bucket_tc3_m<eTF32>(B, dimg, err, s, ov);
         if (B.mode == eBF16) return launch_bucket_tc3_m<eBF16>(B, dimg, err, s, ov);
         return launch_bucket_tc3_m<eBF16X3>(B, dimg, err, s, ov);
     }

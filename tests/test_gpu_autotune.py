@@ -9,7 +9,7 @@ from gpu_util import rel_l2, cuda_tensor
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"bf16x3": 3e-5, "bf16": 1e-2}
+TOL = {"bf16x3": 3e-5, "bf16": 1e-2, "tf32": 2e-3}
 
 
 @pytest.fixture(scope="module")
@@ -20,7 +20,7 @@ def F():
     return fst
 
 
-@pytest.mark.parametrize("prec", ["bf16x3", "bf16"])
+@pytest.mark.parametrize("prec", ["bf16x3", "bf16", "tf32"])
 @pytest.mark.parametrize("r,p", [((24, 24, 24), (31, 31, 31)), ((6, 11, 9), (20, 63, 9)), ((5, 4, 3), (8, 8, 8))])
 def test_autotune_variants_match_oracle(F, oracle_lib, prec, r, p):
     import torch
