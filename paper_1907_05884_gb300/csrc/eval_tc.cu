@@ -951,7 +951,6 @@ struct Bucket {
 
 fst_status build_buckets(const std::vector<HostItem>& hitems, int mode, std::vector<Bucket>& out) {
     out.clear();
-    const int ES = mode == eTF32 ? 4 : 2;
     const int PARTS = mode == eBF16X3 ? 2 : 1;
     const int sms = sm_count();
     std::vector<std::vector<size_t>> members;

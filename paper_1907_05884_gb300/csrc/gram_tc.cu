@@ -112,7 +112,6 @@ gram_tc_kernel(const float* __restrict__ PT, const float* __restrict__ U3T, int6
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int R = r1 * r2 * r3;
-    const int npairs = r1 * r2;
     const int nT = (R + kTile - 1) / kTile;
     const long long ntiles = (long long)nT * (nT + 1) / 2;
     const int nK = (int)((m + C::KC - 1) / C::KC);
@@ -259,7 +258,6 @@ gram_tc_kernel(const float* __restrict__ PT, const float* __restrict__ U3T, int6
                 const float* P = stg0 + buf * stg_floats;
                 const float* U3s = P + 2 * halfp * C::PSTRIDE;
                 unsigned char* sbase = smem + st * C::STAGE_BYTES;
-                const int kl = lane & 7, cl = lane >> 3;
                 for (int ti_ = 0; ti_ < kMaxTasks; ++ti_) {
                     const int task = warp + ti_ * kProducerWarps;
                     if (task >= ntasks) break;

@@ -48,11 +48,9 @@ __global__ void select_hist_kernel(uint64_t seed, int64_t Q, int pass, const Sel
 
 // One block: find the digit holding the rank-th key, fix it, clear the histogram.
 __global__ void select_pick_kernel(int pass, SelectState* st, unsigned int* hist) {
-    __shared__ unsigned long long part[kBins / 64];
-    __shared__ int found;
-    const int t = threadIdx.x;   // blockDim.x == 32 warps' worth of 64 bins each is too many; use 32 threads
-    if (t == 0) found = -1;
-    // 32 threads, each owns 64 consecutive bins
+    __shared__ unsigned long long part[32];
+    const int t = threadIdx.x;   // launched with 32 threads
+    // each thread owns kBins / 32 consecutive bins
     unsigned long long sum = 0;
     for (int i = 0; i < kBins / 32; ++i) sum += hist[t * (kBins / 32) + i];
     part[t] = sum;
@@ -76,7 +74,6 @@ __global__ void select_pick_kernel(int pass, SelectState* st, unsigned int* hist
             st->prefix |= ((unsigned long long)digit) << shift;
             st->mask |= dmask << shift;
             st->rank = rank - before;
-            found = digit;
         }
     }
     __syncthreads();
