@@ -126,7 +126,7 @@ def gpu_index_for_smi():
 
 
 # ----------------------------------------------------------------------------- peaks
-GRAM_PK_BF16_TRAFFIC = 41.62e9 + 0.3798e9
+GRAM_PK_BF16_TRAFFIC = 13.94e9 + 0.3565e9
 
 
 def measured_peaks():

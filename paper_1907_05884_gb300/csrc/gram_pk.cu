@@ -100,6 +100,8 @@ __global__ void __launch_bounds__(256) pack_kr_kernel(const float* __restrict__ 
     }
 }
 
+constexpr int kStripP = 12;   // super-tile columns of a strip (about sqrt of the CTA count)
+
 template <int MODE>
 __global__ void __launch_bounds__(kThreadsP, 1)
 gram_pk_kernel(const unsigned char* __restrict__ pk, int R, int nrt, int nkc, float* __restrict__ G,
@@ -140,12 +142,33 @@ gram_pk_kernel(const unsigned char* __restrict__ pk, int R, int nrt, int nkc, fl
         *abort_flag = 1;
         atomicOr(err, code);
     };
+    // Super-tile t of the lower triangle, in strips of kStripP columns: strip s holds the tiles
+    // with tj in [s S, s S + W), first its triangle (rows s S .. s S + W - 1), then W tiles a
+    // row below.  The 152 tiles a wave of CTAs works on then span about 12 rows and 12 columns,
+    // so a wave streams about half of the operand's row blocks instead of all of them.
     auto tile_of = [&](long long t, int& ti, int& tj) {
-        int x = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
-        while ((long long)(x + 1) * (x + 2) / 2 <= t) ++x;
-        while ((long long)x * (x + 1) / 2 > t) --x;
-        ti = x;
-        tj = (int)(t - (long long)x * (x + 1) / 2);
+        int s0 = 0;
+        for (;;) {
+            const int W = nT - s0 < kStripP ? nT - s0 : kStripP;
+            const long long tri = (long long)W * (W + 1) / 2;
+            const long long cnt = tri + (long long)(nT - s0 - W) * W;
+            if (t < cnt) {
+                if (t < tri) {
+                    int x = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+                    while ((long long)(x + 1) * (x + 2) / 2 <= t) ++x;
+                    while ((long long)x * (x + 1) / 2 > t) --x;
+                    ti = s0 + x;
+                    tj = s0 + (int)(t - (long long)x * (x + 1) / 2);
+                } else {
+                    const long long u = t - tri;
+                    ti = s0 + W + (int)(u / W);
+                    tj = s0 + (int)(u % W);
+                }
+                return;
+            }
+            t -= cnt;
+            s0 += W;
+        }
     };
 
     if (warp == 0) {
