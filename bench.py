@@ -4,9 +4,13 @@
 One step = the randomized least-squares refit of the core on m = 8R rows sampled
 from the Q data points (Sec. 5, eq. rand_core, Algorithm 2 with uniform sampling),
 followed by the evaluation of the refitted model at all Q points (Sec. 6,
-reconstruction by evaluating the basis functions).  Workload: Q = 2^24
-unstructured points (70% uniform, 30% in a band around a curved tanh front),
-ranks 24^3, Legendre degree <= 31, m = 8R = 110,592.
+reconstruction by evaluating the basis functions).
+
+Workloads (``--workload``):
+  precision_64M (default): Q = 2^26 unstructured points (70% uniform, 30% in a band
+      around a curved tanh front), ranks 24^3, Legendre degree <= 63, m = 8R = 110,592;
+      accuracy against the FP64 oracle on the first 2^20 points;
+  fp32_16M: Q = 2^24 points, degree <= 31, otherwise the same.
 
 Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle instead,
 on a bounded sample of the same workload, extrapolated to the same unit.
@@ -31,10 +35,13 @@ sys.path.insert(0, str(ROOT))
 
 METRIC = "Mpoints/s fst_eval + LS refit ms on 1 GB300 at stated rel-L2 vs FP64 oracle"
 UNIT = "Mpoints/s"
-WORKLOAD = "fp32_16M"
 RANKS = (24, 24, 24)
-DEGREE = 31
 OVERSAMPLE = 8
+WORKLOADS = {
+    "precision_64M": {"Q": 1 << 26, "degree": 63, "seed": 303},
+    "fp32_16M": {"Q": 1 << 24, "degree": 31, "seed": 2024},
+}
+ACCURACY_POINTS = 1 << 20       # rel-L2 of the evaluation against the oracle on the first 2^20 points
 
 
 def parse():
@@ -48,24 +55,30 @@ def parse():
                          "refinement with FP64-accumulated residuals makes the core independent of it")
     ap.add_argument("--eval-prec", default="bf16x3", help="evaluation precision: fp32, tf32, bf16, bf16x3")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--Q", type=int, default=1 << 24)
-    return ap.parse_args()
+    ap.add_argument("--workload", default="precision_64M", choices=sorted(WORKLOADS))
+    ap.add_argument("--Q", type=int, default=0, help="point count (default: the workload's)")
+    a = ap.parse_args()
+    w = WORKLOADS[a.workload]
+    a.Q = a.Q or w["Q"]
+    a.degree = w["degree"]
+    a.seed = w["seed"]
+    return a
 
 
 # ----------------------------------------------------------------------------- workload
-def make_workload(Q: int, seed: int):
+def make_workload(Q: int, seed: int, degree: int):
     from paper_1907_05884_gb300 import synth
     xyz = synth.points(Q, seed=seed + 1, clustered=0.3, dtype=np.float32)
     u, _ = synth.field_values(xyz, synth.field_spec(seed + 2, 20), seed=seed + 3)
-    model = synth.random_model(RANKS, (DEGREE,) * 3, seed=seed + 4, orthonormal=True)
+    model = synth.random_model(RANKS, (degree,) * 3, seed=seed + 4, orthonormal=True)
     return xyz, u.astype(np.float32), model
 
 
-def workload_config(Q, R, m, prec, eval_prec):
-    return {"workload": f"{WORKLOAD}: Q={Q} unstructured points in [-1,1]^3 (70% uniform, 30% in a 0.05 band "
-                        f"around a tanh front), 20 Gaussians + 1e-4 noise, ranks {RANKS}, degree <= {DEGREE}, "
+def workload_config(name, Q, R, m, degree, prec, eval_prec):
+    return {"workload": f"{name}: Q={Q} unstructured points in [-1,1]^3 (70% uniform, 30% in a 0.05 band "
+                        f"around a tanh front), 20 Gaussians + 1e-4 noise, ranks {RANKS}, degree <= {degree}, "
                         f"refit on m = {OVERSAMPLE}R = {m} sampled rows, then evaluation at all Q points",
-            "Q": Q, "ranks": list(RANKS), "R": R, "degree": DEGREE, "m": m, "refit_prec": prec,
+            "Q": Q, "ranks": list(RANKS), "R": R, "degree": degree, "m": m, "refit_prec": prec,
             "eval_prec": eval_prec, "model": "seeded synthetic model with orthonormal factor functions",
             "l2": "inputs larger than L2: xyz + u = 16 B/point = %.0f MB per step" % (16 * Q / 1e6)}
 
@@ -127,6 +140,9 @@ def gpu_index_for_smi():
 
 # ----------------------------------------------------------------------------- peaks
 GRAM_PK_BF16_TRAFFIC = 13.94e9 + 0.3565e9
+# DRAM bytes of one evaluation launch, keyed by (precision, points, degree), from one ncu
+# capture of the current kernel (a smaller case scaled by the point count where stated)
+EVAL_TRAFFIC: dict = {}
 
 
 def measured_peaks():
@@ -144,35 +160,38 @@ def fp32_alu_peak_tflops(sm_mhz: float, sms: int) -> float:
 
 
 # ----------------------------------------------------------------------------- oracle timing
-def oracle_sample_timing(model, xyz, u, Q, m, nthreads, budget_scale=1.0):
-    """Time the oracle on a bounded sample of the step and extrapolate to the full step.
-    Returns (seconds per full step, description)."""
+def oracle_sample_timing(model, xyz, u, Q, m, nthreads, n_eval=8192, m_rows=16, R_chol=768):
+    """Time the oracle on a bounded sample of the step and extrapolate to the full step:
+    evaluation on ``n_eval`` points (per-point rate x Q), the normal equations of ``m_rows``
+    sampled rows at the full R (per-row rate x m), and a Cholesky factorisation at
+    ``R_chol`` (x (R / R_chol)^3).  Returns (seconds per full step, parts, description)."""
     import oracle
     R = model.R
-    n_eval = int(8192 * budget_scale)
-    sel = np.arange(n_eval)
-    xs = np.ascontiguousarray(xyz[:, sel].astype(np.float64))
+    xs = np.ascontiguousarray(xyz[:, :n_eval].astype(np.float64))
     t0 = time.perf_counter()
     oracle.eval_points(model, xs, nthreads=nthreads)
     t_eval = (time.perf_counter() - t0) / n_eval * Q
-    m_s = max(4, int(16 * budget_scale))
-    idx = np.arange(m_s, dtype=np.int64)
-    x64 = np.ascontiguousarray(xyz[:, :m_s].astype(np.float64))
-    u64 = np.ascontiguousarray(u[:m_s].astype(np.float64))
+    idx = np.arange(m_rows, dtype=np.int64)
+    x64 = np.ascontiguousarray(xyz[:, :m_rows].astype(np.float64))
+    u64 = np.ascontiguousarray(u[:m_rows].astype(np.float64))
     t0 = time.perf_counter()
     oracle.normal_equations(model, x64, u64, idx, nthreads=nthreads)
-    t_gram = (time.perf_counter() - t0) / m_s * m
-    R_s = int(768 * budget_scale ** (1 / 3))
+    t_gram = (time.perf_counter() - t0) / m_rows * m
     rng = np.random.default_rng(0)
-    B = rng.normal(size=(R_s + 8, R_s))
+    B = rng.normal(size=(R_chol + 8, R_chol))
     G = B.T @ B
     t0 = time.perf_counter()
     oracle.cholesky(G, nthreads=nthreads)
-    t_chol = (time.perf_counter() - t0) * (R / R_s) ** 3
+    t_chol = (time.perf_counter() - t0) * (R / R_chol) ** 3
     total = t_eval + t_gram + t_chol
-    desc = (f"oracle eval on {n_eval} points scaled to Q={Q}; oracle normal equations on {m_s} rows at R={R} "
-            f"scaled to m={m}; oracle Cholesky at R={R_s} scaled by (R/{R_s})^3; {nthreads} threads")
+    desc = (f"oracle eval on {n_eval} points scaled to Q={Q}; oracle normal equations on {m_rows} rows at "
+            f"R={R} scaled to m={m}; oracle Cholesky at R={R_chol} scaled by (R/{R_chol})^3; {nthreads} threads")
     return total, {"eval_s": t_eval, "gram_s": t_gram, "cholesky_s": t_chol}, desc
+
+
+# samples of the CPU baseline: all host cores, and one thread (about 10-20 s of CPU work each)
+CPU_SAMPLE_ALL = {"n_eval": 65536, "m_rows": 256, "R_chol": 2048}
+CPU_SAMPLE_ONE = {"n_eval": 8192, "m_rows": 32, "R_chol": 1536}
 
 
 def run_reference(args):
@@ -182,13 +201,14 @@ def run_reference(args):
     import oracle
     oracle.build()
     Q = args.Q
-    xyz, u, model = make_workload(min(Q, 1 << 16), seed=2024)
+    xyz, u, model = make_workload(1 << 16, seed=args.seed, degree=args.degree)
     R = model.R
     m = OVERSAMPLE * R
     nthreads = oracle.default_threads()
     times = []
+    sample = {"n_eval": 4096, "m_rows": 16, "R_chol": 1024}
     for it in range(args.warmup + args.steps):
-        t, parts, desc = oracle_sample_timing(model, xyz, u, Q, m, nthreads, budget_scale=0.5)
+        t, parts, desc = oracle_sample_timing(model, xyz, u, Q, m, nthreads, **sample)
         if it >= args.warmup:
             times.append(t)
     t = statistics.median(times)
@@ -196,7 +216,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": workload_config(Q, R, m, "fp64", "fp64"),
+            "config": workload_config(args.workload, Q, R, m, args.degree, "fp64", "fp64"),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": nthreads, "kind": "oracle", "sample": desc,
                              "parts_s": parts},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -224,7 +244,7 @@ def main():
 
     Q = args.Q
     from paper_1907_05884_gb300 import shard
-    xyz, u, model = make_workload(Q, seed=shard.rank_seed(2024, rank))
+    xyz, u, model = make_workload(Q, seed=shard.rank_seed(args.seed, rank), degree=args.degree)
     R = model.R
     m = OVERSAMPLE * R
     M = fst.Model(model)
@@ -322,12 +342,14 @@ def main():
     nnz = sum(len(v) for v in model.val)
     gram_flops = m * R * (R + 1)                      # lower triangle of A^T A, 2 flops per product
     eval_tc_flops = 2 * R * Q                         # T = U1 C_(1): 2 r1 r2 r3 flops per point
-    eval_alu_flops_pt = 2 * (RANKS[0] * RANKS[1] + RANKS[0]) + 2 * nnz + 5 * 3 * DEGREE
+    eval_alu_flops_pt = 2 * (RANKS[0] * RANKS[1] + RANKS[0]) + 2 * nnz + 5 * 3 * args.degree
     alu_peak = fp32_alu_peak_tflops(sm_max, sms)
-    # tensor peaks: measured cuBLAS BF16 (sustained: the kernel runs inside a long step);
+    # tensor peaks: the measured cuBLAS BF16 burst figure (each kernel is timed alone, a few
+    # milliseconds at a time, inside steps of well under a second of timed work);
     # TF32 = BF16 x 0.5 (nominal dense ratio); BF16x3 runs three BF16 products per term
-    bf16_peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
-    tc_peak = {"tf32": bf16_peak * 0.5, "bf16": bf16_peak, "bf16x3": bf16_peak / 3.0}
+    bf16_peak = peaks.get("bf16_tflops", peaks.get("bf16_tflops_sustained"))
+    ratio = {"tf32": 0.5, "bf16": 1.0, "bf16x3": 1 / 3}
+    tc_peak = {k: bf16_peak * v for k, v in ratio.items()}
     if args.prec == "fp32":
         roof_gram = {"kernel": "gram_simt (A^T A over sampled Khatri-Rao rows, CUDA cores)", "bound": "alu",
                      "achieved": gram_flops / (gram_ms / 1e3) / 1e12, "peak": alu_peak, "unit": "TFLOP/s",
@@ -337,26 +359,36 @@ def main():
                                "operand, tcgen05; time of the whole Gram phase)",
                      "bound": "tensor", "achieved": gram_flops / (gram_ms / 1e3) / 1e12,
                      "peak": tc_peak[args.prec], "unit": "TFLOP/s",
-                     "peak_source": f"{peak_kind} bf16_tflops_sustained {bf16_peak} x "
-                                    f"{ {'tf32': 0.5, 'bf16': 1.0, 'bf16x3': 1 / 3}[args.prec]:.3f}"}
+                     "peak_source": f"{peak_kind} bf16_tflops (burst) {bf16_peak} x {ratio[args.prec]:.3f}"}
     # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one gram_pk_kernel<BF16>
-    # launch at this workload (R = 13,824, m = 110,592), from one ncu capture of the current
-    # kernel; null for other configurations
-    roof_gram["traffic"] = (GRAM_PK_BF16_TRAFFIC if (args.prec == "bf16" and R == 13824 and m == 110592)
-                            else None)
+    # launch at R = 13,824, m = 110,592 from one ncu capture of the current kernel
+    roof_gram["traffic"] = GRAM_PK_BF16_TRAFFIC if (args.prec == "bf16" and R == 13824 and m == 110592) else None
     roof_gram["frac"] = roof_gram["achieved"] / roof_gram["peak"]
-    roof_eval = {"kernel": f"eval_tc3_kernel ({args.eval_prec}; factor step and contraction on tcgen05)"
-                           if args.eval_prec in ("bf16", "bf16x3") else f"eval ({args.eval_prec})", "ms": ev_ms,
-                 "tensor_TFLOPs": eval_tc_flops / (ev_ms / 1e3) / 1e12,
-                 "alu_TFLOPs": eval_alu_flops_pt * Q / (ev_ms / 1e3) / 1e12, "alu_peak": alu_peak,
-                 "hbm_GBps": 16 * Q / (ev_ms / 1e3) / 1e9, "hbm_peak_GBps": peaks["hbm_gbs"]}
-    if args.eval_prec != "fp32":
-        roof_eval["tensor_frac"] = roof_eval["tensor_TFLOPs"] / tc_peak[args.eval_prec]
-    dominant = roof_gram
+    roof_gram["ms"] = gram_ms
+    # the evaluation's core contraction T = U1 C_(1): 2R flops a point over the evaluation
+    # kernel's CUDA-event time; bytes: 12 B of coordinates in, 4 B of value out a point
+    if args.eval_prec == "fp32":
+        roof_eval = {"kernel": "eval_simt_kernel (FP32, CUDA cores)", "bound": "alu",
+                     "achieved": eval_alu_flops_pt * Q / (ev_ms / 1e3) / 1e12, "peak": alu_peak}
+    else:
+        roof_eval = {"kernel": f"eval_tc3_kernel<{args.eval_prec}> (Legendre basis, factor step and core "
+                               "contraction on tcgen05, Khatri-Rao epilogue from tensor memory)",
+                     "bound": "tensor", "achieved": eval_tc_flops / (ev_ms / 1e3) / 1e12,
+                     "peak": tc_peak[args.eval_prec],
+                     "peak_source": f"{peak_kind} bf16_tflops (burst) {bf16_peak} x {ratio[args.eval_prec]:.3f}"}
+    roof_eval.update({"unit": "TFLOP/s", "ms": ev_ms, "traffic": EVAL_TRAFFIC.get((args.eval_prec, Q, args.degree)),
+                      "algorithmic_bytes": 16 * Q, "hbm_GBps": 16 * Q / (ev_ms / 1e3) / 1e9,
+                      "hbm_peak_GBps": peaks["hbm_gbs"],
+                      "alu_TFLOPs": eval_alu_flops_pt * Q / (ev_ms / 1e3) / 1e12, "alu_peak": alu_peak})
+    roof_eval["frac"] = roof_eval["achieved"] / roof_eval["peak"]
+    # the headline roofline is the core contraction of the evaluation, the largest kernel of
+    # the step at this workload and the one the contraction target is stated for
+    dominant = roof_eval
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": args.prec if args.prec == args.eval_prec else f"{args.prec}+{args.eval_prec}",
-            "data": "synthetic", "config": workload_config(Q, R, m, args.prec, args.eval_prec),
+            "data": "synthetic",
+            "config": workload_config(args.workload, Q, R, m, args.degree, args.prec, args.eval_prec),
             "refit_ms": refit_ms, "refit_gram_ms": gram_ms, "refit_cholesky_ms": chol_ms,
             "refit_pcg_ms": refine_ms,
             "refit_pcg_steps": statistics.mean(r["refine_steps"] for r in reports),
@@ -365,7 +397,7 @@ def main():
             "refit_shifted_preconditioner": max(r["shifted_preconditioner"] for r in reports),
             "eval_ms": ev_ms, "eval_Mpoints_s": Q / ev_ms / 1e3,
             "roofline": {k: v for k, v in dominant.items()},
-            "rooflines": {"gram": roof_gram, "eval": roof_eval},
+            "rooflines": {"eval": roof_eval, "gram": roof_gram},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": xyz.nbytes + u.nbytes,
                     "d2h_bytes_per_step": 4 * Q},
             "gpu_launches": launches, "clocks": clk, "peaks": peak_kind}
@@ -374,29 +406,45 @@ def main():
         import oracle
         oracle.build()
         nthreads = oracle.default_threads()
-        t_cpu, parts, desc = oracle_sample_timing(model, xyz, u, Q, m, nthreads)
+        t_cpu, parts, desc = oracle_sample_timing(model, xyz, u, Q, m, nthreads, **CPU_SAMPLE_ALL)
+        t_one, parts1, desc1 = oracle_sample_timing(model, xyz, u, Q, m, 1, **CPU_SAMPLE_ONE)
         line["cpu_baseline"] = {"value": Q / t_cpu / 1e6, "unit": UNIT, "cores": nthreads, "kind": "oracle",
-                                "sample": desc, "parts_s": parts}
-        # accuracy stated against the FP64 oracle: evaluation at 2048 sampled points with the
-        # refitted core, and the normal-equation residual of the last refit
+                                "sample": desc, "parts_s": parts,
+                                "single_thread": {"value": Q / t_one / 1e6, "cores": 1, "sample": desc1,
+                                                  "parts_s": parts1},
+                                "cpu": platform_cpu()}
+        # accuracy stated against the FP64 oracle: evaluation of the refitted model on the first
+        # 2^20 points, and the normal-equation residual of the last refit (FP64, exact design)
         from paper_1907_05884_gb300 import synth
         cur = M.read()
         om = synth.Model(model.r, model.p, model.colptr, model.rowidx, model.val, cur["alpha"])
-        sel = np.random.default_rng(1).choice(Q, 2048, replace=False)
-        ref = oracle.eval_points(om, xyz[:, sel].astype(np.float64), nthreads=nthreads)
-        got = out_d.cpu().numpy()[sel]
+        na = min(ACCURACY_POINTS, Q)
+        ref = oracle.eval_points(om, xyz[:, :na].astype(np.float64), nthreads=nthreads)
+        got = out_d[:na].cpu().numpy()
         line["rel_l2_eval_vs_oracle"] = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+        line["rel_l2_eval_points"] = na
         idx = oracle.sample(5000 + args.steps - 1, Q, m)   # rows of the last refit (e2e loop)
-        g = oracle.normal_residual(om, xyz.astype(np.float64), u.astype(np.float64), idx, cur["alpha"],
-                                   nthreads=nthreads)
-        h = oracle.normal_residual(om, xyz.astype(np.float64), u.astype(np.float64), idx, np.zeros(R),
-                                   nthreads=nthreads)
+        x64 = xyz.astype(np.float64)
+        u64 = u.astype(np.float64)
+        g = oracle.normal_residual(om, x64, u64, idx, cur["alpha"], nthreads=nthreads)
+        h = oracle.normal_residual(om, x64, u64, idx, np.zeros(R), nthreads=nthreads)
         line["refit_normal_residual_rel"] = float(np.linalg.norm(g) / np.linalg.norm(h))
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
     return 0
+
+
+def platform_cpu() -> str:
+    try:
+        for l in Path("/proc/cpuinfo").read_text().splitlines():
+            if l.lower().startswith(("model name", "cpu part")):
+                return l.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
 
 
 if __name__ == "__main__":

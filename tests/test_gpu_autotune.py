@@ -5,11 +5,11 @@ import numpy as np
 import pytest
 
 from paper_1907_05884_gb300 import synth
-from gpu_util import rel_l2, cuda_tensor
+from gpu_util import EVAL_TOL, rel_l2, cuda_tensor
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"bf16x3": 3e-5, "bf16": 1e-2, "tf32": 2e-3}
+TOL = EVAL_TOL
 
 
 @pytest.fixture(scope="module")

@@ -103,9 +103,12 @@ def test_refit_errors(F):
     assert np.array_equal(M.read()["alpha"], m.alpha)
 
 
-def test_refit_full_size_normal_residual(F, oracle_lib):
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_refit_full_size_normal_residual(F, oracle_lib, prec):
     """2^24 points, ranks 24^3, degree 31, m = 8R = 110,592 rows: the refitted core satisfies the
-    normal equations of the sampled problem, checked by the oracle in FP64 with the exact design."""
+    normal equations of the sampled problem, checked by the oracle in FP64 with the exact design.
+    BF16 is the benchmark's path (packed operand, tensor-core Gram over five strips of
+    super-tiles, tensor-core Cholesky, conjugate gradients)."""
     import torch
     Q = 1 << 24
     m = synth.random_model((24, 24, 24), (31, 31, 31), seed=202, orthonormal=True)
@@ -115,11 +118,12 @@ def test_refit_full_size_normal_residual(F, oracle_lib):
     M = F.Model(m)
     R = m.R
     mm = 8 * R
-    rep = M.refit(cuda_tensor(xyz, torch.float32), cuda_tensor(u, torch.float32), mm, seed=206, prec="fp32")
+    rep = M.refit(cuda_tensor(xyz, torch.float32), cuda_tensor(u, torch.float32), mm, seed=206, prec=prec)
     alpha = M.read()["alpha"]
     idx = oracle_lib.sample(206, Q, mm)
     x64 = xyz.astype(np.float64)
     u64 = u.astype(np.float64)
     g = oracle_lib.normal_residual(m, x64, u64, idx, alpha, nthreads=16)
     h = oracle_lib.normal_residual(m, x64, u64, idx, np.zeros(R), nthreads=16)
+    print(prec, "normal residual", np.linalg.norm(g) / np.linalg.norm(h), rep)
     assert np.linalg.norm(g) < 1e-5 * np.linalg.norm(h), rep

@@ -5,7 +5,7 @@ import numpy as np
 import pytest
 
 from paper_1907_05884_gb300 import synth
-from gpu_util import rel_l2
+from gpu_util import EVAL_TOL, rel_l2
 
 pytestmark = pytest.mark.gpu
 
@@ -50,7 +50,7 @@ def test_results_same_alone_and_in_the_mix(setup, oracle_lib):
         if q.kind != "points":
             continue
         ref = oracle_lib.eval_points(host_models[q.field], pool[:, q.p0:q.p0 + q.n].numpy().astype(np.float64))
-        tol = {"fp32": 1e-5, "bf16x3": 3e-5, "bf16": 1e-2}[q.prec]
+        tol = EVAL_TOL[q.prec]
         assert rel_l2(q.out.cpu().numpy(), ref) < tol
 
 

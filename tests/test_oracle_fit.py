@@ -36,6 +36,24 @@ def test_splat_single_sample_reaches_its_cell_corners():
     assert filled.sum() == 8 and np.allclose(U[filled], 2.5)
 
 
+def test_splat_off_node_weights_by_hand():
+    """Two samples inside cell (0,0,0) of a 3x3x3 node grid (nodes -1, 0, 1): sample 1 at
+    fractions (1/4, 1/2, 3/4) of the cell with value 2, sample 2 at (9/10, 1/5, 2/5) with
+    value -1.  Corner (a,b,c) receives the trilinear weight prod_k (f_k if bit else 1-f_k)
+    from each sample and takes sum(w u) / sum(w).  The eight node values below were worked
+    out by hand in exact fractions (e.g. corner (0,0,0): w1 = 3/4*1/2*1/4 = 3/32,
+    w2 = 1/10*4/5*3/5 = 6/125, (2*3/32 - 6/125) / (3/32 + 6/125) = 62/63); swapped
+    w / 1-w, squared fractions or nearest-node splatting all give other values."""
+    t = np.array([[-0.75, -0.1], [-0.5, -0.8], [-0.25, -0.6]])
+    U, filled = F.interpolate_splat(t, np.array([2.0, -1.0]), (3, 3, 3))
+    expect = {(0, 0, 0): 62 / 63, (0, 0, 1): 2122 / 1253, (0, 1, 0): 78 / 47, (0, 1, 1): 2218 / 1157,
+              (1, 0, 0): -1478 / 1853, (1, 0, 1): -134 / 509, (1, 1, 0): -182 / 557, (1, 1, 1): 154 / 221}
+    assert filled.sum() == 8
+    for ix, v in expect.items():
+        assert filled[ix]
+        assert abs(U[ix] - v) < 1e-14, (ix, U[ix], v)
+
+
 def test_fill_from_one_node():
     U = np.zeros((5, 4, 3))
     filled = np.zeros_like(U, dtype=bool)
