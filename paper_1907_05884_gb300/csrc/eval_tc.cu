@@ -43,9 +43,9 @@ constexpr long long kWaitLimitE = 2000000000LL;
 enum EMode { eTF32 = 0, eBF16 = 1, eBF16X3 = 2 };
 
 __host__ __device__ constexpr int jc_for(int r3p) { return 256 / r3p; }
-// factor-step variant: contraction chunks of 160 columns, factor blocks at TMEM column 160
-__host__ __device__ constexpr int jc3_for(int r3p) { return 160 / r3p; }
-constexpr int kFacRows = 32;           // N of the factor MMA (ranks padded to 32)
+// factor-step (pipelined) variant: contraction chunks of at most 144 columns
+__host__ __device__ constexpr int jc3_for(int r3p) { return 144 / r3p; }
+constexpr int kFacRows = 32;           // ranks padded to 32 in each coefficient part of the factor MMA
 constexpr int kBarBytes = 1024;
 
 // Host-side description of the shared-memory image of C_(1) (and, for the factor-step
@@ -54,7 +54,8 @@ struct CoreImage {
     int mode, r3p, jc, nc, ncp, kp, kb, nchunks, parts;
     size_t chunk_bytes, bytes;
     bool tc3 = false;
-    int kpf = 0;                 // Legendre K of the factor MMA (multiple of 16)
+    int rm = 8;                  // rank bound of the size class (K stride of the BF16X3 operand)
+    int kpf = 0;                 // Legendre K of the factor MMA (multiple of 32)
     size_t fac_off = 0, fac_bytes = 0;
 };
 
@@ -62,8 +63,11 @@ int bucket8(int r) { return r <= 8 ? 8 : r <= 16 ? 16 : r <= 24 ? 24 : 32; }
 
 int kpf_of(const fst_model* m) {
     const int pe = std::max(m->p_eff[0], std::max(m->p_eff[1], m->p_eff[2]));
-    return std::max(16, (pe + 15) / 16 * 16);
+    return std::max(32, (pe + 31) / 32 * 32);
 }
+
+__host__ __device__ constexpr int pipe_kc(int mode, int rm);
+__host__ __device__ constexpr int pipe_kb(int mode, int rm);
 
 CoreImage core_image_shape(const fst_model* m, int mode, int r3p, bool tc3 = false) {
     CoreImage c;
@@ -73,50 +77,44 @@ CoreImage core_image_shape(const fst_model* m, int mode, int r3p, bool tc3 = fal
     c.jc = tc3 ? jc3_for(r3p) : jc_for(r3p);
     c.nc = c.jc * r3p;
     c.ncp = (c.nc + 15) / 16 * 16;
+    c.rm = bucket8(std::max(m->r[0], std::max(m->r[1], m->r[2])));
     const int gran = mode == eTF32 ? 8 : 16;
     c.kp = (m->r[0] + gran - 1) / gran * gran;
     c.kb = c.kp * (mode == eTF32 ? 4 : 2);
-    c.nchunks = (m->r[1] + c.jc - 1) / c.jc;
     c.parts = mode == eBF16X3 ? 2 : 1;
+    if (tc3) {
+        // one part: BF16X3 concatenates [C hi; C hi; C lo] along K with stride rm
+        c.kp = pipe_kc(mode, c.rm);
+        c.kb = pipe_kb(mode, c.rm);
+        c.parts = 1;
+    }
+    c.nchunks = (m->r[1] + c.jc - 1) / c.jc;
     c.chunk_bytes = (size_t)c.ncp * c.kb;
     c.bytes = c.chunk_bytes * c.nchunks * c.parts;
     if (tc3) {
         c.kpf = kpf_of(m);
         c.fac_off = (c.bytes + 1023) & ~(size_t)1023;
-        c.fac_bytes = (size_t)3 * 2 * kFacRows * c.kpf * 2;
+        c.fac_bytes = (size_t)3 * 3 * kFacRows * c.kpf * 2;      // three modes, hi | mid | lo
         c.bytes = c.fac_off + c.fac_bytes;
     }
     return c;
 }
 
-// Shared memory of a factor-step bucket with these largest images.
-// One worker group's operand buffers: the Legendre tile (BF16 hi + lo, 128 x KPF), later
-// overwritten by the w1 operand (parts x 128 x KB), and with nbuf = 2 a second Legendre tile,
-// so that two modes go to the tensor cores in one round trip.
-__host__ __device__ inline size_t tc3_pbytes(int kpf_max) { return (size_t)2 * 128 * kpf_max * 2; }
-__host__ __device__ inline size_t tc3_buf0_bytes(int kb_max, int kpf_max, int parts) {
-    const size_t p = tc3_pbytes(kpf_max), w = (size_t)parts * 128 * kb_max;
-    return p > w ? p : w;
+// Shared memory of a pipelined bucket: alignment slack, the control block, the core and factor
+// images, nps Legendre half-tile slots (BF16 hi + lo, 128 x 32) per basis group, and the w1
+// operand (128 x KB).
+size_t tc3_smem(size_t core_max, int kb_max, int nps) {
+    return 1024 + kBarBytes + core_max + (size_t)2 * nps * (2 * 128 * 32 * 2) + (size_t)128 * kb_max;
 }
-__host__ __device__ inline size_t tc3_group_bytes(int kb_max, int kpf_max, int parts, int nbuf) {
-    return tc3_buf0_bytes(kb_max, kpf_max, parts) + (nbuf == 2 ? tc3_pbytes(kpf_max) : 0);
-}
-// Shared memory of a factor-step bucket: barriers, the core and factor images, and the operand
-// buffers of the three worker groups.
-size_t tc3_smem(size_t core_max, int kb_max, int kpf_max, int parts, int nbuf) {
-    return 1024 + kBarBytes + core_max + 3 * tc3_group_bytes(kb_max, kpf_max, parts, nbuf);
-}
-// Two Legendre buffers per group when they fit.
-int tc3_nbuf(size_t core_max, int kb_max, int kpf_max, int parts) {
-    return tc3_smem(core_max, kb_max, kpf_max, parts, 2) <= 227 * 1024 ? 2 : 1;
-}
+// Two half-tile slots per basis group when they fit.
+int tc3_nps(size_t core_max, int kb_max) { return tc3_smem(core_max, kb_max, 2) <= 227 * 1024 ? 2 : 1; }
 
 // The factor-step variant can serve contractions (TF32, BF16, BF16X3) with degrees below 64
 // whose images fit the shared memory.
 bool tc3_feasible(const fst_model* m, int mode, int r3p) {
     if (kpf_of(m) > 64) return false;
     const CoreImage c = core_image_shape(m, mode, r3p, true);
-    return tc3_smem((c.bytes + 1023) & ~(size_t)1023, c.kb, c.kpf, c.parts, 1) <= 227 * 1024;
+    return tc3_smem((c.bytes + 1023) & ~(size_t)1023, c.kb, 1) <= 227 * 1024;
 }
 
 // Autotune table: per device and size class (mode, rank bound, r3 padding, Legendre K) the
@@ -169,6 +167,52 @@ uint32_t tf32_bits(float x) {
 std::vector<unsigned char> build_core_image(const fst_model* m, const CoreImage& c) {
     std::vector<unsigned char> img(c.bytes, 0);
     const int r1 = m->r[0], r2 = m->r[1], r3 = m->r[2];
+    if (c.tc3) {
+        // pipelined variant: one part; BF16X3 holds C hi at K = i and rm + i, C lo at 2 rm + i
+        for (int ch = 0; ch < c.nchunks; ++ch)
+            for (int n = 0; n < c.nc; ++n) {
+                const int j = ch * c.jc + n / c.r3p, k = n % c.r3p;
+                if (j >= r2 || k >= r3) continue;
+                unsigned char* base = img.data() + (size_t)ch * c.chunk_bytes;
+                for (int i = 0; i < r1; ++i) {
+                    const double v = m->alpha[((size_t)i * r2 + j) * r3 + k];
+                    if (c.mode == eTF32) {
+                        const uint32_t b = tf32_bits((float)v);
+                        memcpy(base + tc::kmajor_offset(n, i * 4, c.kb), &b, 4);
+                        continue;
+                    }
+                    const uint16_t hi = bf16_bits((float)v);
+                    memcpy(base + tc::kmajor_offset(n, i * 2, c.kb), &hi, 2);
+                    if (c.mode == eBF16X3) {
+                        const uint16_t lo = bf16_bits((float)(v - (double)bf16_val((float)v)));
+                        memcpy(base + tc::kmajor_offset(n, (c.rm + i) * 2, c.kb), &hi, 2);
+                        memcpy(base + tc::kmajor_offset(n, (2 * c.rm + i) * 2, c.kb), &lo, 2);
+                    }
+                }
+            }
+        // factor coefficient matrices with sqrt(2n+1) and the leading coefficient k_n of L_n
+        // folded in (the kernel's Legendre tiles hold L_n / k_n), split in three BF16 parts:
+        // mode k, row part * 32 + j (rank j), K = degree n (padded to kpf)
+        const int KPB = c.kpf * 2;
+        const size_t wbytes = (size_t)3 * kFacRows * KPB;
+        std::vector<double> lead(c.kpf, 1.0);     // k_n = prod_{i <= n} (2i - 1) / i
+        for (int nn = 1; nn < c.kpf; ++nn) lead[nn] = lead[nn - 1] * (2.0 * nn - 1.0) / nn;
+        for (int k = 0; k < 3; ++k) {
+            unsigned char* base = img.data() + c.fac_off + (size_t)k * wbytes;
+            for (int j = 0; j < m->r[k]; ++j)
+                for (int e = m->colptr[k][j]; e < m->colptr[k][j + 1]; ++e) {
+                    const int nn = m->rowidx[k][e];
+                    if (nn >= c.kpf) continue;
+                    double w = m->val[k][e] * sqrt(2.0 * nn + 1.0) * lead[nn];
+                    for (int part = 0; part < 3; ++part) {
+                        const uint16_t b = bf16_bits((float)w);
+                        memcpy(base + tc::kmajor_offset(part * kFacRows + j, nn * 2, KPB), &b, 2);
+                        w -= (double)bf16_val((float)w);
+                    }
+                }
+        }
+        return img;
+    }
     for (int ch = 0; ch < c.nchunks; ++ch)
         for (int n = 0; n < c.nc; ++n) {
             const int j = ch * c.jc + n / c.r3p, k = n % c.r3p;
@@ -191,28 +235,6 @@ std::vector<unsigned char> build_core_image(const fst_model* m, const CoreImage&
                 }
             }
         }
-    if (c.tc3) {
-        // factor coefficient matrices with sqrt(2n+1) and the leading coefficient k_n of L_n
-        // folded in (the kernel's Legendre tiles hold L_n / k_n): mode k, part (hi, lo), row j
-        // (rank, padded to 32), K = degree n (padded to kpf)
-        const int KPB = c.kpf * 2;
-        const size_t wbytes = (size_t)kFacRows * KPB;
-        std::vector<double> lead(c.kpf, 1.0);     // k_n = prod_{i <= n} (2i - 1) / i
-        for (int nn = 1; nn < c.kpf; ++nn) lead[nn] = lead[nn - 1] * (2.0 * nn - 1.0) / nn;
-        for (int k = 0; k < 3; ++k) {
-            unsigned char* base = img.data() + c.fac_off + (size_t)k * 2 * wbytes;
-            for (int j = 0; j < m->r[k]; ++j)
-                for (int e = m->colptr[k][j]; e < m->colptr[k][j + 1]; ++e) {
-                    const int nn = m->rowidx[k][e];
-                    if (nn >= c.kpf) continue;
-                    const float w = (float)(m->val[k][e] * sqrt(2.0 * nn + 1.0) * lead[nn]);
-                    const uint32_t off = tc::kmajor_offset(j, nn * 2, KPB);
-                    const uint16_t hi = bf16_bits(w), lo = bf16_bits(w - bf16_val(w));
-                    memcpy(base + off, &hi, 2);
-                    memcpy(base + wbytes + off, &lo, 2);
-                }
-        }
-    }
     return img;
 }
 
@@ -529,25 +551,61 @@ eval_tc_kernel(const TcItem* __restrict__ items, const TcUnit* __restrict__ unit
     if (warp == 0) tc::tmem_dealloc(tmem, 512);
 }
 
-// ---------------------------------------------------------------- factor step on tcgen05
-// Variant for BF16 / BF16X3 contractions with degrees below 64: the factor values are an
-// MMA too.  Three groups of four warps, each on its own 128-point tiles (thread = point =
-// TMEM lane); within a group everything runs in order and one thread of the group's first
-// warp issues the group's MMAs:
-//   * per mode k the workers write the monic Legendre values q_0..q_{KPF-1} of their point
-//     (zero from the mode's highest used degree on) as BF16 high and low parts (A operand,
-//     128 x KPF), and U_k = P_k Wc_k^T (N = 32, BF16x3 products) goes to tensor memory;
-//   * the workers read U_1..U_3 back: w1 becomes the contraction's A operand (written over
-//     the Legendre buffer, which is free by then), w2 and w3 stay in registers;
-//   * T = U1 C_(1) is formed in chunks of JC3 whole j-slices into the same 160 tensor-memory
-//     columns of the group (the U blocks are read by then), and each chunk is reduced
-//     against w2 and w3 (the Khatri-Rao epilogue) before the next is issued.
-// The three groups interleave on the SM's four schedulers, so one group's CUDA-core work
-// overlaps the others' MMAs.  Every wait is bounded.
-constexpr int kGroups3 = 3;
-constexpr int kThreads3 = kGroups3 * 4 * 32;
-constexpr int kGroupCols3 = 160;
-constexpr int kEpiBatch = 3;       // 16-column TMEM reads in flight per wait in the epilogue
+// ---------------------------------------------------------------- pipelined factor-step evaluator
+// Variant for TF32 / BF16 / BF16X3 contractions with degrees below 64: the factor values are
+// an MMA too, and the work of a 128-point tile flows through warp-specialised stages so that
+// the Legendre arithmetic, the tensor cores and the Khatri-Rao epilogue of different tiles
+// overlap:
+//   * a scheduler warp publishes the CTA's tiles into a ring of descriptors (and loads the
+//     core and factor images into shared memory when the instance changes);
+//   * two basis groups of four warps (alternate tiles, thread = point) write the monic
+//     Legendre values q_0..q_{pe-1} of every mode, 32 degrees at a time, as BF16 high and low
+//     parts into half-tile slots;
+//   * one thread issues the MMAs: per mode U_k = P_k Wc_k^T with Wc_k split in three BF16
+//     parts side by side (N = 96: hi | mid | lo), so the hi and lo Legendre parts meet every
+//     coefficient part (six products, FP32-class factor values), into a two-slot ring of
+//     tensor-memory blocks; and T = U1 C_(1) in chunks of whole j-slices into two chunk
+//     buffers.  It issues whichever job is ready first;
+//   * four epilogue warps (thread = point = TMEM lane) add the three parts of each U block,
+//     write w1 as the contraction's A operand (BF16X3: [hi | lo | hi] along K against
+//     [C hi; C hi; C lo], one MMA chain for the three products), keep w2 and w3 in registers
+//     and reduce each chunk against them.
+// Every wait is bounded; on expiry a role records an error code and leaves its loop, and the
+// others time out in turn.
+constexpr int kPipeWarps = 15;                 // 0-7 basis, 8-11 epilogue, 12 factor MMAs, 13 scheduler, 14 contraction MMAs
+constexpr int kThreadsP = kPipeWarps * 32;
+constexpr int kND = 8;                         // tile descriptors in flight
+constexpr int kUCols = 96;                     // factor MMA N: coefficient hi | mid | lo
+constexpr int kChunkCols = 144;                // tensor-memory columns of a contraction chunk buffer
+constexpr int kUBase = 2 * kChunkCols;         // the two U blocks follow the two chunk buffers
+constexpr int kPHalf = 32;                     // Legendre degrees per half tile
+constexpr int kPSlotBytes = 2 * 128 * kPHalf * 2;   // one half tile, BF16 hi + lo
+constexpr int kEpiBatch = 3;                   // 16-column TMEM reads in flight per wait in the epilogue
+// Register split: launched at 128 a thread (15 warps, 61,440 registers); the two basis
+// warpgroups drop to 96 and the epilogue warpgroup rises to 176, warps 12-14 keep 128:
+// 256 x 96 + 128 x 176 + 96 x 128 = 59,392 <= 61,440, and per SM sub-partition (warps w, w+4,
+// w+8, w+12) at most 32 x (96 + 96 + 176 + 128) = 15,872 <= 16,384.
+constexpr int kRegsLaunch = 128, kRegsBasis = 96, kRegsEpi = 176;
+static_assert(256 * kRegsBasis + 128 * kRegsEpi + 96 * kRegsLaunch <= kThreadsP * kRegsLaunch, "register split");
+static_assert(32 * (2 * kRegsBasis + kRegsEpi + kRegsLaunch) <= 16384, "register split per sub-partition");
+
+struct PipeDesc {
+    int item;            // < 0: no more tiles
+    int pad;
+    long long tile;
+};
+struct PipeCtl {
+    uint64_t desc_full[kND], desc_empty[kND];
+    uint64_t p_full[4], p_empty[4];
+    uint64_t u_full[2], u_empty[2];
+    uint64_t w1_full, w1_empty;
+    uint64_t c_full[2], c_empty[2];
+    uint64_t drain[2];                   // one per MMA thread
+    PipeDesc desc[kND];
+    uint32_t tmem_base;
+    int tiles_done;      // epilogue warps finished (one count per warp and tile)
+};
+static_assert(sizeof(PipeCtl) <= kBarBytes, "control block fits");
 
 // N (a multiple of 8) consecutive TMEM columns of this warp's lanes into v; complete after
 // tc::tmem_wait_ld()
@@ -568,357 +626,519 @@ __device__ __forceinline__ void tmem_ld_cols(uint32_t taddr, float* v) {
     }
 }
 
+__device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(tc::smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// contraction K of the operand image: BF16X3 [hi | lo | hi] x [C hi; C hi; C lo] with rank
+// stride RM, BF16 RM, TF32 RM; in elements, padded to the MMA's K granule
+__host__ __device__ constexpr int pipe_kc(int mode, int rm) {
+    return mode == eBF16X3 ? (3 * rm + 15) / 16 * 16 : mode == eBF16 ? (rm + 15) / 16 * 16 : (rm + 7) / 8 * 8;
+}
+__host__ __device__ constexpr int pipe_kb(int mode, int rm) { return pipe_kc(mode, rm) * (mode == eTF32 ? 4 : 2); }
+
 template <int MODE, int R3P, int RM>
-__global__ void __launch_bounds__(kThreads3, 1)
-eval_tc3_kernel(const TcItem* __restrict__ items, const TcUnit* __restrict__ units, const int* __restrict__ cta_start,
-                int nunits, int* unit_ctr,
-                int core_max, int kb_max, int kpf_max, int nbuf, const float* __restrict__ xyz_ov,
-                float* __restrict__ out_ov, int* __restrict__ err) {
-    constexpr int JC = jc3_for(R3P);
+__global__ void __launch_bounds__(kThreadsP, 1)
+eval_pipe_kernel(const TcItem* __restrict__ items, const TcUnit* __restrict__ units, const int* __restrict__ cta_start,
+                 int nunits, int* unit_ctr, int core_max, int nps, const float* __restrict__ xyz_ov,
+                 float* __restrict__ out_ov, int* __restrict__ err) {
+    constexpr int JC = kChunkCols / R3P;
     constexpr int NC = JC * R3P;
     constexpr int NCP = (NC + 15) / 16 * 16;
     constexpr int MAXCH = (FST_MAX_RANK + JC - 1) / JC;
-    static_assert(NCP <= kGroupCols3, "a chunk fits the group's tensor-memory columns");
+    constexpr int KB = pipe_kb(MODE, RM);
+    constexpr uint32_t SBO_A = (KB / 16) * 128;
+    static_assert(NCP <= kChunkCols, "a chunk fits its tensor-memory buffer");
+    static_assert(kUBase + 2 * kUCols <= 512, "tensor-memory budget");
 
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
-    uint64_t* w_bar = bars;                       // [3] the group's 4 warps -> issuer: operand written / chunk read
-    uint64_t* m_bar = bars + kGroups3;            // [3] MMA commit -> the group: MMAs of the step complete
-    uint64_t* drain = bars + 2 * kGroups3;        // [3]
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + kGroups3);
+    PipeCtl& C = *reinterpret_cast<PipeCtl*>(smem);
     unsigned char* core = smem + kBarBytes;
-    const size_t gbytes = tc3_group_bytes(kb_max, kpf_max, MODE == eBF16X3 ? 2 : 1, nbuf);
-    const uint32_t buf1 = (uint32_t)tc3_buf0_bytes(kb_max, kpf_max, MODE == eBF16X3 ? 2 : 1);
-    unsigned char* gbuf = core + core_max;
+    unsigned char* pbuf = core + core_max;
+    unsigned char* w1buf = pbuf + (size_t)2 * nps * kPSlotBytes;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int g = warp >> 2, sub = warp & 3, row = sub * 32 + lane;   // TMEM lane = row
-    const bool issuer = sub == 0 && lane == 0;
-    if (warp == 0) tc::tmem_alloc(tmem_slot, 512);
+    if (warp == 12) tc::tmem_alloc(&C.tmem_base, 512);
     if (tid == 0) {
-        for (int e = 0; e < kGroups3; ++e) {
-            tc::mbar_init(&w_bar[e], 4);
-            tc::mbar_init(&m_bar[e], 1);
-            tc::mbar_init(&drain[e], 1);
+        for (int e = 0; e < kND; ++e) {
+            tc::mbar_init(&C.desc_full[e], 1);
+            tc::mbar_init(&C.desc_empty[e], 10);   // basis group (4 warps), epilogue (4 warps), two MMA threads
         }
+        for (int e = 0; e < 4; ++e) {
+            tc::mbar_init(&C.p_full[e], 4);
+            tc::mbar_init(&C.p_empty[e], 1);
+        }
+        for (int e = 0; e < 2; ++e) {
+            tc::mbar_init(&C.u_full[e], 1);
+            tc::mbar_init(&C.u_empty[e], 4);
+            tc::mbar_init(&C.c_full[e], 1);
+            tc::mbar_init(&C.c_empty[e], 4);
+        }
+        tc::mbar_init(&C.w1_full, 4);
+        tc::mbar_init(&C.w1_empty, 1);
+        tc::mbar_init(&C.drain[0], 1);
+        tc::mbar_init(&C.drain[1], 1);
+        C.tiles_done = 0;
         tc::fence_mbar_init();
     }
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
-    const uint32_t tmem = *tmem_slot;
-    const uint32_t tcol = tmem + (uint32_t)(g * kGroupCols3);               // issuer's view
-    const uint32_t tg = tcol + ((uint32_t)(sub * 32) << 16);                // this warp's lanes
-    unsigned char* P = gbuf + (size_t)g * gbytes;                           // Legendre tile, then w1
-    const uint32_t p_u32 = tc::smem_u32(P);
-    const uint32_t core_u32 = tc::smem_u32(core);
+    const uint32_t tmem = C.tmem_base;
 
-    __shared__ int s_unit;
-    int cur = -1;
-    int nw = 0, nm = 0;        // completed phases of w_bar[g] and m_bar[g]
-    bool issued = false, dead = false;
-    auto wait = [&](uint64_t* bar, int& phase, int code) {
-        if (!dead && !tc::mbar_wait(bar, (uint32_t)(phase & 1), kWaitLimitE)) {
-            atomicOr(err, code);
-            dead = true;
-        }
-        ++phase;
-    };
-    // every warp of the group has written its rows of the operand (or read its TMEM lanes)
-    auto handoff = [&]() {
-        tc::fence_before_sync();
-        __syncwarp();
-        if (lane == 0) tc::mbar_arrive(&w_bar[g]);
-    };
-    // the warp reconverges after the issuer's branch and agrees on `dead` (tcgen05.ld needs
-    // the whole warp)
-    auto converge = [&]() {
-        __syncwarp();
-        dead = __any_sync(0xffffffffu, dead);
-    };
-    // with a counter (several instances), units are taken in order from it (zeroed before
-    // the launch), so the CTAs stay balanced whatever each unit costs; without, the CTA runs
-    // its own range of units and the worker groups never meet at unit boundaries
-    const int u0 = unit_ctr ? 0 : cta_start[blockIdx.x], u1 = unit_ctr ? nunits : cta_start[blockIdx.x + 1];
-    for (int us = u0;; ++us) {
-        int u = us;
-        if (unit_ctr) {
-            if (tid == 0) s_unit = atomicAdd(unit_ctr, 1);
-            __syncthreads();
-            u = s_unit;
-            __syncthreads();
-        }
-        if (u >= u1) break;
-        const TcUnit U = units[u];
-        const TcItem& I = items[U.item];
-        const EvalArgs<float>& a = I.a;
-        if (U.item != cur) {
-            // every MMA of the previous instance completed before its group's last wait
-            tc::fence_before_sync();
-            __syncthreads();
-            const uint4* src = reinterpret_cast<const uint4*>(I.core_img);
-            uint4* dst = reinterpret_cast<uint4*>(core);
-            for (int e = tid; e < I.img_bytes / 16; e += blockDim.x) dst[e] = src[e];
-            tc::fence_async_smem();
-            tc::fence_before_sync();
-            __syncthreads();
-            tc::fence_after_sync();
-            cur = U.item;
-        }
-        const int KB = I.kp * (MODE == eTF32 ? 4 : 2);   // contraction K bytes
-        const int SBO = (KB / 16) * 128;
-        const int abytes = 128 * KB;
-        const int KPB = I.kpf * 2;                 // Legendre row bytes (BF16)
-        const int r1 = a.r[0];
-        const int nch = I.nchunks;
-        const long long n = I.n;
-        const float* X = xyz_ov ? xyz_ov : I.xyz;
-        // issuer constants
-        constexpr uint32_t idesc_c = MODE == eTF32 ? tc::idesc_tf32(128, NCP) : tc::idesc_bf16(128, NCP);
-        constexpr uint32_t idesc_f = tc::idesc_bf16(128, kFacRows);
-        const uint32_t chunk_bytes = (uint32_t)(NCP * KB);
-        const uint32_t SBOP = (uint32_t)(KPB / 16) * 128;
-        const uint32_t wbytes = (uint32_t)(kFacRows * KPB);      // one part of one mode
-        auto issue_chunk = [&](int ch) {
-            const uint32_t bb = core_u32 + ch * chunk_bytes;
-            for (int ks = 0; ks < KB / 32; ++ks) {
-                const uint32_t ko = ks * 256;
-                const uint64_t ad = tc::make_desc(p_u32 + ko, 128, SBO);
-                const uint64_t bd = tc::make_desc(bb + ko, 128, SBO);
-                if (MODE == eTF32) {
-                    tc::mma_tf32(tcol, ad, bd, idesc_c, ks > 0);
-                    continue;
+    if (warp == 13) {
+        // ------------------------------------------------------------ scheduler
+        const int u0 = unit_ctr ? 0 : cta_start[blockIdx.x], u1 = unit_ctr ? nunits : cta_start[blockIdx.x + 1];
+        int cur = -1;
+        long long sd = 0;
+        bool dead = false;
+        for (int us = u0; !dead; ++us) {
+            int u = us;
+            if (unit_ctr) {
+                if (lane == 0) u = atomicAdd(unit_ctr, 1);
+                u = __shfl_sync(0xffffffffu, u, 0);
+            }
+            if (u >= u1) break;
+            const TcUnit U = units[u];
+            if (U.item != cur) {
+                if (cur >= 0) {
+                    // every tile of the previous instance is finished (its MMAs complete)
+                    // before the images in shared memory are replaced
+                    int ok = 1;
+                    if (lane == 0) {
+                        const long long t0 = clock64();
+                        while (*reinterpret_cast<volatile int*>(&C.tiles_done) < 4 * sd) {
+                            if (clock64() - t0 > kWaitLimitE) {
+                                ok = 0;
+                                break;
+                            }
+                            __nanosleep(256);
+                        }
+                    }
+                    if (!__shfl_sync(0xffffffffu, ok, 0)) {
+                        if (lane == 0) atomicOr(err, 128);
+                        dead = true;
+                        break;
+                    }
                 }
-                tc::mma_bf16(tcol, ad, bd, idesc_c, ks > 0);
-                if (MODE == eBF16X3) {
-                    const uint64_t al = tc::make_desc(p_u32 + abytes + ko, 128, SBO);
-                    const uint64_t bl = tc::make_desc(bb + nch * chunk_bytes + ko, 128, SBO);
-                    tc::mma_bf16(tcol, ad, bl, idesc_c, 1u);
-                    tc::mma_bf16(tcol, al, bd, idesc_c, 1u);
+                const TcItem& I = items[U.item];
+                const uint4* src = reinterpret_cast<const uint4*>(I.core_img);
+                uint4* dst = reinterpret_cast<uint4*>(core);
+                for (int e = lane; e < I.img_bytes / 16; e += 32) dst[e] = src[e];
+                tc::fence_async_smem();
+                __syncwarp();
+                cur = U.item;
+            }
+            for (long long t = U.tile0; t < U.tile0 + U.ntiles; ++t, ++sd) {
+                const int slot = (int)(sd % kND);
+                const uint32_t par = (uint32_t)((sd / kND) & 1) ^ 1u;
+                int ok = 1;
+                if (lane == 0) {
+                    if (tc::mbar_wait(&C.desc_empty[slot], par, kWaitLimitE)) {
+                        C.desc[slot].item = U.item;
+                        C.desc[slot].tile = t;
+                        tc::mbar_arrive(&C.desc_full[slot]);
+                    } else {
+                        atomicOr(err, 256);
+                        ok = 0;
+                    }
+                }
+                if (!__shfl_sync(0xffffffffu, ok, 0)) {
+                    dead = true;
+                    break;
                 }
             }
-            tc::mma_commit(&m_bar[g]);
-            issued = true;
-        };
-
-        float nxt[3];
-        {
-            const long long q = (U.tile0 + g) * 128 + row;
-            const bool ok = U.tile0 + g < U.tile0 + U.ntiles && q < n;
-#pragma unroll
-            for (int k = 0; k < 3; ++k) nxt[k] = ok ? X[k * n + q] : 0.f;
         }
-        for (long long t = U.tile0 + g; t < U.tile0 + U.ntiles && !dead; t += kGroups3) {
-            const long long q = t * 128 + row;
-            const bool ok = q < n;
-            float tt[3];
+        // two end markers: one for each basis group (the MMA thread and the epilogue stop at
+        // the first)
+        for (int e = 0; e < 2 && !dead && lane == 0; ++e, ++sd) {
+            const int slot = (int)(sd % kND);
+            if (tc::mbar_wait(&C.desc_empty[slot], (uint32_t)((sd / kND) & 1) ^ 1u, kWaitLimitE)) {
+                C.desc[slot].item = -1;
+                tc::mbar_arrive(&C.desc_full[slot]);
+            } else {
+                atomicOr(err, 256);
+                dead = true;
+            }
+        }
+    } else if (warp < 8) {
+        // ------------------------------------------------------------ basis groups
+        tc::setmaxnreg_dec<kRegsBasis>();
+        const int g = warp >> 2, row = (warp & 3) * 32 + lane;
+        int pi = 0;                    // this group's next half-tile slot (of nps) and its use parity
+        uint32_t pph = 0;
+        float nxt[3] = {0.f, 0.f, 0.f};
+        long long nxt_seq = -1;
+        for (long long sd = g;; sd += 2) {
+            const int slot = (int)(sd % kND);
+            if (!tc::mbar_wait(&C.desc_full[slot], (uint32_t)((sd / kND) & 1), kWaitLimitE)) {
+                atomicOr(err, 1);
+                break;
+            }
+            const PipeDesc d = C.desc[slot];
+            if (d.item < 0) break;
+            const TcItem& I = items[d.item];
+            const EvalArgs<float>& a = I.a;
+            const float* X = xyz_ov ? xyz_ov : I.xyz;
+            const long long n = I.n;
+            float x[3];
+            if (nxt_seq == sd) {
 #pragma unroll
-            for (int k = 0; k < 3; ++k) tt[k] = fmaf(nxt[k], a.sc[k], a.of[k]);
+                for (int k = 0; k < 3; ++k) x[k] = nxt[k];
+            } else {
+                const long long q = d.tile * 128 + row;
+#pragma unroll
+                for (int k = 0; k < 3; ++k) x[k] = q < n ? X[k * n + q] : 0.f;
+            }
+            // coordinates of this group's next tile, if the scheduler has published it
             {
-                const long long q2 = q + kGroups3 * 128;
-                const bool ok2 = t + kGroups3 < U.tile0 + U.ntiles && q2 < n;
+                const long long s2 = sd + 2;
+                const int sl2 = (int)(s2 % kND);
+                if (mbar_test(&C.desc_full[sl2], (uint32_t)((s2 / kND) & 1))) {
+                    const PipeDesc d2 = C.desc[sl2];
+                    if (d2.item >= 0) {
+                        const TcItem& I2 = items[d2.item];
+                        const float* X2 = xyz_ov ? xyz_ov : I2.xyz;
+                        const long long q2 = d2.tile * 128 + row;
 #pragma unroll
-                for (int k = 0; k < 3; ++k) nxt[k] = ok2 ? X[k * n + q2] : 0.f;
+                        for (int k = 0; k < 3; ++k) nxt[k] = q2 < I2.n ? X2[k * I2.n + q2] : 0.f;
+                        nxt_seq = s2;
+                    }
+                }
             }
-            // Legendre tiles of the three modes: with two buffers modes 0 and 1 go to the tensor
-            // cores in one round trip and mode 2 in a second, else one mode a round trip
-            const int nsteps = nbuf == 2 ? 2 : 3;
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(&C.desc_empty[slot]);
+            bool dead = false;
 #pragma unroll 1
-            for (int st = 0; st < nsteps; ++st) {
-                const int kfirst = nbuf == 2 ? 2 * st : st;
-                const int kcount = nbuf == 2 && st == 0 ? 2 : 1;
-#pragma unroll 1
-                for (int kk = 0; kk < kcount; ++kk) {
-                    const int k = kfirst + kk;
-                    unsigned char* Pb = P + (kk ? buf1 : 0u);
-                    const float x = k == 0 ? tt[0] : k == 1 ? tt[1] : tt[2];
-                    const int pe = a.pe[k];
-                    // monic Legendre polynomials q_d = L_d / k_d (k_d the leading coefficient of L_d,
-                    // folded into the factor coefficients): q_d = x q_{d-1} - (d-1)^2 / ((2d-1)(2d-3))
-                    // q_{d-2}, two operations a degree, constants folded into the unrolled code
-                    float Lm = 1.f, L = x;
+            for (int k = 0; k < 3 && !dead; ++k) {
+                const float xt = fmaf(x[k], a.sc[k], a.of[k]);
+                const int pe = a.pe[k];
+                float Lm = 1.f, L = xt;
+                // monic Legendre polynomials q_d = L_d / k_d (the leading coefficients k_d are
+                // folded into the factor coefficients): q_d = x q_{d-1} - (d-1)^2 / ((2d-1)(2d-3))
+                // q_{d-2}, two operations a degree, 32 degrees a half tile
 #pragma unroll
-                    for (int c8 = 0; c8 < 8; ++c8) {
-                        if (c8 * 8 >= I.kpf) break;
+                for (int h = 0; h < 2; ++h) {
+                    if (h * kPHalf >= pe) break;
+                    const int ps = g * nps + pi;
+                    if (!tc::mbar_wait(&C.p_empty[ps], pph ^ 1u, kWaitLimitE)) {
+                        atomicOr(err, 2);
+                        dead = true;
+                        break;
+                    }
+                    unsigned char* Pb = pbuf + (size_t)ps * kPSlotBytes;
+#pragma unroll
+                    for (int c8 = 0; c8 < 4; ++c8) {
                         float v[8];
 #pragma unroll
                         for (int e = 0; e < 8; ++e) {
-                            const int d = c8 * 8 + e;
+                            const int dg = h * kPHalf + c8 * 8 + e;
                             float val;
-                            if (d == 0) {
+                            if (dg == 0) {
                                 val = 1.f;
-                            } else if (d == 1) {
-                                val = x;
+                            } else if (dg == 1) {
+                                val = xt;
                             } else {
-                                const float gd = float((d - 1) * (d - 1)) / float((2 * d - 1) * (2 * d - 3));
-                                const float Ln = fmaf(x, L, -gd * Lm);
+                                const float gd = float((dg - 1) * (dg - 1)) / float((2 * dg - 1) * (2 * dg - 3));
+                                const float Ln = fmaf(xt, L, -gd * Lm);
                                 Lm = L;
                                 L = Ln;
                                 val = Ln;
                             }
-                            v[e] = d < pe ? val : 0.f;
+                            v[e] = dg < pe ? val : 0.f;
                         }
-                        const uint32_t off = tc::kmajor_offset(row, c8 * 16, KPB);
+                        const uint32_t off = tc::kmajor_offset(row, c8 * 16, kPHalf * 2);
                         uint32_t hw[4], lw[4];
 #pragma unroll
                         for (int e = 0; e < 4; ++e) split2_bf16(v[2 * e], v[2 * e + 1], hw[e], lw[e]);
                         *reinterpret_cast<uint4*>(Pb + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-                        *reinterpret_cast<uint4*>(Pb + 128 * KPB + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+                        *reinterpret_cast<uint4*>(Pb + 128 * kPHalf * 2 + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+                    }
+                    tc::fence_async_smem();
+                    __syncwarp();
+                    if (lane == 0) tc::mbar_arrive(&C.p_full[ps]);
+                    if (++pi == nps) {
+                        pi = 0;
+                        pph ^= 1u;
                     }
                 }
-                tc::fence_async_smem();
-                handoff();
-                if (issuer) {
-                    wait(&w_bar[g], nw, 32);
-                    tc::fence_after_sync();
-                    for (int kk = 0; kk < kcount; ++kk) {
-                        const int k = kfirst + kk;
-                        const uint32_t pa = p_u32 + (kk ? buf1 : 0u);
-                        const uint32_t wb = core_u32 + (uint32_t)I.fac_off + (uint32_t)k * 2u * wbytes;
-                        const uint32_t d = tcol + 32u * k;
-                        for (int ks = 0; ks < I.kpf / 16; ++ks) {
-                            const uint32_t ko = ks * 256;
-                            const uint64_t ah = tc::make_desc(pa + ko, 128, SBOP);
-                            const uint64_t al = tc::make_desc(pa + 128 * KPB + ko, 128, SBOP);
-                            const uint64_t bh = tc::make_desc(wb + ko, 128, SBOP);
-                            const uint64_t bl = tc::make_desc(wb + wbytes + ko, 128, SBOP);
-                            tc::mma_bf16(d, ah, bh, idesc_f, ks > 0);
-                            tc::mma_bf16(d, ah, bl, idesc_f, 1u);
-                            tc::mma_bf16(d, al, bh, idesc_f, 1u);
-                        }
-                    }
-                    tc::mma_commit(&m_bar[g]);
-                    issued = true;
-                } else if (sub == 0) {
-                    ++nw;    // the issuer's lanes track the same phase count
-                }
-                wait(&m_bar[g], nm, 64);      // the step's U blocks in TMEM, the buffers free
-                tc::fence_after_sync();
-                converge();
             }
             if (dead) break;
-            // U_1..U_3 back from tensor memory: w1 over P as the contraction's A operand,
-            // w2 and w3 into registers
+        }
+    } else if (warp < 12) {
+        // ------------------------------------------------------------ epilogue
+        tc::setmaxnreg_inc<kRegsEpi>();
+        const int ew = warp & 3, row = ew * 32 + lane;
+        const uint32_t lanes = (uint32_t)(ew * 32) << 16;
+        long long cm = 0, qc = 0;      // factor blocks and contraction chunks consumed
+        bool dead = false;
+        auto wait = [&](uint64_t* bar, uint32_t par, int code) {
+            if (!dead && !tc::mbar_wait(bar, par, kWaitLimitE)) {
+                atomicOr(err, code);
+                dead = true;
+            }
+            tc::fence_after_sync();
+            dead = __any_sync(0xffffffffu, dead);
+        };
+        for (long long sd = 0; !dead; ++sd) {
+            const int slot = (int)(sd % kND);
+            wait(&C.desc_full[slot], (uint32_t)((sd / kND) & 1), 4);
+            if (dead) break;
+            const PipeDesc d = C.desc[slot];
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(&C.desc_empty[slot]);
+            if (d.item < 0) break;
+            const TcItem& I = items[d.item];
+            const int r1 = I.a.r[0], r3 = I.a.r[2];
+            const int nch = I.nchunks;
             float u2[RM], u3[RM];
-            {
-                float w1[RM];
-                tmem_ld_cols<RM>(tg + 0, w1);
-                tmem_ld_cols<RM>(tg + 32, u2);
-                tmem_ld_cols<RM>(tg + 64, u3);
-                tc::tmem_wait_ld();
+#pragma unroll 1
+            for (int k = 0; k < 3 && !dead; ++k, ++cm) {
+                const int us = (int)(cm & 1);
+                wait(&C.u_full[us], (uint32_t)((cm >> 1) & 1), 8);
+                if (dead) break;
+                // the three coefficient parts of the block, added low to high, 8 columns at a time
+                float uk[RM];
+                const uint32_t ub = tmem + lanes + (uint32_t)(kUBase + us * kUCols);
 #pragma unroll
-                for (int e = 0; e < RM; ++e) u3[e] = e < a.r[2] ? u3[e] : 0.f;
-                if (MODE == eTF32) {
-                    // TF32 operand: four elements a 16-byte chunk
+                for (int c = 0; c < RM; c += 8) {
+                    float th[8], tm[8], tl[8];
+                    tc::tmem_ld8(ub + c, th);
+                    tc::tmem_ld8(ub + 32 + c, tm);
+                    tc::tmem_ld8(ub + 64 + c, tl);
+                    tc::tmem_wait_ld();
 #pragma unroll
-                    for (int c16 = 0; c16 < 8; ++c16) {
-                        if (c16 * 16 >= KB) break;
-                        const uint32_t off = tc::kmajor_offset(row, c16 * 16, KB);
-                        uint32_t v4[4];
+                    for (int e = 0; e < 8; ++e) uk[c + e] = (tl[e] + tm[e]) + th[e];
+                }
+                tc::fence_before_sync();
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(&C.u_empty[us]);
+                if (k == 0) {
+                    // w1 as the contraction's A operand (the previous tile's chunks are done)
+                    wait(&C.w1_empty, (uint32_t)(sd & 1) ^ 1u, 16);
+                    if (dead) break;
+                    if (MODE == eTF32) {
 #pragma unroll
-                        for (int e = 0; e < 4; ++e) {
-                            const int i = c16 * 4 + e;
-                            v4[e] = tf32_dev(i < r1 && i < RM ? w1[i < RM ? i : 0] : 0.f);
+                        for (int c16 = 0; c16 < KB / 16; ++c16) {
+                            uint32_t v4[4];
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) {
+                                const int i = c16 * 4 + e;
+                                v4[e] = tf32_dev(i < RM && i < r1 ? uk[i < RM ? i : 0] : 0.f);
+                            }
+                            *reinterpret_cast<uint4*>(w1buf + tc::kmajor_offset(row, c16 * 16, KB)) =
+                                make_uint4(v4[0], v4[1], v4[2], v4[3]);
                         }
-                        *reinterpret_cast<uint4*>(P + off) = make_uint4(v4[0], v4[1], v4[2], v4[3]);
+                    } else {
+                        // BF16 words of the K-concatenated row: element i of [hi | lo | hi]
+                        uint16_t hb[RM], lb[RM];
+#pragma unroll
+                        for (int e = 0; e < RM; e += 2) {
+                            const float a0 = e < r1 ? uk[e] : 0.f, a1 = e + 1 < r1 ? uk[e + 1] : 0.f;
+                            uint32_t hw, lw;
+                            split2_bf16(a0, a1, hw, lw);
+                            hb[e] = (uint16_t)(hw & 0xffffu);
+                            hb[e + 1] = (uint16_t)(hw >> 16);
+                            lb[e] = (uint16_t)(lw & 0xffffu);
+                            lb[e + 1] = (uint16_t)(lw >> 16);
+                        }
+#pragma unroll
+                        for (int c16 = 0; c16 < KB / 16; ++c16) {
+                            uint32_t w4[4];
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) {
+                                uint32_t pr[2];
+#pragma unroll
+                                for (int hf = 0; hf < 2; ++hf) {
+                                    const int i = c16 * 8 + e * 2 + hf;
+                                    uint16_t b = 0;
+                                    if (i < RM) b = hb[i < RM ? i : 0];
+                                    else if (MODE == eBF16X3 && i < 2 * RM) b = lb[i - RM < RM && i >= RM ? i - RM : 0];
+                                    else if (MODE == eBF16X3 && i < 3 * RM) b = hb[i - 2 * RM < RM && i >= 2 * RM ? i - 2 * RM : 0];
+                                    pr[hf] = b;
+                                }
+                                w4[e] = pr[0] | (pr[1] << 16);
+                            }
+                            *reinterpret_cast<uint4*>(w1buf + tc::kmajor_offset(row, c16 * 16, KB)) =
+                                make_uint4(w4[0], w4[1], w4[2], w4[3]);
+                        }
                     }
-                } else
+                    tc::fence_async_smem();
+                    __syncwarp();
+                    if (lane == 0) tc::mbar_arrive(&C.w1_full);
+                } else if (k == 1) {
 #pragma unroll
-                for (int c16 = 0; c16 < 4; ++c16) {
-                    if (c16 * 16 >= KB) break;
-                    const uint32_t off = tc::kmajor_offset(row, c16 * 16, KB);
-                    float hh[8];
+                    for (int e = 0; e < RM; ++e) u2[e] = uk[e];
+                } else {
 #pragma unroll
-                    for (int e = 0; e < 8; ++e) {
-                        const int i = c16 * 8 + e;
-                        hh[e] = i < r1 && i < RM ? w1[i < RM ? i : 0] : 0.f;
-                    }
-                    uint32_t hw[4], lw[4];
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) split2_bf16(hh[2 * e], hh[2 * e + 1], hw[e], lw[e]);
-                    *reinterpret_cast<uint4*>(P + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-                    if (MODE == eBF16X3)
-                        *reinterpret_cast<uint4*>(P + abytes + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+                    for (int e = 0; e < RM; ++e) u3[e] = e < r3 ? uk[e] : 0.f;
                 }
             }
-            tc::fence_async_smem();
-            handoff();                         // w1 written, U read: chunk 0 may overwrite the U blocks
-            if (issuer) {
-                wait(&w_bar[g], nw, 1);
-                tc::fence_after_sync();
-                issue_chunk(0);
-            } else if (sub == 0) {
-                ++nw;
-            }
+            if (dead) break;
             // Khatri-Rao epilogue, chunk by chunk: per j-slice s_j = sum_k T_(j,k) w3_k in packed
             // pairs of k (two independent accumulators), then f += s_j w2_j
             float2 u3p[RM / 2];
 #pragma unroll
             for (int e = 0; e < RM / 2; ++e) u3p[e] = make_float2(u3[2 * e], u3[2 * e + 1]);
             float f = 0.f;
-            // u2 slides down by JC a chunk, so the chunk loop needs no unrolling: w2_{ch JC + jl}
-            // is u2[jl] in chunk ch (zero past the rank bound)
 #pragma unroll 1
             for (int ch = 0; ch < MAXCH; ++ch) {
-                if (ch < nch) {
-                    wait(&m_bar[g], nm, 2);
-                    tc::fence_after_sync();
-                    converge();
-                    if (dead) break;
-                    float2 sa = make_float2(0.f, 0.f), sb = make_float2(0.f, 0.f);
+                if (ch >= nch) break;
+                const int cb = (int)(qc & 1);
+                wait(&C.c_full[cb], (uint32_t)((qc >> 1) & 1), 32);
+                if (dead) break;
+                const uint32_t cbase = tmem + lanes + (uint32_t)(cb * kChunkCols);
+                float2 sa = make_float2(0.f, 0.f), sb = make_float2(0.f, 0.f);
 #pragma unroll
-                    for (int c0 = 0; c0 < NC; c0 += 16 * kEpiBatch) {
-                        float v[kEpiBatch][16];
+                for (int c0 = 0; c0 < NC; c0 += 16 * kEpiBatch) {
+                    float v[kEpiBatch][16];
 #pragma unroll
-                        for (int b = 0; b < kEpiBatch; ++b)
-                            if (c0 + 16 * b < NC) tc::tmem_ld16(tg + c0 + 16 * b, v[b]);
-                        tc::tmem_wait_ld();
+                    for (int b = 0; b < kEpiBatch; ++b)
+                        if (c0 + 16 * b < NC) tc::tmem_ld16(cbase + c0 + 16 * b, v[b]);
+                    tc::tmem_wait_ld();
 #pragma unroll
-                        for (int e = 0; e < 16 * kEpiBatch; e += 2) {
-                            const int col = c0 + e;
-                            if (col < NC) {
-                                const int jl = col / R3P, k = col % R3P;
-                                const float2 vv = make_float2(v[e / 16][e % 16], v[e / 16][e % 16 + 1]);
-                                const float2 ww = u3p[k / 2 < RM / 2 ? k / 2 : 0];
-                                if ((k & 2) == 0)
-                                    sa = __ffma2_rn(vv, ww, sa);
-                                else
-                                    sb = __ffma2_rn(vv, ww, sb);
-                                if (k == R3P - 2) {
-                                    if (jl < RM) f = fmaf((sa.x + sa.y) + (sb.x + sb.y), u2[jl < RM ? jl : 0], f);
-                                    sa = make_float2(0.f, 0.f);
-                                    sb = make_float2(0.f, 0.f);
-                                }
+                    for (int e = 0; e < 16 * kEpiBatch; e += 2) {
+                        const int col = c0 + e;
+                        if (col < NC) {
+                            const int jl = col / R3P, k = col % R3P;
+                            const float2 vv = make_float2(v[e / 16][e % 16], v[e / 16][e % 16 + 1]);
+                            const float2 ww = u3p[k / 2 < RM / 2 ? k / 2 : 0];
+                            if ((k & 2) == 0)
+                                sa = __ffma2_rn(vv, ww, sa);
+                            else
+                                sb = __ffma2_rn(vv, ww, sb);
+                            if (k == R3P - 2) {
+                                if (jl < RM) f = fmaf((sa.x + sa.y) + (sb.x + sb.y), u2[jl < RM ? jl : 0], f);
+                                sa = make_float2(0.f, 0.f);
+                                sb = make_float2(0.f, 0.f);
                             }
                         }
                     }
+                }
+                tc::fence_before_sync();
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(&C.c_empty[cb]);
+                ++qc;
+                // w2_{ch JC + jl} is u2[jl] in chunk ch (zero past the rank bound)
 #pragma unroll
-                    for (int e = 0; e < RM; ++e) u2[e] = e + JC < RM ? u2[e + JC < RM ? e + JC : 0] : 0.f;
-                    if (ch + 1 < nch) {
-                        handoff();             // chunk read: the next one may overwrite it
-                        if (issuer) {
-                            wait(&w_bar[g], nw, 4);
-                            tc::fence_after_sync();
-                            issue_chunk(ch + 1);
-                        } else if (sub == 0) {
-                            ++nw;
+                for (int e = 0; e < RM; ++e) u2[e] = e + JC < RM ? u2[e + JC < RM ? e + JC : 0] : 0.f;
+            }
+            if (dead) break;
+            const long long q = d.tile * 128 + row;
+            if (q < I.n) (out_ov ? out_ov : I.out)[q] = f;
+            __syncwarp();
+            if (lane == 0) atomicAdd(&C.tiles_done, 1);
+        }
+    } else if ((warp == 12 || warp == 14) && lane == 0) {
+        // ------------------------------------------------------------ MMA issuers
+        // Two threads on different schedulers: warp 12 issues the factor MMAs of every tile in
+        // order (modes 0, 1, 2), warp 14 the contraction chunks in order.  Each waits only on
+        // the barriers of its own jobs (suspending, bounded waits), and the matrix descriptors
+        // are formed once and advanced by adding offsets (the start address is their low field).
+        const bool fac = warp == 12;
+        const uint32_t core_u32 = tc::smem_u32(core), p_u32 = tc::smem_u32(pbuf), w1_u32 = tc::smem_u32(w1buf);
+        constexpr uint32_t idesc_c = MODE == eTF32 ? tc::idesc_tf32(128, NCP) : tc::idesc_bf16(128, NCP);
+        constexpr uint32_t idesc_f = tc::idesc_bf16(128, kUCols);
+        long long cf = 0, qc = 0;      // factor blocks and chunks issued
+        int pig[2] = {0, 0};           // next half-tile slot of each basis group and its use parity
+        uint32_t pphg[2] = {0u, 0u};
+        bool dead = false, issued = false;
+        auto wait = [&](uint64_t* bar, uint32_t par, int code) -> bool {
+            if (dead) return false;
+            if (!tc::mbar_wait(bar, par, kWaitLimitE)) {
+                atomicOr(err, code);
+                dead = true;
+                return false;
+            }
+            tc::fence_after_sync();
+            return true;
+        };
+        const uint64_t pdesc0 = tc::make_desc(p_u32, 128, 512);            // half-tile slot 0, hi part
+        const uint64_t adesc0 = tc::make_desc(w1_u32, 128, SBO_A);
+        for (long long sd = 0; !dead; ++sd) {
+            const int slot = (int)(sd % kND);
+            if (!wait(&C.desc_full[slot], (uint32_t)((sd / kND) & 1), 512)) break;
+            const int it = C.desc[slot].item;
+            tc::mbar_arrive(&C.desc_empty[slot]);
+            if (it < 0) break;
+            const TcItem& I = items[it];
+            if (fac) {
+                const int g = (int)(sd & 1);
+                const uint32_t kpb = (uint32_t)I.kpf * 2u;
+                const uint64_t wdesc0 = tc::make_desc(core_u32 + (uint32_t)I.fac_off, 128, (kpb / 16u) * 128u);
+#pragma unroll 1
+                for (int k = 0; k < 3 && !dead; ++k) {
+                    const int us = (int)(cf & 1);
+                    if (!wait(&C.u_empty[us], (uint32_t)((cf >> 1) & 1) ^ 1u, 1024)) break;
+                    const uint32_t dcol = tmem + (uint32_t)(kUBase + us * kUCols);
+                    const uint64_t wk = wdesc0 + (((uint64_t)k * kUCols * kpb) >> 4);
+                    const int nh = (I.a.pe[k] + kPHalf - 1) / kPHalf;
+#pragma unroll 1
+                    for (int hf = 0; hf < nh; ++hf) {
+                        const int ps = g * nps + pig[g];
+                        if (!wait(&C.p_full[ps], pphg[g], 2048)) break;
+                        const uint64_t pa = pdesc0 + (((uint64_t)ps * kPSlotBytes) >> 4);
+                        const uint64_t wb = wk + (uint64_t)(hf * 32);              // 512 bytes on
+#pragma unroll
+                        for (int ks = 0; ks < 2; ++ks)
+#pragma unroll
+                            for (int part = 0; part < 2; ++part)
+                                tc::mma_bf16(dcol, pa + (uint64_t)(part * (128 * kPHalf * 2 / 16) + ks * 16),
+                                             wb + (uint64_t)(ks * 16), idesc_f,
+                                             (hf > 0 || ks > 0 || part > 0) ? 1u : 0u);
+                        tc::mma_commit(&C.p_empty[ps]);
+                        issued = true;
+                        if (++pig[g] == nps) {
+                            pig[g] = 0;
+                            pphg[g] ^= 1u;
                         }
                     }
+                    if (dead) break;
+                    tc::mma_commit(&C.u_full[us]);
+                    ++cf;
                 }
+            } else {
+                if (!wait(&C.w1_full, (uint32_t)(sd & 1), 4096)) break;
+#pragma unroll 1
+                for (int ch = 0; ch < I.nchunks; ++ch) {
+                    const int cb = (int)(qc & 1);
+                    if (!wait(&C.c_empty[cb], (uint32_t)((qc >> 1) & 1) ^ 1u, 8192)) break;
+                    const uint64_t bd0 = tc::make_desc(core_u32 + (uint32_t)ch * (uint32_t)(NCP * KB), 128, SBO_A);
+                    const uint32_t dcol = tmem + (uint32_t)(cb * kChunkCols);
+#pragma unroll
+                    for (int ks = 0; ks < KB / 32; ++ks) {
+                        if (MODE == eTF32)
+                            tc::mma_tf32(dcol, adesc0 + (uint64_t)(ks * 16), bd0 + (uint64_t)(ks * 16), idesc_c, ks > 0);
+                        else
+                            tc::mma_bf16(dcol, adesc0 + (uint64_t)(ks * 16), bd0 + (uint64_t)(ks * 16), idesc_c, ks > 0);
+                    }
+                    tc::mma_commit(&C.c_full[cb]);
+                    issued = true;
+                    ++qc;
+                }
+                if (dead) break;
+                tc::mma_commit(&C.w1_empty);     // the tile's A operand is read
             }
-            if (ok && !dead) (out_ov ? out_ov : I.out)[q] = f;
         }
-    }
-    if (issuer && issued) {
-        // every MMA of this group completes before tensor memory is released
-        tc::mma_commit(&drain[g]);
-        if (!tc::mbar_wait(&drain[g], 0u, kWaitLimitE)) atomicOr(err, 16);
+        if (issued) {
+            // every MMA of this thread completes before tensor memory is released
+            tc::mma_commit(&C.drain[fac ? 0 : 1]);
+            if (!tc::mbar_wait(&C.drain[fac ? 0 : 1], 0u, kWaitLimitE)) atomicOr(err, 16);
+        }
     }
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
-    if (warp == 0) tc::tmem_dealloc(tmem, 512);
+    if (warp == 12) tc::tmem_dealloc(tmem, 512);
 }
 
 struct EvalErr {
@@ -938,9 +1158,9 @@ struct HostItem {
 // One size class of a batch: instances sharing the (rank, r3) padding, one launch.
 struct Bucket {
     int mode = 0, r3p = 8, rm = 8;
-    bool tc3 = false;            // factor step on the tensor cores (eval_tc3_kernel)
-    int kpf_max = 16;
-    int nbuf = 1;                // Legendre buffers per worker group (factor-step variant)
+    bool tc3 = false;            // factor step on the tensor cores (eval_pipe_kernel)
+    int kpf_max = 32;
+    int nps = 1;                 // Legendre half-tile slots per basis group (pipelined variant)
     std::vector<TcItem> items;
     std::vector<TcUnit> units;
     std::vector<int> cta_start;
@@ -1005,8 +1225,8 @@ fst_status build_buckets(const std::vector<HostItem>& hitems, int mode, std::vec
             tile_cost.push_back(fac + (double)ci.nchunks * ci.ncp * (PARTS == 2 ? 1.5 : 1.0) / 64.0);
             B.items.push_back(it);
         }
-        if (B.tc3) B.nbuf = tc3_nbuf(B.core_max, B.kb_max, B.kpf_max, PARTS);
-        B.smem = B.tc3 ? tc3_smem(B.core_max, B.kb_max, B.kpf_max, PARTS, B.nbuf)
+        if (B.tc3) B.nps = tc3_nps(B.core_max, B.kb_max);
+        B.smem = B.tc3 ? tc3_smem(B.core_max, B.kb_max, B.nps)
                        : 1024 + kBarBytes + B.core_max + (size_t)kGroups * PARTS * 128 * B.kb_max + tab_max + 16;
         if (B.smem > 227 * 1024) {
             set_error("model too large for the tensor-core evaluator (%zu bytes of shared memory)", B.smem);
@@ -1094,7 +1314,7 @@ fst_status launch_bucket_m(const Bucket& B, const unsigned char* dimg, int* err,
 
 template <int MODE, int R3P, int RM>
 fst_status launch_bucket_tc3_t(const Bucket& B, const unsigned char* dimg, int* err, cudaStream_t s, Overrides ov) {
-    auto kern = eval_tc3_kernel<MODE, R3P, RM>;
+    auto kern = eval_pipe_kernel<MODE, R3P, RM>;
     FST_TRY(allow_smem(kern, B.smem));
     // several instances: units from a counter; one: the static per-CTA ranges
     int* ctr = nullptr;
@@ -1102,10 +1322,10 @@ fst_status launch_bucket_tc3_t(const Bucket& B, const unsigned char* dimg, int* 
         ctr = reinterpret_cast<int*>(const_cast<unsigned char*>(dimg) + B.ctr_off);
         FST_CUDA(cudaMemsetAsync(ctr, 0, sizeof(int), s));
     }
-    kern<<<B.grid, kThreads3, B.smem, s>>>(reinterpret_cast<const TcItem*>(dimg + B.items_off),
+    kern<<<B.grid, kThreadsP, B.smem, s>>>(reinterpret_cast<const TcItem*>(dimg + B.items_off),
                                            reinterpret_cast<const TcUnit*>(dimg + B.units_off),
                                            reinterpret_cast<const int*>(dimg + B.cta_off), (int)B.units.size(), ctr,
-                                           B.core_max, B.kb_max, B.kpf_max, B.nbuf, ov.xyz, ov.out, err);
+                                           B.core_max, B.nps, ov.xyz, ov.out, err);
     FST_CHECK_LAUNCH();
     return FST_OK;
 }

@@ -132,6 +132,18 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
+// ---------------------------------------------------------------- register split
+// Per-warpgroup register budget (all four warps of the warpgroup execute it).  Increases draw
+// on what decreases of other warpgroups released from the block's launch allocation.
+template <int N>
+__device__ __forceinline__ void setmaxnreg_inc() {
+    asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(N));
+}
+template <int N>
+__device__ __forceinline__ void setmaxnreg_dec() {
+    asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(N));
+}
+
 // ---------------------------------------------------------------- descriptors and MMA
 // Shared-memory matrix descriptor: start address, leading (K) and stride (M/N) byte
 // offsets, descriptor version 1 (bits 46-48 = 0b001), no swizzle.
