@@ -602,6 +602,7 @@ struct PipeCtl {
     uint64_t c_full[2], c_empty[2];
     uint64_t drain[2];                   // one per MMA thread
     PipeDesc desc[kND];
+    TcItem item;         // the instance being evaluated (copied with its images)
     uint32_t tmem_base;
     int tiles_done;      // epilogue warps finished (one count per warp and tile)
 };
@@ -734,6 +735,11 @@ eval_pipe_kernel(const TcItem* __restrict__ items, const TcUnit* __restrict__ un
                 const uint4* src = reinterpret_cast<const uint4*>(I.core_img);
                 uint4* dst = reinterpret_cast<uint4*>(core);
                 for (int e = lane; e < I.img_bytes / 16; e += 32) dst[e] = src[e];
+                // the instance's parameters next to the images: every role reads them from
+                // shared memory (the descriptors published after this release them)
+                static_assert(sizeof(TcItem) % 4 == 0, "item copied in words");
+                for (int e = lane; e < (int)(sizeof(TcItem) / 4); e += 32)
+                    reinterpret_cast<int*>(&C.item)[e] = reinterpret_cast<const int*>(&I)[e];
                 tc::fence_async_smem();
                 __syncwarp();
                 cur = U.item;
@@ -786,7 +792,7 @@ eval_pipe_kernel(const TcItem* __restrict__ items, const TcUnit* __restrict__ un
             }
             const PipeDesc d = C.desc[slot];
             if (d.item < 0) break;
-            const TcItem& I = items[d.item];
+            const TcItem& I = C.item;
             const EvalArgs<float>& a = I.a;
             const float* X = xyz_ov ? xyz_ov : I.xyz;
             const long long n = I.n;
@@ -806,7 +812,7 @@ eval_pipe_kernel(const TcItem* __restrict__ items, const TcUnit* __restrict__ un
                 if (mbar_test(&C.desc_full[sl2], (uint32_t)((s2 / kND) & 1))) {
                     const PipeDesc d2 = C.desc[sl2];
                     if (d2.item >= 0) {
-                        const TcItem& I2 = items[d2.item];
+                        const TcItem& I2 = C.item;
                         const float* X2 = xyz_ov ? xyz_ov : I2.xyz;
                         const long long q2 = d2.tile * 128 + row;
 #pragma unroll
@@ -897,7 +903,7 @@ eval_pipe_kernel(const TcItem* __restrict__ items, const TcUnit* __restrict__ un
             __syncwarp();
             if (lane == 0) tc::mbar_arrive(&C.desc_empty[slot]);
             if (d.item < 0) break;
-            const TcItem& I = items[d.item];
+            const TcItem& I = C.item;
             const int r1 = I.a.r[0], r3 = I.a.r[2];
             const int nch = I.nchunks;
             float u2[RM], u3[RM];
@@ -1070,7 +1076,7 @@ eval_pipe_kernel(const TcItem* __restrict__ items, const TcUnit* __restrict__ un
             const int it = C.desc[slot].item;
             tc::mbar_arrive(&C.desc_empty[slot]);
             if (it < 0) break;
-            const TcItem& I = items[it];
+            const TcItem& I = C.item;
             if (fac) {
                 const int g = (int)(sd & 1);
                 const uint32_t kpb = (uint32_t)I.kpf * 2u;
