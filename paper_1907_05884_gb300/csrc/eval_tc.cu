@@ -912,7 +912,8 @@ eval_pipe_kernel(const TcItem* __restrict__ items, const TcUnit* __restrict__ un
                 const int us = (int)(cm & 1);
                 wait(&C.u_full[us], (uint32_t)((cm >> 1) & 1), 8);
                 if (dead) break;
-                // the three coefficient parts of the block, added low to high, 8 columns at a time
+                // the three coefficient parts of the block (all loads in flight, one wait), added
+                // low to high
                 float uk[RM];
                 const uint32_t ub = tmem + lanes + (uint32_t)(kUBase + us * kUCols);
 #pragma unroll
@@ -945,34 +946,27 @@ eval_pipe_kernel(const TcItem* __restrict__ items, const TcUnit* __restrict__ un
                                 make_uint4(v4[0], v4[1], v4[2], v4[3]);
                         }
                     } else {
-                        // BF16 words of the K-concatenated row: element i of [hi | lo | hi]
-                        uint16_t hb[RM], lb[RM];
+                        // BF16 words of the K-concatenated row [hi | lo | hi] (RM is even, so
+                        // every word is one split pair): word w < RM/2 is hi pair w, then the lo
+                        // pairs, then the hi pairs again, then zeros
+                        static_assert(RM % 2 == 0, "rank bound is even");
+                        uint32_t hw[RM / 2], lw[RM / 2];
 #pragma unroll
-                        for (int e = 0; e < RM; e += 2) {
-                            const float a0 = e < r1 ? uk[e] : 0.f, a1 = e + 1 < r1 ? uk[e + 1] : 0.f;
-                            uint32_t hw, lw;
-                            split2_bf16(a0, a1, hw, lw);
-                            hb[e] = (uint16_t)(hw & 0xffffu);
-                            hb[e + 1] = (uint16_t)(hw >> 16);
-                            lb[e] = (uint16_t)(lw & 0xffffu);
-                            lb[e + 1] = (uint16_t)(lw >> 16);
+                        for (int e = 0; e < RM / 2; ++e) {
+                            const float a0 = 2 * e < r1 ? uk[2 * e] : 0.f, a1 = 2 * e + 1 < r1 ? uk[2 * e + 1] : 0.f;
+                            split2_bf16(a0, a1, hw[e], lw[e]);
                         }
+                        constexpr int H = RM / 2;
 #pragma unroll
                         for (int c16 = 0; c16 < KB / 16; ++c16) {
                             uint32_t w4[4];
 #pragma unroll
                             for (int e = 0; e < 4; ++e) {
-                                uint32_t pr[2];
-#pragma unroll
-                                for (int hf = 0; hf < 2; ++hf) {
-                                    const int i = c16 * 8 + e * 2 + hf;
-                                    uint16_t b = 0;
-                                    if (i < RM) b = hb[i < RM ? i : 0];
-                                    else if (MODE == eBF16X3 && i < 2 * RM) b = lb[i - RM < RM && i >= RM ? i - RM : 0];
-                                    else if (MODE == eBF16X3 && i < 3 * RM) b = hb[i - 2 * RM < RM && i >= 2 * RM ? i - 2 * RM : 0];
-                                    pr[hf] = b;
-                                }
-                                w4[e] = pr[0] | (pr[1] << 16);
+                                const int w = c16 * 4 + e;
+                                w4[e] = w < H ? hw[w < H ? w : 0]
+                                        : (MODE == eBF16X3 && w < 2 * H) ? lw[w >= H && w < 2 * H ? w - H : 0]
+                                        : (MODE == eBF16X3 && w < 3 * H) ? hw[w >= 2 * H && w < 3 * H ? w - 2 * H : 0]
+                                                                         : 0u;
                             }
                             *reinterpret_cast<uint4*>(w1buf + tc::kmajor_offset(row, c16 * 16, KB)) =
                                 make_uint4(w4[0], w4[1], w4[2], w4[3]);
