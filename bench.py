@@ -142,7 +142,12 @@ def gpu_index_for_smi():
 GRAM_PK_BF16_TRAFFIC = 13.94e9 + 0.3565e9
 # DRAM bytes of one evaluation launch, keyed by (precision, points, degree), from one ncu
 # capture of the current kernel (a smaller case scaled by the point count where stated)
-EVAL_TRAFFIC: dict = {}
+EVAL_TRAFFIC = {
+    # eval_pipe_kernel<BF16X3, 24, 24>: 202.8 MB read + 48.1 MB written at 2^24 points, degree 63
+    # (ncu --set full), scaled by the point count (traffic is 15 B/point of streamed coordinates
+    # and values at both sizes)
+    ("bf16x3", 1 << 26, 63): 4 * (202.756352e6 + 48.059648e6),
+}
 
 
 def measured_peaks():

@@ -1,9 +1,10 @@
-"""Run one libfst entry point on seeded synthetic inputs, for timing and profiling.
+"""Run one libfst entry point on seeded synthetic inputs, for timing and profiling (the
+commands the summaries under profiles/ were made with).
 
-    python -m paper_1907_05884_gb300.drive gram  --prec bf16   --m 16384
-    python -m paper_1907_05884_gb300.drive eval  --prec bf16x3 --n 4194304
-    python -m paper_1907_05884_gb300.drive refit --prec bf16   --n 1048576
-    python -m paper_1907_05884_gb300.drive chol  --m 110592
+    python measure.py gram  --prec bf16   --m 16384
+    python measure.py eval  --prec bf16x3 --n 4194304
+    python measure.py refit --prec bf16   --n 1048576
+    python measure.py chol  --m 110592
 
 The model has ranks 24^3 and Legendre degree 31 with orthonormal factor functions (unless
 --ranks/--degree say otherwise); each call is repeated --reps times and timed with CUDA events.
@@ -11,8 +12,12 @@ The model has ranks 24^3 and Legendre degree 31 with orthonormal factor function
 from __future__ import annotations
 
 import argparse
+import sys
+from pathlib import Path
 
 import numpy as np
+
+sys.path.insert(0, str(Path(__file__).resolve().parent))
 
 
 def main():
