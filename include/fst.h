@@ -311,6 +311,17 @@ fst_status fst_normal_matrix(const fst_model* model, const float* xyz, const flo
  * 16 eps_32 max_i G_ii. */
 fst_status fst_cholesky_f32(float* G, int32_t R, fst_stream stream);
 
+/* Fault-injection hook for tests (the paper has no counterpart): the clock-cycle budget of
+ * the bounded spin waits of the one-launch triangular solves (refit, its conjugate
+ * gradients) on the current device, for calls made after this one; 0 restores the default
+ * (about one second).  A budget of a few cycles makes a solve block give up on a value the
+ * previous block row has not published yet: the block records the expiry in the solve's
+ * error word and finishes, and the refit returns FST_ETIMEOUT without touching the model;
+ * the device context stays usable.  The waits are plain loads, with no asynchronous copies
+ * or tensor-core work in flight, so an expiry leaves nothing behind.  FST_EINVAL for
+ * cycles < 0.  Not thread-safe with respect to refits running on the device. */
+fst_status fst_set_wait_limit(int64_t cycles);
+
 /* FP64 refit (xyz 3Q doubles, u Q doubles; FP64 Gram, FP64 Cholesky). */
 fst_status fst_refit_f64(fst_model* model, const double* xyz, const double* u, int64_t Q,
                          const int64_t* idx, int64_t m, uint64_t seed,

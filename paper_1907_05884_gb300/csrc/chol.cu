@@ -836,6 +836,8 @@ __global__ void __launch_bounds__(256) link_blocks_kernel(const T* __restrict__ 
 // on with what it read (the rows after it then finish without waiting out their own
 // limits).  sync: [0] error word, [1] ticket (zeroed before the launch).
 constexpr long long kSolveWaitLimit = 2000000000LL;
+// A shorter budget set by fst_set_wait_limit (0: kSolveWaitLimit), read once per block.
+__device__ long long g_solve_wait_limit = 0;
 
 __device__ __forceinline__ bool unpublished(float v) { return __float_as_uint(v) == 0xffffffffu; }
 __device__ __forceinline__ bool unpublished(double v) {
@@ -863,14 +865,14 @@ __device__ __forceinline__ T publishable(T v) {
     return unpublished(v) ? (T)NAN : v;
 }
 
-// wait for p to be published (bounded); returns the value
+// wait for p to be published (bounded by `limit` clock cycles); returns the value
 template <typename T>
-__device__ __forceinline__ T wait_value(const T* p, int* err) {
+__device__ __forceinline__ T wait_value(const T* p, int* err, long long limit) {
     T v = ld_relaxed(p);
     if (!unpublished(v)) return v;
     const long long t0 = clock64();
     while (unpublished(v = ld_relaxed(p))) {
-        if (clock64() - t0 > kSolveWaitLimit) {
+        if (clock64() - t0 > limit) {
             atomicOr(err, 1);
             return T(0);
         }
@@ -885,6 +887,7 @@ __global__ void __launch_bounds__(256) trsv_kernel(const T* __restrict__ M, cons
                                                    const T* __restrict__ K, int R, int nblk, const T* bin, T* out,
                                                    int* sync, const int* stop) {
     if (stop && *stop) return;   // the caller's iteration has already stopped (no block waits then)
+    const long long limit = g_solve_wait_limit > 0 ? g_solve_wait_limit : kSolveWaitLimit;
     __shared__ T lis[NB][NB + 1];   // Linv of the diagonal block
     __shared__ T red[8][NB];
     __shared__ T vs[NB];
@@ -944,8 +947,8 @@ __global__ void __launch_bounds__(256) trsv_kernel(const T* __restrict__ M, cons
                 // both values in one batch of L2 loads; spin only on one not yet published
                 T x0 = j0 + lane < R ? __ldcg(xj + lane) : T(0);
                 T x1 = j0 + lane + 32 < R ? __ldcg(xj + lane + 32) : T(0);
-                if (unpublished(x0)) x0 = wait_value(xj + lane, sync);
-                if (unpublished(x1)) x1 = wait_value(xj + lane + 32, sync);
+                if (unpublished(x0)) x0 = wait_value(xj + lane, sync, limit);
+                if (unpublished(x1)) x1 = wait_value(xj + lane + 32, sync, limit);
 #pragma unroll
                 for (int u = 0; u < 8; ++u) acc[u] += ring[d][2 * u] * x0 + ring[d][2 * u + 1] * x1;
             }
@@ -987,8 +990,8 @@ __global__ void __launch_bounds__(256) trsv_kernel(const T* __restrict__ M, cons
         const T* xj = out + j0;
         T x0 = j0 + lane < R ? __ldcg(xj + lane) : T(0);
         T x1 = j0 + lane + 32 < R ? __ldcg(xj + lane + 32) : T(0);
-        if (unpublished(x0)) x0 = wait_value(xj + lane, sync);
-        if (unpublished(x1)) x1 = wait_value(xj + lane + 32, sync);
+        if (unpublished(x0)) x0 = wait_value(xj + lane, sync, limit);
+        if (unpublished(x1)) x1 = wait_value(xj + lane + 32, sync, limit);
         xl[lane] = x0;
         xl[lane + 32] = x1;
     }
@@ -1153,5 +1156,13 @@ extern "C" fst_status fst_cholesky_f32(float* G, int32_t R, fst_stream stream) {
         set_error("matrix is not positive definite in FP32 (pivot below 16 eps max diag)");
         return FST_ENOTSPD;
     }
+    return FST_OK;
+}
+
+extern "C" fst_status fst_set_wait_limit(int64_t cycles) {
+    using namespace fst;
+    FST_REQUIRE(cycles >= 0, "cycles < 0");
+    const long long v = (long long)cycles;
+    FST_CUDA(cudaMemcpyToSymbol(g_solve_wait_limit, &v, sizeof v));
     return FST_OK;
 }

@@ -122,6 +122,7 @@ def _load():
         "fst_normal_matrix": (I32, [P, P, P, I64, P, I64, I32, P, P, P]),
         "fst_fit": (I32, [P, P, I64, P, P, P, I32, P, P, P, P, P]),
         "fst_cholesky_f32": (I32, [P, I32, P]),
+        "fst_set_wait_limit": (I32, [I64]),
         "fst_status_str": (C.c_char_p, [I32]),
         "fst_last_error": (C.c_char_p, []),
         "fst_build_info": (C.c_char_p, []),
@@ -468,6 +469,11 @@ def slice_points(axis: int, value: float, lo, hi, res0: int, res1: int, out=None
 
 def eval_check(stream=None):
     _check(lib.fst_eval_check(_stream(stream)))
+
+
+def set_wait_limit(cycles: int = 0):
+    """fst_set_wait_limit: budget of the triangular solves' bounded waits (0: the default)."""
+    _check(lib.fst_set_wait_limit(int(cycles)))
 
 
 def kernel_launches() -> int:
