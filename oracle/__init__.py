@@ -9,7 +9,9 @@ import, link or call it, and share no code with it.
 row sampler and the least-squares core refit (Sec. 5, eq. rand_core,
 Algorithm 2); ``mixing.py`` holds Algorithm 2's sign flip and fast mixing of the
 rows; ``fit.py`` holds the construction steps of Algorithm 1 (interpolation,
-ST-HOSVD, sparse Legendre fit).  Parity status of each function
+ST-HOSVD, sparse Legendre fit, choice between the Legendre and multiwavelet
+spaces); ``wavelet.py`` holds the multiwavelet spaces and the evaluation and
+refit of models whose factor functions use them.  Parity status of each function
 is stated in its docstring; every function here is pinned by a ``-m "not gpu"``
 test against closed forms, library routines or brute force, except where a
 docstring says "parity unpinned".
@@ -145,10 +147,19 @@ def factor_values(model, k: int, yk: float) -> np.ndarray:
     return out
 
 
+def _wavelet_model(model) -> bool:
+    """Models with columns in a multiwavelet space go to the numpy path of wavelet.py."""
+    from . import wavelet
+    return not isinstance(model, OracleModel) and wavelet.has_wavelets(model)
+
+
 def eval_points(model, xyz: np.ndarray, nthreads: int = 1) -> np.ndarray:
     """u~ at the columns of xyz (3, n), eq. func_tuck by the plain triple sum.
     Pinned: rank-one cores vs numpy legval products, the full tensor-product
     expansion of Sec. 2, and the affine box map."""
+    if _wavelet_model(model):
+        from . import wavelet
+        return wavelet.eval_points(model, xyz)
     om = model if isinstance(model, OracleModel) else OracleModel(model)
     y = np.ascontiguousarray(xyz, dtype=np.float64)
     n = y.shape[1]
@@ -172,6 +183,9 @@ def sample(seed: int, Q: int, m: int) -> np.ndarray:
 
 
 def design_matrix(model, xyz: np.ndarray, idx: np.ndarray) -> np.ndarray:
+    if _wavelet_model(model):
+        from . import wavelet
+        return wavelet.design_matrix(model, xyz, idx)
     om = model if isinstance(model, OracleModel) else OracleModel(model)
     y = np.ascontiguousarray(xyz, dtype=np.float64)
     idx = np.ascontiguousarray(idx, dtype=np.int64)
@@ -181,6 +195,11 @@ def design_matrix(model, xyz: np.ndarray, idx: np.ndarray) -> np.ndarray:
 
 
 def normal_equations(model, xyz, u, idx, nthreads: int = 1):
+    if _wavelet_model(model):
+        from . import wavelet
+        A = wavelet.design_matrix(model, xyz, idx)
+        b = np.asarray(u, dtype=np.float64)[np.asarray(idx, dtype=np.int64)]
+        return A.T @ A, A.T @ b, float(b @ b)
     om = model if isinstance(model, OracleModel) else OracleModel(model)
     y = np.ascontiguousarray(xyz, dtype=np.float64)
     u = np.ascontiguousarray(u, dtype=np.float64)
@@ -219,6 +238,9 @@ def refit(model, xyz, u, idx, nthreads: int = 1):
     """Core refit on rows idx (eq. rand_core): normal equations + Cholesky, QR fallback.
     Returns (alpha (r1, r2, r3), rc) with rc 0 = Cholesky, 1 = QR.  Pinned: normal-equation
     residual, m = Q against numpy lstsq, exact recovery, orthogonal-mixing invariance."""
+    if _wavelet_model(model):
+        from . import wavelet
+        return wavelet.refit(model, xyz, u, idx), 0
     om = model if isinstance(model, OracleModel) else OracleModel(model)
     y = np.ascontiguousarray(xyz, dtype=np.float64)
     u = np.ascontiguousarray(u, dtype=np.float64)
@@ -230,6 +252,11 @@ def refit(model, xyz, u, idx, nthreads: int = 1):
 
 
 def normal_residual(model, xyz, u, idx, alpha, nthreads: int = 1) -> np.ndarray:
+    if _wavelet_model(model):
+        from . import wavelet
+        A = wavelet.design_matrix(model, xyz, idx)
+        b = np.asarray(u, dtype=np.float64)[np.asarray(idx, dtype=np.int64)]
+        return A.T @ (A @ np.asarray(alpha, dtype=np.float64).reshape(-1) - b)
     om = model if isinstance(model, OracleModel) else OracleModel(model)
     y = np.ascontiguousarray(xyz, dtype=np.float64)
     u = np.ascontiguousarray(u, dtype=np.float64)

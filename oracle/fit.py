@@ -23,6 +23,9 @@ Readings where the paper is silent (stated again in the design notes):
     capped at max_rank; each eigenvector's largest-magnitude entry is made positive;
   * the stored coefficients are the least-squares fit on the chosen support
     (hybrid LARS), the support being the path breakpoint with the least LOO error;
+  * with a multiwavelet space W_{s,q} given (Sec. 4.2, Algorithm 1's basis choice, Fig. 3),
+    every column is fitted in P_p and in W_{s,q} and keeps the fit with the smaller LOO
+    error (within 1e-12 mean(y^2) of each other, P_p); wavelet.py defines the space;
   * a fitted factor function that lies in the span of the earlier ones of its mode
     (relative residual norm <= 1e-6 after in-order Gram-Schmidt on the orthonormal
     Legendre coefficients) is dropped: the refit's least squares (Sec. 5) needs
@@ -39,6 +42,7 @@ from dataclasses import dataclass, field
 import numpy as np
 
 from . import refit as _c_refit, sample as _c_sample
+from . import wavelet as _wav
 
 REFIT_SEED_OFFSET = 0x632BE59BD9B4E019
 
@@ -347,9 +351,13 @@ class FitModel:
     def nnz(self) -> int:
         return int(sum(len(v) for v in self.val))
 
+    wav: tuple | None = None            # (s, q) when some columns use W_{s,q}
+    col_wavelet: list | None = None     # per mode, a bool per column
+
     def with_alpha(self, alpha) -> "FitModel":
         return FitModel(self.r, self.p, self.colptr, self.rowidx, self.val,
-                        np.asarray(alpha, dtype=np.float64).reshape(self.r), self.lo, self.hi)
+                        np.asarray(alpha, dtype=np.float64).reshape(self.r), self.lo, self.hi,
+                        self.wav, self.col_wavelet)
 
 
 @dataclass
@@ -362,6 +370,7 @@ class FitParams:
     oversample: float = 4.0
     seed: int = 1
     fixed_rank: bool = False
+    wavelet: tuple | None = None      # (s, q): also fit every column in W_{s,q} and keep the better
 
 
 @dataclass
@@ -369,12 +378,31 @@ class FitReport:
     ranks: tuple = ()                 # after dropping dependent factor functions
     hosvd_ranks: tuple = ()           # chosen by the ST-HOSVD
     dropped: list = field(default_factory=list)   # per mode: dropped column indices
+    chose_wavelet: list = field(default_factory=list)   # per mode, per ST-HOSVD column
     nnz: list = field(default_factory=list)       # per ST-HOSVD column
     loo: list = field(default_factory=list)
     fill_sweeps: int = 0
     m: int = 0
     refit_rc: int = 0
     compression_ratio: float = 0.0
+
+
+def function_samples(p: int, wav, rows_vals_wavelet) -> np.ndarray:
+    """Columns sampled so that dot products are the inner products <f, g> = 1/2 int f g
+    of the functions: sqrt(weight / 2) f(x) at Gauss-Legendre nodes of every finest cell
+    (exact for the piecewise polynomials of degree <= max(p, q) here).  rows_vals_wavelet:
+    per column (rows, values, is_wavelet)."""
+    s_, q_ = wav
+    nc = 2 ** s_
+    xg, wg = np.polynomial.legendre.leggauss(max(p, q_) + 1)
+    nodes = np.concatenate([-1.0 + (2.0 * c + 1.0 + xg) / nc for c in range(nc)])
+    wts = np.concatenate([wg / nc for _ in range(nc)])          # weights in t
+    Pl = legendre_matrix(nodes, p)
+    Bw = _wav.basis_matrix(nodes, -1.0, 1.0, s_, q_)
+    S = np.empty((nodes.size, len(rows_vals_wavelet)))
+    for j, (rows, vals, isw) in enumerate(rows_vals_wavelet):
+        S[:, j] = (Bw if isw else Pl)[:, rows] @ vals
+    return S * np.sqrt(wts / 2.0)[:, None]
 
 
 def compression_ratio(Q: int, R: int, nnz: int) -> float:
@@ -404,17 +432,32 @@ def fit(xyz: np.ndarray, u: np.ndarray, params: FitParams, lo=None, hi=None,
         U = np.asarray(grid_values, dtype=np.float64)
     core, Ws, _ = st_hosvd(U, params.eps, params.max_rank, params.fixed_rank)
     rep.hosvd_ranks = tuple(W.shape[1] for W in Ws)
-    colptr, rowidx, val = [], [], []
+    colptr, rowidx, val, colwav = [], [], [], []
     for k in range(3):
         Phi = legendre_matrix(grid_nodes(U.shape[k]), params.max_degree)
         fits = [sparse_fit(Phi, Ws[k][:, j]) for j in range(Ws[k].shape[1])]
+        isw = [False] * len(fits)
+        if params.wavelet is not None:
+            Phw = _wav.grid_basis_matrix(U.shape[k], int(params.wavelet[0]), int(params.wavelet[1]))
+            for j in range(len(fits)):
+                fw = sparse_fit(Phw, Ws[k][:, j])
+                y = Ws[k][:, j]
+                # the smaller LOO error; within 1e-12 mean(y^2) of each other, P_p
+                if fw[2] < fits[j][2] - 1e-12 * float(np.mean(y * y)):
+                    fits[j], isw[j] = fw, True
+        rep.chose_wavelet.append(list(isw))
         rep.nnz.append([int(f[0].size) for f in fits])
         rep.loo.append([f[2] for f in fits])
-        C = np.zeros((params.max_degree + 1, len(fits)))
-        for j, (rows, coef, _) in enumerate(fits):
-            C[rows, j] = coef
+        if params.wavelet is None:
+            C = np.zeros((params.max_degree + 1, len(fits)))
+            for j, (rows, coef, _) in enumerate(fits):
+                C[rows, j] = coef
+        else:
+            C = function_samples(params.max_degree, params.wavelet,
+                                 [(f[0], f[1], isw[j]) for j, f in enumerate(fits)])
         kept = independent_columns(C)
         rep.dropped.append([j for j in range(len(fits)) if j not in kept])
+        colwav.append(np.asarray([isw[j] for j in kept], dtype=bool))
         core = np.take(core, kept, axis=k)
         cp = np.concatenate([[0], np.cumsum([fits[j][0].size for j in kept])]).astype(np.int32)
         colptr.append(cp)
@@ -423,11 +466,16 @@ def fit(xyz: np.ndarray, u: np.ndarray, params: FitParams, lo=None, hi=None,
     r = tuple(c.size - 1 for c in colptr)
     rep.ranks = r
     p3 = (params.max_degree,) * 3
-    model = FitModel(r, p3, colptr, rowidx, val, core, lo, hi)
+    anyw = params.wavelet is not None and any(c.any() for c in colwav)
+    model = FitModel(r, p3, colptr, rowidx, val, core, lo, hi,
+                     tuple(params.wavelet) if anyw else None, colwav if anyw else None)
     R = model.R
     m = min(int(math.ceil(params.oversample * R)), Q)
     idx = _c_sample((params.seed + REFIT_SEED_OFFSET) & 0xFFFFFFFFFFFFFFFF, Q, m)
-    alpha, rc = _c_refit(model, xyz, u, idx, nthreads=nthreads)
+    if anyw:
+        alpha, rc = _wav.refit(model, xyz, u, idx), 0
+    else:
+        alpha, rc = _c_refit(model, xyz, u, idx, nthreads=nthreads)
     rep.m, rep.refit_rc = m, rc
     model = model.with_alpha(alpha)
     rep.compression_ratio = compression_ratio(Q, R, model.nnz())

@@ -135,6 +135,8 @@ class Model:
     alpha: np.ndarray
     lo: np.ndarray = dc_field(default_factory=lambda: -np.ones(3))
     hi: np.ndarray = dc_field(default_factory=lambda: np.ones(3))
+    wav: tuple | None = None            # (s, q): the multiwavelet space W_{s,q} of wavelet columns
+    col_wavelet: list | None = None     # per mode, a bool per column: its rows index W_{s,q}
 
     @property
     def R(self) -> int:
@@ -153,7 +155,8 @@ class Model:
 
     def with_alpha(self, alpha: np.ndarray) -> "Model":
         return Model(self.r, self.p, self.colptr, self.rowidx, self.val,
-                     np.asarray(alpha, dtype=np.float64).reshape(self.r), self.lo, self.hi)
+                     np.asarray(alpha, dtype=np.float64).reshape(self.r), self.lo, self.hi,
+                     self.wav, self.col_wavelet)
 
 
 def random_model(r, p, seed: int, density: float = 0.6, decay: float = 1.0,
@@ -203,6 +206,40 @@ def random_model(r, p, seed: int, density: float = 0.6, decay: float = 1.0,
     lo = -np.ones(3) if lo is None else np.asarray(lo, dtype=np.float64)
     hi = np.ones(3) if hi is None else np.asarray(hi, dtype=np.float64)
     return Model(r, p, colptr, rowidx, val, alpha, lo, hi)
+
+
+def with_wavelet_columns(m: Model, wav=(3, 5), share: float = 0.5, seed: int = 0, density: float = 0.3) -> Model:
+    """A copy of model m where a share of the columns of every mode (at least one, never all
+    when r_k > 1) are replaced by random sparse unit-norm expansions in the multiwavelet
+    space W_{s,q} (function indices 0 .. (q+1) 2^s - 1), the rest kept."""
+    s_, q_ = int(wav[0]), int(wav[1])
+    nw = (q_ + 1) * 2 ** s_
+    rng = _rng(seed, 7)
+    colptr, rowidx, val, flags = [], [], [], []
+    for k in range(3):
+        r = m.r[k]
+        nwc = max(1, min(r - 1 if r > 1 else 1, int(round(share * r))))
+        wcols = set(rng.choice(r, size=nwc, replace=False).tolist())
+        cp, ri, vv, fl = [0], [], [], []
+        for j in range(r):
+            if j in wcols:
+                keep = max(1, int(round(density * nw)))
+                rows = np.sort(rng.choice(nw, size=keep, replace=False)).astype(np.int32)
+                c = rng.normal(size=rows.size)
+                c /= np.linalg.norm(c)
+            else:
+                s0, e0 = m.colptr[k][j], m.colptr[k][j + 1]
+                rows = np.asarray(m.rowidx[k][s0:e0], dtype=np.int32)
+                c = np.asarray(m.val[k][s0:e0], dtype=np.float64)
+            ri.append(rows)
+            vv.append(c)
+            cp.append(cp[-1] + rows.size)
+            fl.append(j in wcols)
+        colptr.append(np.asarray(cp, dtype=np.int32))
+        rowidx.append(np.concatenate(ri).astype(np.int32))
+        val.append(np.concatenate(vv).astype(np.float64))
+        flags.append(np.asarray(fl, dtype=bool))
+    return Model(m.r, m.p, colptr, rowidx, val, m.alpha, m.lo, m.hi, (s_, q_), flags)
 
 
 def row_indices(Q: int, m: int, seed: int) -> np.ndarray:
