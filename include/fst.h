@@ -33,6 +33,8 @@ extern "C" {
 
 #define FST_MAX_RANK 32
 #define FST_MAX_DEGREE 127
+#define FST_MAX_WAVELET_LEVEL 6       /* 2^s <= 64 cells */
+#define FST_MAX_WAVELET_DEGREE 15
 
 typedef struct fst_model fst_model;            /* opaque, device-resident, owned by the library */
 typedef struct CUstream_st* fst_stream;        /* a cudaStream_t */
@@ -96,6 +98,41 @@ fst_status fst_model_read(const fst_model* model, int32_t* colptr[3], int32_t* r
 
 /* Replace the core with r1 r2 r3 host values (C order).  Synchronous. */
 fst_status fst_model_set_core(fst_model* model, const double* alpha);
+
+/* Factor functions in a multiwavelet space (Sec. 4.2, Algorithm 1's choice between the
+ * Legendre space and a multiresolution space per singular vector, Fig. 3).  W_{s,q} is the
+ * space of piecewise polynomials of degree <= q on the 2^s equal cells of each box axis,
+ * with the orthonormal multiresolution basis (inner product 1/2 int f g over [-1, 1]):
+ * function n = 0..q is phi_n on the whole axis; function (q+1)(2^l + c) + i is the wavelet
+ * psi_{l,c,i}(t) = 2^{l/2} psi_i(2^l (t+1) - 2c - 1) on cell c of level l (l < s, i <= q),
+ * where psi_0..psi_q are sgn(t) phi_i(t) orthonormalised in order against phi_0..phi_q and
+ * the earlier psi.  A coordinate y is in finest cell f when f of the interior boundaries
+ * lo + ((hi - lo) c) 2^-s, c = 1..2^s-1, are <= y (exact FP64 comparison of y); points
+ * outside the box continue the first or last cell's polynomial.
+ *   level, degree  s (0..FST_MAX_WAVELET_LEVEL) and q (0..FST_MAX_WAVELET_DEGREE), with
+ *                  (q+1) 2^s <= 256
+ *   col_wavelet[k] r[k] flags (host); column j of mode k with a nonzero flag holds, in
+ *                  desc->rowidx / val, indices (0 <= idx < (q+1) 2^s, strictly increasing)
+ *                  and coefficients of the functions of W_{s,q}; the other columns are
+ *                  Legendre columns as in fst_model_desc.  col_wavelet[k] may be NULL
+ *                  (no wavelet columns in mode k).
+ * fst_model_create_wavelet copies everything like fst_model_create; the evaluators, refits,
+ * fits and model files handle such models.  The factor-step tensor-core evaluator serves
+ * Legendre-only models; wavelet models take the variant with factor values on the CUDA
+ * cores.  FST_EINVAL on out-of-range parameters or indices. */
+typedef struct {
+    int32_t level;
+    int32_t degree;
+    const uint8_t* col_wavelet[3];
+} fst_wavelet_desc;
+
+fst_status fst_model_create_wavelet(const fst_model_desc* desc, const fst_wavelet_desc* wav, fst_model** out);
+
+/* The model's multiwavelet space and column flags: *level = -1 when no column uses one
+ * (then *degree = 0 and the flags are all 0).  col_wavelet[k] (r[k] bytes, host) may be
+ * NULL.  Any pointer may be NULL. */
+fst_status fst_model_read_wavelet(const fst_model* model, int32_t* level, int32_t* degree,
+                                  uint8_t* col_wavelet[3]);
 
 /* Binary model file (".fstm", little-endian): magic "FSTM", version, ranks,
  * degrees, box, CSC coefficients and the core, all values FP64. */
@@ -342,6 +379,10 @@ typedef struct {
     uint64_t seed;            /* interpolation subset: fst_sample_rows(seed); refit rows: seed + 0x632BE59BD9B4E019 */
     const double* grid_values;/* host, optional: grid[0]*grid[1]*grid[2] values (C order) that replace the
                                  interpolation step (sample_frac is then ignored) */
+    int32_t wavelet;          /* 1: also fit every column in W_{wav_level, wav_degree} (fst_wavelet_desc) and
+                                 keep the fit with the smaller leave-one-out error; 0: Legendre only */
+    int32_t wav_level;        /* s, with (wav_degree + 1) 2^s <= 64 */
+    int32_t wav_degree;       /* q */
 } fst_fit_params;
 
 typedef struct {
@@ -355,6 +396,7 @@ typedef struct {
     double compression_ratio; /* Q / (R + nnz): values only, positions not counted (Sec. 2, Table 2) */
     double ms_interp, ms_hosvd, ms_sparse, ms_refit;   /* GPU time per step */
     fst_refit_report refit;
+    int32_t n_wavelet[3];     /* kept columns in the multiwavelet space, per mode */
 } fst_fit_report;
 
 /* Optional host outputs of the intermediate steps; any pointer may be NULL.
@@ -367,6 +409,9 @@ typedef struct {
  *   col_nnz      r1 + r2 + r3 (capacity, mode-major): coefficients kept per column
  *   col_loo      r1 + r2 + r3 (capacity): leave-one-out error of the chosen support
  *   col_kept     r1 + r2 + r3 (capacity): 1 if the fitted function was kept, 0 if dropped
+ *   col_wavelet  r1 + r2 + r3 (capacity): 1 if the column's fit is in W_{s,q}, 0 if in P_p
+ *   col_loo_alt  r1 + r2 + r3 (capacity): leave-one-out error of the other space's fit
+ *                (only with params->wavelet)
  * (r here: the ST-HOSVD ranks) */
 typedef struct {
     double* grid_values;
@@ -376,6 +421,8 @@ typedef struct {
     int32_t* col_nnz;
     double* col_loo;
     int32_t* col_kept;
+    int32_t* col_wavelet;
+    double* col_loo_alt;
 } fst_fit_trace;
 
 /* Build a model from Q scattered values (Algorithm 1, then the core refit of Algorithm 2):
@@ -388,9 +435,13 @@ typedef struct {
  *      eigenvectors of the FP64 mode Gram matrix (parallel cyclic Jacobi);
  *   3. each factor column gets a sparse orthonormal-Legendre expansion: the Lasso-LARS path
  *      on the grid nodes, every visited support refitted by least squares and the one with
- *      the least leave-one-out error kept (Sec. 3, Sec. 4.2); a fitted function in the span
- *      of the earlier ones of its mode (relative residual <= 1e-6, in-order Gram-Schmidt on
- *      the coefficients) is dropped, so the refit below has independent columns;
+ *      the least leave-one-out error kept (Sec. 3, Sec. 4.2); with params->wavelet the same
+ *      fit in W_{s,q} too, and the column keeps the space whose fit has the smaller
+ *      leave-one-out error (within 1e-12 mean(y^2) of each other: Legendre; Algorithm 1's
+ *      basis choice); a fitted function in the span of the earlier ones of its mode
+ *      (relative residual <= 1e-6, in-order Gram-Schmidt on the coefficients, or with
+ *      wavelets on exact quadrature samples of the functions) is dropped, so the refit
+ *      below has independent columns;
  *   4. fst_refit of the core on m = min(ceil(oversample R), Q) rows drawn with
  *      seed + 0x632BE59BD9B4E019, in `prec` (FST_FP64: the points are widened to FP64 and
  *      fst_refit_f64 runs).

@@ -59,7 +59,7 @@ __global__ void __launch_bounds__(128) eval_simt_kernel(const EvalArgs<T> a, con
 
     const int64_t stride = (int64_t)gridDim.x * BP;
     for (int64_t base = (int64_t)blockIdx.x * BP; base < n; base += stride) {
-        T t[3][PPT];
+        T t[3][PPT], yv[3][PPT];
 #pragma unroll
         for (int pp = 0; pp < PPT; ++pp) {
             const int64_t q = base + pp * B + tid;
@@ -67,21 +67,25 @@ __global__ void __launch_bounds__(128) eval_simt_kernel(const EvalArgs<T> a, con
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
                 const T y = ok ? xyz[k * n + q] : T(0);
+                yv[k][pp] = y;
                 t[k][pp] = fma(y, a.sc[k], a.of[k]);
             }
         }
         T acc[PPT][RM];
         factor_values<T, RM, PPT>(t[0], Ws[0], mk, a.pe[0], ra, rb, acc);
+        piecewise_values<T, RM, PPT>(yv[0], t[0], a, 0, acc);
 #pragma unroll
         for (int pp = 0; pp < PPT; ++pp)
 #pragma unroll
             for (int j = 0; j < RM; ++j) u1s[j * BP + pp * B + tid] = acc[pp][j];
         factor_values<T, RM, PPT>(t[1], Ws[1], mk + a.pm, a.pe[1], ra, rb, acc);
+        piecewise_values<T, RM, PPT>(yv[1], t[1], a, 1, acc);
 #pragma unroll
         for (int pp = 0; pp < PPT; ++pp)
 #pragma unroll
             for (int j = 0; j < RM; ++j) u2s[j * BP + pp * B + tid] = acc[pp][j];
         factor_values<T, RM, PPT>(t[2], Ws[2], mk + 2 * a.pm, a.pe[2], ra, rb, acc);  // w3 in registers
+        piecewise_values<T, RM, PPT>(yv[2], t[2], a, 2, acc);
 
         T f[PPT];
 #pragma unroll

@@ -112,7 +112,7 @@ int tc3_nps(size_t core_max, int kb_max) { return tc3_smem(core_max, kb_max, 2) 
 // The factor-step variant can serve contractions (TF32, BF16, BF16X3) with degrees below 64
 // whose images fit the shared memory.
 bool tc3_feasible(const fst_model* m, int mode, int r3p) {
-    if (kpf_of(m) > 64) return false;
+    if (kpf_of(m) > 64 || m->wav_s >= 0) return false;   // wavelet columns: factor values on the CUDA cores
     const CoreImage c = core_image_shape(m, mode, r3p, true);
     return tc3_smem((c.bytes + 1023) & ~(size_t)1023, c.kb, 1) <= 227 * 1024;
 }
@@ -387,9 +387,12 @@ eval_tc_kernel(const TcItem* __restrict__ items, const TcUnit* __restrict__ unit
             for (long long t = U.tile0 + g; t < U.tile0 + U.ntiles; t += kGroups, ++lt) {
                 const long long q = t * 128 + row;
                 const bool ok = q < n;
-                float tt[3][1];
+                float tt[3][1], yy[3][1];
 #pragma unroll
-                for (int k = 0; k < 3; ++k) tt[k][0] = fmaf(nxt[k], a.sc[k], a.of[k]);
+                for (int k = 0; k < 3; ++k) {
+                    yy[k][0] = nxt[k];
+                    tt[k][0] = fmaf(nxt[k], a.sc[k], a.of[k]);
+                }
                 {
                     const long long q2 = q + kGroups * 128;
                     const bool ok2 = t + kGroups < U.tile0 + U.ntiles && q2 < n;
@@ -398,12 +401,15 @@ eval_tc_kernel(const TcItem* __restrict__ items, const TcUnit* __restrict__ unit
                 }
                 float w[1][RM], u2[RM], u3[RM];
                 factor_values<float, RM, 1>(tt[1], Ws1, mk + a.pm, a.pe[1], ra, rb, w);
+                piecewise_values<float, RM, 1>(yy[1], tt[1], a, 1, w);
 #pragma unroll
                 for (int j = 0; j < RM; ++j) u2[j] = w[0][j];
                 factor_values<float, RM, 1>(tt[2], Ws2, mk + 2 * a.pm, a.pe[2], ra, rb, w);
+                piecewise_values<float, RM, 1>(yy[2], tt[2], a, 2, w);
 #pragma unroll
                 for (int j = 0; j < RM; ++j) u3[j] = j < a.r[2] ? w[0][j] : 0.f;
                 factor_values<float, RM, 1>(tt[0], Ws0, mk, a.pe[0], ra, rb, w);   // w1 -> A operand
+                piecewise_values<float, RM, 1>(yy[0], tt[0], a, 0, w);
                 if (!tc::mbar_wait(&a_empty[g], (uint32_t)(lt & 1) ^ 1u, kWaitLimitE)) {
                     atomicOr(err, 1);
                     dead = true;

@@ -732,6 +732,12 @@ fst_status validate_params(const fst_fit_params* P, int64_t Q, fst_prec prec) {
                 "sample_frac must be in (0, 1]");
     FST_REQUIRE(P->eps >= 0.0 && isfinite(P->eps), "eps must be finite and >= 0");
     FST_REQUIRE(P->oversample > 0.0 && isfinite(P->oversample), "oversample must be positive");
+    if (P->wavelet) {
+        FST_REQUIRE(P->wav_level >= 0 && P->wav_level <= FST_MAX_WAVELET_LEVEL && P->wav_degree >= 0 &&
+                        P->wav_degree <= FST_MAX_WAVELET_DEGREE && ((P->wav_degree + 1) << P->wav_level) <= kLarsMaxP,
+                    "wavelet space W_{%d,%d} outside the fit's limits ((q+1) 2^s <= %d)", P->wav_level,
+                    P->wav_degree, kLarsMaxP);
+    }
     return FST_OK;
 }
 
@@ -918,35 +924,77 @@ extern "C" fst_status fst_fit(const float* xyz, const float* u, int64_t Q, const
     // ---------------------------------------------------------------- step 3
     const int Pn = P.max_degree + 1;
     const int ncols = r[0] + r[1] + r[2];
+    const bool wav = P.wavelet != 0;
+    const int Pw = wav ? (P.wav_degree + 1) << P.wav_level : 0;
+    const int njobs = wav ? 2 * ncols : ncols;          // Legendre fits, then (with wavelets) W_{s,q} fits
     double* Phi[3] = {nullptr, nullptr, nullptr};
+    double* Phw[3] = {nullptr, nullptr, nullptr};
     LarsJob* jobs_d = nullptr;
     int32_t *rows_d = nullptr, *nnz_d = nullptr;
     double *coef_d = nullptr, *loo_d = nullptr;
     std::vector<LarsJob> jobs;
+    std::vector<double> phw_h[3];
     for (int k = 0; k < 3; ++k) {
         FST_TRY(sc.get(&Phi[k], (size_t)I[k] * Pn));
         legendre_design_kernel<<<1, 256, 0, s>>>(I[k], Pn, Phi[k]);
         FST_CHECK_LAUNCH();
         for (int j = 0; j < r[k]; ++j) jobs.push_back(LarsJob{Phi[k], W[k], r[k], j, I[k], Pn});
     }
-    FST_TRY(sc.get(&jobs_d, ncols));
-    FST_TRY(sc.get(&rows_d, (size_t)ncols * kLarsMaxP));
-    FST_TRY(sc.get(&coef_d, (size_t)ncols * kLarsMaxP));
-    FST_TRY(sc.get(&nnz_d, ncols));
-    FST_TRY(sc.get(&loo_d, ncols));
-    FST_CUDA(cudaMemcpyAsync(jobs_d, jobs.data(), ncols * sizeof(LarsJob), cudaMemcpyHostToDevice, s));
+    if (wav)
+        for (int k = 0; k < 3; ++k) {
+            wavelet_grid_design(I[k], P.wav_level, P.wav_degree, phw_h[k]);
+            FST_TRY(sc.get(&Phw[k], phw_h[k].size()));
+            FST_CUDA(cudaMemcpyAsync(Phw[k], phw_h[k].data(), phw_h[k].size() * sizeof(double),
+                                     cudaMemcpyHostToDevice, s));
+            for (int j = 0; j < r[k]; ++j) jobs.push_back(LarsJob{Phw[k], W[k], r[k], j, I[k], Pw});
+        }
+    FST_TRY(sc.get(&jobs_d, njobs));
+    FST_TRY(sc.get(&rows_d, (size_t)njobs * kLarsMaxP));
+    FST_TRY(sc.get(&coef_d, (size_t)njobs * kLarsMaxP));
+    FST_TRY(sc.get(&nnz_d, njobs));
+    FST_TRY(sc.get(&loo_d, njobs));
+    FST_CUDA(cudaMemcpyAsync(jobs_d, jobs.data(), njobs * sizeof(LarsJob), cudaMemcpyHostToDevice, s));
     const size_t lsm = 2 * (size_t)kLarsMaxP * kLarsMaxP * sizeof(double);
     FST_TRY(allow_smem(lars_loo_kernel, lsm));
-    lars_loo_kernel<<<ncols, kLarsThreads, lsm, s>>>(jobs_d, rows_d, coef_d, nnz_d, loo_d);
+    lars_loo_kernel<<<njobs, kLarsThreads, lsm, s>>>(jobs_d, rows_d, coef_d, nnz_d, loo_d);
     FST_CHECK_LAUNCH();
-    std::vector<int32_t> rows_h((size_t)ncols * kLarsMaxP), nnz_h(ncols);
-    std::vector<double> coef_h((size_t)ncols * kLarsMaxP), loo_h(ncols);
+    std::vector<int32_t> rows_h((size_t)njobs * kLarsMaxP), nnz_h(njobs);
+    std::vector<double> coef_h((size_t)njobs * kLarsMaxP), loo_h(njobs);
     FST_CUDA(cudaMemcpyAsync(rows_h.data(), rows_d, rows_h.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     FST_CUDA(cudaMemcpyAsync(coef_h.data(), coef_d, coef_h.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
-    FST_CUDA(cudaMemcpyAsync(nnz_h.data(), nnz_d, ncols * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-    FST_CUDA(cudaMemcpyAsync(loo_h.data(), loo_d, ncols * sizeof(double), cudaMemcpyDeviceToHost, s));
+    FST_CUDA(cudaMemcpyAsync(nnz_h.data(), nnz_d, njobs * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    FST_CUDA(cudaMemcpyAsync(loo_h.data(), loo_d, njobs * sizeof(double), cudaMemcpyDeviceToHost, s));
+    std::vector<double> Wh[3];
+    if (wav)
+        for (int k = 0; k < 3; ++k) {
+            Wh[k].resize((size_t)I[k] * r[k]);
+            FST_CUDA(cudaMemcpyAsync(Wh[k].data(), W[k], Wh[k].size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+        }
     tm.mark(3);
     FST_CUDA(cudaStreamSynchronize(s));
+    // Algorithm 1's basis choice: a column keeps its W_{s,q} fit when that fit's leave-one-out
+    // error is below the Legendre fit's by more than 1e-12 mean(y^2); `pick[c]` is the job whose
+    // fit the column keeps
+    std::vector<int> pick(ncols);
+    std::vector<uint8_t> chose(ncols, 0);
+    {
+        int c0 = 0;
+        for (int k = 0; k < 3; ++k) {
+            for (int j = 0; j < r[k]; ++j) {
+                const int c = c0 + j;
+                pick[c] = c;
+                if (!wav) continue;
+                double ms = 0.0;
+                for (int i = 0; i < I[k]; ++i) ms += Wh[k][(size_t)i * r[k] + j] * Wh[k][(size_t)i * r[k] + j];
+                ms /= I[k];
+                if (loo_h[ncols + c] < loo_h[c] - 1e-12 * ms) {
+                    pick[c] = ncols + c;
+                    chose[c] = 1;
+                }
+            }
+            c0 += r[k];
+        }
+    }
     if (trace && trace->core_hosvd) std::copy(core.begin(), core.end(), trace->core_hosvd);
     // step 4: drop dependent factor functions; the core keeps the matching slices
     std::vector<int32_t> colptr[3], rowidx[3];
@@ -954,24 +1002,51 @@ extern "C" fst_status fst_fit(const float* xyz, const float* u, int64_t Q, const
     std::vector<int> keep[3];
     int col0 = 0;
     int64_t nnz_total = 0;
+    std::vector<uint8_t> colwav[3];
     for (int k = 0; k < 3; ++k) {
-        std::vector<double> C((size_t)Pn * r[k], 0.0);
         for (int j = 0; j < r[k]; ++j) {
-            const int c = col0 + j;
-            for (int i = 0; i < nnz_h[c]; ++i)
-                C[(size_t)j * Pn + rows_h[(size_t)c * kLarsMaxP + i]] = coef_h[(size_t)c * kLarsMaxP + i];
-            if (trace && trace->col_nnz) trace->col_nnz[c] = nnz_h[c];
-            if (trace && trace->col_loo) trace->col_loo[c] = loo_h[c];
+            const int c = col0 + j, pc = pick[c];
+            if (trace && trace->col_nnz) trace->col_nnz[c] = nnz_h[pc];
+            if (trace && trace->col_loo) trace->col_loo[c] = loo_h[pc];
+            if (trace && trace->col_wavelet) trace->col_wavelet[c] = chose[c];
+            if (trace && trace->col_loo_alt && wav) trace->col_loo_alt[c] = loo_h[chose[c] ? c : ncols + c];
         }
-        keep[k] = independent_columns(C, Pn, r[k]);
+        if (!wav) {
+            std::vector<double> C((size_t)Pn * r[k], 0.0);
+            for (int j = 0; j < r[k]; ++j) {
+                const int c = col0 + j;
+                for (int i = 0; i < nnz_h[c]; ++i)
+                    C[(size_t)j * Pn + rows_h[(size_t)c * kLarsMaxP + i]] = coef_h[(size_t)c * kLarsMaxP + i];
+            }
+            keep[k] = independent_columns(C, Pn, r[k]);
+        } else {
+            // mixed spaces: the functions' inner products from exact quadrature samples
+            std::vector<const int32_t*> rr;
+            std::vector<const double*> vv;
+            std::vector<int> ln;
+            std::vector<uint8_t> iw;
+            for (int j = 0; j < r[k]; ++j) {
+                const int pc = pick[col0 + j];
+                rr.push_back(&rows_h[(size_t)pc * kLarsMaxP]);
+                vv.push_back(&coef_h[(size_t)pc * kLarsMaxP]);
+                ln.push_back(nnz_h[pc]);
+                iw.push_back(chose[col0 + j]);
+            }
+            std::vector<double> Smp;
+            int L = 0;
+            function_samples(P.max_degree, P.wav_level, P.wav_degree, rr, vv, ln, iw, Smp, L);
+            keep[k] = independent_columns(Smp, L, r[k]);
+        }
         colptr[k].push_back(0);
         for (int j : keep[k]) {
-            const int c = col0 + j;
-            for (int i = 0; i < nnz_h[c]; ++i) {
-                rowidx[k].push_back(rows_h[(size_t)c * kLarsMaxP + i]);
-                val[k].push_back(coef_h[(size_t)c * kLarsMaxP + i]);
+            const int pc = pick[col0 + j];
+            for (int i = 0; i < nnz_h[pc]; ++i) {
+                rowidx[k].push_back(rows_h[(size_t)pc * kLarsMaxP + i]);
+                val[k].push_back(coef_h[(size_t)pc * kLarsMaxP + i]);
             }
-            colptr[k].push_back(colptr[k].back() + nnz_h[c]);
+            colptr[k].push_back(colptr[k].back() + nnz_h[pc]);
+            colwav[k].push_back(chose[col0 + j]);
+            rep.n_wavelet[k] += chose[col0 + j];
         }
         if (trace && trace->col_kept)
             for (int j = 0; j < r[k]; ++j)
@@ -1004,7 +1079,15 @@ extern "C" fst_status fst_fit(const float* xyz, const float* u, int64_t Q, const
     }
     d.alpha = core.data();
     fst_model* model = nullptr;
-    FST_TRY(fst_model_create(&d, &model));
+    if (rep.n_wavelet[0] + rep.n_wavelet[1] + rep.n_wavelet[2] > 0) {
+        fst_wavelet_desc w{};
+        w.level = P.wav_level;
+        w.degree = P.wav_degree;
+        for (int k = 0; k < 3; ++k) w.col_wavelet[k] = colwav[k].data();
+        FST_TRY(fst_model_create_wavelet(&d, &w, &model));
+    } else {
+        FST_TRY(fst_model_create(&d, &model));
+    }
 
     // ---------------------------------------------------------------- step 4
     const int Rf = r[0] * r[1] * r[2];

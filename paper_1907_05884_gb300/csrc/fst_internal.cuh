@@ -150,6 +150,13 @@ struct fst_model {
 
     double* W64[3] = {nullptr, nullptr, nullptr};
     float* W32[3] = {nullptr, nullptr, nullptr};
+    // wavelet columns (Sec. 4.2): the space W_{s,q} (wav_s < 0: none), which columns use it,
+    // and their coefficients on the finest cells as local Legendre expansions
+    int wav_s = -1, wav_q = 0;
+    int wav_cols[3] = {0, 0, 0};
+    std::vector<uint8_t> colwav[3];
+    double* Wp64[3] = {nullptr, nullptr, nullptr};
+    float* Wp32[3] = {nullptr, nullptr, nullptr};
     uint8_t* rowmask[3] = {nullptr, nullptr, nullptr};
     double* alpha64 = nullptr;
     float* alpha32 = nullptr;
@@ -179,6 +186,16 @@ struct fst_model {
 namespace fst {
 
 void plan_free(fst_eval_plan* p);
+
+// Multiwavelet spaces W_{s,q} (wavelet.cu): Gauss-Legendre rules, the mother wavelets as
+// local Legendre expansions on the two halves, the finest-cell expansion of one function of
+// W_{s,q}, and the space's design at the fit's grid nodes.
+void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w);
+std::vector<double> mother_wavelets(int q);
+void wavelet_piecewise(int s, int q, int idx, const std::vector<double>& mw, std::vector<double>& out);
+void wavelet_grid_design(int N, int s, int q, std::vector<double>& Phi);
+void function_samples(int p, int s, int q, const std::vector<const int32_t*>& rows, const std::vector<const double*>& vals,
+                      const std::vector<int>& len, const std::vector<uint8_t>& is_wav, std::vector<double>& S, int& L);
 
 // Device upload of the derived layouts after the host copy changed.
 fst_status model_upload_core(fst_model* m);

@@ -4,6 +4,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <atomic>
 #include <map>
 #include <memory>
@@ -110,9 +111,13 @@ static void free_device(fst_model* m) {
         if (m->W64[k]) cudaFree(m->W64[k]);
         if (m->W32[k]) cudaFree(m->W32[k]);
         if (m->rowmask[k]) cudaFree(m->rowmask[k]);
+        if (m->Wp64[k]) cudaFree(m->Wp64[k]);
+        if (m->Wp32[k]) cudaFree(m->Wp32[k]);
         m->W64[k] = nullptr;
         m->W32[k] = nullptr;
         m->rowmask[k] = nullptr;
+        m->Wp64[k] = nullptr;
+        m->Wp32[k] = nullptr;
     }
     if (m->alpha64) cudaFree(m->alpha64);
     if (m->alpha32) cudaFree(m->alpha32);
@@ -169,8 +174,21 @@ fst_status model_upload_core(fst_model* m) {
     return model_invalidate_tc(m);
 }
 
-static fst_status validate_desc(const fst_model_desc* d) {
+static bool is_wavelet_col(const fst_wavelet_desc* w, int k, int j) {
+    return w && w->col_wavelet[k] && w->col_wavelet[k][j];
+}
+
+static fst_status validate_desc(const fst_model_desc* d, const fst_wavelet_desc* w) {
     FST_REQUIRE(d != nullptr, "model description is NULL");
+    int nwav = 0;
+    if (w) {
+        FST_REQUIRE(w->level >= 0 && w->level <= FST_MAX_WAVELET_LEVEL, "wavelet level %d outside [0,%d]", w->level,
+                    FST_MAX_WAVELET_LEVEL);
+        FST_REQUIRE(w->degree >= 0 && w->degree <= FST_MAX_WAVELET_DEGREE, "wavelet degree %d outside [0,%d]",
+                    w->degree, FST_MAX_WAVELET_DEGREE);
+        nwav = (w->degree + 1) << w->level;
+        FST_REQUIRE(nwav <= 256, "wavelet space of dimension %d above 256", nwav);
+    }
     FST_REQUIRE(d->alpha != nullptr, "alpha is NULL");
     for (int k = 0; k < 3; ++k) {
         FST_REQUIRE(d->r[k] >= 1 && d->r[k] <= FST_MAX_RANK, "rank r[%d]=%d outside [1,%d]", k,
@@ -184,11 +202,16 @@ static fst_status validate_desc(const fst_model_desc* d) {
         FST_REQUIRE(cp[0] == 0, "colptr[%d][0] must be 0", k);
         for (int j = 0; j < d->r[k]; ++j) {
             FST_REQUIRE(cp[j + 1] >= cp[j], "colptr[%d] decreases at %d", k, j);
+            const bool wc = is_wavelet_col(w, k, j);
             for (int e = cp[j]; e < cp[j + 1]; ++e) {
                 FST_REQUIRE(d->rowidx[k] && d->val[k], "rowidx/val[%d] is NULL", k);
                 int n = d->rowidx[k][e];
-                FST_REQUIRE(n >= 0 && n <= d->p[k], "degree %d of mode %d column %d outside [0,%d]",
-                            n, k, j, d->p[k]);
+                if (wc)
+                    FST_REQUIRE(n >= 0 && n < nwav, "wavelet index %d of mode %d column %d outside [0,%d)", n, k,
+                                j, nwav);
+                else
+                    FST_REQUIRE(n >= 0 && n <= d->p[k], "degree %d of mode %d column %d outside [0,%d]",
+                                n, k, j, d->p[k]);
                 FST_REQUIRE(e == cp[j] || n > d->rowidx[k][e - 1],
                             "degrees of mode %d column %d not strictly increasing", k, j);
                 FST_REQUIRE(isfinite(d->val[k][e]), "non-finite coefficient in mode %d", k);
@@ -202,10 +225,10 @@ static fst_status validate_desc(const fst_model_desc* d) {
 
 using namespace fst;
 
-extern "C" fst_status fst_model_create(const fst_model_desc* desc, fst_model** out) {
+static fst_status create_model(const fst_model_desc* desc, const fst_wavelet_desc* wav, fst_model** out) {
     FST_REQUIRE(out != nullptr, "out is NULL");
     *out = nullptr;
-    FST_TRY(validate_desc(desc));
+    FST_TRY(validate_desc(desc, wav));
     std::unique_ptr<fst_model> m(new fst_model());
     FST_CUDA(cudaGetDevice(&m->device));
     for (int k = 0; k < 3; ++k) {
@@ -217,6 +240,16 @@ extern "C" fst_status fst_model_create(const fst_model_desc* desc, fst_model** o
         m->colptr[k].assign(desc->colptr[k], desc->colptr[k] + desc->r[k] + 1);
         m->rowidx[k].assign(desc->rowidx[k], desc->rowidx[k] + nnz);
         m->val[k].assign(desc->val[k], desc->val[k] + nnz);
+        m->colwav[k].assign(desc->r[k], 0);
+        for (int j = 0; j < desc->r[k]; ++j)
+            if (is_wavelet_col(wav, k, j)) {
+                m->colwav[k][j] = 1;
+                ++m->wav_cols[k];
+            }
+    }
+    if (wav && m->wav_cols[0] + m->wav_cols[1] + m->wav_cols[2] > 0) {
+        m->wav_s = wav->level;
+        m->wav_q = wav->degree;
     }
     const size_t R = (size_t)m->R();
     m->alpha.assign(desc->alpha, desc->alpha + R);
@@ -231,7 +264,7 @@ extern "C" fst_status fst_model_create(const fst_model_desc* desc, fst_model** o
         std::vector<uint8_t> mask(np, 0);
         int pe = 1;
         for (int j = 0; j < rk; ++j)
-            for (int e = m->colptr[k][j]; e < m->colptr[k][j + 1]; ++e) {
+            for (int e = m->colptr[k][j]; e < m->colptr[k][j + 1] && !m->colwav[k][j]; ++e) {
                 const int n = m->rowidx[k][e];
                 const double c = m->val[k][e] * sqrt(2.0 * n + 1.0);
                 W[(size_t)n * rk + j] = c;
@@ -252,7 +285,42 @@ extern "C" fst_status fst_model_create(const fst_model_desc* desc, fst_model** o
         e1 = cudaMemcpy(m->W64[k], W.data(), W.size() * sizeof(double), cudaMemcpyHostToDevice);
         e2 = cudaMemcpy(m->W32[k], W32.data(), W32.size() * sizeof(float), cudaMemcpyHostToDevice);
         e3 = cudaMemcpy(m->rowmask[k], mask.data(), mask.size(), cudaMemcpyHostToDevice);
-        if (e1 || e2 || e3) st = cuda_fail(e1 ? e1 : e2 ? e2 : e3, "cudaMemcpy(model)", __FILE__, __LINE__);
+        if (e1 || e2 || e3) {
+            st = cuda_fail(e1 ? e1 : e2 ? e2 : e3, "cudaMemcpy(model)", __FILE__, __LINE__);
+            break;
+        }
+        if (m->wav_cols[k] == 0) continue;
+        // wavelet columns: the exact expansion of each on the finest cells, as coefficients of
+        // sqrt(2n+1) L_n of the cell's local coordinate (sqrt(2n+1) folded in)
+        const int nq = m->wav_q + 1, cells = 1 << m->wav_s;
+        const std::vector<double> mw = mother_wavelets(m->wav_q);
+        std::vector<double> Wp((size_t)cells * nq * rk, 0.0), pw;
+        for (int j = 0; j < rk; ++j) {
+            if (!m->colwav[k][j]) continue;
+            for (int e = m->colptr[k][j]; e < m->colptr[k][j + 1]; ++e) {
+                wavelet_piecewise(m->wav_s, m->wav_q, m->rowidx[k][e], mw, pw);
+                for (int f = 0; f < cells; ++f)
+                    for (int n = 0; n < nq; ++n)
+                        Wp[((size_t)f * nq + n) * rk + j] += m->val[k][e] * pw[(size_t)f * nq + n];
+            }
+        }
+        std::vector<float> Wp32(Wp.size());
+        for (int f = 0; f < cells; ++f)
+            for (int n = 0; n < nq; ++n)
+                for (int j = 0; j < rk; ++j) {
+                    double& v = Wp[((size_t)f * nq + n) * rk + j];
+                    v *= sqrt(2.0 * n + 1.0);
+                    Wp32[((size_t)f * nq + n) * rk + j] = (float)v;
+                }
+        e1 = cudaMalloc(&m->Wp64[k], Wp.size() * sizeof(double));
+        e2 = cudaMalloc(&m->Wp32[k], Wp.size() * sizeof(float));
+        if (e1 || e2) {
+            st = cuda_fail(e1 ? e1 : e2, "cudaMalloc(model)", __FILE__, __LINE__);
+            break;
+        }
+        e1 = cudaMemcpy(m->Wp64[k], Wp.data(), Wp.size() * sizeof(double), cudaMemcpyHostToDevice);
+        e2 = cudaMemcpy(m->Wp32[k], Wp32.data(), Wp32.size() * sizeof(float), cudaMemcpyHostToDevice);
+        if (e1 || e2) st = cuda_fail(e1 ? e1 : e2, "cudaMemcpy(model)", __FILE__, __LINE__);
     }
     if (st == FST_OK) {
         cudaError_t e1 = cudaMalloc(&m->alpha64, R * sizeof(double));
@@ -265,6 +333,26 @@ extern "C" fst_status fst_model_create(const fst_model_desc* desc, fst_model** o
         return st;
     }
     *out = m.release();
+    return FST_OK;
+}
+
+extern "C" fst_status fst_model_create(const fst_model_desc* desc, fst_model** out) {
+    return create_model(desc, nullptr, out);
+}
+
+extern "C" fst_status fst_model_create_wavelet(const fst_model_desc* desc, const fst_wavelet_desc* wav,
+                                               fst_model** out) {
+    FST_REQUIRE(wav != nullptr, "wavelet description is NULL");
+    return create_model(desc, wav, out);
+}
+
+extern "C" fst_status fst_model_read_wavelet(const fst_model* m, int32_t* level, int32_t* degree,
+                                             uint8_t* col_wavelet[3]) {
+    FST_REQUIRE(m != nullptr, "model is NULL");
+    if (level) *level = m->wav_s;
+    if (degree) *degree = m->wav_s >= 0 ? m->wav_q : 0;
+    for (int k = 0; k < 3; ++k)
+        if (col_wavelet && col_wavelet[k]) memcpy(col_wavelet[k], m->colwav[k].data(), m->r[k]);
     return FST_OK;
 }
 
@@ -322,7 +410,7 @@ extern "C" fst_status fst_model_set_core(fst_model* m, const double* alpha) {
 
 // ------------------------------------------------------------------ model files
 static const char kMagic[4] = {'F', 'S', 'T', 'M'};
-static const uint32_t kVersion = 1;
+static const uint32_t kVersion = 2;    // 2 adds the wavelet section; 1 is still read
 
 extern "C" fst_status fst_model_save(const fst_model* m, const char* path) {
     FST_REQUIRE(m != nullptr && path != nullptr, "model or path is NULL");
@@ -344,6 +432,10 @@ extern "C" fst_status fst_model_save(const fst_model* m, const char* path) {
         ok = ok && fwrite(m->val[k].data(), 8, nnz, f) == (size_t)nnz;
     }
     ok = ok && fwrite(m->alpha.data(), 8, m->alpha.size(), f) == m->alpha.size();
+    int32_t wv[2] = {m->wav_s, m->wav_s >= 0 ? m->wav_q : 0};
+    ok = ok && fwrite(wv, 4, 2, f) == 2;
+    for (int k = 0; k < 3 && ok && m->wav_s >= 0; ++k)
+        ok = fwrite(m->colwav[k].data(), 1, m->r[k], f) == (size_t)m->r[k];
     ok = (fclose(f) == 0) && ok;
     if (!ok) {
         set_error("write to %s failed", path);
@@ -367,7 +459,7 @@ extern "C" fst_status fst_model_load(const char* path, fst_model** out) {
     fst_model_desc d;
     memset(&d, 0, sizeof d);
     if (fread(magic, 1, 4, f) != 4 || memcmp(magic, kMagic, 4) != 0 || fread(&ver, 4, 1, f) != 1 ||
-        ver != kVersion || fread(hdr, 4, 6, f) != 6 || fread(d.lo, 8, 3, f) != 3 ||
+        (ver != 1 && ver != kVersion) || fread(hdr, 4, 6, f) != 6 || fread(d.lo, 8, 3, f) != 3 ||
         fread(d.hi, 8, 3, f) != 3) {
         set_error("%s: not an FSTM v%u file", path, kVersion);
         return FST_EFORMAT;
@@ -384,7 +476,7 @@ extern "C" fst_status fst_model_load(const char* path, fst_model** out) {
     std::vector<double> vv[3];
     for (int k = 0; k < 3; ++k) {
         int32_t nnz = -1;
-        if (fread(&nnz, 4, 1, f) != 1 || nnz < 0 || nnz > d.r[k] * (d.p[k] + 1)) {
+        if (fread(&nnz, 4, 1, f) != 1 || nnz < 0 || nnz > d.r[k] * std::max(d.p[k] + 1, 256)) {
             set_error("%s: bad coefficient count", path);
             return FST_EFORMAT;
         }
@@ -407,7 +499,31 @@ extern "C" fst_status fst_model_load(const char* path, fst_model** out) {
         return FST_EFORMAT;
     }
     d.alpha = al.data();
-    fst_status st = fst_model_create(&d, out);
+    fst_wavelet_desc w;
+    memset(&w, 0, sizeof w);
+    std::vector<uint8_t> cw[3];
+    bool has_wav = false;
+    if (ver >= 2) {
+        int32_t wv[2];
+        if (fread(wv, 4, 2, f) != 2) {
+            set_error("%s: truncated wavelet section", path);
+            return FST_EFORMAT;
+        }
+        if (wv[0] >= 0) {
+            has_wav = true;
+            w.level = wv[0];
+            w.degree = wv[1];
+            for (int k = 0; k < 3; ++k) {
+                cw[k].resize(d.r[k]);
+                if (fread(cw[k].data(), 1, d.r[k], f) != (size_t)d.r[k]) {
+                    set_error("%s: truncated wavelet flags", path);
+                    return FST_EFORMAT;
+                }
+                w.col_wavelet[k] = cw[k].data();
+            }
+        }
+    }
+    fst_status st = has_wav ? fst_model_create_wavelet(&d, &w, out) : fst_model_create(&d, out);
     if (st == FST_EINVAL) st = FST_EFORMAT;
     return st;
 }

@@ -63,9 +63,11 @@ __global__ void __launch_bounds__(128) sampled_factors_kernel(const EvalArgs<dou
         bvec[s] = u[q];
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            double t[1] = {fma((double)xyz[k * Q + q], a.sc[k], a.of[k])};
+            double y[1] = {(double)xyz[k * Q + q]};
+            double t[1] = {fma(y[0], a.sc[k], a.of[k])};
             double acc[1][RM];
             factor_values<double, RM, 1>(t, Ws[k], mk + k * a.pm, a.pe[k], ra, rb, acc);
+            piecewise_values<double, RM, 1>(y, t, a, k, acc);
             const int rk = a.r[k];
             for (int j = 0; j < rk; ++j) outs[k][s * rk + j] = (T)acc[0][j];
         }

@@ -37,6 +37,10 @@ class ModelDesc(C.Structure):
     ]
 
 
+class WaveletDesc(C.Structure):
+    _fields_ = [("level", C.c_int32), ("degree", C.c_int32), ("col_wavelet", C.c_void_p * 3)]
+
+
 class EvalItem(C.Structure):
     _fields_ = [("model", C.c_void_p), ("xyz", C.c_void_p), ("n", C.c_int64), ("out", C.c_void_p)]
 
@@ -64,7 +68,8 @@ class RefitItem(C.Structure):
 class FitParams(C.Structure):
     _fields_ = [("grid", C.c_int32 * 3), ("sample_frac", C.c_double), ("eps", C.c_double),
                 ("max_rank", C.c_int32 * 3), ("max_degree", C.c_int32), ("fixed_rank", C.c_int32),
-                ("oversample", C.c_double), ("seed", C.c_uint64), ("grid_values", C.c_void_p)]
+                ("oversample", C.c_double), ("seed", C.c_uint64), ("grid_values", C.c_void_p),
+                ("wavelet", C.c_int32), ("wav_level", C.c_int32), ("wav_degree", C.c_int32)]
 
 
 class FitReport(C.Structure):
@@ -72,20 +77,22 @@ class FitReport(C.Structure):
                 ("fill_sweeps", C.c_int32),
                 ("eig_sweeps", C.c_int32 * 3), ("n_interp", C.c_int64), ("m", C.c_int64),
                 ("compression_ratio", C.c_double), ("ms_interp", C.c_double), ("ms_hosvd", C.c_double),
-                ("ms_sparse", C.c_double), ("ms_refit", C.c_double), ("refit", RefitReport)]
+                ("ms_sparse", C.c_double), ("ms_refit", C.c_double), ("refit", RefitReport),
+                ("n_wavelet", C.c_int32 * 3)]
 
     def as_dict(self):
         d = {}
         for f, _ in self._fields_:
             v = getattr(self, f)
-            d[f] = v.as_dict() if f == "refit" else (tuple(v) if f in ("r", "r_hosvd", "nnz", "eig_sweeps") else v)
+            d[f] = v.as_dict() if f == "refit" else (tuple(v) if f in ("r", "r_hosvd", "nnz", "eig_sweeps",
+                                                                           "n_wavelet") else v)
         return d
 
 
 class FitTrace(C.Structure):
     _fields_ = [("grid_values", C.c_void_p), ("eigvals", C.c_void_p * 3), ("W", C.c_void_p * 3),
                 ("core_hosvd", C.c_void_p), ("col_nnz", C.c_void_p), ("col_loo", C.c_void_p),
-                ("col_kept", C.c_void_p)]
+                ("col_kept", C.c_void_p), ("col_wavelet", C.c_void_p), ("col_loo_alt", C.c_void_p)]
 
 
 def _load():
@@ -96,6 +103,8 @@ def _load():
     P, I32, I64, U64 = C.c_void_p, C.c_int32, C.c_int64, C.c_uint64
     sig = {
         "fst_model_create": (I32, [P, P]),
+        "fst_model_create_wavelet": (I32, [P, P, P]),
+        "fst_model_read_wavelet": (I32, [P, P, P, P]),
         "fst_model_free": (None, [P]),
         "fst_model_shape": (I32, [P, P, P, P]),
         "fst_model_read": (I32, [P, P, P, P, P, P, P]),
@@ -179,7 +188,17 @@ class Model:
         al = np.ascontiguousarray(np.asarray(m.alpha, dtype=np.float64).reshape(-1))
         keep.append(al)
         d.alpha = al.ctypes.data
-        _check(lib.fst_model_create(C.byref(d), C.byref(self._h)))
+        cw = getattr(m, "col_wavelet", None)
+        if cw is not None and getattr(m, "wav", None) is not None and any(np.any(c) for c in cw):
+            w = WaveletDesc()
+            w.level, w.degree = int(m.wav[0]), int(m.wav[1])
+            for k in range(3):
+                f = np.ascontiguousarray(np.asarray(cw[k], dtype=bool).astype(np.uint8))
+                keep.append(f)
+                w.col_wavelet[k] = f.ctypes.data
+            _check(lib.fst_model_create_wavelet(C.byref(d), C.byref(w), C.byref(self._h)))
+        else:
+            _check(lib.fst_model_create(C.byref(d), C.byref(self._h)))
 
     @classmethod
     def load(cls, path: str) -> "Model":
@@ -221,8 +240,20 @@ class Model:
         arr = lambda xs: (C.c_void_p * 3)(*[x.ctypes.data for x in xs])
         _check(lib.fst_model_read(self._h, arr(cps), arr(ris), arr(vvs), al.ctypes.data,
                                   lo.ctypes.data, hi.ctypes.data))
+        level, degree = C.c_int32(), C.c_int32()
+        flags = [np.zeros(r[k], np.uint8) for k in range(3)]
+        _check(lib.fst_model_read_wavelet(self._h, C.byref(level), C.byref(degree), arr(flags)))
+        wav = (level.value, degree.value) if level.value >= 0 else None
         return {"r": r, "p": p, "colptr": cps, "rowidx": [ris[k][:nnz[k]] for k in range(3)],
-                "val": [vvs[k][:nnz[k]] for k in range(3)], "alpha": al.reshape(r), "lo": lo, "hi": hi}
+                "val": [vvs[k][:nnz[k]] for k in range(3)], "alpha": al.reshape(r), "lo": lo, "hi": hi,
+                "wav": wav, "col_wavelet": [f.astype(bool) for f in flags] if wav else None}
+
+    def host_model(self):
+        """The model as a host synth.Model (the form the oracle and fst.Model take)."""
+        from . import synth
+        d = self.read()
+        return synth.Model(d["r"], d["p"], d["colptr"], d["rowidx"], d["val"], d["alpha"], d["lo"], d["hi"],
+                           d["wav"], d["col_wavelet"])
 
     def set_core(self, alpha):
         al = np.ascontiguousarray(np.asarray(alpha, dtype=np.float64).reshape(-1))
@@ -323,8 +354,9 @@ def refit_batched(models, xyzs, us, ms, seeds, prec: str = "bf16", streams: int 
 def fit(xyz, u, grid=(32, 32, 32), sample_frac: float = 0.05, eps: float = 1e-3, max_rank=(8, 8, 8),
         max_degree: int = 15, oversample: float = 4.0, seed: int = 1, fixed_rank: bool = False,
         prec: str = "fp32", lo=None, hi=None, grid_values=None, trace: bool = False,
-        max_refine: int = 32, refine_tol: float = 0.0, stream=None):
+        max_refine: int = 32, refine_tol: float = 0.0, wavelet=None, stream=None):
     """Algorithm 1 and the core refit (fst_fit).  xyz (3, Q) and u (Q,): CUDA float32 tensors.
+    wavelet=(s, q) also fits every column in the multiwavelet space W_{s,q} and keeps the better.
     Returns (Model, report dict) or, with trace=True, (Model, report dict, trace dict)."""
     import torch
     assert xyz.is_cuda and xyz.dtype == torch.float32 and xyz.is_contiguous() and xyz.shape[0] == 3
@@ -336,6 +368,8 @@ def fit(xyz, u, grid=(32, 32, 32), sample_frac: float = 0.05, eps: float = 1e-3,
         prm.max_rank[k] = int(max_rank[k])
     prm.sample_frac, prm.eps, prm.max_degree = float(sample_frac), float(eps), int(max_degree)
     prm.fixed_rank, prm.oversample, prm.seed = int(bool(fixed_rank)), float(oversample), seed & 0xFFFFFFFFFFFFFFFF
+    if wavelet is not None:
+        prm.wavelet, prm.wav_level, prm.wav_degree = 1, int(wavelet[0]), int(wavelet[1])
     keep = []
     if grid_values is not None:
         gv = np.ascontiguousarray(np.asarray(grid_values, dtype=np.float64).reshape(-1))
@@ -358,7 +392,8 @@ def fit(xyz, u, grid=(32, 32, 32), sample_frac: float = 0.05, eps: float = 1e-3,
         bufs = {"grid_values": np.zeros(G), "eigvals": [np.zeros(g) for g in G],
                 "W": [np.zeros(g * int(mr)) for g, mr in zip(G, max_rank)],
                 "core_hosvd": np.zeros(int(np.prod(max_rank))), "col_nnz": np.zeros(int(sum(max_rank)), np.int32),
-                "col_loo": np.zeros(int(sum(max_rank))), "col_kept": np.zeros(int(sum(max_rank)), np.int32)}
+                "col_loo": np.zeros(int(sum(max_rank))), "col_kept": np.zeros(int(sum(max_rank)), np.int32),
+                "col_wavelet": np.zeros(int(sum(max_rank)), np.int32), "col_loo_alt": np.zeros(int(sum(max_rank)))}
         tr = FitTrace()
         tr.grid_values = bufs["grid_values"].ctypes.data
         for k in range(3):
@@ -368,6 +403,8 @@ def fit(xyz, u, grid=(32, 32, 32), sample_frac: float = 0.05, eps: float = 1e-3,
         tr.col_nnz = bufs["col_nnz"].ctypes.data
         tr.col_loo = bufs["col_loo"].ctypes.data
         tr.col_kept = bufs["col_kept"].ctypes.data
+        tr.col_wavelet = bufs["col_wavelet"].ctypes.data
+        tr.col_loo_alt = bufs["col_loo_alt"].ctypes.data
     h = C.c_void_p()
     _check(lib.fst_fit(_dptr(xyz), _dptr(u), Q, box[0], box[1], C.byref(prm), PREC[prec], C.byref(opts),
                        C.byref(tr) if tr is not None else None, C.byref(rep), C.byref(h), _stream(stream)))
@@ -381,7 +418,8 @@ def fit(xyz, u, grid=(32, 32, 32), sample_frac: float = 0.05, eps: float = 1e-3,
          "W": [bufs["W"][k][:G[k] * r[k]].reshape(G[k], r[k]) for k in range(3)],
          "core_hosvd": bufs["core_hosvd"][:r[0] * r[1] * r[2]].reshape(r),
          "col_nnz": bufs["col_nnz"][:ncol].copy(), "col_loo": bufs["col_loo"][:ncol].copy(),
-         "col_kept": bufs["col_kept"][:ncol].copy()}
+         "col_kept": bufs["col_kept"][:ncol].copy(), "col_wavelet": bufs["col_wavelet"][:ncol].copy(),
+         "col_loo_alt": bufs["col_loo_alt"][:ncol].copy()}
     return model, d, t
 
 

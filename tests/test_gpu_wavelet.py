@@ -1,0 +1,151 @@
+"""Models whose factor functions live in a multiwavelet space W_{s,q} (Sec. 4.2, Algorithm 1's
+per-column basis choice, Fig. 3) on the GPU, against the oracle (oracle/wavelet.py): evaluation
+in every precision, the core refit, model files, and fst_fit choosing between P_p and W_{s,q}
+per column step by step."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import fit as OF
+from oracle import wavelet as OW
+from paper_1907_05884_gb300 import synth
+from gpu_util import EVAL_TOL, rel_l2, cuda_tensor
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def F():
+    from paper_1907_05884_gb300 import build
+    build.build()
+    from paper_1907_05884_gb300 import fst
+    return fst
+
+
+MODELS = [((6, 5, 7), (11, 9, 13), (3, 5)), ((12, 10, 14), (15, 15, 15), (2, 3)), ((24, 24, 24), (31, 31, 31), (3, 5)),
+          ((3, 1, 2), (4, 0, 5), (0, 2)), ((8, 8, 8), (15, 15, 15), (4, 1))]
+
+
+def _points(n, seed, wav):
+    """Random points plus points exactly on the finest cell boundaries and outside the box."""
+    s = wav[0]
+    x = synth.points(n, seed=seed).astype(np.float32)
+    b = OW.cell_boundaries(-1.0, 1.0, s).astype(np.float32) if s > 0 else np.zeros(0, np.float32)
+    extra = np.stack([np.concatenate([b, [-1.0, 1.0, 1.05, -1.1]]).astype(np.float32)] * 3)
+    extra[1] = np.roll(extra[1], 1)
+    return np.ascontiguousarray(np.concatenate([x, extra], axis=1))
+
+
+@pytest.mark.parametrize("r,p,wav", MODELS)
+def test_eval_wavelet_models_match_oracle(F, r, p, wav):
+    import torch
+    base = synth.random_model(r, p, seed=sum(r), density=0.6)
+    m = synth.with_wavelet_columns(base, wav, share=0.5, seed=sum(r) + 1)
+    x32 = _points(3001, sum(r) + 2, wav)
+    x64 = x32.astype(np.float64)
+    ref = OW.eval_points(m, x64)
+    M = F.Model(m)
+    got64 = M.eval_f64(cuda_tensor(x64, torch.float64)).cpu().numpy()
+    assert rel_l2(got64, ref) < EVAL_TOL["fp64"]
+    xt = cuda_tensor(x32, torch.float32)
+    for prec in ("fp32", "bf16x3", "tf32", "bf16"):
+        if prec != "fp32":
+            M.prepare(prec)
+        got = M.eval(xt, prec=prec).cpu().numpy()
+        F.eval_check()
+        err = rel_l2(got, ref)
+        print(prec, r, wav, err)
+        assert err < EVAL_TOL[prec], (prec, err)
+
+
+def test_wavelet_model_read_and_file_roundtrip(F, tmp_path):
+    import torch
+    m = synth.with_wavelet_columns(synth.random_model((5, 6, 4), (9, 9, 9), seed=3), (3, 2), seed=4)
+    M = F.Model(m)
+    d = M.read()
+    assert d["wav"] == (3, 2)
+    for k in range(3):
+        assert np.array_equal(d["col_wavelet"][k], m.col_wavelet[k])
+        assert np.array_equal(d["rowidx"][k], m.rowidx[k])
+    path = tmp_path / "w.fstm"
+    M.save(str(path))
+    M2 = F.Model.load(str(path))
+    d2 = M2.read()
+    assert d2["wav"] == (3, 2) and all(np.array_equal(a, b) for a, b in zip(d2["col_wavelet"], m.col_wavelet))
+    x = cuda_tensor(_points(500, 5, (3, 2)).astype(np.float64), torch.float64)
+    assert np.array_equal(M.eval_f64(x).cpu().numpy(), M2.eval_f64(x).cpu().numpy())
+    # Legendre-only models carry no wavelet section
+    assert F.Model(synth.random_model((2, 2, 2), (3, 3, 3), seed=1)).read()["wav"] is None
+
+
+def test_wavelet_model_rejects_bad_indices(F):
+    m = synth.with_wavelet_columns(synth.random_model((3, 3, 3), (5, 5, 5), seed=8), (2, 1), seed=9)
+    bad = [v.copy() for v in m.rowidx]
+    j = int(np.flatnonzero(m.col_wavelet[0])[0])
+    bad[0][m.colptr[0][j + 1] - 1] = 8               # (q+1) 2^s = 8: one past the end
+    mb = synth.Model(m.r, m.p, m.colptr, bad, m.val, m.alpha, m.lo, m.hi, m.wav, m.col_wavelet)
+    with pytest.raises(F.FstError) as e:
+        F.Model(mb)
+    assert e.value.status == -1
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16"])
+def test_refit_wavelet_model_matches_oracle(F, oracle_lib, prec):
+    import torch
+    base = synth.random_model((6, 7, 5), (12, 12, 12), seed=21, orthonormal=True)
+    m = synth.with_wavelet_columns(base, (3, 3), share=0.4, seed=22, density=0.5)
+    Q = 12000
+    xyz = synth.points(Q, seed=23)
+    u, _ = synth.field_values(xyz, synth.field_spec(24, 4), seed=25)
+    if prec != "fp64":
+        xyz, u = xyz.astype(np.float32), u.astype(np.float32)
+    mm = 8 * m.R
+    idx = oracle_lib.sample(26, Q, mm)
+    x64, u64 = xyz.astype(np.float64), u.astype(np.float64)
+    ref = OW.refit(m, x64, u64, idx)
+    M = F.Model(m)
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    rep = M.refit(cuda_tensor(xyz, dt), cuda_tensor(u, dt), mm, seed=26, prec=prec)
+    G = OW.design_matrix(m, x64, idx)
+    kappa = np.linalg.cond(G.T @ G)
+    tol = max(1e-10, 10 * kappa * np.finfo(np.float64).eps) if prec == "fp64" else 1e-5
+    assert rel_l2(M.read()["alpha"], ref) < tol, (rep, kappa)
+
+
+def test_fit_wavelet_choice_matches_oracle(F, oracle_lib):
+    """fst_fit with W_{3,5} against the oracle step by step: the same per-column choice of
+    space, supports, leave-one-out errors and kept columns, and the same model."""
+    import torch
+    Q, grid = 40000, (32, 32, 32)
+    xyz = synth.points(Q, seed=41, clustered=0.3).astype(np.float32)
+    u, _ = synth.field_values(xyz.astype(np.float64), synth.field_spec(42, 6), seed=43)
+    u = u.astype(np.float32)
+    x64, u64 = xyz.astype(np.float64), u.astype(np.float64)
+    params = OF.FitParams(grid=grid, sample_frac=0.08, eps=1e-3, max_rank=(7, 7, 7), max_degree=15,
+                          oversample=4.0, seed=44, wavelet=(3, 5))
+    omodel, orep = OF.fit(x64, u64, params, nthreads=8)
+    M, rep, tr = F.fit(cuda_tensor(xyz, torch.float32), cuda_tensor(u, torch.float32), grid=grid,
+                       sample_frac=params.sample_frac, eps=params.eps, max_rank=params.max_rank,
+                       max_degree=params.max_degree, oversample=params.oversample, seed=params.seed,
+                       prec="fp64", trace=True, wavelet=(3, 5))
+    assert rep["r_hosvd"] == orep.hosvd_ranks and rep["r"] == orep.ranks
+    ochose = [int(c) for k in range(3) for c in orep.chose_wavelet[k]]
+    assert list(tr["col_wavelet"]) == ochose
+    assert sum(ochose) > 0                           # the case uses the wavelet space
+    assert list(tr["col_nnz"]) == [n for k in range(3) for n in orep.nnz[k]]
+    assert np.allclose(tr["col_loo"], [e for k in range(3) for e in orep.loo[k]], rtol=1e-6, atol=1e-14)
+    okept = [int(j not in orep.dropped[k]) for k in range(3) for j in range(orep.hosvd_ranks[k])]
+    assert list(tr["col_kept"]) == okept
+    d = M.read()
+    assert (d["wav"] is not None) == (omodel.wav is not None)
+    for k in range(3):
+        assert np.array_equal(d["rowidx"][k], omodel.rowidx[k]), k
+        assert np.max(np.abs(d["val"][k] - omodel.val[k])) <= 1e-7, k
+        if d["wav"] is not None:
+            assert np.array_equal(d["col_wavelet"][k], omodel.col_wavelet[k])
+    test = synth.points(4000, seed=45, clustered=0.0)
+    got = M.eval_f64(cuda_tensor(test, torch.float64)).cpu().numpy()
+    ref = oracle_lib.eval_points(omodel, test)
+    assert rel_l2(got, ref) <= 1e-8
+    assert list(rep["n_wavelet"]) == [int(np.sum(c)) for c in omodel.col_wavelet]
