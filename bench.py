@@ -47,7 +47,7 @@ ACCURACY_POINTS = 1 << 20       # rel-L2 of the evaluation against the oracle on
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="fst", choices=["fst", "reference"])
     ap.add_argument("--prec", default="bf16",
@@ -143,10 +143,10 @@ GRAM_PK_BF16_TRAFFIC = 13.94e9 + 0.3565e9
 # DRAM bytes of one evaluation launch, keyed by (precision, points, degree), from one ncu
 # capture of the current kernel (a smaller case scaled by the point count where stated)
 EVAL_TRAFFIC = {
-    # eval_pipe_kernel<BF16X3, 24, 24>: 202.8 MB read + 48.1 MB written at 2^24 points, degree 63
+    # eval_pipe_kernel<BF16X3, 24, 24>: 201.9 MB read + 47.9 MB written at 2^24 points, degree 63
     # (ncu --set full), scaled by the point count (traffic is 15 B/point of streamed coordinates
     # and values at both sizes)
-    ("bf16x3", 1 << 26, 63): 4 * (202.756352e6 + 48.059648e6),
+    ("bf16x3", 1 << 26, 63): 4 * (201.908224e6 + 47.862784e6),
 }
 
 
@@ -347,7 +347,12 @@ def main():
     nnz = sum(len(v) for v in model.val)
     gram_flops = m * R * (R + 1)                      # lower triangle of A^T A, 2 flops per product
     eval_tc_flops = 2 * R * Q                         # T = U1 C_(1): 2 r1 r2 r3 flops per point
-    eval_alu_flops_pt = 2 * (RANKS[0] * RANKS[1] + RANKS[0]) + 2 * nnz + 5 * 3 * args.degree
+    # CUDA-core work a point: the Khatri-Rao epilogue (2 (r2 r3 + r2)) and the Legendre
+    # recurrence of the three modes (~5 flops a degree), plus the sparse factor values
+    # (2 nnz) where they are not on the tensor cores (the FP32 form)
+    eval_alu_flops_pt = 2 * (RANKS[1] * RANKS[2] + RANKS[1]) + 5 * 3 * args.degree
+    if args.eval_prec == "fp32":
+        eval_alu_flops_pt += 2 * nnz
     alu_peak = fp32_alu_peak_tflops(sm_max, sms)
     # tensor peaks: the measured cuBLAS BF16 burst figure (each kernel is timed alone, a few
     # milliseconds at a time, inside steps of well under a second of timed work);
@@ -376,8 +381,8 @@ def main():
         roof_eval = {"kernel": "eval_simt_kernel (FP32, CUDA cores)", "bound": "alu",
                      "achieved": eval_alu_flops_pt * Q / (ev_ms / 1e3) / 1e12, "peak": alu_peak}
     else:
-        roof_eval = {"kernel": f"eval_tc3_kernel<{args.eval_prec}> (Legendre basis, factor step and core "
-                               "contraction on tcgen05, Khatri-Rao epilogue from tensor memory)",
+        roof_eval = {"kernel": f"eval_pipe_kernel<{args.eval_prec}> (Legendre basis on the CUDA cores, factor "
+                               "step and core contraction on tcgen05, Khatri-Rao epilogue from tensor memory)",
                      "bound": "tensor", "achieved": eval_tc_flops / (ev_ms / 1e3) / 1e12,
                      "peak": tc_peak[args.eval_prec],
                      "peak_source": f"{peak_kind} bf16_tflops (burst) {bf16_peak} x {ratio[args.eval_prec]:.3f}"}
@@ -441,11 +446,15 @@ def main():
     return 0
 
 
+ARM_PARTS = {"0xd4f": "Arm Neoverse-V2", "0xd40": "Arm Neoverse-V1", "0xd0c": "Arm Neoverse-N1"}
+
+
 def platform_cpu() -> str:
     try:
         for l in Path("/proc/cpuinfo").read_text().splitlines():
             if l.lower().startswith(("model name", "cpu part")):
-                return l.split(":", 1)[1].strip()
+                v = l.split(":", 1)[1].strip()
+                return ARM_PARTS.get(v.lower(), v)
     except OSError:
         pass
     import platform

@@ -23,8 +23,9 @@ def _peaks():
     p = Path(__file__).resolve().parents[1] / "MEASURED_PEAKS.json"
     if p.exists():
         d = json.loads(p.read_text())
-        return d.get("bf16_tflops_sustained", 1709.9), "measured"
-    return 1700.0, "fallback"
+        # burst figure: each evaluation and Gram is timed alone, a few milliseconds at a time
+        return d.get("bf16_tflops", d.get("bf16_tflops_sustained")), "measured"
+    return 1900.0, "fallback"
 
 
 def _timed(fn, reps):
@@ -75,7 +76,7 @@ def precision(args):
                 "ms": ms, "Mpoints_s": Q / ms / 1e3, "rel_l2_first_2^20_vs_oracle": rel}
         if prec != "fp32":
             line["contraction_roofline_frac"] = 2 * R * Q / (ms / 1e3) / 1e12 / tc_peak[prec]
-            line["peak"] = f"{kind} bf16 sustained {bf16_peak} TFLOP/s x {tc_peak[prec] / bf16_peak:.3f}"
+            line["peak"] = f"{kind} bf16 burst {bf16_peak} TFLOP/s x {tc_peak[prec] / bf16_peak:.3f}"
         print(json.dumps(line), flush=True)
     m = 8 * R
     for prec in ("tf32", "bf16", "bf16x3"):
