@@ -20,6 +20,12 @@
  *     xyz[2n..3n) = y3.  Points outside the model box are evaluated by polynomial
  *     extrapolation (no clamping).
  *   - Limits: 1 <= r_k <= FST_MAX_RANK, 0 <= p_k <= FST_MAX_DEGREE.
+ *   - One model may be evaluated from several host threads and streams at once.  A call
+ *     that changes a model's core (fst_refit*, fst_model_set_core) must not overlap, on
+ *     the host or on the GPU, evaluations of that model: order them (the same stream, or
+ *     an event).  Tensor-core operand images of a changed core are rebuilt by the next
+ *     evaluation after a device synchronisation, so no kernel still reads a buffer that
+ *     is being rewritten.
  */
 #ifndef FST_H
 #define FST_H

@@ -1204,12 +1204,17 @@ fst_status build_buckets(const std::vector<HostItem>& hitems, int mode, std::vec
         int tab_max = 0;
         for (size_t idx : members[b]) {
             fst_model* m = hitems[idx].m;
-            FST_TRY(prepare_core_image(m, mode, B.r3p));
-            const CoreImage ci = core_image_shape(m, mode, B.r3p, B.tc3);
             TcItem it;
+            {
+                // one model's lock at a time (never two held together): the image slots and
+                // tc_core are shared with single-instance evaluations on other threads
+                std::lock_guard<std::mutex> lk(m->mu);
+                FST_TRY(prepare_core_image(m, mode, B.r3p));
+                it.core_img = static_cast<const unsigned char*>(m->tc_core);   // this kind's image
+            }
+            const CoreImage ci = core_image_shape(m, mode, B.r3p, B.tc3);
             it.a = make_args<float>(m);
             bind(it.a, m);
-            it.core_img = static_cast<const unsigned char*>(m->tc_core);   // this kind's image
             it.img_bytes = (int)ci.bytes;
             it.nchunks = ci.nchunks;
             it.kp = ci.kp;
@@ -1394,12 +1399,11 @@ fst_status prepare_core_image(fst_model* m, int mode, int r3p) {
             slot = &t;
             break;
         }
-    if (!slot) {
-        // every slot holds a live kind (8 kinds): wait for the device before replacing one
-        FST_CUDA(cudaDeviceSynchronize());
-        slot = &m->tc_img[0];
-    }
+    if (!slot) slot = &m->tc_img[0];   // every slot holds a live kind (8 kinds): replace the first
     std::vector<unsigned char> img = build_core_image(m, ci);
+    // a stale slot's buffer may still be read by evaluations queued on other (non-blocking)
+    // streams before the core changed: the synchronous copy below does not wait for them
+    if (slot->ptr) FST_CUDA(cudaDeviceSynchronize());
     if (slot->bytes < img.size()) {
         if (slot->ptr) cudaFree(slot->ptr);
         slot->ptr = nullptr;
