@@ -1208,7 +1208,7 @@ fst_status build_buckets(const std::vector<HostItem>& hitems, int mode, std::vec
             {
                 // one model's lock at a time (never two held together): the image slots and
                 // tc_core are shared with single-instance evaluations on other threads
-                std::lock_guard<std::mutex> lk(m->mu);
+                std::lock_guard<std::recursive_mutex> lk(m->mu);
                 FST_TRY(prepare_core_image(m, mode, B.r3p));
                 it.core_img = static_cast<const unsigned char*>(m->tc_core);   // this kind's image
             }
@@ -1539,7 +1539,7 @@ fst_status eval_tc_batch(const std::vector<HostItem>& items, fst_prec prec, cuda
 
 fst_status eval_tc_launch(fst_model* m, const float* xyz, int64_t n, float* out, fst_prec prec, cudaStream_t s) {
     if (n == 0) return FST_OK;
-    std::lock_guard<std::mutex> lk(m->mu);
+    std::lock_guard<std::recursive_mutex> lk(m->mu);
     // single instance: the work list depends on n, the precision and the core image only; it
     // is kept in the model, and the point and output buffers are passed at launch
     const int mode = mode_of(prec);
@@ -1704,7 +1704,7 @@ extern "C" fst_status fst_eval_prepare(fst_model* m, fst_prec prec) {
     FST_REQUIRE(dev == m->device, "model lives on device %d, current device is %d", m->device, dev);
     // a zero-length evaluation on the legacy stream builds the operand image
     cudaStream_t s = 0;
-    std::lock_guard<std::mutex> lk(m->mu);
+    std::lock_guard<std::recursive_mutex> lk(m->mu);
     const int mode = prec == FST_TF32 ? 0 : prec == FST_BF16 ? 1 : 2;
     int rmax = m->r[0] > m->r[1] ? m->r[0] : m->r[1];
     rmax = m->r[2] > rmax ? m->r[2] : rmax;
@@ -1729,7 +1729,7 @@ extern "C" fst_status fst_eval_autotune(fst_model* m, fst_prec prec, int64_t n_p
     int dev = 0;
     FST_CUDA(cudaGetDevice(&dev));
     FST_REQUIRE(dev == m->device, "model lives on device %d, current device is %d", m->device, dev);
-    std::lock_guard<std::mutex> lk(m->mu);
+    std::lock_guard<std::recursive_mutex> lk(m->mu);
     float ms[2];
     int c = 0;
     FST_TRY(fst::eval_autotune(m, prec, n_probe, (cudaStream_t)stream, ms, &c));

@@ -178,7 +178,7 @@ struct fst_model {
     int eval_plan_prec = -1;
 
     fst::RefitScratch rs;
-    std::mutex mu;
+    std::recursive_mutex mu;   // re-entered by single-instance evaluations that build a work list
 
     int R() const { return r[0] * r[1] * r[2]; }
 };

@@ -398,7 +398,7 @@ extern "C" fst_status fst_model_set_core(fst_model* m, const double* alpha) {
     FST_REQUIRE(m != nullptr && alpha != nullptr, "model or alpha is NULL");
     const size_t R = (size_t)m->R();
     for (size_t i = 0; i < R; ++i) FST_REQUIRE(isfinite(alpha[i]), "non-finite core entry %zu", i);
-    std::lock_guard<std::mutex> lk(m->mu);
+    std::lock_guard<std::recursive_mutex> lk(m->mu);
     m->alpha.assign(alpha, alpha + R);
     int cur = 0;
     cudaGetDevice(&cur);

@@ -858,7 +858,7 @@ static fst_status refit_entry(fst_model* M, const T* xyz, const T* u, int64_t Q,
     FST_REQUIRE(dev == M->device, "model lives on device %d, current device is %d", M->device, dev);
     FST_REQUIRE(pointer_device(xyz) == dev && pointer_device(u) == dev, "xyz and u must be device memory");
     FST_REQUIRE(!idx || pointer_device(idx) == dev, "idx must be device memory");
-    std::lock_guard<std::mutex> lk(M->mu);
+    std::lock_guard<std::recursive_mutex> lk(M->mu);
     return refit_impl<T>(M, xyz, u, Q, idx, m, seed, prec, opts, rep, s);
 }
 
@@ -1152,7 +1152,7 @@ extern "C" fst_status fst_refit_mixed(fst_model* model, const double* xyz, const
     FST_CUDA(cudaGetDevice(&dev));
     FST_REQUIRE(dev == model->device, "model lives on device %d, current device is %d", model->device, dev);
     FST_REQUIRE(pointer_device(xyz) == dev && pointer_device(u) == dev, "xyz and u must be device memory");
-    std::lock_guard<std::mutex> lk(model->mu);
+    std::lock_guard<std::recursive_mutex> lk(model->mu);
     return refit_mixed_impl(model, xyz, u, Q, m, seed_signs, seed_rows, report, (cudaStream_t)stream);
 }
 
@@ -1171,7 +1171,7 @@ extern "C" fst_status fst_normal_matrix(const fst_model* M, const float* xyz, co
                     pointer_device(G) == dev && (!h || pointer_device(h) == dev),
                 "xyz, u, idx, G and h must be device memory");
     fst_model* MM = const_cast<fst_model*>(M);
-    std::lock_guard<std::mutex> lk(MM->mu);
+    std::lock_guard<std::recursive_mutex> lk(MM->mu);
     cudaStream_t s = (cudaStream_t)stream;
     RefitScratch& W = MM->rs;
     float* U[3];
