@@ -848,33 +848,43 @@ eval_pipe_kernel(const TcItem* __restrict__ items, const TcUnit* __restrict__ un
                         break;
                     }
                     unsigned char* Pb = pbuf + (size_t)ps * kPSlotBytes;
+                    // degrees at or beyond pe are zeroed (their coefficient rows are zero, and
+                    // far outside the box the recurrence could overflow); a half tile wholly
+                    // below pe needs no mask
+                    auto half = [&](auto masked) {
 #pragma unroll
-                    for (int c8 = 0; c8 < 4; ++c8) {
-                        float v[8];
+                        for (int c8 = 0; c8 < 4; ++c8) {
+                            float v[8];
 #pragma unroll
-                        for (int e = 0; e < 8; ++e) {
-                            const int dg = h * kPHalf + c8 * 8 + e;
-                            float val;
-                            if (dg == 0) {
-                                val = 1.f;
-                            } else if (dg == 1) {
-                                val = xt;
-                            } else {
-                                const float gd = float((dg - 1) * (dg - 1)) / float((2 * dg - 1) * (2 * dg - 3));
-                                const float Ln = fmaf(xt, L, -gd * Lm);
-                                Lm = L;
-                                L = Ln;
-                                val = Ln;
+                            for (int e = 0; e < 8; ++e) {
+                                const int dg = h * kPHalf + c8 * 8 + e;
+                                float val;
+                                if (dg == 0) {
+                                    val = 1.f;
+                                } else if (dg == 1) {
+                                    val = xt;
+                                } else {
+                                    const float gd = float((dg - 1) * (dg - 1)) / float((2 * dg - 1) * (2 * dg - 3));
+                                    const float Ln = fmaf(xt, L, -gd * Lm);
+                                    Lm = L;
+                                    L = Ln;
+                                    val = Ln;
+                                }
+                                v[e] = (decltype(masked)::value && dg >= pe) ? 0.f : val;
                             }
-                            v[e] = dg < pe ? val : 0.f;
-                        }
-                        const uint32_t off = tc::kmajor_offset(row, c8 * 16, kPHalf * 2);
-                        uint32_t hw[4], lw[4];
+                            const uint32_t off = tc::kmajor_offset(row, c8 * 16, kPHalf * 2);
+                            uint32_t hw[4], lw[4];
 #pragma unroll
-                        for (int e = 0; e < 4; ++e) split2_bf16(v[2 * e], v[2 * e + 1], hw[e], lw[e]);
-                        *reinterpret_cast<uint4*>(Pb + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-                        *reinterpret_cast<uint4*>(Pb + 128 * kPHalf * 2 + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
-                    }
+                            for (int e = 0; e < 4; ++e) split2_bf16(v[2 * e], v[2 * e + 1], hw[e], lw[e]);
+                            *reinterpret_cast<uint4*>(Pb + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+                            *reinterpret_cast<uint4*>(Pb + 128 * kPHalf * 2 + off) =
+                                make_uint4(lw[0], lw[1], lw[2], lw[3]);
+                        }
+                    };
+                    if ((h + 1) * kPHalf <= pe)
+                        half(std::false_type{});
+                    else
+                        half(std::true_type{});
                     tc::fence_async_smem();
                     __syncwarp();
                     if (lane == 0) tc::mbar_arrive(&C.p_full[ps]);
