@@ -940,7 +940,12 @@ eval_pipe_kernel(const TcItem* __restrict__ items, const TcUnit* __restrict__ un
                     tc::tmem_ld8(ub + 64 + c, tl);
                     tc::tmem_wait_ld();
 #pragma unroll
-                    for (int e = 0; e < 8; ++e) uk[c + e] = (tl[e] + tm[e]) + th[e];
+                    for (int e = 0; e < 8; e += 2) {
+                        const float2 t = __fadd2_rn(__fadd2_rn(make_float2(tl[e], tl[e + 1]), make_float2(tm[e], tm[e + 1])),
+                                                    make_float2(th[e], th[e + 1]));
+                        uk[c + e] = t.x;
+                        uk[c + e + 1] = t.y;
+                    }
                 }
                 tc::fence_before_sync();
                 __syncwarp();
@@ -1033,7 +1038,8 @@ eval_pipe_kernel(const TcItem* __restrict__ items, const TcUnit* __restrict__ un
                             else
                                 sb = __ffma2_rn(vv, ww, sb);
                             if (k == R3P - 2) {
-                                if (jl < RM) f = fmaf((sa.x + sa.y) + (sb.x + sb.y), u2[jl < RM ? jl : 0], f);
+                                const float2 s2 = __fadd2_rn(sa, sb);
+                                if (jl < RM) f = fmaf(s2.x + s2.y, u2[jl < RM ? jl : 0], f);
                                 sa = make_float2(0.f, 0.f);
                                 sb = make_float2(0.f, 0.f);
                             }
