@@ -320,6 +320,25 @@ typedef struct {
 fst_status fst_refit_batched(const fst_refit_item* items, int32_t count, fst_prec prec,
                              const fst_refit_opts* opts, int32_t streams, fst_refit_report* reports);
 
+/* Refit many models (Sec. 5, eq. rand_core; Algorithm 2 per item) with shared launches, on
+ * one stream.  Per item: the rows (fst_sample_rows with the item's seed), the factor values,
+ * A^T b and the Gram in `prec`.  Then the FP32 factorisations of all items run as one
+ * schedule, every launch doing the same panel step for each matrix that still has it; and the
+ * preconditioned conjugate gradients of all items advance together, one launch per step for
+ * every item (per rank class r3 <= 8 / 16 / 24 / 32 where a kernel is specialised), the
+ * triangular solves of all items in one launch per direction.  Small instances, which leave
+ * most of the GPU idle alone and are bound by their chains of short launches, then share
+ * those launches.  Each item's arithmetic is that of fst_refit, so every core equals
+ * fst_refit's on the item bit for bit; an item whose factorisation fails or whose iteration
+ * does not converge is redone alone by the fst_refit procedure (with its fallbacks), as is
+ * every item when opts asks for the FP64 factorisation.  items: host array (the
+ * fst_refit_batched item; one model per item); reports: host array of count, or NULL (for a
+ * grouped item, ms_cholesky and ms_refine are those of the whole group).  The items' data
+ * must be ready in `stream`'s order.  Synchronous; returns the status of the first failed
+ * item after all items have run (the others' cores are replaced). */
+fst_status fst_refit_grouped(const fst_refit_item* items, int32_t count, fst_prec prec,
+                             const fst_refit_opts* opts, fst_refit_report* reports, fst_stream stream);
+
 /* Algorithm 2 with its mixing step (Sec. 5): the core minimising || S F D W alpha - S F D u ||
  * over all Q points, W the Khatri-Rao rows of the points (eq. rand_core), D = diag(+-1) with
  * D_q = -1 when bit 63 of the splitmix64 key of row q under seed_signs is set, F the

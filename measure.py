@@ -37,7 +37,8 @@ def main():
     ap.add_argument("--ranks", type=int, nargs=3, default=[24, 24, 24])
     ap.add_argument("--degree", type=int, default=31)
     ap.add_argument("--reps", type=int, default=2)
-    ap.add_argument("--streams", type=int, nargs="+", default=[1, 2, 4, 8])
+    ap.add_argument("--streams", type=int, nargs="*", default=[1, 2, 4, 8])
+    ap.add_argument("--grouped-only", action="store_true", help="refit-batch: time fst_refit_grouped alone")
     ap.add_argument("--variant", type=int, default=-1,
                     help="evaluator variant (0: factor values on the CUDA cores, 1: on the tensor cores); "
                          "default: autotuned")
@@ -144,7 +145,8 @@ def batch(args):
 def refit_batch(args):
     """Batched refits over the batching workload's instances (ranks U{4..24} per mode, point
     counts log-uniform in [--q-lo, --q-hi], m = 8R rows each): one fst_refit_batched call on S
-    streams against one fst_refit per instance, one after another."""
+    streams and one fst_refit_grouped call against one fst_refit per instance, one after
+    another."""
     import time
     import torch
     from paper_1907_05884_gb300 import fst, synth
@@ -166,22 +168,31 @@ def refit_batch(args):
     rows = sum(ms)
     torch.cuda.synchronize()
     for r in range(args.reps):
-        # wall-clock on both sides: the batched call runs on several streams of its own
-        torch.cuda.synchronize()
-        h0 = time.perf_counter()
-        reps = [Mi.refit(x, u, mm, seed=sd, prec=args.prec) for Mi, x, u, mm, sd in zip(models, xs, us, ms, seeds)]
-        torch.cuda.synchronize()
-        seq = (time.perf_counter() - h0) * 1e3
-        phases = {k: sum(rp[k] for rp in reps) for k in ("ms_sample", "ms_factors", "ms_gram", "ms_cholesky",
-                                                          "ms_refine")}
-        line = (f"refit-batch instances={len(models)} rows={rows} prec={args.prec} sequential_ms={seq:.2f} "
-                + " ".join(f"{k}={v:.1f}" for k, v in phases.items()))
-        for S in args.streams:
+        line = f"refit-batch instances={len(models)} rows={rows} prec={args.prec}"
+        if not args.grouped_only:
+            # wall-clock on both sides: the batched call runs on several streams of its own
+            torch.cuda.synchronize()
+            h0 = time.perf_counter()
+            reps = [Mi.refit(x, u, mm, seed=sd, prec=args.prec)
+                    for Mi, x, u, mm, sd in zip(models, xs, us, ms, seeds)]
+            torch.cuda.synchronize()
+            seq = (time.perf_counter() - h0) * 1e3
+            phases = {k: sum(rp[k] for rp in reps) for k in ("ms_sample", "ms_factors", "ms_gram", "ms_cholesky",
+                                                              "ms_refine")}
+            line += f" sequential_ms={seq:.2f} " + " ".join(f"{k}={v:.1f}" for k, v in phases.items())
+        for S in ([] if args.grouped_only else args.streams):
             torch.cuda.synchronize()
             h0 = time.perf_counter()
             fst.refit_batched(models, xs, us, ms, seeds, prec=args.prec, streams=S)
             torch.cuda.synchronize()
             line += f" streams{S}_ms={(time.perf_counter() - h0) * 1e3:.2f}"
+        torch.cuda.synchronize()
+        h0 = time.perf_counter()
+        greps = fst.refit_grouped(models, xs, us, ms, seeds, prec=args.prec)
+        torch.cuda.synchronize()
+        line += (f" grouped_ms={(time.perf_counter() - h0) * 1e3:.2f} grouped_rows_gram_ms={greps[0]['ms_gram']:.1f}"
+                 f" grouped_cholesky_ms={greps[0]['ms_cholesky']:.1f} grouped_refine_ms={greps[0]['ms_refine']:.1f}"
+                 f" grouped_steps_max={max(rp['refine_steps'] for rp in greps)}")
         print(line, flush=True)
 
 

@@ -185,8 +185,8 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
 // transposed sub-panel P (FS x PB), reused for the inverses (4 x 32 x 32 floats).
 constexpr int FS = 16;
 static_assert(FS * PB <= 4 * SUB * SUB, "the sub-panel buffer is reused for the diagonal inverses");
-__global__ void __launch_bounds__(512) potrf_inv_kernel(float* G, int R, int k0, int kb, int* flag,
-                                                        const float* floors, float* Dinv, int want_inv) {
+__device__ __forceinline__ void potrf_inv_body(float* G, int R, int k0, int kb, int* flag, const float* floors,
+                                               float* Dinv, int want_inv) {
     extern __shared__ __align__(16) unsigned char dsm[];
     float (*A)[AS] = reinterpret_cast<float (*)[AS]>(dsm);
     float (*P)[PB] = reinterpret_cast<float (*)[PB]>(dsm + sizeof(float) * PB * AS);   // P[k][row]
@@ -331,6 +331,38 @@ __global__ void __launch_bounds__(512) potrf_inv_kernel(float* G, int R, int k0,
     }
 }
 
+__global__ void __launch_bounds__(512) potrf_inv_kernel(float* G, int R, int k0, int kb, int* flag,
+                                                        const float* floors, float* Dinv, int want_inv) {
+    potrf_inv_body(G, R, k0, kb, flag, floors, Dinv, want_inv);
+}
+
+// One step of a factorisation of several normal matrices at once (a grouped refit): the
+// same panel of every matrix that still has it.  Each kernel below takes the step's jobs,
+// one per matrix; a job's blocks (or tiles) are [first, first of the next job).
+struct CholJob {
+    float* G;
+    const float* floors;
+    float* Dinv;
+    unsigned char* Lp;      // the packed panel this step writes (trsm) or the first panel (update)
+    size_t pstride;
+    int* flag;
+    int R, k0, kb, want_inv;
+    int t0, nt, ncol, npan; // trailing update: first row/column, tile rows, tile columns, panels
+    long long first;
+};
+__device__ __forceinline__ int job_of(const CholJob* jobs, int njobs, long long x) {
+    int lo = 0, hi = njobs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (jobs[mid].first <= x) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+__global__ void __launch_bounds__(512) potrf_inv_group_kernel(const CholJob* __restrict__ jobs) {
+    const CholJob& j = jobs[blockIdx.x];
+    potrf_inv_body(j.G, j.R, j.k0, j.kb, j.flag, j.floors, j.Dinv, j.want_inv);
+}
+
 // L21 = A21 L11^-T for kTrsmRows panel rows per block (256 threads): 32-column block
 // substitution, X_d = (A_d - sum_{e<d} X_e L_de^T) Dinv_d^T.  Writes L21 (FP32) into G and the
 // BF16 hi/lo operand tiles of the trailing update (rows at or beyond R as zeros).  Few rows a
@@ -339,15 +371,15 @@ __global__ void __launch_bounds__(512) potrf_inv_kernel(float* G, int R, int k0,
 constexpr int kTrsmRows = 32;
 constexpr int kTrsmCQ = 256 / kTrsmRows;          // threads per row
 constexpr int kTrsmNJ = SUB / kTrsmCQ;            // columns of a 32-column block per thread
-__global__ void __launch_bounds__(256) trsm_pack_kernel(float* G, int R, int k0, const float* Dinv,
-                                                        unsigned char* Lp) {
+__device__ __forceinline__ void trsm_pack_body(float* G, int R, int k0, const float* Dinv, unsigned char* Lp,
+                                               int blk) {
     extern __shared__ __align__(16) unsigned char dsm[];
     float (*X)[AS] = reinterpret_cast<float (*)[AS]>(dsm);                                        // panel rows
     float (*L)[AS] = reinterpret_cast<float (*)[AS]>(dsm + sizeof(float) * kTrsmRows * AS);      // L11
     float (*D)[SUB + 4] = reinterpret_cast<float (*)[SUB + 4]>(dsm + sizeof(float) * (kTrsmRows + PB) * AS);
     const int tid = threadIdx.x;
     const int t0 = k0 + PB;
-    const int r0 = blockIdx.x * kTrsmRows;
+    const int r0 = blk * kTrsmRows;
     const bool vec = (R & 3) == 0;
     {
         // the panel rows and L11: every load of a thread in flight at once
@@ -447,6 +479,15 @@ __global__ void __launch_bounds__(256) trsm_pack_kernel(float* G, int R, int k0,
     }
 }
 
+__global__ void __launch_bounds__(256) trsm_pack_kernel(float* G, int R, int k0, const float* Dinv,
+                                                        unsigned char* Lp) {
+    trsm_pack_body(G, R, k0, Dinv, Lp, blockIdx.x);
+}
+__global__ void __launch_bounds__(256) trsm_pack_group_kernel(const CholJob* __restrict__ jobs, int njobs) {
+    const CholJob& j = jobs[job_of(jobs, njobs, blockIdx.x)];
+    trsm_pack_body(j.G, j.R, j.k0, j.Dinv, j.Lp, (int)(blockIdx.x - j.first));
+}
+
 // A22 -= L21_i L21_j^T over the lower 128 x 128 tiles (ti >= tj) of the trailing matrix
 // that starts at row/column t0.  Persistent: one CTA per SM walks tiles blockIdx.x,
 // blockIdx.x + gridDim.x, ...  Warp 8 (one thread) moves the operands through a ring of
@@ -481,9 +522,41 @@ __device__ __forceinline__ void trapezoid_tile(long long t, int ncol, int& ti, i
 // npan panels of 128 columns each make the K = 128 npan of the update; panel p's packed
 // rows start 128 (npan - 1 - p) rows above t0 (each panel was packed from the row after its
 // own diagonal block), at Lp + p * pstride.
-__global__ void __launch_bounds__(kSyrkThreads, 1)
-syrk_tc_kernel(float* G, int R, int t0, int nt, int ncol, const unsigned char* Lp, size_t pstride, int npan,
-               int* err) {
+struct SyrkTile {
+    float* G;
+    const unsigned char* Lp;
+    size_t pstride;
+    int R, t0, npan, ti, tj;
+};
+// the tiles of one trailing update
+struct SyrkOne {
+    float* G;
+    const unsigned char* Lp;
+    size_t pstride;
+    int R, t0, nt, ncol, npan;
+    __device__ long long count() const { return (long long)ncol * (ncol + 1) / 2 + (long long)(nt - ncol) * ncol; }
+    __device__ SyrkTile tile(long long t) const {
+        SyrkTile x{G, Lp, pstride, R, t0, npan, 0, 0};
+        trapezoid_tile(t, ncol, x.ti, x.tj);
+        return x;
+    }
+};
+// the tiles of the updates of several matrices (CholJob: first = the job's first tile)
+struct SyrkGroup {
+    const CholJob* jobs;
+    int njobs;
+    long long total;
+    __device__ long long count() const { return total; }
+    __device__ SyrkTile tile(long long t) const {
+        const CholJob& j = jobs[job_of(jobs, njobs, t)];
+        SyrkTile x{j.G, j.Lp, j.pstride, j.R, j.t0, j.npan, 0, 0};
+        trapezoid_tile(t - j.first, j.ncol, x.ti, x.tj);
+        return x;
+    }
+};
+
+template <class Src>
+__device__ __forceinline__ void syrk_tc_body(const Src& src, int* err) {
     extern __shared__ unsigned char syrk_raw[];
     unsigned char* sm = reinterpret_cast<unsigned char*>(((uintptr_t)syrk_raw + 1023) & ~(uintptr_t)1023);
     uint64_t* full = reinterpret_cast<uint64_t*>(sm + kSyrkStages * 2 * kHalfBytes);
@@ -494,8 +567,7 @@ syrk_tc_kernel(float* G, int R, int t0, int nt, int ncol, const unsigned char* L
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const long long ntiles = (long long)ncol * (ncol + 1) / 2 + (long long)(nt - ncol) * ncol;
-    const int nh = 2 * npan;   // K-halves of 64 per tile
+    const long long ntiles = src.count();
 
     if (warp == 0) tc::tmem_alloc(tmem_slot, 256);
     if (tid == 0) {
@@ -525,8 +597,10 @@ syrk_tc_kernel(float* G, int R, int t0, int nt, int ncol, const unsigned char* L
         if (lane == 0) {
             int it = 0;
             for (long long t = blockIdx.x; t < ntiles && !*abort_flag; t += gridDim.x) {
-                int ti, tj;
-                trapezoid_tile(t, ncol, ti, tj);
+                const SyrkTile x = src.tile(t);
+                const int ti = x.ti, tj = x.tj, npan = x.npan, nh = 2 * npan;   // K-halves of 64
+                const unsigned char* Lp = x.Lp;
+                const size_t pstride = x.pstride;
                 const bool diag = ti == tj;
                 for (int h = 0; h < nh; ++h, ++it) {
                     const int s = it % kSyrkStages;
@@ -553,9 +627,9 @@ syrk_tc_kernel(float* G, int R, int t0, int nt, int ncol, const unsigned char* L
             int it = 0, n = 0;
             bool issued = false;
             for (long long t = blockIdx.x; t < ntiles && !*abort_flag; t += gridDim.x, ++n) {
-                int ti, tj;
-                trapezoid_tile(t, ncol, ti, tj);
-                const bool diag = ti == tj;
+                const SyrkTile x = src.tile(t);
+                const bool diag = x.ti == x.tj;
+                const int nh = 2 * x.npan;
                 const int b = n & 1;
                 if (!tc::mbar_wait(&tempty[b], (uint32_t)((n >> 1) & 1) ^ 1u, kCholWaitLimit)) {
                     fail(2);
@@ -600,11 +674,12 @@ syrk_tc_kernel(float* G, int R, int t0, int nt, int ncol, const unsigned char* L
         }
     } else {
         // ---------------------------------------------------------------- epilogue
-        const bool vec = (R & 3) == 0;
         int n = 0;
         for (long long t = blockIdx.x; t < ntiles && !*abort_flag; t += gridDim.x, ++n) {
-            int ti, tj;
-            trapezoid_tile(t, ncol, ti, tj);
+            const SyrkTile x = src.tile(t);
+            const int ti = x.ti, tj = x.tj, R = x.R, t0 = x.t0;
+            float* G = x.G;
+            const bool vec = (R & 3) == 0;
             const bool diag = ti == tj;
             const int grow = t0 + ti * 128 + (warp & 3) * 32 + lane;
             const int gcol0 = t0 + tj * 128 + (warp >> 2) * 64;
@@ -663,6 +738,16 @@ syrk_tc_kernel(float* G, int R, int t0, int nt, int ncol, const unsigned char* L
     if (warp == 0) tc::tmem_dealloc(tmem, 256);
 }
 
+__global__ void __launch_bounds__(kSyrkThreads, 1)
+syrk_tc_kernel(float* G, int R, int t0, int nt, int ncol, const unsigned char* Lp, size_t pstride, int npan,
+               int* err) {
+    syrk_tc_body(SyrkOne{G, Lp, pstride, R, t0, nt, ncol, npan}, err);
+}
+__global__ void __launch_bounds__(kSyrkThreads, 1)
+syrk_tc_group_kernel(const CholJob* __restrict__ jobs, int njobs, long long total, int* err) {
+    syrk_tc_body(SyrkGroup{jobs, njobs, total}, err);
+}
+
 // FP32 factorisation in super-panels of kSuperPanels 128-column panels.  Per panel: factor
 // the diagonal block, solve and pack the panel below it, and update only the columns of the
 // rest of the super-panel (K = 128); after the super-panel, one update of the whole trailing
@@ -719,6 +804,156 @@ static fst_status cholesky_lower_tc(float* G, int R, int* d_flag, const float* f
         const int nt = (R - T0 + PB - 1) / PB;
         FST_TRY(syrk_tc(G, R, T0, nt, nt, Lp, pstride, npan, d_flag + 1, syrk_smem, s));
     }
+    return FST_OK;
+}
+
+// FP32 factorisations of several normal matrices in shared launches (a grouped refit): the
+// schedule of cholesky_lower_tc run for all matrices at once, panel by panel, each launch
+// doing one step for every matrix that still has it, so a matrix's arithmetic is exactly
+// that of its own factorisation.  The whole schedule is built on the host and uploaded
+// once (sched); gerr collects expired device waits of every matrix.
+fst_status cholesky_lower_group(const std::vector<CholItem>& items, DevBuf& sched, int* gerr, cudaStream_t s) {
+    const size_t potrf_smem = sizeof(float) * (PB * AS + 4 * SUB * SUB);
+    const size_t trsm_smem = sizeof(float) * ((kTrsmRows + PB) * AS + 4 * SUB * (SUB + 4));
+    const size_t syrk_smem = kSyrkStages * 2 * kHalfBytes + 1024 + 1024;
+    FST_TRY(allow_smem(potrf_inv_group_kernel, potrf_smem));
+    FST_TRY(allow_smem(trsm_pack_group_kernel, trsm_smem));
+    FST_TRY(allow_smem(syrk_tc_group_kernel, syrk_smem));
+    const int n = (int)items.size();
+    std::vector<const float*> floors(n);
+    std::vector<float*> dinv(n);
+    std::vector<unsigned char*> lp(n);
+    std::vector<size_t> pstride(n);
+    int maxR = 0;
+    for (int i = 0; i < n; ++i) {
+        const int R = items[i].R;
+        const size_t floor_bytes = ((size_t)R * sizeof(float) + 255) / 256 * 256;
+        const size_t tail = 4 * SUB * SUB * sizeof(float) + kSuperPanels * packed_panel_bytes(R);
+        FST_TRY(items[i].ws->ensure(floor_bytes + tail));
+        float* fl = items[i].ws->as<float>();
+        pivot_floor_kernel<float><<<(R + 255) / 256 < 1024 ? (R + 255) / 256 : 1024, 256, 0, s>>>(items[i].G, R, fl);
+        FST_CHECK_LAUNCH();
+        floors[i] = fl;
+        dinv[i] = reinterpret_cast<float*>(items[i].ws->as<unsigned char>() + floor_bytes);
+        lp[i] = items[i].ws->as<unsigned char>() + floor_bytes + 4 * SUB * SUB * sizeof(float);
+        pstride[i] = packed_panel_bytes(R);
+        maxR = std::max(maxR, R);
+    }
+    // the schedule: launches of kind 0 (diagonal blocks), 1 (panel solves), 2 (updates)
+    struct Launch {
+        int kind, off, njobs;
+        long long total;
+    };
+    std::vector<CholJob> jobs;
+    std::vector<Launch> launches;
+    std::vector<char> done(n, 0);
+    std::vector<int> npan(n, 0);
+    auto job = [&](int i) {
+        CholJob j{};
+        j.G = items[i].G;
+        j.floors = floors[i];
+        j.Dinv = dinv[i];
+        j.pstride = pstride[i];
+        j.flag = items[i].flag;
+        j.R = items[i].R;
+        return j;
+    };
+    constexpr int SBW = kSuperPanels * PB;
+    for (int K0 = 0; K0 < maxR; K0 += SBW) {
+        std::fill(npan.begin(), npan.end(), 0);
+        for (int p = 0; p < kSuperPanels; ++p) {
+            const int k0 = K0 + p * PB;
+            Launch lf{0, (int)jobs.size(), 0, 0}, ls{1, 0, 0, 0}, lu{2, 0, 0, 0};
+            std::vector<CholJob> tj, uj;
+            for (int i = 0; i < n; ++i) {
+                const int R = items[i].R;
+                if (done[i] || k0 >= R) continue;
+                const int kb = R - k0 < PB ? R - k0 : PB;
+                const int rest = R - k0 - kb;
+                CholJob f = job(i);
+                f.k0 = k0;
+                f.kb = kb;
+                f.want_inv = rest > 0 ? 1 : 0;
+                f.first = lf.njobs;
+                jobs.push_back(f);
+                ++lf.njobs;
+                if (rest <= 0) {
+                    done[i] = 1;
+                    continue;
+                }
+                ++npan[i];
+                const int nt = (rest + PB - 1) / PB;
+                CholJob t = job(i);
+                t.k0 = k0;
+                t.Lp = lp[i] + (size_t)p * pstride[i];
+                t.first = ls.total;
+                ls.total += (long long)(PB / kTrsmRows) * nt;
+                tj.push_back(t);
+                int ncol = (K0 + SBW - (k0 + PB)) / PB;
+                if (ncol > nt) ncol = nt;
+                if (ncol > 0) {
+                    CholJob u = t;
+                    u.t0 = k0 + PB;
+                    u.nt = nt;
+                    u.ncol = ncol;
+                    u.npan = 1;
+                    u.first = lu.total;
+                    lu.total += (long long)ncol * (ncol + 1) / 2 + (long long)(nt - ncol) * ncol;
+                    uj.push_back(u);
+                }
+            }
+            lf.total = lf.njobs;
+            if (lf.njobs) launches.push_back(lf);
+            if (!tj.empty()) {
+                ls.off = (int)jobs.size();
+                ls.njobs = (int)tj.size();
+                jobs.insert(jobs.end(), tj.begin(), tj.end());
+                launches.push_back(ls);
+            }
+            if (!uj.empty()) {
+                lu.off = (int)jobs.size();
+                lu.njobs = (int)uj.size();
+                jobs.insert(jobs.end(), uj.begin(), uj.end());
+                launches.push_back(lu);
+            }
+        }
+        Launch lu{2, (int)jobs.size(), 0, 0};
+        for (int i = 0; i < n; ++i) {
+            const int R = items[i].R;
+            if (done[i] || npan[i] == 0) continue;
+            const int T0 = K0 + npan[i] * PB;
+            if (T0 >= R) continue;
+            CholJob u = job(i);
+            u.Lp = lp[i];
+            u.t0 = T0;
+            u.nt = (R - T0 + PB - 1) / PB;
+            u.ncol = u.nt;
+            u.npan = npan[i];
+            u.first = lu.total;
+            lu.total += (long long)u.nt * (u.nt + 1) / 2;
+            jobs.push_back(u);
+            ++lu.njobs;
+        }
+        if (lu.njobs) launches.push_back(lu);
+    }
+    if (jobs.empty()) return FST_OK;
+    FST_TRY(sched.ensure(sizeof(CholJob) * jobs.size()));
+    CholJob* dj = sched.as<CholJob>();
+    FST_CUDA(cudaMemcpyAsync(dj, jobs.data(), sizeof(CholJob) * jobs.size(), cudaMemcpyHostToDevice, s));
+    for (const Launch& L : launches) {
+        const CholJob* j = dj + L.off;
+        if (L.kind == 0) {
+            potrf_inv_group_kernel<<<L.njobs, 512, potrf_smem, s>>>(j);
+        } else if (L.kind == 1) {
+            trsm_pack_group_kernel<<<(unsigned)L.total, 256, trsm_smem, s>>>(j, L.njobs);
+        } else {
+            const int grid = L.total < sm_count() ? (int)L.total : sm_count();
+            syrk_tc_group_kernel<<<grid, kSyrkThreads, syrk_smem, s>>>(j, L.njobs, L.total, gerr);
+        }
+        FST_CHECK_LAUNCH();
+    }
+    // the upload's host buffer must outlive the copy: wait for it before `jobs` is freed
+    FST_CUDA(cudaStreamSynchronize(s));
     return FST_OK;
 }
 
@@ -883,21 +1118,14 @@ __device__ __forceinline__ T wait_value(const T* p, int* err, long long limit) {
 // M is L (forward) or L^T (backward, TRANS), both row-major: block row i reads the tiles
 // M[i-block][j-block] for j < i (forward) or j > i (backward) along its own rows.
 template <typename T, bool TRANS>
-__global__ void __launch_bounds__(256) trsv_kernel(const T* __restrict__ M, const T* __restrict__ Linv,
-                                                   const T* __restrict__ K, int R, int nblk, const T* bin, T* out,
-                                                   int* sync, const int* stop) {
-    if (stop && *stop) return;   // the caller's iteration has already stopped (no block waits then)
-    const long long limit = g_solve_wait_limit > 0 ? g_solve_wait_limit : kSolveWaitLimit;
+__device__ __forceinline__ void trsv_body(const T* __restrict__ M, const T* __restrict__ Linv,
+                                          const T* __restrict__ K, int R, int nblk, const T* bin, T* out,
+                                          int* sync, int i, long long limit) {
     __shared__ T lis[NB][NB + 1];   // Linv of the diagonal block
     __shared__ T red[8][NB];
     __shared__ T vs[NB];
     __shared__ T xl[NB];            // the values of the last dependency
-    __shared__ int s_ticket;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    if (tid == 0) s_ticket = atomicAdd(&sync[1], 1);
-    __syncthreads();
-    const int t = s_ticket;
-    const int i = TRANS ? nblk - 1 - t : t;
     const int k0 = i * NB, kb = R - k0 < NB ? R - k0 : NB;
     {
         const T* Li = Linv + (size_t)i * NB * NB;
@@ -1007,6 +1235,59 @@ __global__ void __launch_bounds__(256) trsv_kernel(const T* __restrict__ M, cons
     }
 }
 
+template <typename T, bool TRANS>
+__global__ void __launch_bounds__(256) trsv_kernel(const T* __restrict__ M, const T* __restrict__ Linv,
+                                                   const T* __restrict__ K, int R, int nblk, const T* bin, T* out,
+                                                   int* sync, const int* stop) {
+    if (stop && *stop) return;   // the caller's iteration has already stopped (no block waits then)
+    const long long limit = g_solve_wait_limit > 0 ? g_solve_wait_limit : kSolveWaitLimit;
+    __shared__ int s_ticket;
+    if (threadIdx.x == 0) s_ticket = atomicAdd(&sync[1], 1);
+    __syncthreads();
+    const int t = s_ticket;
+    trsv_body<T, TRANS>(M, Linv, K, R, nblk, bin, out, sync, TRANS ? nblk - 1 - t : t, limit);
+}
+
+// The solves of several factored matrices in one launch per direction (a grouped refit).
+// Tickets are handed out step by step across the matrices: ticket t is block row step
+// tmap[t] & 0xffff (in solve order) of matrix tmap[t] >> 16, and every ticket of an earlier
+// step precedes it, so a block again waits only for rows already taken.
+template <typename T, bool TRANS>
+__global__ void __launch_bounds__(256) trsv_group_kernel(const SolveJob* __restrict__ jobs,
+                                                         const int* __restrict__ tmap, int* sync) {
+    const long long limit = g_solve_wait_limit > 0 ? g_solve_wait_limit : kSolveWaitLimit;
+    __shared__ int s_ticket;
+    if (threadIdx.x == 0) s_ticket = atomicAdd(&sync[1], 1);
+    __syncthreads();
+    const int code = tmap[s_ticket];
+    const SolveJob& J = jobs[code >> 16];
+    if (J.stop && *J.stop) return;   // this matrix's iteration has stopped: nothing waits on it
+    const int step = code & 0xffff;
+    const T* Li = static_cast<const T*>(J.Linv);
+    const size_t nb2 = (size_t)J.nblk * NB * NB;
+    if (TRANS)
+        trsv_body<T, true>(static_cast<const T*>(J.LT), Li, Li + 2 * nb2, J.R, J.nblk, static_cast<const T*>(J.y),
+                           static_cast<T*>(J.x), sync, J.nblk - 1 - step, limit);
+    else
+        trsv_body<T, false>(static_cast<const T*>(J.L), Li, Li + nb2, J.R, J.nblk, static_cast<const T*>(J.x),
+                            static_cast<T*>(J.y), sync, step, limit);
+}
+
+// fills the solve's output vector of every matrix with the unpublished pattern (which 0: y,
+// 1: x) and, from the first block, zeroes the ticket
+template <typename T>
+__global__ void solve_fill_group_kernel(const SolveJob* __restrict__ jobs, int which, int* sync) {
+    const SolveJob& J = jobs[blockIdx.y];
+    T* v = static_cast<T*>(which ? J.x : J.y);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < J.R; i += gridDim.x * blockDim.x) {
+        if (sizeof(T) == 4)
+            reinterpret_cast<unsigned int*>(v)[i] = 0xffffffffu;
+        else
+            reinterpret_cast<unsigned long long*>(v)[i] = ~0ull;
+    }
+    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) sync[1] = 0;
+}
+
 // LT = L^T on the lower triangle's 32 x 32 tiles (the strict upper blocks of LT that the
 // backward solve reads are all written).
 template <typename T>
@@ -1068,6 +1349,37 @@ fst_status chol_solve(const T* L, const T* LT, const T* Linv, int R, T* x, T* y,
     trsv_kernel<T, true><<<nblk, 256, 0, s>>>(LT, Linv, Kb, R, nblk, y, x, sync, stop);
     FST_CHECK_LAUNCH();
     return FST_OK;
+}
+
+// x <- (L L^T)^-1 x for every job of a grouped refit (device job array, ticket map of
+// `tickets` entries built by solve_tickets); sync: [0] error word, [1] ticket.
+template <typename T>
+fst_status chol_solve_group(const SolveJob* jobs, int njobs, int maxR, const int* tmap, int tickets, int* sync,
+                            cudaStream_t s) {
+    const dim3 fg((unsigned)std::min((maxR + 255) / 256, 64), (unsigned)njobs);
+    solve_fill_group_kernel<T><<<fg, 256, 0, s>>>(jobs, 0, sync);
+    FST_CHECK_LAUNCH();
+    trsv_group_kernel<T, false><<<tickets, 256, 0, s>>>(jobs, tmap, sync);
+    FST_CHECK_LAUNCH();
+    solve_fill_group_kernel<T><<<fg, 256, 0, s>>>(jobs, 1, sync);
+    FST_CHECK_LAUNCH();
+    trsv_group_kernel<T, true><<<tickets, 256, 0, s>>>(jobs, tmap, sync);
+    FST_CHECK_LAUNCH();
+    return FST_OK;
+}
+template fst_status chol_solve_group<float>(const SolveJob*, int, int, const int*, int, int*, cudaStream_t);
+template fst_status chol_solve_group<double>(const SolveJob*, int, int, const int*, int, int*, cudaStream_t);
+
+// The ticket map of a grouped solve: step by step (block row in solve order), every matrix
+// that has that many block rows.
+std::vector<int> solve_tickets(const std::vector<int>& R) {
+    int maxb = 0;
+    for (int r : R) maxb = std::max(maxb, (r + NB - 1) / NB);
+    std::vector<int> t;
+    for (int b = 0; b < maxb; ++b)
+        for (size_t j = 0; j < R.size(); ++j)
+            if (b < (R[j] + NB - 1) / NB) t.push_back((int)(j << 16) | b);
+    return t;
 }
 
 template fst_status cholesky_lower<float>(float*, int, int*, DevBuf&, cudaStream_t);

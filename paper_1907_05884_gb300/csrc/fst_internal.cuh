@@ -262,4 +262,27 @@ fst_status chol_solve_graph(SolveGraph& g, const T* L, const T* LT, const T* Lin
 template <typename T>
 fst_status chol_transpose(const T* L, int R, T* LT, cudaStream_t s);
 
+// Grouped refits: the factorisations of several FP32 normal matrices in shared launches,
+// and the solves of several factored matrices in one launch per direction.
+struct CholItem {
+    float* G;
+    int R;
+    int* flag;      // [0] pivot flag
+    DevBuf* ws;     // the matrix's factorisation workspace
+};
+fst_status cholesky_lower_group(const std::vector<CholItem>& items, DevBuf& sched, int* gerr, cudaStream_t s);
+struct SolveJob {
+    const void* L;
+    const void* LT;
+    const void* Linv;   // diagonal-block inverses, then the forward and backward link matrices
+    void* x;            // right-hand side in, solution out
+    void* y;            // scratch
+    const int* stop;    // nothing is solved while *stop is set
+    int R, nblk;
+};
+template <typename T>
+fst_status chol_solve_group(const SolveJob* jobs, int njobs, int maxR, const int* tmap, int tickets, int* sync,
+                            cudaStream_t s);
+std::vector<int> solve_tickets(const std::vector<int>& R);
+
 }  // namespace fst

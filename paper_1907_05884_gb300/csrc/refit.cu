@@ -17,6 +17,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <functional>
 #include <vector>
 #include <thread>
 #include <string>
@@ -148,19 +149,17 @@ __global__ void __launch_bounds__(256) gram_simt_kernel(const T* __restrict__ U1
 // staged through shared memory.  Block b writes its R partial sums to part[b * R ..];
 // sum_partials_kernel adds them in FP64 (deterministic, no atomics).
 template <typename T, int R3M, int PPT>
-__global__ void __launch_bounds__(256) atr_kernel(const T* __restrict__ U1, const T* __restrict__ U2,
-                                                  const T* __restrict__ U3, const double* __restrict__ rv,
-                                                  int64_t m, int r1, int r2, int r3, int64_t rows_per_block,
-                                                  double* __restrict__ part, const int* stop) {
-    if (stop && *stop) return;
+__device__ __forceinline__ void atr_body(const T* __restrict__ U1, const T* __restrict__ U2,
+                                         const T* __restrict__ U3, const double* __restrict__ rv, int64_t m, int r1,
+                                         int r2, int r3, int64_t rows_per_block, double* __restrict__ part, int blk) {
     constexpr int S = 64;
     __shared__ T u1s[S][FST_MAX_RANK + 1], u2s[S][FST_MAX_RANK + 1];
     __shared__ __align__(16) T u3s[S][R3M];
     __shared__ T rs[S];
-    const int64_t lo = (int64_t)blockIdx.x * rows_per_block;
+    const int64_t lo = (int64_t)blk * rows_per_block;
     const int64_t hi = lo + rows_per_block < m ? lo + rows_per_block : m;
     const int npairs = r1 * r2;
-    double* out = part + (size_t)blockIdx.x * npairs * r3;
+    double* out = part + (size_t)blk * npairs * r3;
     for (int p0 = 0; p0 < npairs; p0 += PPT * blockDim.x) {
         int pi[PPT], pj[PPT];
 #pragma unroll
@@ -218,6 +217,15 @@ __global__ void __launch_bounds__(256) atr_kernel(const T* __restrict__ U1, cons
     }
 }
 
+template <typename T, int R3M, int PPT>
+__global__ void __launch_bounds__(256) atr_kernel(const T* __restrict__ U1, const T* __restrict__ U2,
+                                                  const T* __restrict__ U3, const double* __restrict__ rv,
+                                                  int64_t m, int r1, int r2, int r3, int64_t rows_per_block,
+                                                  double* __restrict__ part, const int* stop) {
+    if (stop && *stop) return;
+    atr_body<T, R3M, PPT>(U1, U2, U3, rv, m, r1, r2, r3, rows_per_block, part, blockIdx.x);
+}
+
 __global__ void sum_partials_kernel(const double* __restrict__ part, int nparts, int R, double* __restrict__ g,
                                     const int* stop) {
     if (stop && *stop) return;
@@ -234,13 +242,11 @@ __global__ void sum_partials_kernel(const double* __restrict__ part, int nparts,
 // subtraction from b run in FP64.
 constexpr int kMaxRank = FST_MAX_RANK;
 template <typename T, int R3M>
-__global__ void __launch_bounds__(256) residual_kernel(const T* __restrict__ U1, const T* __restrict__ U2,
-                                                       const T* __restrict__ U3, const T* __restrict__ bvec,
-                                                       const double* __restrict__ alpha, int64_t m, int r1,
-                                                       int r2, int r3, double scale, double* rv,
-                                                       const int* stop) {
+__device__ __forceinline__ void residual_body(const T* __restrict__ U1, const T* __restrict__ U2,
+                                              const T* __restrict__ U3, const T* __restrict__ bvec,
+                                              const double* __restrict__ alpha, int64_t m, int r1, int r2, int r3,
+                                              double scale, double* rv, int blk, int nblk) {
     constexpr bool kSplit = sizeof(T) == 4;
-    if (stop && *stop) return;   // the conjugate gradients have stopped
     extern __shared__ __align__(16) unsigned char smem[];
     T* As = reinterpret_cast<T*>(smem);        // [r1*r2][R3M]
     T* Al = As + r1 * r2 * R3M;                // low parts (FP32 only)
@@ -252,7 +258,7 @@ __global__ void __launch_bounds__(256) residual_kernel(const T* __restrict__ U1,
         if (kSplit) Al[e] = (T)(a - (double)hi);
     }
     __syncthreads();
-    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < m; s += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t s = (int64_t)blk * blockDim.x + threadIdx.x; s < m; s += (int64_t)nblk * blockDim.x) {
         // the row's factor values in registers (w2 indexed by the unrolled j loop)
         T w3[R3M], w2[kMaxRank];
 #pragma unroll
@@ -300,6 +306,16 @@ __global__ void __launch_bounds__(256) residual_kernel(const T* __restrict__ U1,
     }
 }
 
+template <typename T, int R3M>
+__global__ void __launch_bounds__(256) residual_kernel(const T* __restrict__ U1, const T* __restrict__ U2,
+                                                       const T* __restrict__ U3, const T* __restrict__ bvec,
+                                                       const double* __restrict__ alpha, int64_t m, int r1,
+                                                       int r2, int r3, double scale, double* rv,
+                                                       const int* stop) {
+    if (stop && *stop) return;   // the conjugate gradients have stopped
+    residual_body<T, R3M>(U1, U2, U3, bvec, alpha, m, r1, r2, r3, scale, rv, blockIdx.x, gridDim.x);
+}
+
 // Relative diagonal shift of the preconditioner's matrix, G_jj <- (1 + delta) G_jj: the
 // factor of G + delta diag(G) still preconditions the conjugate gradients, which solve the
 // unshifted normal equations.
@@ -312,8 +328,8 @@ __global__ void shift_diag_kernel(float* G, int R, float delta) {
 // out[k] = sum_i x_k[i] * y_k[i] for k < nd, by one block in a fixed order, so that a refit
 // repeats bit for bit (the step lengths of the conjugate gradients depend on these sums)
 constexpr int kDotThreads = 1024;
-__global__ void __launch_bounds__(kDotThreads) dots_kernel(const double* x0, const double* y0, const double* x1,
-                                                           const double* y1, int n, int nd, double* out) {
+__device__ __forceinline__ void dots_body(const double* x0, const double* y0, const double* x1, const double* y1,
+                                          int n, int nd, double* out) {
     __shared__ double red[2][kDotThreads / 32];
     double a0 = 0.0, a1 = 0.0;
     for (int i = threadIdx.x; i < n; i += kDotThreads) {
@@ -343,6 +359,10 @@ __global__ void __launch_bounds__(kDotThreads) dots_kernel(const double* x0, con
         }
     }
 }
+__global__ void __launch_bounds__(kDotThreads) dots_kernel(const double* x0, const double* y0, const double* x1,
+                                                           const double* y1, int n, int nd, double* out) {
+    dots_body(x0, y0, x1, y1, n, nd, out);
+}
 
 // Scalars of the conjugate gradients, kept on the device so that iterations are launched
 // without a host round trip; stop: 1 converged, 2 broke down (not converged).
@@ -351,15 +371,16 @@ struct PcgState {
     int stop, steps;
 };
 
-__global__ void pcg_init_kernel(const double* __restrict__ norms, PcgState* st) {
+__device__ __forceinline__ void pcg_init_body(const double* __restrict__ norms, PcgState* st) {
     st->rz = norms[0];
     st->ak = st->pp2 = st->beta = st->last = st->prev = 0.0;
     st->stop = 0;
     st->steps = 0;
 }
+__global__ void pcg_init_kernel(const double* __restrict__ norms, PcgState* st) { pcg_init_body(norms, st); }
 
 // after w = A^T A p: norms = (p.w, p.p); the step length
-__global__ void pcg_step_length_kernel(const double* __restrict__ norms, PcgState* st) {
+__device__ __forceinline__ void pcg_step_length_body(const double* __restrict__ norms, PcgState* st) {
     if (st->stop) return;
     const double pw = norms[0];
     if (!(pw > 0.0) || !isfinite(st->rz)) {
@@ -369,10 +390,11 @@ __global__ void pcg_step_length_kernel(const double* __restrict__ norms, PcgStat
     st->ak = st->rz / pw;
     st->pp2 = norms[1];
 }
+__global__ void pcg_step_length_kernel(const double* __restrict__ norms, PcgState* st) { pcg_step_length_body(norms, st); }
 
 // after z = M^-1 r: norms = (r.z, alpha.alpha); the relative update and the stopping rule
 // (below tol, or no longer shrinking at a level below floor_ok), else the next direction's beta
-__global__ void pcg_step_end_kernel(const double* __restrict__ norms, PcgState* st, double tol, double floor_ok) {
+__device__ __forceinline__ void pcg_step_end_body(const double* __restrict__ norms, PcgState* st, double tol, double floor_ok) {
     if (st->stop) return;
     st->steps += 1;
     st->prev = st->last;
@@ -390,6 +412,7 @@ __global__ void pcg_step_end_kernel(const double* __restrict__ norms, PcgState* 
     st->beta = nx0 / st->rz;
     st->rz = nx0;
 }
+__global__ void pcg_step_end_kernel(const double* __restrict__ norms, PcgState* st, double tol, double floor_ok) { pcg_step_end_body(norms, st, tol, floor_ok); }
 
 // alpha += ak p (which 0), r -= ak w (1), p = z + beta p (2), with the scalars of st
 __global__ void pcg_axpy_kernel(double* y, const double* x, const PcgState* st, int which, int n) {
@@ -409,6 +432,118 @@ template <typename T>
 __global__ void from_double_kernel(const double* src, T* dst, int64_t n) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         dst[i] = (T)src[i];
+}
+
+// ------------------------------------------------------------------ grouped refits
+// The conjugate gradients of several refits advanced in shared launches: job j carries the
+// vectors of one refit, and each kernel below does one step of the single-refit sequence for
+// every job at once, with the single kernels' arithmetic (the same bodies and reduction
+// orders), so a job's iterates equal those of its own refit bit for bit.
+enum PcgVec { vRV = 0, vG, vAlpha, vAlpha0, vRR, vZZ, vPP, vWW, kPcgVecs };
+struct PcgJob {
+    const float* U1;
+    const float* U2;
+    const float* U3;
+    const float* b;
+    int64_t m;
+    int r1, r2, r3, R;
+    double* v[kPcgVecs];   // rv (m), then the R-vectors g, alpha, alpha0, r, z, p, w
+    double* norms;
+    double* part;          // A^T partial sums (nparts x R)
+    PcgState* st;
+    float* xw;             // the preconditioner solve's working copy
+    int nparts, parts_per_block;   // A^T partition (the single refit's) and parts a block takes
+    int64_t rows_per_block;
+    long long rfirst, afirst;   // first block in its class's residual / A^T launch
+};
+template <long long PcgJob::*F>
+__device__ __forceinline__ int pcg_job_of(const PcgJob* jobs, int n, long long x) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (jobs[mid].*F <= x) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// rv = (b if use_b) + scale * A v[src], for the jobs of one rank class
+template <int R3M>
+__global__ void __launch_bounds__(256) residual_group_kernel(const PcgJob* __restrict__ jobs, int n, int src,
+                                                             int use_b, double scale, int gated) {
+    const int q = pcg_job_of<&PcgJob::rfirst>(jobs, n, blockIdx.x);
+    const PcgJob& j = jobs[q];
+    if (gated && j.st->stop) return;
+    const long long nb = (q + 1 < n ? jobs[q + 1].rfirst : (long long)gridDim.x) - j.rfirst;
+    residual_body<float, R3M>(j.U1, j.U2, j.U3, use_b ? j.b : nullptr, j.v[src], j.m, j.r1, j.r2, j.r3, scale,
+                              j.v[vRV], (int)(blockIdx.x - j.rfirst), (int)nb);
+}
+
+// the partial sums of A^T rv (the single refit's row partition)
+template <int R3M, int PPT>
+__global__ void __launch_bounds__(256) atr_group_kernel(const PcgJob* __restrict__ jobs, int n, int gated) {
+    const int q = pcg_job_of<&PcgJob::afirst>(jobs, n, blockIdx.x);
+    const PcgJob& j = jobs[q];
+    if (gated && j.st->stop) return;
+    const int b0 = (int)(blockIdx.x - j.afirst) * j.parts_per_block;
+    const int b1 = b0 + j.parts_per_block < j.nparts ? b0 + j.parts_per_block : j.nparts;
+    for (int b = b0; b < b1; ++b)
+        atr_body<float, R3M, PPT>(j.U1, j.U2, j.U3, j.v[vRV], j.m, j.r1, j.r2, j.r3, j.rows_per_block, j.part, b);
+}
+
+__global__ void sum_partials_group_kernel(const PcgJob* __restrict__ jobs, int dst, int gated) {
+    const PcgJob& j = jobs[blockIdx.y];
+    if (gated && j.st->stop) return;
+    for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < j.R; a += gridDim.x * blockDim.x) {
+        double sum = 0.0;
+        for (int b = 0; b < j.nparts; ++b) sum += j.part[(size_t)b * j.R + a];
+        j.v[dst][a] = sum;
+    }
+}
+
+__global__ void __launch_bounds__(kDotThreads) dots_group_kernel(const PcgJob* __restrict__ jobs, int x0, int y0,
+                                                                 int x1, int y1) {
+    const PcgJob& j = jobs[blockIdx.x];
+    dots_body(j.v[x0], j.v[y0], j.v[x1], j.v[y1], j.R, 2, j.norms);
+}
+
+// kind 0: init, 1: step length, 2: step end (one thread a job)
+__global__ void pcg_scalar_group_kernel(const PcgJob* __restrict__ jobs, int n, int kind, double tol,
+                                        double floor_ok) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    const PcgJob& j = jobs[q];
+    if (kind == 0) pcg_init_body(j.norms, j.st);
+    else if (kind == 1) pcg_step_length_body(j.norms, j.st);
+    else pcg_step_end_body(j.norms, j.st, tol, floor_ok);
+}
+
+// alpha += ak p (which 0), r -= ak w (1), p = z + beta p (2)
+__global__ void pcg_axpy_group_kernel(const PcgJob* __restrict__ jobs, int which) {
+    const PcgJob& j = jobs[blockIdx.y];
+    const PcgState* st = j.st;
+    if (st->stop) return;
+    const double a = which == 0 ? st->ak : which == 1 ? -st->ak : st->beta;
+    double* y = j.v[which == 0 ? vAlpha : which == 1 ? vRR : vPP];
+    const double* x = j.v[which == 0 ? vPP : which == 1 ? vWW : vZZ];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < j.R; i += gridDim.x * blockDim.x)
+        y[i] = which == 2 ? x[i] + a * y[i] : y[i] + a * x[i];
+}
+
+// v[dst] = v[src]; dir 0: xw = (float) v[vec]; dir 1: v[vec] = xw (all R-vectors)
+__global__ void pcg_copy_group_kernel(const PcgJob* __restrict__ jobs, int dst, int src) {
+    const PcgJob& j = jobs[blockIdx.y];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < j.R; i += gridDim.x * blockDim.x) j.v[dst][i] = j.v[src][i];
+}
+__global__ void pcg_convert_group_kernel(const PcgJob* __restrict__ jobs, int vec, int dir) {
+    const PcgJob& j = jobs[blockIdx.y];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < j.R; i += gridDim.x * blockDim.x) {
+        if (dir == 0) j.xw[i] = (float)j.v[vec][i];
+        else j.v[vec][i] = (double)j.xw[i];
+    }
+}
+__global__ void pcg_gather_states_kernel(const PcgJob* __restrict__ jobs, int n, PcgState* out) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < n) out[q] = *jobs[q].st;
 }
 
 // ------------------------------------------------------------------ driver
@@ -862,6 +997,419 @@ static fst_status refit_entry(fst_model* M, const T* xyz, const T* u, int64_t Q,
     return refit_impl<T>(M, xyz, u, Q, idx, m, seed, prec, opts, rep, s);
 }
 
+// Scratch of grouped refits on one device: the factorisation schedule and the job tables.
+constexpr int kGroupStreams = 8;
+struct GroupScratch {
+    std::mutex mu;
+    DevBuf sched, tab, states;
+    cudaStream_t side[kGroupStreams] = {};
+    cudaEvent_t ev[kGroupStreams + 1] = {};
+};
+GroupScratch g_group[64];
+
+static int rank_class(int r3) { return r3 <= 8 ? 0 : r3 <= 16 ? 1 : r3 <= 24 ? 2 : 3; }
+
+using FailFn = std::function<void(int, fst_status)>;
+static fst_status refit_group_shared(const std::vector<fst_refit_item>& items, const std::vector<int>& act,
+                                     int max_refine, double tol, double floor_ok, GroupScratch& GS,
+                                     std::vector<fst_refit_report>& reps, std::vector<char>& alone,
+                                     const FailFn& fail, bool& expired, cudaStream_t s);
+
+// Several refits with their factorisations and conjugate gradients in shared launches.
+// Steps 1-3 (rows, factor values, A^T b, the Gram in `prec`) run per item; the FP32
+// factorisations run as one schedule (cholesky_lower_group); the conjugate gradients of all
+// items advance together, one launch per step for every item (per rank class where the kernel
+// is specialised on r3).  An item whose factorisation fails, or whose iteration does not
+// converge, is then redone alone by refit_impl (with its fallbacks), so every result equals
+// that of fst_refit on the item.  The caller holds every model's lock.
+static fst_status refit_group_impl(const std::vector<fst_refit_item>& items, fst_prec prec,
+                                   const fst_refit_opts* opts, std::vector<fst_refit_report>& reps,
+                                   std::vector<fst_status>& status, std::vector<std::string>& errors,
+                                   cudaStream_t s) {
+    const int n = (int)items.size();
+    const int max_refine = opts ? opts->max_refine : 32;
+    const double tol = (opts && opts->refine_tol > 0) ? opts->refine_tol : 1e-8;
+    const double floor_ok = 1e-5;
+    int dev = 0;
+    FST_CUDA(cudaGetDevice(&dev));
+    GroupScratch& GS = g_group[dev & 63];
+    std::lock_guard<std::mutex> glk(GS.mu);
+    std::vector<char> alone(n, 0);   // redo with refit_impl
+    const FailFn fail = [&](int i, fst_status st) {
+        status[i] = st;
+        errors[i] = fst_last_error();
+    };
+    // 1-3 per item, spread over side streams that start after the caller's stream
+    if (!GS.side[0]) {
+        for (int k = 0; k < kGroupStreams; ++k) {
+            FST_CUDA(cudaStreamCreateWithFlags(&GS.side[k], cudaStreamNonBlocking));
+            FST_CUDA(cudaEventCreateWithFlags(&GS.ev[k], cudaEventDisableTiming));
+        }
+        FST_CUDA(cudaEventCreateWithFlags(&GS.ev[kGroupStreams], cudaEventDisableTiming));
+    }
+    EventTimer t1(s);
+    FST_CUDA(cudaEventRecord(GS.ev[kGroupStreams], s));
+    for (int k = 0; k < kGroupStreams; ++k) FST_CUDA(cudaStreamWaitEvent(GS.side[k], GS.ev[kGroupStreams], 0));
+    std::vector<int> act;
+    int nside = 0;
+    for (int i = 0; i < n; ++i) {
+        if (status[i] != FST_OK) continue;
+        if (opts && opts->fp64_cholesky) {
+            alone[i] = 1;
+            continue;
+        }
+        fst_model* M = items[i].model;
+        RefitScratch& W = M->rs;
+        const int R = M->R();
+        const int64_t m = items[i].m;
+        fst_refit_report& r = reps[i];
+        memset(&r, 0, sizeof r);
+        r.m = m;
+        cudaStream_t ss = GS.side[nside++ % kGroupStreams];
+        auto step = [&]() -> fst_status {
+            const cudaStream_t s = ss;
+            FST_TRY(W.idx.ensure(sizeof(int64_t) * (size_t)m));
+            FST_TRY(sample_rows(items[i].seed, items[i].Q, m, W.idx.as<int64_t>(), s));
+            float* U[3];
+            for (int k = 0; k < 3; ++k) {
+                FST_TRY(W.U[k].ensure(sizeof(float) * (size_t)m * M->r[k]));
+                U[k] = W.U[k].as<float>();
+            }
+            FST_TRY(W.b.ensure(sizeof(float) * (size_t)m));
+            FST_TRY(launch_factors<float>(M, items[i].xyz, items[i].Q, W.idx.as<int64_t>(), m, items[i].u, U,
+                                          W.b.as<float>(), s));
+            FST_TRY(W.res.ensure(sizeof(double) * (size_t)m));
+            FST_TRY(W.g.ensure(sizeof(double) * (size_t)R));
+            FST_TRY(W.alpha.ensure(sizeof(double) * (size_t)R));
+            FST_TRY(W.z.ensure(sizeof(double) * (size_t)R));
+            FST_TRY(W.norms.ensure(sizeof(double) * 2));
+            FST_TRY(W.flag.ensure(4 * sizeof(int)));
+            const float* const Uc[3] = {U[0], U[1], U[2]};
+            to_double_kernel<float><<<grid_for(m, 256), 256, 0, s>>>(W.b.as<float>(), W.res.as<double>(), m);
+            FST_CHECK_LAUNCH();
+            FST_TRY(launch_atr<float>(M, Uc, W.res.as<double>(), m, W.g.as<double>(), s));
+            FST_CUDA(cudaMemsetAsync(W.flag.as<int>(), 0, 2 * sizeof(int), s));
+            FST_TRY(W.G.ensure(sizeof(float) * (size_t)R * R));
+            if (prec == FST_FP32)
+                FST_TRY(launch_gram_simt<float>(M, Uc, m, W.G.as<float>(), s));
+            else
+                FST_TRY(gram_tensor(M, Uc, m, W.G.as<float>(), prec, s));
+            return FST_OK;
+        };
+        const fst_status st = step();
+        if (st != FST_OK) fail(i, st);
+        else act.push_back(i);
+    }
+    for (int k = 0; k < kGroupStreams; ++k) {
+        FST_CUDA(cudaEventRecord(GS.ev[k], GS.side[k]));
+        FST_CUDA(cudaStreamWaitEvent(s, GS.ev[k], 0));
+    }
+    const double ms1 = t1.stop();
+    for (int i : act) reps[i].ms_gram = ms1;   // rows, factor values and Grams of the whole group
+    // 4-6 (a device wait that expired fails every item still to be done)
+    bool expired = false;
+    if (!act.empty())
+        FST_TRY(refit_group_shared(items, act, max_refine, tol, floor_ok, GS, reps, alone, fail, expired, s));
+    // 7. items redone alone (failed factorisation, no convergence, or FP64 asked for)
+    for (int i = 0; i < n; ++i) {
+        if (!alone[i] || status[i] != FST_OK) continue;
+        if (expired) {
+            status[i] = FST_ETIMEOUT;
+            errors[i] = "a bounded device wait of the group expired";
+            continue;
+        }
+        const fst_status st = refit_impl<float>(items[i].model, items[i].xyz, items[i].u, items[i].Q, nullptr,
+                                                items[i].m, items[i].seed, prec, opts, &reps[i], s);
+        if (st != FST_OK) fail(i, st);
+    }
+    return FST_OK;
+}
+
+// Steps 4-6 of a grouped refit for the items `act` (their Grams formed): the shared
+// factorisation, then the shared conjugate gradients of the items whose factor exists, then
+// their new cores.  Items to redo alone are marked in `alone`.
+static fst_status refit_group_shared(const std::vector<fst_refit_item>& items, const std::vector<int>& act,
+                                     int max_refine, double tol, double floor_ok, GroupScratch& GS,
+                                     std::vector<fst_refit_report>& reps, std::vector<char>& alone,
+                                     const FailFn& fail, bool& expired, cudaStream_t s) {
+    const int n = (int)items.size();
+    // 4. the factorisations, one schedule
+    EventTimer tg(s);
+    FST_TRY(GS.states.ensure(sizeof(int) * 4 + sizeof(PcgState) * (size_t)n));
+    int* gsync = GS.states.as<int>();   // [0] factorisation waits, [2] solve error, [3] solve ticket
+    PcgState* gst = reinterpret_cast<PcgState*>(gsync + 4);
+    FST_CUDA(cudaMemsetAsync(gsync, 0, 4 * sizeof(int), s));
+    {
+        std::vector<CholItem> ci;
+        for (int i : act) {
+            RefitScratch& W = items[i].model->rs;
+            ci.push_back(CholItem{W.G.as<float>(), items[i].model->R(), W.flag.as<int>(), &W.chol_ws});
+        }
+        FST_TRY(cholesky_lower_group(ci, GS.sched, gsync, s));
+    }
+    for (int i : act) {
+        RefitScratch& W = items[i].model->rs;
+        const int R = items[i].model->R();
+        FST_TRY(W.Linv.ensure(3 * sizeof(float) * (size_t)((R + 63) / 64) * 64 * 64));
+        FST_TRY(chol_invert_diag<float>(W.G.as<float>(), R, W.Linv.as<float>(), s));
+        FST_TRY(W.LT.ensure(sizeof(float) * (size_t)R * R));
+        FST_TRY(chol_transpose<float>(W.G.as<float>(), R, W.LT.as<float>(), s));
+    }
+    std::vector<int> hflag(act.size(), 0);
+    for (size_t a = 0; a < act.size(); ++a)
+        FST_CUDA(cudaMemcpyAsync(&hflag[a], items[act[a]].model->rs.flag.as<int>(), sizeof(int),
+                                 cudaMemcpyDeviceToHost, s));
+    int hg = 0;
+    FST_CUDA(cudaMemcpyAsync(&hg, gsync, sizeof(int), cudaMemcpyDeviceToHost, s));
+    FST_CUDA(cudaStreamSynchronize(s));
+    const double ms_chol = tg.stop();
+    if (hg) {
+        set_error("Cholesky: a bounded device wait expired (code %d)", hg);
+        for (int i : act) fail(i, FST_ETIMEOUT);
+        expired = true;
+        return FST_OK;
+    }
+    std::vector<int> pc;   // items going on to the conjugate gradients
+    for (size_t a = 0; a < act.size(); ++a) {
+        reps[act[a]].ms_cholesky = ms_chol;
+        if (hflag[a]) alone[act[a]] = 1;
+        else pc.push_back(act[a]);
+    }
+
+    // 5. the conjugate gradients of every remaining item, in shared launches
+    if (!pc.empty()) {
+        std::sort(pc.begin(), pc.end(), [&](int a, int b) {
+            const int ca = rank_class(items[a].model->r[2]), cb = rank_class(items[b].model->r[2]);
+            return ca != cb ? ca < cb : a < b;
+        });
+        const int np = (int)pc.size();
+        std::vector<PcgJob> jobs(np);
+        std::vector<SolveJob> sj(np);
+        std::vector<int> Rs(np);
+        int cls_off[5] = {0, 0, 0, 0, 0};
+        long long rnext[4] = {0, 0, 0, 0}, anext[4] = {0, 0, 0, 0};
+        int maxR = 0;
+        for (int q = 0; q < np; ++q) {
+            fst_model* M = items[pc[q]].model;
+            RefitScratch& W = M->rs;
+            const int R = M->R();
+            const int64_t m = items[pc[q]].m;
+            FST_TRY(W.xw.ensure(sizeof(double) * (size_t)R));
+            FST_TRY(W.yw.ensure(sizeof(double) * (size_t)R));
+            FST_TRY(W.pcg_state.ensure(sizeof(PcgState)));
+            FST_TRY(W.pcg.ensure(sizeof(double) * (size_t)R * 4));
+            FST_CUDA(cudaMemsetAsync(W.pcg_state.ptr, 0, sizeof(PcgState), s));
+            // the single refit's A^T row partition
+            int64_t nparts = 2LL * sm_count();
+            const int64_t rpb = ((m + nparts - 1) / nparts + 31) / 32 * 32;
+            nparts = (m + rpb - 1) / rpb;
+            FST_TRY(W.atr_part.ensure(sizeof(double) * (size_t)nparts * R));
+            PcgJob& j = jobs[q];
+            j.U1 = W.U[0].as<float>();
+            j.U2 = W.U[1].as<float>();
+            j.U3 = W.U[2].as<float>();
+            j.b = W.b.as<float>();
+            j.m = m;
+            j.r1 = M->r[0];
+            j.r2 = M->r[1];
+            j.r3 = M->r[2];
+            j.R = R;
+            double* pv = W.pcg.as<double>();
+            j.v[vRV] = W.res.as<double>();
+            j.v[vG] = W.g.as<double>();
+            j.v[vAlpha] = W.alpha.as<double>();
+            j.v[vAlpha0] = W.z.as<double>();
+            j.v[vRR] = pv;
+            j.v[vZZ] = pv + R;
+            j.v[vPP] = pv + 2 * R;
+            j.v[vWW] = pv + 3 * R;
+            j.norms = W.norms.as<double>();
+            j.part = W.atr_part.as<double>();
+            j.st = W.pcg_state.as<PcgState>();
+            j.xw = W.xw.as<float>();
+            j.nparts = (int)nparts;
+            j.rows_per_block = rpb;
+            // one A^T part a block (fewer, longer blocks serialise the small items' parts)
+            j.parts_per_block = 1;
+            const int c = rank_class(j.r3);
+            ++cls_off[c + 1];
+            j.rfirst = rnext[c];
+            rnext[c] += (m + 255) / 256;
+            j.afirst = anext[c];
+            anext[c] += (nparts + j.parts_per_block - 1) / j.parts_per_block;
+            sj[q] = SolveJob{W.G.as<float>(), W.LT.as<float>(), W.Linv.as<float>(), W.xw.as<float>(),
+                             W.yw.as<float>(), &j.st->stop, R, (R + 63) / 64};
+            Rs[q] = R;
+            maxR = std::max(maxR, R);
+        }
+        for (int c = 0; c < 4; ++c) cls_off[c + 1] += cls_off[c];
+        const std::vector<int> tmap = solve_tickets(Rs);
+        const size_t jb = (sizeof(PcgJob) * np + 255) / 256 * 256, sb = (sizeof(SolveJob) * np + 255) / 256 * 256;
+        FST_TRY(GS.tab.ensure(jb + sb + sizeof(int) * tmap.size()));
+        PcgJob* dj = GS.tab.as<PcgJob>();
+        SolveJob* ds = reinterpret_cast<SolveJob*>(GS.tab.as<unsigned char>() + jb);
+        int* dt = reinterpret_cast<int*>(GS.tab.as<unsigned char>() + jb + sb);
+        FST_CUDA(cudaMemcpyAsync(dj, jobs.data(), sizeof(PcgJob) * np, cudaMemcpyHostToDevice, s));
+        FST_CUDA(cudaMemcpyAsync(ds, sj.data(), sizeof(SolveJob) * np, cudaMemcpyHostToDevice, s));
+        FST_CUDA(cudaMemcpyAsync(dt, tmap.data(), sizeof(int) * tmap.size(), cudaMemcpyHostToDevice, s));
+        size_t res_smem[4] = {0, 0, 0, 0};
+        for (int q = 0; q < np; ++q) {
+            const int c = rank_class(jobs[q].r3);
+            res_smem[c] = std::max(res_smem[c], (size_t)jobs[q].r1 * jobs[q].r2 * ((c + 1) * 8) * sizeof(float) * 2);
+        }
+        const dim3 vg((unsigned)std::min((maxR + 255) / 256, 64), (unsigned)np);
+        auto residual = [&](int src, int use_b, double scale, int gated) -> fst_status {
+            for (int c = 0; c < 4; ++c) {
+                const int cn = cls_off[c + 1] - cls_off[c];
+                if (!cn) continue;
+                const PcgJob* jc = dj + cls_off[c];
+#define FST_RESG(V)                                                                                     \
+    {                                                                                                   \
+        auto kern = residual_group_kernel<V>;                                                           \
+        FST_TRY(allow_smem(kern, res_smem[c]));                                                         \
+        kern<<<(unsigned)rnext[c], 256, res_smem[c], s>>>(jc, cn, src, use_b, scale, gated);            \
+    }
+                if (c == 0) FST_RESG(8) else if (c == 1) FST_RESG(16) else if (c == 2) FST_RESG(24) else FST_RESG(32)
+#undef FST_RESG
+                FST_CHECK_LAUNCH();
+            }
+            return FST_OK;
+        };
+        auto atr = [&](int dst, int gated) -> fst_status {
+            for (int c = 0; c < 4; ++c) {
+                const int cn = cls_off[c + 1] - cls_off[c];
+                if (!cn) continue;
+                const PcgJob* jc = dj + cls_off[c];
+                const unsigned g = (unsigned)anext[c];
+                if (c == 0) atr_group_kernel<8, 3><<<g, 256, 0, s>>>(jc, cn, gated);
+                else if (c == 1) atr_group_kernel<16, 3><<<g, 256, 0, s>>>(jc, cn, gated);
+                else if (c == 2) atr_group_kernel<24, 3><<<g, 256, 0, s>>>(jc, cn, gated);
+                else atr_group_kernel<32, 2><<<g, 256, 0, s>>>(jc, cn, gated);
+                FST_CHECK_LAUNCH();
+            }
+            sum_partials_group_kernel<<<vg, 256, 0, s>>>(dj, dst, gated);
+            FST_CHECK_LAUNCH();
+            return FST_OK;
+        };
+        auto copy = [&](int dst, int src) -> fst_status {
+            pcg_copy_group_kernel<<<vg, 256, 0, s>>>(dj, dst, src);
+            FST_CHECK_LAUNCH();
+            return FST_OK;
+        };
+        auto solve = [&](int vec) -> fst_status {
+            pcg_convert_group_kernel<<<vg, 256, 0, s>>>(dj, vec, 0);
+            FST_CHECK_LAUNCH();
+            FST_TRY(chol_solve_group<float>(ds, np, maxR, dt, (int)tmap.size(), gsync + 2, s));
+            pcg_convert_group_kernel<<<vg, 256, 0, s>>>(dj, vec, 1);
+            FST_CHECK_LAUNCH();
+            return FST_OK;
+        };
+        auto dots = [&](int x0, int y0, int x1, int y1) -> fst_status {
+            dots_group_kernel<<<np, kDotThreads, 0, s>>>(dj, x0, y0, x1, y1);
+            FST_CHECK_LAUNCH();
+            return FST_OK;
+        };
+        auto scalar = [&](int kind) -> fst_status {
+            pcg_scalar_group_kernel<<<(np + 127) / 128, 128, 0, s>>>(dj, np, kind, tol, floor_ok);
+            FST_CHECK_LAUNCH();
+            return FST_OK;
+        };
+        auto axpy = [&](int which) -> fst_status {
+            pcg_axpy_group_kernel<<<vg, 256, 0, s>>>(dj, which);
+            FST_CHECK_LAUNCH();
+            return FST_OK;
+        };
+        EventTimer tr(s);
+        // alpha_0 = G^-1 h
+        FST_TRY(copy(vAlpha, vG));
+        FST_TRY(solve(vAlpha));
+        FST_TRY(copy(vAlpha0, vAlpha));
+        std::vector<PcgState> hs(np);
+        memset(hs.data(), 0, sizeof(PcgState) * np);
+        if (max_refine > 0) {
+            FST_TRY(residual(vAlpha, 1, -1.0, 0));        // b - A alpha
+            FST_TRY(atr(vRR, 0));                         // r = A^T (b - A alpha)
+            FST_TRY(copy(vZZ, vRR));
+            FST_TRY(solve(vZZ));
+            FST_TRY(copy(vPP, vZZ));
+            FST_TRY(dots(vRR, vZZ, vAlpha, vAlpha));
+            FST_TRY(scalar(0));
+            constexpr int kCheckEvery = 2;
+            for (int it = 0; it < max_refine; ++it) {
+                FST_TRY(residual(vPP, 0, 1.0, 1));        // q = A p
+                FST_TRY(atr(vWW, 1));                     // w = A^T q
+                FST_TRY(dots(vPP, vWW, vPP, vPP));
+                FST_TRY(scalar(1));
+                FST_TRY(axpy(0));                         // alpha += ak p
+                FST_TRY(axpy(1));                         // r -= ak w
+                FST_TRY(copy(vZZ, vRR));
+                FST_TRY(solve(vZZ));
+                FST_TRY(dots(vRR, vZZ, vAlpha, vAlpha));
+                FST_TRY(scalar(2));
+                FST_TRY(axpy(2));                         // p = z + beta p
+                if ((it + 1) % kCheckEvery == 0 || it + 1 == max_refine) {
+                    pcg_gather_states_kernel<<<(np + 127) / 128, 128, 0, s>>>(dj, np, gst);
+                    FST_CHECK_LAUNCH();
+                    FST_CUDA(cudaMemcpyAsync(hs.data(), gst, sizeof(PcgState) * np, cudaMemcpyDeviceToHost, s));
+                    FST_CUDA(cudaStreamSynchronize(s));
+                    bool all = true;
+                    for (const PcgState& x : hs) all = all && x.stop != 0;
+                    if (all) break;
+                }
+            }
+        }
+        int serr = 0;
+        FST_CUDA(cudaMemcpyAsync(&serr, gsync + 2, sizeof(int), cudaMemcpyDeviceToHost, s));
+        FST_CUDA(cudaStreamSynchronize(s));
+        const double ms_ref = tr.stop();
+        if (serr) {
+            set_error("triangular solve: a bounded device wait expired");
+            for (int i : pc) fail(i, FST_ETIMEOUT);
+            expired = true;
+            return FST_OK;
+        }
+        // 6. the new cores
+        for (int q = 0; q < np; ++q) {
+            const int i = pc[q];
+            fst_model* M = items[i].model;
+            fst_refit_report& r = reps[i];
+            r.ms_refine = ms_ref;
+            const int R = M->R();
+            bool converged = max_refine <= 0;
+            if (max_refine > 0) {
+                r.refine_steps = hs[q].steps;
+                r.last_rel_update = hs[q].last;
+                converged = hs[q].stop == 1 || (isfinite(hs[q].last) && hs[q].last <= floor_ok);
+            }
+            if (!converged) {
+                alone[i] = 1;
+                continue;
+            }
+            std::vector<double> ha(R), h0(R);
+            FST_CUDA(cudaMemcpyAsync(ha.data(), jobs[q].v[vAlpha], sizeof(double) * R, cudaMemcpyDeviceToHost, s));
+            FST_CUDA(cudaMemcpyAsync(h0.data(), jobs[q].v[vAlpha0], sizeof(double) * R, cudaMemcpyDeviceToHost, s));
+            FST_CUDA(cudaStreamSynchronize(s));
+            double dn = 0, an = 0;
+            bool finite = true;
+            for (int e = 0; e < R; ++e) {
+                dn += (ha[e] - h0[e]) * (ha[e] - h0[e]);
+                an += ha[e] * ha[e];
+                finite = finite && isfinite(ha[e]);
+            }
+            r.first_rel_change = an > 0 ? sqrt(dn / an) : 0.0;
+            if (!finite) {
+                set_error("refit produced a non-finite core");
+                fail(i, FST_ENOTSPD);
+                continue;
+            }
+            M->alpha = ha;
+            const fst_status st = model_upload_core(M);
+            if (st != FST_OK) fail(i, st);
+        }
+    }
+    return FST_OK;
+}
+
 }  // namespace fst
 
 using namespace fst;
@@ -919,6 +1467,59 @@ extern "C" fst_status fst_refit_batched(const fst_refit_item* items, int32_t cou
         });
     }
     for (auto& t : workers) t.join();
+    for (int i = 0; i < count; ++i)
+        if (status[i] != FST_OK) {
+            set_error("item %d: %s", i, errors[i].c_str());
+            return status[i];
+        }
+    return FST_OK;
+}
+
+// Many refits with shared launches (see refit_group_impl): every item is checked as fst_refit
+// checks it, the models are locked in address order, and the first failed item's status is
+// returned after all items have run.
+extern "C" fst_status fst_refit_grouped(const fst_refit_item* items, int32_t count, fst_prec prec,
+                                        const fst_refit_opts* opts, fst_refit_report* reports, fst_stream stream) {
+    FST_REQUIRE(count >= 0 && (count == 0 || items != nullptr), "items is NULL");
+    FST_REQUIRE(prec == FST_FP32 || prec == FST_TF32 || prec == FST_BF16 || prec == FST_BF16X3,
+                "fst_refit_grouped takes FP32/TF32/BF16/BF16X3");
+    for (int i = 0; i < count; ++i)
+        for (int j = 0; j < i; ++j)
+            FST_REQUIRE(items[i].model != items[j].model, "items %d and %d refit the same model", j, i);
+    if (count == 0) return FST_OK;
+    int dev = 0;
+    FST_CUDA(cudaGetDevice(&dev));
+    std::vector<fst_refit_item> it(items, items + count);
+    std::vector<fst_status> status(count, FST_OK);
+    std::vector<std::string> errors(count);
+    std::vector<fst_refit_report> reps(count);
+    for (int i = 0; i < count; ++i) {
+        fst_refit_item& x = it[i];
+        memset(&reps[i], 0, sizeof(fst_refit_report));
+        auto bad = [&](fst_status st, const char* msg) {
+            status[i] = st;
+            errors[i] = msg;
+        };
+        if (!x.model) bad(FST_EINVAL, "model is NULL");
+        else if (x.Q <= 0 || x.m <= 0) bad(FST_EINVAL, "Q and m must be positive");
+        else if (!x.xyz || !x.u) bad(FST_EINVAL, "xyz or u is NULL");
+        else if (x.model->device != dev) bad(FST_EINVAL, "model lives on another device");
+        else if (pointer_device(x.xyz) != dev || pointer_device(x.u) != dev) bad(FST_EINVAL, "xyz and u must be device memory");
+        else {
+            if (x.m > x.Q) x.m = x.Q;
+            if (x.m > ((int64_t)1 << 31)) bad(FST_EINVAL, "m too large");
+            else if (x.m < (int64_t)x.model->R()) bad(FST_ERANK, "fewer sampled rows than unknowns (m < R)");
+        }
+    }
+    std::vector<fst_model*> order;
+    for (const fst_refit_item& x : it)
+        if (x.model) order.push_back(x.model);
+    std::sort(order.begin(), order.end());
+    std::vector<std::unique_lock<std::recursive_mutex>> locks;
+    for (fst_model* M : order) locks.emplace_back(M->mu);
+    FST_TRY(refit_group_impl(it, prec, opts, reps, status, errors, (cudaStream_t)stream));
+    if (reports)
+        for (int i = 0; i < count; ++i) reports[i] = reps[i];
     for (int i = 0; i < count; ++i)
         if (status[i] != FST_OK) {
             set_error("item %d: %s", i, errors[i].c_str());

@@ -127,6 +127,7 @@ def _load():
         "fst_refit": (I32, [P, P, P, I64, P, I64, U64, I32, P, P, P]),
         "fst_refit_f64": (I32, [P, P, P, I64, P, I64, U64, P, P, P]),
         "fst_refit_batched": (I32, [P, I32, I32, P, I32, P]),
+        "fst_refit_grouped": (I32, [P, I32, I32, P, P, P]),
         "fst_refit_mixed": (I32, [P, P, P, I64, I64, U64, U64, P, P]),
         "fst_normal_matrix": (I32, [P, P, P, I64, P, I64, I32, P, P, P]),
         "fst_fit": (I32, [P, P, I64, P, P, P, I32, P, P, P, P, P]),
@@ -348,6 +349,23 @@ def refit_batched(models, xyzs, us, ms, seeds, prec: str = "bf16", streams: int 
     opts = RefitOpts(int(max_refine), float(refine_tol), 0)
     torch.cuda.synchronize()     # the library's streams do not wait on the caller's
     _check(lib.fst_refit_batched(arr, n, PREC[prec], C.byref(opts), int(streams), reps))
+    return [reps[i].as_dict() for i in range(n)]
+
+
+def refit_grouped(models, xyzs, us, ms, seeds, prec: str = "bf16", max_refine: int = 32, refine_tol: float = 0.0,
+                  fp64_cholesky: bool = False, stream=None):
+    """fst_refit_grouped: refit every model on its own points, the factorisations and the
+    conjugate gradients of all items in shared launches on one stream.  Returns the reports."""
+    import torch
+    n = len(models)
+    arr = (RefitItem * max(n, 1))()
+    for i, (M, x, u, m, sd) in enumerate(zip(models, xyzs, us, ms, seeds)):
+        assert x.is_cuda and x.dtype == torch.float32 and x.is_contiguous() and x.shape[0] == 3
+        assert u.is_cuda and u.dtype == torch.float32 and u.is_contiguous()
+        arr[i] = RefitItem(M._h, x.data_ptr(), u.data_ptr(), x.shape[1], int(m), int(sd) & 0xFFFFFFFFFFFFFFFF)
+    reps = (RefitReport * max(n, 1))()
+    opts = RefitOpts(int(max_refine), float(refine_tol), int(bool(fp64_cholesky)))
+    _check(lib.fst_refit_grouped(arr, n, PREC[prec], C.byref(opts), reps, _stream(stream)))
     return [reps[i].as_dict() for i in range(n)]
 
 
