@@ -11,7 +11,8 @@ Algorithm 2); ``mixing.py`` holds Algorithm 2's sign flip and fast mixing of the
 rows; ``fit.py`` holds the construction steps of Algorithm 1 (interpolation,
 ST-HOSVD, sparse Legendre fit, choice between the Legendre and multiwavelet
 spaces); ``wavelet.py`` holds the multiwavelet spaces and the evaluation and
-refit of models whose factor functions use them.  Parity status of each function
+refit of models whose factor functions use them; ``order4.py`` holds the
+evaluation and refit of order-4 models (the SP4D case).  Parity status of each function
 is stated in its docstring; every function here is pinned by a ``-m "not gpu"``
 test against closed forms, library routines or brute force, except where a
 docstring says "parity unpinned".

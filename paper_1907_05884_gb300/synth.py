@@ -294,3 +294,112 @@ def batch_instances(n_fields: int = 64, n_steps: int = 8, seed: int = 404,
             out.append({"field": f, "step": t, "r": r, "Q": Q,
                         "seed": int(rng.integers(0, 2**62))})
     return out
+
+
+# ----------------------------------------------------------------------------- order 4
+# Four-way models and inputs, the SP4D-like case (three space axes and time): the same
+# recipes with a fourth coordinate.
+@dataclass
+class Model4:
+    """An order-4 functional sparse Tucker model (eq. func_tuck with d = 4): CSC coefficient
+    matrices of the orthonormal Legendre functions per mode, the core alpha[j1][j2][j3][j4]
+    in C order, and the box [lo_k, hi_k] of each coordinate."""
+    r: tuple
+    p: tuple
+    colptr: list
+    rowidx: list
+    val: list
+    alpha: np.ndarray
+    lo: np.ndarray = dc_field(default_factory=lambda: -np.ones(4))
+    hi: np.ndarray = dc_field(default_factory=lambda: np.ones(4))
+
+    @property
+    def R(self) -> int:
+        return int(np.prod(self.r))
+
+    def with_alpha(self, alpha: np.ndarray) -> "Model4":
+        return Model4(self.r, self.p, self.colptr, self.rowidx, self.val,
+                      np.asarray(alpha, dtype=np.float64).reshape(self.r), self.lo, self.hi)
+
+
+def random_model4(r, p, seed: int, density: float = 0.6, orthonormal: bool = False, lo=None, hi=None) -> Model4:
+    """A random order-4 model: the coefficient columns and core of random_model drawn for
+    four modes (orthonormal columns when asked; core entries normal, decaying like
+    1/(1 + j1 + j2 + j3 + j4))."""
+    r = tuple(int(v) for v in r)
+    p = tuple(int(v) for v in (p if np.ndim(p) else (p,) * 4))
+    rng = _rng(seed, 8)
+    colptr, rowidx, val = [], [], []
+    for k in range(4):
+        n = p[k] + 1
+        if orthonormal:
+            if r[k] > n:
+                raise ValueError("orthonormal factors need r_k <= p_k + 1")
+            Qm = np.linalg.qr(rng.normal(size=(n, n)))[0][:, :r[k]]
+            colptr.append(np.arange(0, n * r[k] + 1, n, dtype=np.int32))
+            rowidx.append(np.tile(np.arange(n, dtype=np.int32), r[k]))
+            val.append(np.ascontiguousarray(Qm.T).reshape(-1))
+            continue
+        keep = max(1, min(n, int(round(density * n))))
+        cp, ri, vv = [0], [], []
+        for j in range(r[k]):
+            low = int(rng.integers(0, min(j, n - 1) + 1))
+            others = rng.permutation(np.setdiff1d(np.arange(n), [low]))[:keep - 1]
+            rows = np.sort(np.concatenate([[low], others])).astype(np.int32)
+            c = rng.normal(size=rows.size)
+            c /= np.linalg.norm(c)
+            ri.append(rows)
+            vv.append(c)
+            cp.append(cp[-1] + rows.size)
+        colptr.append(np.asarray(cp, dtype=np.int32))
+        rowidx.append(np.concatenate(ri).astype(np.int32))
+        val.append(np.concatenate(vv).astype(np.float64))
+    g = np.meshgrid(*[np.arange(v) for v in r], indexing="ij")
+    alpha = rng.normal(size=r) / (1.0 + g[0] + g[1] + g[2] + g[3])
+    lo = -np.ones(4) if lo is None else np.asarray(lo, dtype=np.float64)
+    hi = np.ones(4) if hi is None else np.asarray(hi, dtype=np.float64)
+    return Model4(r, p, colptr, rowidx, val, alpha, lo, hi)
+
+
+def points4(Q: int, seed: int, clustered: float = 0.3, dtype=np.float64) -> np.ndarray:
+    """Q points in [-1,1]^4 as a (4, Q) structure-of-arrays array: the three space axes of
+    points() (uniform share and the band around the moving front) and a time coordinate t
+    uniform in [-1, 1]; the band follows the front x1 = -0.3 sin(3 x2) + 0.2 x3 + 0.2 t."""
+    Q = int(Q)
+    rng = _rng(seed, 9)
+    t = rng.uniform(-1.0, 1.0, size=Q)
+    n_c = int(round(clustered * Q))
+    n_u = Q - n_c
+    uni = rng.uniform(-1.0, 1.0, size=(3, n_u))
+    cl = np.empty((3, n_c))
+    tc = t[n_u:]
+    todo = np.arange(n_c)
+    while todo.size:
+        x2 = rng.uniform(-1.0, 1.0, size=todo.size)
+        x3 = rng.uniform(-1.0, 1.0, size=todo.size)
+        x1 = -0.3 * np.sin(3.0 * x2) + 0.2 * x3 + 0.2 * tc[todo] + rng.uniform(-0.025, 0.025, size=todo.size)
+        ok = np.abs(x1) <= 1.0
+        cl[0, todo[ok]] = x1[ok]
+        cl[1, todo[ok]] = x2[ok]
+        cl[2, todo[ok]] = x3[ok]
+        todo = todo[~ok]
+    perm = rng.permutation(Q)
+    out = np.empty((4, Q), dtype=dtype)
+    for k in range(3):
+        out[k] = np.take(np.concatenate([uni[k], cl[k]]), perm)
+    out[3] = np.take(t, perm)
+    return out
+
+
+def field_values4(xyzt: np.ndarray, spec: FieldSpec, seed: int):
+    """Return (u, u_clean) of a moving field: the fronts of ``spec`` advected along x1 by
+    0.2 t and its Gaussian blobs with amplitudes modulated by (1 + 0.3 sin(2 t))."""
+    x1, x2, x3, t = (np.asarray(xyzt[k], dtype=np.float64) for k in range(4))
+    f = np.zeros_like(x1)
+    for nrm, off, width, amp in spec.fronts:
+        f += np.tanh((nrm[0] * x1 + nrm[1] * x2 + nrm[2] * x3 + amp * np.sin(3.0 * x2) - 0.2 * t - off) / width)
+    for a, sig, c in spec.gauss:
+        d2 = (x1 - c[0]) ** 2 + (x2 - c[1]) ** 2 + (x3 - c[2]) ** 2
+        f += a * (1.0 + 0.3 * np.sin(2.0 * t)) * np.exp(-d2 / (2.0 * sig * sig))
+    noise = _rng(seed, 10).normal(size=x1.size) * spec.noise
+    return f + noise, f
