@@ -478,6 +478,53 @@ fst_status fst_fit(const float* xyz, const float* u, int64_t Q, const double lo[
                    const fst_fit_params* params, fst_prec prec, const fst_refit_opts* opts,
                    fst_fit_trace* trace, fst_fit_report* report, fst_model** out, fst_stream stream);
 
+/* ---------------------------------------------------------------- order-4 models */
+
+/* Models of order 4 (eq. func_tuck with d = 4: three space axes and time, the SP4D case of
+ * Sec. 6 and Table 1), f(y) = sum alpha_{j1 j2 j3 j4} w1_{j1}(y1) w2_{j2}(y2) w3_{j3}(y3)
+ * w4_{j4}(y4), each factor function a sparse combination of the orthonormal Legendre
+ * functions of the coordinate mapped to [-1,1] by the model's box (eq. sparse).  Ranks up to
+ * FST4_MAX_RANK a mode (the paper's SP4D ranks are 30 x 38 x 5 x 11), degrees up to
+ * FST_MAX_DEGREE, r1 r2 r3 r4 <= 2^24.  Evaluation runs on the CUDA cores. */
+#define FST4_MAX_RANK 64
+typedef struct fst_model4 fst_model4;
+typedef struct {
+    int32_t r[4];
+    int32_t p[4];
+    double lo[4], hi[4];
+    const int32_t* colptr[4];   /* host CSC of each mode, as fst_model_desc */
+    const int32_t* rowidx[4];
+    const double* val[4];
+    const double* alpha;        /* host, r1 r2 r3 r4 values, C order [j1][j2][j3][j4] */
+} fst_model4_desc;
+/* Copies the description to the device.  Synchronous.  *out: fst_model4_free. */
+fst_status fst_model4_create(const fst_model4_desc* desc, fst_model4** out);
+void fst_model4_free(fst_model4* model);
+/* The core (host, r1 r2 r3 r4 doubles, C order). */
+fst_status fst_model4_read_core(const fst_model4* model, double* alpha);
+/* f at n points (device, 4n values SoA: x[0..n) = y1, ..., x[3n..4n) = y4) into out (device,
+ * n values): FP32 or FP64 arithmetic on the CUDA cores.  Asynchronous. */
+fst_status fst_eval4(const fst_model4* model, const float* x, int64_t n, float* out, fst_stream stream);
+fst_status fst_eval4_f64(const fst_model4* model, const double* x, int64_t n, double* out, fst_stream stream);
+/* The core refit (Sec. 5, eq. rand_core; Algorithm 2 with uniform sampling): m rows drawn by
+ * fst_sample_rows(seed, Q, m), factor values in FP64 rounded to FP32; the normal matrix
+ * G = A^T A of the rows (w1 (x) w2) (x) (w3 (x) w4) from the packed Khatri-Rao operand on the
+ * tensor cores in `prec` (TF32, BF16 or BF16X3; 4 R^2 bytes, 15.7 GB at R = 62,700), its FP32
+ * Cholesky factor (G is the FP32 sum of the Grams of blocks of 16,384 rows: the tensor cores'
+ * FP32 sums over all m rows at once round at about 1e-3 of the largest diagonal entry at
+ * R = 62,700; if G still does not factor, that of G + delta diag(G), delta 2^-12 .. 2^-2, which
+ * preconditions the unshifted equations; report->shifted_preconditioner is the step of delta
+ * taken), alpha_0 = G^-1 A^T b,
+ * then conjugate gradients on A^T A alpha = A^T b preconditioned by the factor, with A p and
+ * A^T q applied in the four-way factored form (FP32 products, FP64 sums) -- as fst_refit.
+ * opts: max_refine steps (default 200), refine_tol (default 1e-8; the iteration also stops
+ * when the update stops shrinking below 1e-6).  x (4Q floats SoA), u (Q floats):
+ * device.  report: host, may be NULL.  Synchronous; on success the core is replaced.
+ * R <= 131072; FST_ERANK if m < R, FST_ENOTSPD if no Gram factors, FST_ENOTCONV if the
+ * iteration does not converge. */
+fst_status fst_refit4(fst_model4* model, const float* x, const float* u, int64_t Q, int64_t m, uint64_t seed,
+                      fst_prec prec, const fst_refit_opts* opts, fst_refit_report* report, fst_stream stream);
+
 /* ---------------------------------------------------------------- errors */
 
 const char* fst_status_str(fst_status s);

@@ -23,7 +23,7 @@ sys.path.insert(0, str(Path(__file__).resolve().parent))
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("what", choices=["gram", "eval", "refit", "sample", "batch", "serve", "fit", "chol",
-                                     "refit-batch", "mixed"])
+                                     "refit-batch", "mixed", "order4"])
     ap.add_argument("--grid", type=int, default=64)
     ap.add_argument("--frac", type=float, default=0.05)
     ap.add_argument("--eps", type=float, default=1e-3)
@@ -59,6 +59,8 @@ def main():
         return serve_loads(args)
     if args.what == "fit":
         return fit(args)
+    if args.what == "order4":
+        return order4(args)
     model = synth.random_model(tuple(args.ranks), (args.degree,) * 3, seed=4, orthonormal=True)
     M = fst.Model(model)
     Q = max(args.n, 2 * args.m)
@@ -194,6 +196,39 @@ def refit_batch(args):
                  f" grouped_cholesky_ms={greps[0]['ms_cholesky']:.1f} grouped_refine_ms={greps[0]['ms_refine']:.1f}"
                  f" grouped_steps_max={max(rp['refine_steps'] for rp in greps)}")
         print(line, flush=True)
+
+
+def order4(args):
+    """Order-4 models at the paper's SP4D ranks 30 x 38 x 5 x 11 (R = 62,700; degrees 40, 40,
+    15, 20, orthonormal factor functions): evaluation at --n points in FP32 and FP64, and the
+    core refit on m = 4R rows of 2^19 points (values of the model itself)."""
+    import torch
+    from paper_1907_05884_gb300 import fst, synth
+    m = synth.random_model4((30, 38, 5, 11), (40, 40, 15, 20), seed=77, orthonormal=True)
+    M = fst.Model4(m)
+    x = torch.from_numpy(synth.points4(args.n, seed=78).astype(np.float32)).cuda()
+    x64 = x.double()
+    for r in range(args.reps):
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        e[0].record()
+        M.eval(x)
+        e[1].record()
+        M.eval(x64)
+        e[2].record()
+        torch.cuda.synchronize()
+        t32, t64 = e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2])
+        print(f"order4 eval n={args.n} R={m.R} fp32_ms={t32:.3f} ({args.n / t32 / 1e3:.1f} Mpoints/s, "
+              f"{2 * m.R * args.n / t32 / 1e9:.1f} TFLOP/s of contraction) fp64_ms={t64:.3f}", flush=True)
+    Q = 1 << 19
+    xr = synth.points4(Q, seed=79)
+    u = M.eval(torch.from_numpy(xr).cuda()).float().contiguous()
+    xr32 = torch.from_numpy(xr.astype(np.float32)).cuda()
+    for r in range(args.reps):
+        M0 = fst.Model4(m.with_alpha(np.zeros(m.r)))
+        torch.cuda.synchronize()
+        rep = M0.refit(xr32, u, 4 * m.R, seed=80, prec=args.prec, max_refine=200)
+        err = np.linalg.norm(M0.core() - m.alpha) / np.linalg.norm(m.alpha)
+        print(f"order4 refit R={m.R} m={4 * m.R} prec={args.prec} {rep} core_rel_l2={err:.3e}", flush=True)
 
 
 def mixed(args):

@@ -242,6 +242,10 @@ fst_status gram_tc_launch(const fst_model* m, const float* U1, const float* U2, 
 // (gram_pk.cu); FST_ENOMEM if that copy cannot be allocated.
 fst_status gram_pk_launch(const fst_model* m, const float* U1, const float* U2, const float* U3, int64_t rows,
                           float* G, fst_prec prec, cudaStream_t s);
+// The packed-operand Gram of rows u1 (x) u2 (x) u3 (gram_pk.cu): G lower triangle, err the
+// expired-wait word; FST_ENOMEM when the packed copy does not fit.
+fst_status gram_pk_rows(const float* U1, const float* U2, const float* U3, int64_t m, int r1, int r2, int r3,
+                        float* G, fst_prec prec, int* err, cudaStream_t s);
 // PT[(i r2 + j) mpad + q] = w1_i(q) w2_j(q), U3T[k mpad + q] = w3_k(q), zero for q >= m.
 fst_status pair_products(const float* U1, const float* U2, const float* U3, int64_t m, int64_t mpad, int r1, int r2,
                          int r3, float* PT, float* U3T, cudaStream_t s);

@@ -347,17 +347,22 @@ fst_status pack_and_multiply(const float* PT, const float* U3T, int64_t m, int64
 // on-the-fly kernel).
 fst_status gram_pk_launch(const fst_model* M, const float* U1, const float* U2, const float* U3, int64_t m,
                           float* G, fst_prec prec, cudaStream_t s) {
-    int dev = 0;
-    FST_CUDA(cudaGetDevice(&dev));
     // the error word is the model's (the caller holds the model's lock)
     DevBuf& eb = const_cast<fst_model*>(M)->rs.gram_err;
     FST_TRY(eb.ensure(sizeof(int)));
-    int* err = eb.as<int>();
+    return gram_pk_rows(U1, U2, U3, m, M->r[0], M->r[1], M->r[2], G, prec, eb.as<int>(), s);
+}
+
+// The same for rows A_s = u1_s (x) u2_s (x) u3_s given as three factor arrays (m x r_k each;
+// u3 may itself be a Kronecker product of further factors, as for order-4 models).
+fst_status gram_pk_rows(const float* U1, const float* U2, const float* U3, int64_t m, int r1, int r2, int r3,
+                        float* G, fst_prec prec, int* err, cudaStream_t s) {
+    int dev = 0;
+    FST_CUDA(cudaGetDevice(&dev));
     {
         SlotLease lease(g_pk[dev & 63]);
         FST_TRY(lease.begin(s));
         FST_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
-        const int r1 = M->r[0], r2 = M->r[1], r3 = M->r[2];
         const int R = r1 * r2 * r3;
         const int64_t mpad = (m + 63) / 64 * 64;
         FST_TRY(lease.ensure(0, sizeof(float) * (size_t)r1 * r2 * mpad));

@@ -37,6 +37,15 @@ class ModelDesc(C.Structure):
     ]
 
 
+class Model4Desc(C.Structure):
+    _fields_ = [
+        ("r", C.c_int32 * 4), ("p", C.c_int32 * 4),
+        ("lo", C.c_double * 4), ("hi", C.c_double * 4),
+        ("colptr", C.c_void_p * 4), ("rowidx", C.c_void_p * 4), ("val", C.c_void_p * 4),
+        ("alpha", C.c_void_p),
+    ]
+
+
 class WaveletDesc(C.Structure):
     _fields_ = [("level", C.c_int32), ("degree", C.c_int32), ("col_wavelet", C.c_void_p * 3)]
 
@@ -103,6 +112,12 @@ def _load():
     P, I32, I64, U64 = C.c_void_p, C.c_int32, C.c_int64, C.c_uint64
     sig = {
         "fst_model_create": (I32, [P, P]),
+        "fst_model4_create": (I32, [P, P]),
+        "fst_model4_free": (None, [P]),
+        "fst_model4_read_core": (I32, [P, P]),
+        "fst_eval4": (I32, [P, P, I64, P, P]),
+        "fst_eval4_f64": (I32, [P, P, I64, P, P]),
+        "fst_refit4": (I32, [P, P, P, I64, I64, U64, I32, P, P, P]),
         "fst_model_create_wavelet": (I32, [P, P, P]),
         "fst_model_read_wavelet": (I32, [P, P, P, P]),
         "fst_model_free": (None, [P]),
@@ -350,6 +365,69 @@ def refit_batched(models, xyzs, us, ms, seeds, prec: str = "bf16", streams: int 
     torch.cuda.synchronize()     # the library's streams do not wait on the caller's
     _check(lib.fst_refit_batched(arr, n, PREC[prec], C.byref(opts), int(streams), reps))
     return [reps[i].as_dict() for i in range(n)]
+
+
+class Model4:
+    """A device-resident order-4 model (fst_model4) built from a host synth.Model4."""
+
+    def __init__(self, host_model):
+        m = host_model
+        d = Model4Desc()
+        keep = []
+        for k in range(4):
+            d.r[k] = int(m.r[k])
+            d.p[k] = int(m.p[k])
+            d.lo[k] = float(m.lo[k])
+            d.hi[k] = float(m.hi[k])
+            cp = np.ascontiguousarray(m.colptr[k], dtype=np.int32)
+            ri = np.ascontiguousarray(m.rowidx[k], dtype=np.int32)
+            vv = np.ascontiguousarray(m.val[k], dtype=np.float64)
+            if ri.size == 0:
+                ri, vv = np.zeros(1, np.int32), np.zeros(1)
+            keep += [cp, ri, vv]
+            d.colptr[k], d.rowidx[k], d.val[k] = cp.ctypes.data, ri.ctypes.data, vv.ctypes.data
+        al = np.ascontiguousarray(np.asarray(m.alpha, dtype=np.float64).reshape(-1))
+        keep.append(al)
+        d.alpha = al.ctypes.data
+        self.r = tuple(int(v) for v in m.r)
+        self._h = C.c_void_p()
+        _check(lib.fst_model4_create(C.byref(d), C.byref(self._h)))
+
+    def __del__(self):
+        try:
+            if self._h:
+                lib.fst_model4_free(self._h)
+                self._h = C.c_void_p()
+        except Exception:
+            pass
+
+    def core(self):
+        a = np.empty(int(np.prod(self.r)))
+        _check(lib.fst_model4_read_core(self._h, a.ctypes.data))
+        return a.reshape(self.r)
+
+    def eval(self, x, out=None, stream=None):
+        """f at the points x (4, n) CUDA tensor, float32 or float64 (the arithmetic follows)."""
+        import torch
+        assert x.is_cuda and x.is_contiguous() and x.shape[0] == 4
+        n = x.shape[1]
+        if out is None:
+            out = torch.empty(n, device=x.device, dtype=x.dtype)
+        fn = lib.fst_eval4_f64 if x.dtype == torch.float64 else lib.fst_eval4
+        _check(fn(self._h, _dptr(x), n, _dptr(out), _stream(stream)))
+        return out
+
+    def refit(self, x, u, m: int, seed: int = 0, prec: str = "bf16x3", max_refine: int = 200,
+              refine_tol: float = 0.0, stream=None):
+        """Least-squares core refit over m sampled rows (x (4, Q), u (Q,) float32 CUDA tensors)."""
+        import torch
+        assert x.dtype == torch.float32 and u.dtype == torch.float32
+        opts = RefitOpts(int(max_refine), float(refine_tol), 0)
+        rep = RefitReport()
+        _check(lib.fst_refit4(self._h, _dptr(x), _dptr(u), x.shape[1], int(m),
+                              C.c_uint64(seed & 0xFFFFFFFFFFFFFFFF), PREC[prec], C.byref(opts), C.byref(rep),
+                              _stream(stream)))
+        return rep.as_dict()
 
 
 def refit_grouped(models, xyzs, us, ms, seeds, prec: str = "bf16", max_refine: int = 32, refine_tol: float = 0.0,
