@@ -316,18 +316,20 @@ def serve_loads(args):
     models = [fst.Model(synth.random_model(tuple(int(v) for v in rng.integers(4, 25, size=3)),
                                            (args.degree,) * 3, seed=200 + i, density=0.6)) for i in range(64)]
     pool = torch.from_numpy(synth.points(10_000_000, seed=12, clustered=0.3).astype(np.float32)).pin_memory()
-    srv = serve.FieldServer(models, pool, mem_budget=8 << 30, streams=2)
-    srv.prepare(("bf16",))
-    closed = serve.make_queries(min(args.queries, 400), 64, rate_qps=0.0, seed=13)
-    srv.run(closed[:50])
-    sat = serve.latency_stats(srv.run(closed))
-    print(json.dumps({"load": "closed", **sat}), flush=True)
-    mean_pts = np.mean([q.npoints() for q in closed])
-    for frac in (0.25, 0.5, 0.75, 0.9):
-        rate = frac * sat["Mpoints_s"] * 1e6 / mean_pts
-        qs = serve.make_queries(args.queries, 64, rate_qps=rate, seed=14 + int(frac * 100))
-        st = serve.latency_stats(srv.run(qs))
-        print(json.dumps({"load": frac, "rate_qps": rate, **st}), flush=True)
+    for via in ("fp32", "bf16x3"):
+        # FP32-accuracy queries on the CUDA cores, or on the tensor cores in BF16x3 (same bound)
+        srv = serve.FieldServer(models, pool, mem_budget=8 << 30, streams=2, fp32_via=via)
+        srv.prepare(("bf16", "bf16x3"))
+        closed = serve.make_queries(min(args.queries, 400), 64, rate_qps=0.0, seed=13)
+        srv.run(closed[:50])
+        sat = serve.latency_stats(srv.run(closed))
+        print(json.dumps({"fp32_via": via, "load": "closed", **sat}), flush=True)
+        mean_pts = np.mean([q.npoints() for q in closed])
+        for frac in (0.25, 0.5, 0.75, 0.9):
+            rate = frac * sat["Mpoints_s"] * 1e6 / mean_pts
+            qs = serve.make_queries(args.queries, 64, rate_qps=rate, seed=14 + int(frac * 100))
+            st = serve.latency_stats(srv.run(qs))
+            print(json.dumps({"fp32_via": via, "load": frac, "rate_qps": rate, **st}), flush=True)
 
 
 if __name__ == "__main__":

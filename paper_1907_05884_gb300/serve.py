@@ -60,7 +60,10 @@ class _Batch:
 
 class FieldServer:
     def __init__(self, models, point_pool, mem_budget: int = 2 << 30, streams: int = 2,
-                 keep_results: bool = False):
+                 keep_results: bool = False, fp32_via: str = "fp32"):
+        """fp32_via: the evaluator that serves queries asking for FP32 accuracy -- "fp32" (CUDA
+        cores) or "bf16x3" (tensor cores, the same 1e-5 accuracy bound at several times the
+        throughput)."""
         import torch
         from paper_1907_05884_gb300 import fst
         self.fst = fst
@@ -70,6 +73,8 @@ class FieldServer:
         self.budget = int(mem_budget)
         self.streams = [torch.cuda.Stream() for _ in range(streams)]
         self.keep = keep_results
+        assert fp32_via in ("fp32", "bf16x3")
+        self.fp32_via = fp32_via
         self.mem_used = 0
         self.peak_mem = 0
         self.inflight: list[_Batch] = []
@@ -120,7 +125,8 @@ class FieldServer:
                 q.out = out
                 q.t_admit = now_fn()
                 bufs += [xyz, out]
-                groups[q.prec].append((self.models[q.field], xyz, out))
+                prec = self.fp32_via if q.prec == "fp32" else q.prec
+                groups[prec].append((self.models[q.field], xyz, out))
             for prec, items in groups.items():
                 fst.eval_batched([m for m, _, _ in items], [x for _, x, _ in items], [o for _, _, o in items],
                                  prec=prec, stream=stream)

@@ -72,3 +72,28 @@ def test_oversize_query_admitted_alone(setup):
     srv.run(qs)
     torch.cuda.synchronize()
     assert all(np.isfinite(q.t_done) for q in qs)
+
+
+def test_fp32_queries_served_by_bf16x3(setup, oracle_lib):
+    """With fp32_via="bf16x3" the queries asking for FP32 accuracy run the BF16x3 evaluator:
+    each result equals that evaluator alone and meets the FP32 bound against the oracle."""
+    import torch
+    fst, serve, host_models, models, pool = setup
+    srv = serve.FieldServer(models, pool, mem_budget=64 << 20, streams=2, keep_results=True, fp32_via="bf16x3")
+    srv.prepare(("bf16x3", "bf16"))
+    qs = serve.make_queries(60, len(models), rate_qps=20000.0, seed=7, precs=("fp32", "bf16"),
+                            pool_points=pool.shape[1], slice_res=(32, 128), point_range=(1e2, 1e5))
+    srv.run(qs)
+    torch.cuda.synchronize()
+    checked = 0
+    for q in qs:
+        if q.kind != "points":
+            continue
+        x = pool[:, q.p0:q.p0 + q.n].cuda().contiguous()
+        want = "bf16x3" if q.prec == "fp32" else q.prec
+        assert torch.equal(models[q.field].eval(x, prec=want), q.out), q.qid
+        if q.prec == "fp32" and checked < 4:
+            ref = oracle_lib.eval_points(host_models[q.field], pool[:, q.p0:q.p0 + q.n].numpy().astype(np.float64))
+            assert rel_l2(q.out.cpu().numpy(), ref) < EVAL_TOL["fp32"]
+            checked += 1
+    assert checked > 0
