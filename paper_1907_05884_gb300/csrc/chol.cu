@@ -759,18 +759,63 @@ constexpr int kSuperPanels = 4;
 static size_t packed_panel_bytes(int R) { return (size_t)((R + PB - 1) / PB) * kTileBytes; }
 
 static fst_status syrk_tc(float* G, int R, int t0, int nt, int ncol, const unsigned char* Lp, size_t pstride,
-                          int npan, int* err, size_t smem, cudaStream_t s) {
+                          int npan, int* err, size_t smem, cudaStream_t s, int max_grid = 0) {
     const long long ntiles = (long long)ncol * (ncol + 1) / 2 + (long long)(nt - ncol) * ncol;
-    const int grid = ntiles < sm_count() ? (int)ntiles : sm_count();
+    const int cap = max_grid > 0 ? max_grid : sm_count();
+    const int grid = ntiles < cap ? (int)ntiles : cap;
     syrk_tc_kernel<<<grid, kSyrkThreads, smem, s>>>(G, R, t0, nt, ncol, Lp, pstride, npan, err);
     FST_CHECK_LAUNCH();
     return FST_OK;
 }
 
+// The side stream of the look-ahead trailing updates, with its events: one set per host
+// thread (the factorisations a thread issues run one after another; concurrent refits run on
+// different threads), created on first use and destroyed with the thread.
+struct LookAhead {
+    int device = -1;
+    cudaStream_t side = nullptr;
+    cudaEvent_t chain = nullptr, rest = nullptr;
+    ~LookAhead() {
+        if (side) {
+            cudaStreamSynchronize(side);
+            cudaStreamDestroy(side);
+            cudaEventDestroy(chain);
+            cudaEventDestroy(rest);
+        }
+    }
+};
+static fst_status look_ahead(LookAhead*& out) {
+    thread_local LookAhead la;
+    int dev = 0;
+    FST_CUDA(cudaGetDevice(&dev));
+    if (la.side && la.device != dev) {
+        cudaStreamSynchronize(la.side);
+        cudaStreamDestroy(la.side);
+        cudaEventDestroy(la.chain);
+        cudaEventDestroy(la.rest);
+        la.side = nullptr;
+    }
+    if (!la.side) {
+        FST_CUDA(cudaStreamCreateWithFlags(&la.side, cudaStreamNonBlocking));
+        FST_CUDA(cudaEventCreateWithFlags(&la.chain, cudaEventDisableTiming));
+        FST_CUDA(cudaEventCreateWithFlags(&la.rest, cudaEventDisableTiming));
+        la.device = dev;
+    }
+    out = &la;
+    return FST_OK;
+}
+
+// With look-ahead: after a super-panel's panels, the update of the next super-panel's columns
+// (all rows below) runs on the caller's stream, so the next panels can start at once, and the
+// update of the rest of the trailing matrix runs on a side stream, on all but kChainSMs of the
+// SMs, overlapping the next super-panel's latency-bound panel chain.  The packed panels of
+// consecutive super-panels alternate between two sets, so the side update never reads panels
+// that the next chain rewrites.  Every tile still receives the same updates in the same order.
+constexpr int kChainSMs = 24;
 static fst_status cholesky_lower_tc(float* G, int R, int* d_flag, const float* floors, unsigned char* ws_tail,
                                     cudaStream_t s) {
     float* Dinv = reinterpret_cast<float*>(ws_tail);
-    unsigned char* Lp = ws_tail + 4 * SUB * SUB * sizeof(float);
+    unsigned char* Lbase = ws_tail + 4 * SUB * SUB * sizeof(float);
     const size_t pstride = packed_panel_bytes(R);
     const size_t potrf_smem = sizeof(float) * (PB * AS + 4 * SUB * SUB);   // P: FS x PB, then the inverses
     const size_t trsm_smem = sizeof(float) * ((kTrsmRows + PB) * AS + 4 * SUB * (SUB + 4));
@@ -778,8 +823,16 @@ static fst_status cholesky_lower_tc(float* G, int R, int* d_flag, const float* f
     FST_TRY(allow_smem(potrf_inv_kernel, potrf_smem));
     FST_TRY(allow_smem(trsm_pack_kernel, trsm_smem));
     FST_TRY(allow_smem(syrk_tc_kernel, syrk_smem));
+    LookAhead* la = nullptr;
+    FST_TRY(look_ahead(la));
+    bool rest_pending = false;   // a side update was issued (la->rest marks its end)
+    auto finish = [&]() -> fst_status {
+        if (rest_pending) FST_CUDA(cudaStreamWaitEvent(s, la->rest, 0));
+        return FST_OK;
+    };
     constexpr int SBW = kSuperPanels * PB;
     for (int K0 = 0; K0 < R; K0 += SBW) {
+        unsigned char* Lp = Lbase + (size_t)((K0 / SBW) & 1) * kSuperPanels * pstride;
         int npan = 0;
         for (int p = 0; p < kSuperPanels; ++p) {
             const int k0 = K0 + p * PB;
@@ -788,7 +841,7 @@ static fst_status cholesky_lower_tc(float* G, int R, int* d_flag, const float* f
             const int rest = R - k0 - kb;
             potrf_inv_kernel<<<1, 512, potrf_smem, s>>>(G, R, k0, kb, d_flag, floors, Dinv, rest > 0 ? 1 : 0);
             FST_CHECK_LAUNCH();
-            if (rest <= 0) return FST_OK;
+            if (rest <= 0) return finish();
             ++npan;
             const int nt = (rest + PB - 1) / PB;
             unsigned char* Lpp = Lp + (size_t)p * pstride;
@@ -802,9 +855,23 @@ static fst_status cholesky_lower_tc(float* G, int R, int* d_flag, const float* f
         const int T0 = K0 + npan * PB;
         if (T0 >= R) break;
         const int nt = (R - T0 + PB - 1) / PB;
-        FST_TRY(syrk_tc(G, R, T0, nt, nt, Lp, pstride, npan, d_flag + 1, syrk_smem, s));
+        const int nnext = nt < kSuperPanels ? nt : kSuperPanels;
+        // the previous side update wrote into the next strip's tiles, and read the panel set
+        // the chain after this one rewrites: both wait for it here
+        FST_TRY(finish());
+        if (nt > nnext) {
+            FST_CUDA(cudaEventRecord(la->chain, s));               // this super-panel's panels are packed
+            FST_CUDA(cudaStreamWaitEvent(la->side, la->chain, 0));
+            FST_TRY(syrk_tc(G, R, T0 + nnext * PB, nt - nnext, nt - nnext, Lp + (size_t)nnext * kTileBytes, pstride,
+                            npan, d_flag + 1, syrk_smem, la->side, sm_count() - kChainSMs));
+            FST_CUDA(cudaEventRecord(la->rest, la->side));
+            rest_pending = true;
+        } else {
+            rest_pending = false;
+        }
+        FST_TRY(syrk_tc(G, R, T0, nt, nnext, Lp, pstride, npan, d_flag + 1, syrk_smem, s));
     }
-    return FST_OK;
+    return finish();
 }
 
 // FP32 factorisations of several normal matrices in shared launches (a grouped refit): the
@@ -961,7 +1028,7 @@ template <typename T>
 fst_status cholesky_lower(T* G, int R, int* d_flag, DevBuf& ws, cudaStream_t s) {
     // ws: per-column pivot floors, then (FP32) the panel scratch of the tensor-core path
     const size_t floor_bytes = ((size_t)R * sizeof(T) + 255) / 256 * 256;
-    const size_t tail = sizeof(T) == 4 ? 4 * SUB * SUB * sizeof(float) + kSuperPanels * packed_panel_bytes(R) : 0;
+    const size_t tail = sizeof(T) == 4 ? 4 * SUB * SUB * sizeof(float) + 2 * kSuperPanels * packed_panel_bytes(R) : 0;
     FST_TRY(ws.ensure(floor_bytes + tail));
     T* floors = ws.as<T>();
     pivot_floor_kernel<T><<<(R + 255) / 256 < 1024 ? (R + 255) / 256 : 1024, 256, 0, s>>>(G, R, floors);
