@@ -143,10 +143,10 @@ GRAM_PK_BF16_TRAFFIC = 13.94e9 + 0.3565e9
 # DRAM bytes of one evaluation launch, keyed by (precision, points, degree), from one ncu
 # capture of the current kernel (a smaller case scaled by the point count where stated)
 EVAL_TRAFFIC = {
-    # eval_pipe_kernel<BF16X3, 24, 24>: 201.9 MB read + 47.9 MB written at 2^24 points, degree 63
-    # (ncu --set full), scaled by the point count (traffic is 15 B/point of streamed coordinates
-    # and values at both sizes)
-    ("bf16x3", 1 << 26, 63): 4 * (201.908224e6 + 47.862784e6),
+    # eval_pipe_kernel<BF16X3, 24, 24>: 201.70 MB read + 47.05 MB written at 2^24 points, degree 63
+    # (ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum on the current kernel), scaled by
+    # the point count (the traffic is the streamed coordinates and values at both sizes)
+    ("bf16x3", 1 << 26, 63): 4 * (201.70e6 + 47.05e6),
 }
 
 
