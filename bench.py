@@ -307,23 +307,51 @@ def main():
     ms_step = ms / args.steps
     value = shard.job_throughput(Q, world, args.steps, ms)
 
-    # end to end through the public API with host buffers (pinned), copies inside the region
+    # end to end through the public API with host buffers (pinned), copies inside the region:
+    # every step copies its inputs in and its result out, on a copy stream with two device
+    # buffer sets, so step i+1's inputs and step i-1's result move while step i computes
     xyz_h = torch.from_numpy(xyz).pin_memory()
     u_h = torch.from_numpy(u).pin_memory()
-    out_h = torch.empty(Q, dtype=torch.float32).pin_memory()
+    outs_h = [torch.empty(Q, dtype=torch.float32).pin_memory() for _ in range(2)]
+    sets = [(xyz_d, u_d, out_d), (torch.empty_like(xyz_d), torch.empty_like(u_d), torch.empty_like(out_d))]
+    copy = torch.cuda.Stream()
+    ev_in = [torch.cuda.Event() for _ in range(2)]
+    ev_done = [torch.cuda.Event() for _ in range(2)]
+    ev_out = [torch.cuda.Event() for _ in range(2)]
     barrier()
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
+
+    def copy_in(k):
+        with torch.cuda.stream(copy):
+            sets[k][0].copy_(xyz_h, non_blocking=True)
+            sets[k][1].copy_(u_h, non_blocking=True)
+            ev_in[k].record(copy)
+
+    copy.wait_event(e0)
+    copy_in(0)
     for i in range(args.steps):
-        xyz_d.copy_(xyz_h, non_blocking=True)
-        u_d.copy_(u_h, non_blocking=True)
-        M.refit(xyz_d, u_d, m, seed=5000 + i, prec=args.prec)
+        k, nk = i % 2, (i + 1) % 2
+        if i + 1 < args.steps:
+            if i >= 1:
+                copy.wait_event(ev_done[nk])      # step i-1 has finished reading set nk
+            copy_in(nk)
+        stream.wait_event(ev_in[k])
+        if i >= 2:
+            stream.wait_event(ev_out[k])          # step i-2's result has left set k
+        xk, uk, ok = sets[k]
+        M.refit(xk, uk, m, seed=5000 + i, prec=args.prec)
         if args.eval_prec != "fp32":
             M.prepare(args.eval_prec)
-        M.eval(xyz_d, prec=args.eval_prec, out=out_d)
-        out_h.copy_(out_d, non_blocking=True)
+        M.eval(xk, prec=args.eval_prec, out=ok)
+        ev_done[k].record(stream)
+        copy.wait_event(ev_done[k])
+        with torch.cuda.stream(copy):
+            outs_h[k].copy_(ok, non_blocking=True)
+            ev_out[k].record(copy)
+    stream.wait_stream(copy)
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = shard.job_time_ms(e0.elapsed_time(e1), world, device="cuda")
@@ -430,7 +458,7 @@ def main():
         om = synth.Model(model.r, model.p, model.colptr, model.rowidx, model.val, cur["alpha"])
         na = min(ACCURACY_POINTS, Q)
         ref = oracle.eval_points(om, xyz[:, :na].astype(np.float64), nthreads=nthreads)
-        got = out_d[:na].cpu().numpy()
+        got = sets[(args.steps - 1) % 2][2][:na].cpu().numpy()   # the last step's evaluation
         line["rel_l2_eval_vs_oracle"] = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
         line["rel_l2_eval_points"] = na
         idx = oracle.sample(5000 + args.steps - 1, Q, m)   # rows of the last refit (e2e loop)
