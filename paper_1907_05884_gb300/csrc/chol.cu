@@ -480,8 +480,8 @@ __device__ __forceinline__ void trsm_pack_body(float* G, int R, int k0, const fl
 }
 
 __global__ void __launch_bounds__(256) trsm_pack_kernel(float* G, int R, int k0, const float* Dinv,
-                                                        unsigned char* Lp) {
-    trsm_pack_body(G, R, k0, Dinv, Lp, blockIdx.x);
+                                                        unsigned char* Lp, int blk0) {
+    trsm_pack_body(G, R, k0, Dinv, Lp, blk0 + blockIdx.x);
 }
 __global__ void __launch_bounds__(256) trsm_pack_group_kernel(const CholJob* __restrict__ jobs, int njobs) {
     const CholJob& j = jobs[job_of(jobs, njobs, blockIdx.x)];
@@ -534,10 +534,13 @@ struct SyrkOne {
     const unsigned char* Lp;
     size_t pstride;
     int R, t0, nt, ncol, npan;
-    __device__ long long count() const { return (long long)ncol * (ncol + 1) / 2 + (long long)(nt - ncol) * ncol; }
+    long long first;    // tiles [first, count) of the trapezoid
+    __device__ long long count() const {
+        return (long long)ncol * (ncol + 1) / 2 + (long long)(nt - ncol) * ncol - first;
+    }
     __device__ SyrkTile tile(long long t) const {
         SyrkTile x{G, Lp, pstride, R, t0, npan, 0, 0};
-        trapezoid_tile(t, ncol, x.ti, x.tj);
+        trapezoid_tile(t + first, ncol, x.ti, x.tj);
         return x;
     }
 };
@@ -740,8 +743,8 @@ __device__ __forceinline__ void syrk_tc_body(const Src& src, int* err) {
 
 __global__ void __launch_bounds__(kSyrkThreads, 1)
 syrk_tc_kernel(float* G, int R, int t0, int nt, int ncol, const unsigned char* Lp, size_t pstride, int npan,
-               int* err) {
-    syrk_tc_body(SyrkOne{G, Lp, pstride, R, t0, nt, ncol, npan}, err);
+               int* err, long long first) {
+    syrk_tc_body(SyrkOne{G, Lp, pstride, R, t0, nt, ncol, npan, first}, err);
 }
 __global__ void __launch_bounds__(kSyrkThreads, 1)
 syrk_tc_group_kernel(const CholJob* __restrict__ jobs, int njobs, long long total, int* err) {
@@ -759,11 +762,13 @@ constexpr int kSuperPanels = 4;
 static size_t packed_panel_bytes(int R) { return (size_t)((R + PB - 1) / PB) * kTileBytes; }
 
 static fst_status syrk_tc(float* G, int R, int t0, int nt, int ncol, const unsigned char* Lp, size_t pstride,
-                          int npan, int* err, size_t smem, cudaStream_t s, int max_grid = 0) {
-    const long long ntiles = (long long)ncol * (ncol + 1) / 2 + (long long)(nt - ncol) * ncol;
+                          int npan, int* err, size_t smem, cudaStream_t s, int max_grid = 0, long long first = 0) {
+    // tiles [first, end) of the trapezoid of nt tile rows and ncol tile columns
+    const long long ntiles = (long long)ncol * (ncol + 1) / 2 + (long long)(nt - ncol) * ncol - first;
+    if (ntiles <= 0) return FST_OK;
     const int cap = max_grid > 0 ? max_grid : sm_count();
     const int grid = ntiles < cap ? (int)ntiles : cap;
-    syrk_tc_kernel<<<grid, kSyrkThreads, smem, s>>>(G, R, t0, nt, ncol, Lp, pstride, npan, err);
+    syrk_tc_kernel<<<grid, kSyrkThreads, smem, s>>>(G, R, t0, nt, ncol, Lp, pstride, npan, err, first);
     FST_CHECK_LAUNCH();
     return FST_OK;
 }
@@ -773,50 +778,54 @@ static fst_status syrk_tc(float* G, int R, int t0, int nt, int ncol, const unsig
 // different threads), created on first use and destroyed with the thread.
 struct LookAhead {
     int device = -1;
-    cudaStream_t side = nullptr;
-    cudaEvent_t chain = nullptr, rest = nullptr;
-    ~LookAhead() {
-        if (side) {
-            cudaStreamSynchronize(side);
-            cudaStreamDestroy(side);
-            cudaEventDestroy(chain);
-            cudaEventDestroy(rest);
-        }
+    cudaStream_t side = nullptr, panel = nullptr;
+    cudaEvent_t chain = nullptr, rest = nullptr, head = nullptr, tail = nullptr;
+    void release() {
+        if (!side) return;
+        cudaStreamSynchronize(side);
+        cudaStreamSynchronize(panel);
+        cudaStreamDestroy(side);
+        cudaStreamDestroy(panel);
+        cudaEventDestroy(chain);
+        cudaEventDestroy(rest);
+        cudaEventDestroy(head);
+        cudaEventDestroy(tail);
+        side = nullptr;
     }
+    ~LookAhead() { release(); }
 };
 static fst_status look_ahead(LookAhead*& out) {
     thread_local LookAhead la;
     int dev = 0;
     FST_CUDA(cudaGetDevice(&dev));
-    if (la.side && la.device != dev) {
-        cudaStreamSynchronize(la.side);
-        cudaStreamDestroy(la.side);
-        cudaEventDestroy(la.chain);
-        cudaEventDestroy(la.rest);
-        la.side = nullptr;
-    }
+    if (la.side && la.device != dev) la.release();
     if (!la.side) {
         FST_CUDA(cudaStreamCreateWithFlags(&la.side, cudaStreamNonBlocking));
-        FST_CUDA(cudaEventCreateWithFlags(&la.chain, cudaEventDisableTiming));
-        FST_CUDA(cudaEventCreateWithFlags(&la.rest, cudaEventDisableTiming));
+        FST_CUDA(cudaStreamCreateWithFlags(&la.panel, cudaStreamNonBlocking));
+        for (cudaEvent_t* e : {&la.chain, &la.rest, &la.head, &la.tail})
+            FST_CUDA(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
         la.device = dev;
     }
     out = &la;
     return FST_OK;
 }
 
-// With look-ahead: after a super-panel's panels, the update of the next super-panel's columns
-// (all rows below) runs on the caller's stream, so the next panels can start at once, and the
-// update of the rest of the trailing matrix runs on a side stream, on all but kChainSMs of the
-// SMs (80 of 152 measured best: 9.87 ms at R = 13,824 against 10.32 with 24 and 11.05 without
-// look-ahead), overlapping the next super-panel's latency-bound panel chain.  The packed panels of
-// consecutive super-panels alternate between two sets, so the side update never reads panels
-// that the next chain rewrites.  Every tile still receives the same updates in the same order.
+// Two levels of look-ahead.  Across super-panels: after a super-panel's panels, the update of
+// the next super-panel's columns (all rows below) runs on the caller's stream and the update
+// of the rest of the trailing matrix on a side stream, on all but kChainSMs of the SMs, so it
+// overlaps the next super-panel's latency-bound panel chain (80 of 152 SMs left to the chain
+// measured best: 9.87 ms at R = 13,824 against 10.32 with 24 and 11.05 without); the packed
+// panels of consecutive super-panels alternate between two sets, so that update never reads
+// panels the next chain rewrites.  Within a super-panel: of panel p's solve and update, only
+// the rows and the tile the next panel's diagonal block needs run on the caller's stream; the
+// rest runs on a panel stream while the next diagonal block is factored (the diagonal-block
+// inverses alternate between two buffers for that), and the next panel's solve waits for it.
+// Every tile still receives the same updates in the same order: the factor is bit-identical.
 constexpr int kChainSMs = 80;
 static fst_status cholesky_lower_tc(float* G, int R, int* d_flag, const float* floors, unsigned char* ws_tail,
                                     cudaStream_t s) {
-    float* Dinv = reinterpret_cast<float*>(ws_tail);
-    unsigned char* Lbase = ws_tail + 4 * SUB * SUB * sizeof(float);
+    float* Dinv2[2] = {reinterpret_cast<float*>(ws_tail), reinterpret_cast<float*>(ws_tail) + 4 * SUB * SUB};
+    unsigned char* Lbase = ws_tail + 2 * 4 * SUB * SUB * sizeof(float);
     const size_t pstride = packed_panel_bytes(R);
     const size_t potrf_smem = sizeof(float) * (PB * AS + 4 * SUB * SUB);   // P: FS x PB, then the inverses
     const size_t trsm_smem = sizeof(float) * ((kTrsmRows + PB) * AS + 4 * SUB * (SUB + 4));
@@ -826,39 +835,65 @@ static fst_status cholesky_lower_tc(float* G, int R, int* d_flag, const float* f
     FST_TRY(allow_smem(syrk_tc_kernel, syrk_smem));
     LookAhead* la = nullptr;
     FST_TRY(look_ahead(la));
-    bool rest_pending = false;   // a side update was issued (la->rest marks its end)
+    bool rest_pending = false;    // a side update was issued (la->rest marks its end)
+    bool panel_pending = false;   // panel-stream work was issued (la->tail marks its end)
+    auto join_panel = [&]() -> fst_status {
+        if (panel_pending) FST_CUDA(cudaStreamWaitEvent(s, la->tail, 0));
+        panel_pending = false;
+        return FST_OK;
+    };
     auto finish = [&]() -> fst_status {
+        FST_TRY(join_panel());
         if (rest_pending) FST_CUDA(cudaStreamWaitEvent(s, la->rest, 0));
         return FST_OK;
     };
     constexpr int SBW = kSuperPanels * PB;
+    constexpr int kHeadBlocks = PB / kTrsmRows;   // solve blocks of the rows of the next diagonal block
+    int pan_index = 0;
     for (int K0 = 0; K0 < R; K0 += SBW) {
         unsigned char* Lp = Lbase + (size_t)((K0 / SBW) & 1) * kSuperPanels * pstride;
         int npan = 0;
-        for (int p = 0; p < kSuperPanels; ++p) {
+        for (int p = 0; p < kSuperPanels; ++p, ++pan_index) {
             const int k0 = K0 + p * PB;
             if (k0 >= R) break;
             const int kb = R - k0 < PB ? R - k0 : PB;
             const int rest = R - k0 - kb;
+            float* Dinv = Dinv2[pan_index & 1];
             potrf_inv_kernel<<<1, 512, potrf_smem, s>>>(G, R, k0, kb, d_flag, floors, Dinv, rest > 0 ? 1 : 0);
             FST_CHECK_LAUNCH();
             if (rest <= 0) return finish();
             ++npan;
             const int nt = (rest + PB - 1) / PB;
             unsigned char* Lpp = Lp + (size_t)p * pstride;
-            trsm_pack_kernel<<<(PB / kTrsmRows) * nt, 256, trsm_smem, s>>>(G, R, k0, Dinv, Lpp);
-            FST_CHECK_LAUNCH();
-            // the columns of the super-panel right of this panel
-            int ncol = (K0 + SBW - (k0 + PB)) / PB;
+            int ncol = (K0 + SBW - (k0 + PB)) / PB;   // columns of the super-panel right of this panel
             if (ncol > nt) ncol = nt;
-            if (ncol > 0) FST_TRY(syrk_tc(G, R, k0 + PB, nt, ncol, Lpp, pstride, 1, d_flag + 1, syrk_smem, s));
+            // this panel's solve reads rows the previous panel's remaining update writes
+            FST_TRY(join_panel());
+            const int nblk = (PB / kTrsmRows) * nt;
+            if (ncol > 0 && nblk > kHeadBlocks) {
+                // the next diagonal block first: its rows of the solve, then its tile of the update
+                trsm_pack_kernel<<<kHeadBlocks, 256, trsm_smem, s>>>(G, R, k0, Dinv, Lpp, 0);
+                FST_CHECK_LAUNCH();
+                FST_TRY(syrk_tc(G, R, k0 + PB, 1, 1, Lpp, pstride, 1, d_flag + 1, syrk_smem, s));
+                FST_CUDA(cudaEventRecord(la->head, s));
+                FST_CUDA(cudaStreamWaitEvent(la->panel, la->head, 0));
+                trsm_pack_kernel<<<nblk - kHeadBlocks, 256, trsm_smem, la->panel>>>(G, R, k0, Dinv, Lpp, kHeadBlocks);
+                FST_CHECK_LAUNCH();
+                FST_TRY(syrk_tc(G, R, k0 + PB, nt, ncol, Lpp, pstride, 1, d_flag + 1, syrk_smem, la->panel, 0, 1));
+                FST_CUDA(cudaEventRecord(la->tail, la->panel));
+                panel_pending = true;
+            } else {
+                trsm_pack_kernel<<<nblk, 256, trsm_smem, s>>>(G, R, k0, Dinv, Lpp, 0);
+                FST_CHECK_LAUNCH();
+                if (ncol > 0) FST_TRY(syrk_tc(G, R, k0 + PB, nt, ncol, Lpp, pstride, 1, d_flag + 1, syrk_smem, s));
+            }
         }
         const int T0 = K0 + npan * PB;
         if (T0 >= R) break;
         const int nt = (R - T0 + PB - 1) / PB;
         const int nnext = nt < kSuperPanels ? nt : kSuperPanels;
         // the previous side update wrote into the next strip's tiles, and read the panel set
-        // the chain after this one rewrites: both wait for it here
+        // the chain after this one rewrites: both wait for it here (and the panel stream's last work)
         FST_TRY(finish());
         if (nt > nnext) {
             FST_CUDA(cudaEventRecord(la->chain, s));               // this super-panel's panels are packed
@@ -1029,7 +1064,7 @@ template <typename T>
 fst_status cholesky_lower(T* G, int R, int* d_flag, DevBuf& ws, cudaStream_t s) {
     // ws: per-column pivot floors, then (FP32) the panel scratch of the tensor-core path
     const size_t floor_bytes = ((size_t)R * sizeof(T) + 255) / 256 * 256;
-    const size_t tail = sizeof(T) == 4 ? 4 * SUB * SUB * sizeof(float) + 2 * kSuperPanels * packed_panel_bytes(R) : 0;
+    const size_t tail = sizeof(T) == 4 ? 2 * 4 * SUB * SUB * sizeof(float) + 2 * kSuperPanels * packed_panel_bytes(R) : 0;
     FST_TRY(ws.ensure(floor_bytes + tail));
     T* floors = ws.as<T>();
     pivot_floor_kernel<T><<<(R + 255) / 256 < 1024 ? (R + 255) / 256 : 1024, 256, 0, s>>>(G, R, floors);
