@@ -509,7 +509,8 @@ fst_status fst_eval4_f64(const fst_model4* model, const double* x, int64_t n, do
 /* The core refit (Sec. 5, eq. rand_core; Algorithm 2 with uniform sampling): m rows drawn by
  * fst_sample_rows(seed, Q, m), factor values in FP64 rounded to FP32; the normal matrix
  * G = A^T A of the rows (w1 (x) w2) (x) (w3 (x) w4) from the packed Khatri-Rao operand on the
- * tensor cores in `prec` (TF32, BF16 or BF16X3; 4 R^2 bytes, 15.7 GB at R = 62,700), its FP32
+ * tensor cores in `prec` (TF32, BF16 or BF16X3; G and its saved copy / transpose take 8 R^2
+ * bytes of device memory, 31 GB at R = 62,700, besides the packed operand of a row block), its FP32
  * Cholesky factor (G is the FP32 sum of the Grams of blocks of 16,384 rows: the tensor cores'
  * FP32 sums over all m rows at once round at about 1e-3 of the largest diagonal entry at
  * R = 62,700; if G still does not factor, that of G + delta diag(G), delta 2^-12 .. 2^-2, which
@@ -520,8 +521,8 @@ fst_status fst_eval4_f64(const fst_model4* model, const double* x, int64_t n, do
  * opts: max_refine steps (default 200), refine_tol (default 1e-8; the iteration also stops
  * when the update stops shrinking below 1e-6).  x (4Q floats SoA), u (Q floats):
  * device.  report: host, may be NULL.  Synchronous; on success the core is replaced.
- * R <= 131072; FST_ERANK if m < R, FST_ENOTSPD if no Gram factors, FST_ENOTCONV if the
- * iteration does not converge. */
+ * R <= 131072; FST_ERANK if m < R, FST_ENOMEM if G does not fit, FST_ENOTSPD if no Gram
+ * factors, FST_ENOTCONV if the iteration does not converge. */
 fst_status fst_refit4(fst_model4* model, const float* x, const float* u, int64_t Q, int64_t m, uint64_t seed,
                       fst_prec prec, const fst_refit_opts* opts, fst_refit_report* report, fst_stream stream);
 
